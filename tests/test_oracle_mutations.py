@@ -1,0 +1,102 @@
+"""Planted mistakes in the oracle (on the CPU) must be caught by its pins.
+
+Each mutant replaces the oracle's robust-PS line evaluation with a version
+carrying one plausible error (a dropped term, a wrong sign, a wrong index or
+transposed operand).  The exact-limit pin (P1) and the 4-index definition pin
+(P3) are re-evaluated with the mutant; at least one must fail.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.exx as ox
+from cellgen import basis_on_grid, build_cell, config_spec, draw_coefficients, potentials
+from cellgen.cells import CellSpec, Shell
+
+
+_ORIG = ox.rps_lines
+
+
+def _lines_parts(phi, idx, V, W, C):
+    psi = phi @ C
+    psig = psi[idx]
+    return psi, psig, phi[idx]
+
+
+def m_drop_line3(phi, idx, V, W, C, gblock=512):
+    l1, l2, l3 = _ORIG(phi, idx, V, W, C)
+    return l1, l2, 0 * l3
+
+
+def m_sign_line2(phi, idx, V, W, C, gblock=512):
+    l1, l2, l3 = _ORIG(phi, idx, V, W, C)
+    return l1, -l2, l3
+
+
+def m_line2_bra_at_points(phi, idx, V, W, C, gblock=512):
+    # line 2 with its phi_nu evaluated on the full grid index instead of R_g
+    psi, psig, phig = _lines_parts(phi, idx, V, W, C)
+    l1, _, l3 = _ORIG(phi, idx, V, W, C)
+    V2 = V * (psig @ psi.T)
+    M2 = V2 @ psi
+    return l1, M2.T @ phi[: idx.size], l3
+
+
+def m_pair_kernel_transposed(phi, idx, V, W, C, gblock=512):
+    # P built from psi at R_g on both sides (the line-3 kernel) in lines 1-2
+    psi, psig, phig = _lines_parts(phi, idx, V, W, C)
+    P = psig @ psig.T
+    V2 = V[:, idx] * P
+    l1 = (psig.T @ V2) @ phig
+    l2 = (V2 @ psig).T @ phig
+    _, _, l3 = _ORIG(phi, idx, V, W, C)
+    return l1, l2, l3
+
+
+def m_W_unsquared(phi, idx, V, W, C, gblock=512):
+    # line 3 without the Hadamard with Q
+    psi, psig, phig = _lines_parts(phi, idx, V, W, C)
+    l1, l2, _ = _ORIG(phi, idx, V, W, C)
+    return l1, l2, (W @ psig).T @ phig
+
+
+MUTANTS = [m_drop_line3, m_sign_line2, m_line2_bra_at_points, m_pair_kernel_transposed,
+           m_W_unsquared]
+
+
+@pytest.fixture(scope="module")
+def settings():
+    spec = config_spec(1)
+    rng = np.random.default_rng(spec.seed)
+    cen = spec.frac * spec.L + rng.uniform(-0.05, 0.05, size=spec.frac.shape)
+    phi = basis_on_grid(cen, spec.L, 10, spec.shells)
+    Ng = phi.shape[0]
+    dV = spec.L ** 3 / Ng
+    C = draw_coefficients(dV * phi.T @ phi, 6, 3)
+    V = potentials(np.eye(Ng), spec.L, 10)
+    exact = dict(phi=phi, idx=np.arange(Ng), V=V, W=V.copy(), C=C, dV=dV, L=spec.L, grid=10)
+    tspec = CellSpec("tiny", np.array([[0.1, 0.2, 0.15], [0.55, 0.6, 0.45]]), 5.0, 10,
+                     [Shell(0, (0.6,), (1.0,)), Shell(1, (0.9,), (1.0,))], 3, 30, 77)
+    return exact, build_cell(tspec)
+
+
+def _pins_hold(exact, tiny):
+    f = exact
+    K, E = oracle.exx_rps_occri(f["phi"], f["idx"], f["V"], f["W"], f["C"], f["dV"])
+    _, Kx, Ex = oracle.exx_exact_fft(f["phi"], f["C"], f["L"], f["grid"], f["dV"])
+    p1 = abs(E - Ex) < 1e-11 * abs(Ex) and np.max(np.abs(K - Kx)) < 1e-11 * np.max(np.abs(Kx))
+    c = tiny
+    K, E = oracle.exx_rps_occri(c.phi, c.idx, c.V, c.W, c.C, c.dV)
+    _, K4, E4 = oracle.exx_rps_4index(c.phi, c.idx, c.V, c.W, c.C, c.dV)
+    p3 = abs(E - E4) < 1e-12 * abs(E4) and np.max(np.abs(K - K4)) < 1e-12 * np.max(np.abs(K4))
+    return p1 and p3
+
+
+def test_unmutated_pins_hold(settings):
+    assert _pins_hold(*settings)
+
+
+@pytest.mark.parametrize("mutant", MUTANTS, ids=[m.__name__ for m in MUTANTS])
+def test_mutant_is_caught(settings, mutant, monkeypatch):
+    monkeypatch.setattr(ox, "rps_lines", mutant)
+    assert not _pins_hold(*settings)
