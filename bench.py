@@ -1,0 +1,322 @@
+"""Benchmark of the exchange build: K builds/s on the 64-centre diamond cell.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--mode bf16x3|fp64]
+                    [--impl xk|reference]
+
+One step is one complete occ-RI robust-PS exchange build (orbitals, pair
+kernel, the three lines, K_{mu i}, E_x) of the seeded synthetic 64-centre
+cell (N=832, n=128, N_g=60^3, N_aux=4000) for a new C from a seeded
+pseudo-SCF sequence.  `value` times K builds on device-resident inputs with
+CUDA events on the launching stream; `e2e` times the same builds through the
+blocking C-ABI call with host buffers (H2D of C, D2H of K and E_x inside).
+Every table is far larger than L2 (V alone is 6.9 GB in FP64), so no flush
+is needed between builds.  Under torchrun each rank builds its own cell
+instance (weak scaling, no collective on the data path); rank 0 prints one
+JSON line with the max-over-ranks time.
+
+--impl reference times the FP64 CPU oracle on the host cores on the same
+workload (one full build per step) and prints the same line with
+"impl": "reference".
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from cellgen import config_spec, load_cell, perturb_coefficients  # noqa: E402
+
+WORKLOAD = ("64-centre 2x2x2 diamond supercell, L=13.48 bohr, 13 Gaussians/centre "
+            "(2s,2p,1d), N=832, n_occ=128, 60^3 grid, N_aux=4000")
+METRIC = "K builds/s (64-atom cell)"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# FP64 on the CUDA cores of GB300: measured DFMA issue rate (see the design doc,
+# "FP64 ALU peak"): flops/clock/SM x 152 SMs x max SM clock.
+FP64_FLOPS_PER_CLK_SM = 4.0
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=0)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--mode", default="auto", choices=["auto", "bf16x3", "fp64"])
+    p.add_argument("--impl", default="xk", choices=["xk", "reference"])
+    p.add_argument("--config", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return FALLBACK_PEAKS, "fallback"
+
+
+def step_flops(N, n, Ng, Na):
+    """Algorithmic FLOPs of each build step (the contraction counts of the
+    step list in include/xk.h)."""
+    return {
+        "orbitals": 2.0 * Ng * N * n,
+        "pair": 2.0 * Na * Ng * n + Na * Ng,
+        "m2": 2.0 * Na * Ng * n,
+        "m1": 2.0 * Na * Ng * n,
+        "line1": 2.0 * n * Ng * N,
+        "line2": 2.0 * n * Na * N,
+        "line3": 4.0 * Na * Na * n + 2.0 * n * Na * N + Na * Na,
+        "assemble": 4.0 * N * n,
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.proc = None
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if uuid:
+                cmd += ["-i", uuid]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def pseudo_scf(cell, count, seed):
+    Cs = [cell.C]
+    for t in range(count - 1):
+        Cs.append(perturb_coefficients(cell.S, Cs[-1], seed + t))
+    return Cs
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    cell = load_cell(config_spec(args.config))
+    steps = args.steps or 5
+    Cs = pseudo_scf(cell, steps + args.warmup, 77)
+    for i in range(args.warmup):
+        oracle.exx_rps_occri(cell.phi, cell.idx, cell.V, cell.W, Cs[i], cell.dV)
+    t0 = time.perf_counter()
+    for i in range(steps):
+        oracle.exx_rps_occri(cell.phi, cell.idx, cell.V, cell.W, Cs[args.warmup + i], cell.dV)
+    dt = time.perf_counter() - t0
+    v = steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "builds/s",
+        "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded cell generator)",
+        "config": {"workload": WORKLOAD, "impl": "FP64 NumPy oracle of Eq. exoccri"},
+        "cpu_baseline": {"value": v, "unit": "builds/s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": f"{steps} full builds of the 64-centre cell"},
+        "e2e": {"value": v, "unit": "builds/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import paper_2207_04636_gb300 as xk
+    from paper_2207_04636_gb300 import build as xkbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    xkbuild.build_library()
+
+    mode = args.mode
+    if mode == "auto":
+        mode = os.environ.get("XK_BENCH_MODE", "fp64")
+    steps = args.steps or (20 if mode != "fp64" else 6)
+    warm = max(3, args.warmup)
+
+    cell = load_cell(config_spec(args.config))
+    N, n, Ng, Na = cell.N, cell.n, cell.Ng, cell.Naux
+    h = xk.Handle(cell.phi, cell.idx, cell.V, cell.W, cell.dV, n, mode=mode)
+    Cs = pseudo_scf(cell, steps + warm, 1000 + rank)
+    Cd = [torch.from_numpy(C).cuda() for C in Cs]
+    Kd = torch.empty((N, n), dtype=torch.float64, device="cuda")
+    Ed = torch.empty(1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for i in range(warm):
+        h.build_device(Cd[i].data_ptr(), Kd.data_ptr(), Ed.data_ptr(), stream.cuda_stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    h.timing(True)
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    time.sleep(0.3)
+    launches0 = xk.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        h.build_device(Cd[warm + i].data_ptr(), Kd.data_ptr(), Ed.data_ptr(), stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = xk.kernel_launches() - launches0
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    st = h.step_times()
+    h.timing(False)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    K_last = Kd.cpu().numpy()
+    E_last = float(Ed.item())
+
+    # e2e through the blocking C-ABI call, host buffers (pinned) in and out.
+    Ch = [torch.from_numpy(C).pin_memory() for C in Cs[warm:warm + steps]]
+    Kh = torch.empty((N, n), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        K_e2e, E_e2e = h.build(Ch[i].numpy())
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    del Kh
+    h.release()
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank == 0:
+        pk, pk_src = peaks()
+        fl = step_flops(N, n, Ng, Na)
+        dom = max((k for k in st if st[k][1] > 0), key=lambda k: st[k][0])
+        dom_ms = st[dom][0] / max(1, st[dom][1])
+        if mode == "fp64":
+            dom_flops = fl[dom]
+            peak = FP64_FLOPS_PER_CLK_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
+            roof = {"bound": "alu", "kernel": f"step '{dom}' (FP64 DFMA GEMM)",
+                    "achieved": dom_flops / (dom_ms * 1e-3) / 1e12, "peak": peak,
+                    "unit": "TFLOP/s", "peak_source": "derived FP64 DFMA rate x SMs x max clock",
+                    "traffic": None}
+        else:
+            dom_flops = fl["pair"] + fl["m2"] + fl["m1"]
+            peak = pk.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"])
+            roof = {"bound": "tensor", "kernel": "fused pair/Hadamard/M1/M2 (tcgen05)",
+                    "achieved": dom_flops / (dom_ms * 1e-3) / 1e12, "peak": peak,
+                    "unit": "TFLOP/s", "peak_source": f"bf16 burst ({pk_src})",
+                    "traffic": None}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["ms_per_launch"] = dom_ms
+        value = world * steps / (ms * 1e-3)
+        line = {
+            "metric": METRIC, "value": value, "unit": "builds/s", "n_gpus": world,
+            "steps": steps, "warmup": warm, "ms_per_step": ms / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if mode == "fp64" else "bf16x3",
+            "data": "synthetic (seeded cell generator; inputs resident in HBM)",
+            "config": {"workload": WORKLOAD, "mode": mode, "N": N, "n": n, "N_g": Ng,
+                       "N_aux": Na, "l2": "inputs larger than L2 (V is N_aux x N_g)",
+                       "parallelism": f"replicas x{world}"},
+            "E_x": E_last,
+            "step_ms": {k: v[0] / max(1, v[1]) for k, v in st.items()},
+            "algorithmic_tflops_per_s": sum(fl.values()) / (ms * 1e-3 / steps) / 1e12,
+            "roofline": roof,
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "e2e": {"value": world * steps / e2e_s, "unit": "builds/s",
+                    "h2d_bytes_per_step": N * n * 8, "d2h_bytes_per_step": N * n * 8 + 8},
+        }
+        if not args.no_cpu_baseline and world == 1:
+            import oracle
+            C_last = Cs[warm + steps - 1]
+            t0 = time.perf_counter()
+            nb = 0
+            while True:
+                K0, E0 = oracle.exx_rps_occri(cell.phi, cell.idx, cell.V, cell.W, C_last, cell.dV)
+                nb += 1
+                if time.perf_counter() - t0 > 10.0 or nb >= 3:
+                    break
+            dt = time.perf_counter() - t0
+            line["cpu_baseline"] = {"value": nb / dt, "unit": "builds/s", "cores": cpu_cores(),
+                                    "kind": "oracle",
+                                    "sample": f"{nb} full FP64 oracle builds of the same cell"}
+            line["parity_last_step"] = {"dE_x": abs(E_last - E0),
+                                        "max_dK": float(np.max(np.abs(K_last - K0)))}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * xk.h -- C ABI of the GB300 robust-pseudospectral occ-RI exchange build.
+ *
+ * The library evaluates, for one periodic cell whose auxiliary tables are
+ * kept in device memory, the occ-RI exchange rectangle of arXiv 2207.04636,
+ * Eq. exoccri (Sec. III.C, with the robust-PS integrals of Eq. rps,
+ * Sec. III.B), and the exchange energy:
+ *
+ *   Psi   = Phi C,  Psi_g = Psi[idx]                     (Eq. rpsEx, step 1)
+ *   P     = Psi_g Psi^T,  V2 = V o P                     (Eq. rpsEx, steps 2-3)
+ *   line1 = (Psi_g^T V2) Phi                             (Eq. exoccri, line 1)
+ *   line2 = (V2 Psi)^T Phi_g   (contraction order (a), Sec. IV.D)
+ *   line3 = ((W o (Psi_g Psi_g^T)) Psi_g)^T Phi_g        (Eq. exoccri, line 3)
+ *   K_{mu i} = dV (line1 + line2 - line3)^T,   E_x = -sum_{mu,i} K_{mu i} C_{mu i}
+ *
+ * One factor dV = Omega / N_g multiplies every term (the grid form of the
+ * Coulomb integral, Eq. 2eint).  No FFT runs inside a build: V and W are
+ * computed once per geometry by the caller (Eq. rpsPot, Eq. thcpot).
+ *
+ * Conventions for every entry point:
+ *   - All matrices are row-major, double precision, densely packed.
+ *   - Host pointers are owned by the caller; the library copies what it
+ *     needs before returning (xk_setup, xk_build, xk_submit) and never keeps
+ *     a caller pointer.  Device pointers (xk_build_device) stay owned by the
+ *     caller and must stay valid until the work on the given stream is done.
+ *   - Return codes only; nothing throws across this boundary.  On failure
+ *     xk_last_error() gives a message for the calling thread.
+ *   - Grid points are flat indices (ix*N2 + iy)*N3 + iz of the uniform grid
+ *     (Sec. II.A.2); the library only needs Phi and V to agree on them.
+ */
+#ifndef XK_H
+#define XK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct xk_handle xk_handle;
+typedef uint64_t xk_ticket;
+
+enum {
+  XK_OK = 0,
+  XK_PENDING = 1,     /* xk_poll: the build is still running              */
+  XK_EINVAL = -1,     /* bad shape, null pointer, bad index, bad table     */
+  XK_ENOMEM = -2,     /* footprint beyond the admission budget; retry later */
+  XK_ETIMEDOUT = -3,  /* a bounded wait or a ticket deadline expired       */
+  XK_ECUDA = -4,      /* any other CUDA error (message in xk_last_error)   */
+  XK_EBUSY = -5       /* every submission slot of the handle is in use     */
+};
+
+enum {
+  XK_FP64 = 0,        /* every step in FP64                                 */
+  XK_TF32 = 1,        /* reserved                                           */
+  XK_BF16X3 = 2       /* bulk contractions as split-BF16x3 on tensor cores,
+                         FP32 accumulation, FP64 cross-tile sums and E_x    */
+};
+
+/*
+ * Device bytes one handle of this shape and mode holds (tables + scratch).
+ * This is the paper's extra memory cost O(N_chi N_g) of the stored
+ * potentials (Sec. IV, memory column of the cost table), plus scratch.
+ * Returns XK_EINVAL on non-positive sizes or an unknown mode.
+ */
+int xk_footprint(int64_t Ng, int32_t N, int32_t n, int32_t Naux, int mode, size_t* bytes);
+
+/*
+ * Copy the per-geometry tables to the current CUDA device and return a
+ * handle.  Inputs (host memory, read only, may be freed after return):
+ *   basis_on_points  Ng x N      Phi[R, mu] = phi_mu(R)        (Sec. II.A.3)
+ *   interp_idx       Naux        grid index of each R_g, each in [0, Ng),
+ *                                no duplicates                  (Eq. isdf)
+ *   V_aux            Naux x Ng   V(R_g, R), potential of chi_g  (Eq. rpsPot)
+ *   W_aux            Naux x Naux W(R_g, R_g'), symmetric        (Eq. thcpot)
+ *   dV               Omega / N_g, > 0
+ *   mode             XK_FP64 or XK_BF16X3
+ * Errors: XK_EINVAL (sizes, null pointers, idx out of range or duplicated,
+ * W not symmetric to 1e-12 relative, dV <= 0, n > N, Naux > Ng),
+ * XK_ENOMEM (footprint above the admission budget: free device memory less
+ * a reserve, or XK_HBM_BUDGET_BYTES when set), XK_ECUDA.
+ */
+int xk_setup(int64_t Ng, int32_t N, int32_t n, int32_t Naux,
+             const double* basis_on_points, const int32_t* interp_idx,
+             const double* V_aux, const double* W_aux,
+             double dV, int mode, xk_handle** out);
+
+/*
+ * One exchange build, blocking.  C (host, N x n) are the occupied
+ * coefficients; K_out (host, N x n) receives K_{mu i}; Ex (host) receives
+ * E_x.  Builds on one handle are serialised.
+ * Errors: XK_EINVAL (null pointers), XK_ECUDA.
+ */
+int xk_build(xk_handle* h, const double* C, double* K_out, double* Ex);
+
+/*
+ * The same build on device memory, enqueued on `stream` (a cudaStream_t,
+ * NULL = the legacy default stream) and returning at once.  C_dev (N x n),
+ * K_dev (N x n) and Ex_dev (1 double) are device pointers owned by the
+ * caller.  The handle's scratch is reused, so builds on one handle must not
+ * overlap: enqueue them on one stream.  Errors: XK_EINVAL, XK_ECUDA.
+ */
+int xk_build_device(xk_handle* h, const double* C_dev, double* K_dev, double* Ex_dev,
+                    void* stream);
+
+/*
+ * occ-RI K_ij of the last completed build on this handle and its ACE
+ * factorisation (Sec. III.C), computed on the device in FP64:
+ * K_ij = C^T K_{mu i} symmetrised; Cholesky K_ij = L L^T when it is positive
+ * definite (branch 0, xi = K_{mu i} L^{-T}, K ~ xi xi^T on the occupied
+ * space), else a Jacobi eigendecomposition keeping |lambda| > 1e-12 max|lambda|
+ * (branch 1, xi = K_{mu i} U |Lambda|^{-1/2}; sign_out gets sign(lambda),
+ * zero for dropped columns).  Outputs are host memory: Kij_out n x n,
+ * xi_out N x n, sign_out n (nullable), branch (nullable).
+ * Errors: XK_EINVAL (no build yet, null pointers), XK_ECUDA.
+ */
+int xk_ace(xk_handle* h, double* Kij_out, double* xi_out, double* sign_out, int* branch);
+
+/*
+ * Serving: enqueue a build and return a ticket at once.  C is copied into a
+ * pinned slot before return.  Each handle runs its builds in order on its
+ * own stream, so builds of different handles (different SCF runs, cells of
+ * different sizes) overlap on the GPU.  deadline_ms > 0 sets how long the
+ * ticket may stay pending before xk_poll reports XK_ETIMEDOUT (0 = none).
+ * Errors: XK_EINVAL, XK_EBUSY (all slots of the handle in flight), XK_ECUDA.
+ */
+int xk_submit(xk_handle* h, const double* C, double deadline_ms, xk_ticket* t);
+
+/*
+ * Non-blocking completion check.  XK_PENDING while the build runs;
+ * XK_OK once done, after copying K_{mu i} (N x n) to K_out and E_x to Ex;
+ * err_bound (nullable) receives the a-priori bound on |E_x error| of the
+ * handle's mode relative to FP64 (0 for XK_FP64).  A ticket is consumed by
+ * the XK_OK, XK_ETIMEDOUT or XK_ECUDA result.  XK_EINVAL for an unknown ticket.
+ */
+int xk_poll(xk_ticket t, double* K_out, double* Ex, double* err_bound);
+
+/* Free every device and host resource of the handle (waits for its work). */
+int xk_release(xk_handle* h);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* xk_last_error(void);
+
+/*
+ * Steps of a build, for xk_timing_read.  XK_STEP_PAIR covers the pair
+ * kernel P and the Hadamard with V (Eq. rpsEx, steps 2-3); in the
+ * mixed-precision path it also covers M2 and M1, which one fused kernel
+ * computes, and XK_STEP_M2 / XK_STEP_M1 stay at zero.
+ */
+enum {
+  XK_STEP_ORBITALS = 0,  /* Psi = Phi C and the gathers at R_g             */
+  XK_STEP_PAIR = 1,      /* P = Psi_g Psi^T, V2 = V o P                     */
+  XK_STEP_M2 = 2,        /* M2 = V2 Psi                                     */
+  XK_STEP_M1 = 3,        /* M1 = Psi_g^T V2                                 */
+  XK_STEP_LINE1 = 4,     /* line1 = M1 Phi                                  */
+  XK_STEP_LINE2 = 5,     /* line2 = M2^T Phi_g                              */
+  XK_STEP_LINE3 = 6,     /* line3 = ((W o Q) Psi_g)^T Phi_g                 */
+  XK_STEP_ASSEMBLE = 7,  /* K = dV (line1 + line2 - line3)^T, E_x           */
+  XK_NSTEPS = 8
+};
+
+/*
+ * Step timing with CUDA events on the handle's stream.  enable != 0 turns it
+ * on and clears the accumulators; 0 turns it off.  While on, every build
+ * records an event pair around each step.  xk_timing_read waits for the
+ * handle's stream, then returns the summed device milliseconds of `step`
+ * over the builds since enabling and how many builds contributed.
+ * Errors: XK_EINVAL (NULL handle, step out of range), XK_ECUDA.
+ */
+int xk_timing_enable(xk_handle* h, int enable);
+int xk_timing_read(xk_handle* h, int step, double* ms, uint64_t* builds);
+
+/*
+ * Kernel launches issued by the library since load (counts every kernel of
+ * every build): lets a caller confirm the device path ran.
+ */
+uint64_t xk_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XK_H */

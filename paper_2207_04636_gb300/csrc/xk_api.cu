@@ -1,0 +1,617 @@
+// Host side of libxk: the C ABI of include/xk.h.  Handles own the
+// per-geometry tables and the build scratch in device memory; builds are
+// sequences of kernel launches on the handle's stream; submissions ride
+// pinned host slots and CUDA events so that builds of different handles
+// overlap on the GPU.
+#include "xk_internal.h"
+#include "xk_mixed.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/xk.h"
+
+namespace {
+
+thread_local std::string t_err;
+
+int fail(int code, const std::string& msg) {
+  t_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(XK_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define XK_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+constexpr int kSlots = 4;
+
+struct Slot {
+  double* C = nullptr;    // pinned, N x n
+  double* K = nullptr;    // pinned, N x n
+  double* Ex = nullptr;   // pinned, 1
+  cudaEvent_t done = nullptr;
+  int state = 0;          // 0 free, 1 in flight, 2 abandoned (timed out)
+  xk_ticket ticket = 0;
+  std::chrono::steady_clock::time_point deadline;
+  bool has_deadline = false;
+};
+
+size_t g_admitted = 0;    // bytes held by live handles (all devices)
+std::mutex g_admit_mu;
+
+}  // namespace
+
+struct xk_handle {
+  int64_t Ng = 0;
+  int N = 0, n = 0, Naux = 0, mode = 0, device = 0;
+  double dV = 0.0;
+  size_t footprint = 0;
+  cudaStream_t stream = nullptr;
+  std::mutex mu;
+  bool has_build = false;
+  std::vector<void*> allocs;
+
+  // FP64 tables and scratch
+  double *phi = nullptr, *phig = nullptr, *V = nullptr, *W = nullptr;
+  int32_t* idx = nullptr;
+  double *C = nullptr, *psi = nullptr, *psig = nullptr, *V2 = nullptr, *M1 = nullptr,
+         *M2 = nullptr, *Q = nullptr, *M3 = nullptr, *L1 = nullptr, *L2 = nullptr,
+         *L3 = nullptr, *K = nullptr, *Ex = nullptr, *work = nullptr, *red = nullptr;
+  // occ-RI K_ij factorisation scratch
+  double *Kij = nullptr, *Lf = nullptr, *U = nullptr, *Y = nullptr, *xi = nullptr,
+         *sgn = nullptr;
+  int* status = nullptr;
+
+  xk::MixedState* mixed = nullptr;
+  Slot slots[kSlots];
+
+  // step timing (xk_timing_enable / xk_timing_read)
+  bool timing = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+  double step_ms[XK_NSTEPS] = {0};
+  uint64_t step_builds[XK_NSTEPS] = {0};
+};
+
+namespace {
+
+std::mutex g_tickets_mu;
+std::unordered_map<xk_ticket, std::pair<xk_handle*, int>> g_tickets;
+xk_ticket g_next_ticket = 1;
+
+struct Plan {
+  size_t f64 = 0;   // doubles
+  size_t i32 = 0;   // int32
+  size_t work = 0;  // doubles of split-K work
+};
+
+size_t max_work(int64_t Ng, int N, int n, int Naux) {
+  const int ng = (int)Ng;
+  size_t w = 0;
+  auto acc = [&](int M, int Nc, int K) {
+    w = std::max(w, (size_t)xk::dgemm_ksplit(M, Nc, K) * (size_t)M * (size_t)Nc);
+  };
+  acc(ng, n, N);        // Psi = Phi C
+  acc(Naux, ng, n);     // V2 = V o (Psi_g Psi^T)
+  acc(Naux, n, ng);     // M2 = V2 Psi
+  acc(n, ng, Naux);     // M1 = Psi_g^T V2
+  acc(n, N, ng);        // line1
+  acc(n, N, Naux);      // line2, line3
+  acc(Naux, Naux, n);   // W o Q
+  acc(Naux, n, Naux);   // M3
+  acc(n, n, N);         // K_ij
+  acc(N, n, n);         // K U
+  return w;
+}
+
+Plan plan_fp64(int64_t Ng, int N, int n, int Naux) {
+  Plan p;
+  const size_t ng = (size_t)Ng, na = (size_t)Naux;
+  p.f64 = ng * N + na * N + na * ng + na * na       // Phi, Phi_g, V, W
+          + (size_t)N * n + ng * n + na * n         // C, Psi, Psi_g
+          + na * ng + (size_t)n * ng + na * n       // V2, M1, M2
+          + na * na + na * n + 3 * (size_t)n * N    // Q, M3, lines
+          + (size_t)N * n + 1 + xk::reduce_work_elems()  // K, Ex, reduction
+          + 3 * (size_t)n * n + 2 * (size_t)N * n + n;   // K_ij, L, U, Y, xi, sign
+  p.work = max_work(Ng, N, n, Naux);
+  p.f64 += p.work;
+  p.i32 = na + 2;
+  return p;
+}
+
+size_t plan_bytes(const Plan& p) { return p.f64 * 8 + p.i32 * 4 + 64 * 256; }
+
+bool valid_sizes(int64_t Ng, int32_t N, int32_t n, int32_t Naux) {
+  return Ng > 0 && N > 0 && n > 0 && Naux > 0 && n <= N && (int64_t)Naux <= Ng &&
+         Ng < (int64_t)1 << 31;
+}
+
+template <class T>
+cudaError_t dalloc(xk_handle* h, T** p, size_t elems) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(elems, 1) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  h->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return cudaSuccess;
+}
+
+void fold_marks(xk_handle* h);
+
+void free_handle(xk_handle* h) {
+  if (!h) return;
+  DeviceGuard g(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (Slot& s : h->slots) {
+    if (s.done) cudaEventDestroy(s.done);
+    if (s.C) cudaFreeHost(s.C);
+    if (s.K) cudaFreeHost(s.K);
+    if (s.Ex) cudaFreeHost(s.Ex);
+  }
+  if (h->mixed) xk::mixed_destroy(h->mixed);
+  fold_marks(h);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  {
+    std::lock_guard<std::mutex> lk(g_admit_mu);
+    g_admitted -= std::min(g_admitted, h->footprint);
+  }
+  delete h;
+}
+
+// Records the start or the end of `step` when timing is on.
+struct StepMark {
+  xk_handle* h;
+  int step;
+  cudaEvent_t a = nullptr, b = nullptr;
+  StepMark(xk_handle* hh, int st) : h(hh), step(st) {
+    if (!h->timing) return;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, h->stream);
+  }
+  ~StepMark() {
+    if (!a) return;
+    cudaEventRecord(b, h->stream);
+    h->marks.push_back({step, {a, b}});
+  }
+};
+
+// Begin (begin != 0) or end a step of the mixed path: same events as StepMark.
+void step_hook(void* ctx, int step, int begin) {
+  xk_handle* h = static_cast<xk_handle*>(ctx);
+  static thread_local cudaEvent_t open[XK_NSTEPS] = {nullptr};
+  if (begin) {
+    cudaEventCreate(&open[step]);
+    cudaEventRecord(open[step], h->stream);
+  } else if (open[step]) {
+    cudaEvent_t b;
+    cudaEventCreate(&b);
+    cudaEventRecord(b, h->stream);
+    h->marks.push_back({step, {open[step], b}});
+    open[step] = nullptr;
+  }
+}
+
+void fold_marks(xk_handle* h) {
+  for (auto& m : h->marks) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, m.second.first, m.second.second) == cudaSuccess) {
+      h->step_ms[m.first] += ms;
+      h->step_builds[m.first] += 1;
+    }
+    cudaEventDestroy(m.second.first);
+    cudaEventDestroy(m.second.second);
+  }
+  h->marks.clear();
+}
+
+// Enqueue one FP64 build on h->stream.  C is in h->C; results land in h->K, h->Ex.
+int enqueue_fp64(xk_handle* h) {
+  using xk::DGemm;
+  cudaStream_t s = h->stream;
+  const int ng = (int)h->Ng, N = h->N, n = h->n, na = h->Naux;
+  auto G = [&](int M, int Nc, int K, const double* A, long lda, bool ta, const double* B, long ldb,
+               bool tb, double* C, long ldc, const double* H, long ldh) {
+    DGemm g{M, Nc, K, A, lda, ta, B, ldb, tb, C, ldc, 1.0, H, ldh, 0, h->work};
+    return xk::dgemm(g, s);
+  };
+  {  // Eq. rpsEx step 1: orbitals on the grid and at the interpolation points.
+    StepMark m(h, XK_STEP_ORBITALS);
+    XK_CUDA(G(ng, n, N, h->phi, N, false, h->C, n, false, h->psi, n, nullptr, 0));
+    XK_CUDA(xk::gather_rows_f64(h->psi, n, h->idx, na, n, h->psig, n, s));
+  }
+  {  // Steps 2-3: pair kernel at (R_g, R) and the Hadamard with V, fused.
+    StepMark m(h, XK_STEP_PAIR);
+    XK_CUDA(G(na, ng, n, h->psig, n, false, h->psi, n, true, h->V2, ng, h->V, ng));
+  }
+  {  // Line 2, first contraction (order (a)): M2 = V2 Psi.
+    StepMark m(h, XK_STEP_M2);
+    XK_CUDA(G(na, n, ng, h->V2, ng, false, h->psi, n, false, h->M2, n, nullptr, 0));
+  }
+  {  // Line 1, first contraction: M1 = Psi_g^T V2.
+    StepMark m(h, XK_STEP_M1);
+    XK_CUDA(G(n, ng, na, h->psig, n, true, h->V2, ng, false, h->M1, ng, nullptr, 0));
+  }
+  {  // Line 1, contraction with the basis on the grid.
+    StepMark m(h, XK_STEP_LINE1);
+    XK_CUDA(G(n, N, ng, h->M1, ng, false, h->phi, N, false, h->L1, N, nullptr, 0));
+  }
+  {  // Line 2, contraction with the basis at R_g.
+    StepMark m(h, XK_STEP_LINE2);
+    XK_CUDA(G(n, N, na, h->M2, n, true, h->phig, N, false, h->L2, N, nullptr, 0));
+  }
+  {  // Line 3: W o (Psi_g Psi_g^T), then two contractions.
+    StepMark m(h, XK_STEP_LINE3);
+    XK_CUDA(G(na, na, n, h->psig, n, false, h->psig, n, true, h->Q, na, h->W, na));
+    XK_CUDA(G(na, n, na, h->Q, na, false, h->psig, n, false, h->M3, n, nullptr, 0));
+    XK_CUDA(G(n, N, na, h->M3, n, true, h->phig, N, false, h->L3, N, nullptr, 0));
+  }
+  {  // K_{mu i} = dV (line1 + line2 - line3)^T and E_x = -sum K o C.
+    StepMark m(h, XK_STEP_ASSEMBLE);
+    XK_CUDA(xk::assemble_k_f64(h->L1, h->L2, h->L3, n, N, h->dV, h->K, s));
+    XK_CUDA(xk::neg_dot_f64(h->K, h->C, (long)N * n, h->red, h->Ex, s));
+  }
+  return XK_OK;
+}
+
+int enqueue_build(xk_handle* h) {
+  if (h->mode == XK_FP64) return enqueue_fp64(h);
+  xk::StepHook hook{h->timing ? &step_hook : nullptr, h};
+  cudaError_t e = xk::mixed_enqueue(h->mixed, h->C, h->K, h->Ex, h->stream, hook);
+  if (e != cudaSuccess) return cuda_fail(e, "mixed-precision build");
+  return XK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* xk_last_error(void) { return t_err.c_str(); }
+
+uint64_t xk_kernel_launches(void) { return xk::g_launches.load(); }
+
+int xk_footprint(int64_t Ng, int32_t N, int32_t n, int32_t Naux, int mode, size_t* bytes) {
+  if (!bytes) return fail(XK_EINVAL, "xk_footprint: bytes is NULL");
+  if (!valid_sizes(Ng, N, n, Naux)) return fail(XK_EINVAL, "xk_footprint: invalid sizes");
+  if (mode == XK_FP64) {
+    *bytes = plan_bytes(plan_fp64(Ng, N, n, Naux));
+    return XK_OK;
+  }
+  if (mode == XK_BF16X3) {
+    *bytes = xk::mixed_footprint(Ng, N, n, Naux) + (size_t)N * n * 8 * 2 + 4096;
+    return XK_OK;
+  }
+  return fail(XK_EINVAL, "xk_footprint: unknown mode");
+}
+
+int xk_setup(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* phi,
+             const int32_t* idx, const double* V, const double* W, double dV, int mode,
+             xk_handle** out) {
+  if (!out) return fail(XK_EINVAL, "xk_setup: out is NULL");
+  *out = nullptr;
+  if (!phi || !idx || !V || !W) return fail(XK_EINVAL, "xk_setup: NULL table pointer");
+  if (!valid_sizes(Ng, N, n, Naux)) return fail(XK_EINVAL, "xk_setup: invalid sizes");
+  if (!(dV > 0.0) || !std::isfinite(dV)) return fail(XK_EINVAL, "xk_setup: dV must be > 0");
+  if (mode != XK_FP64 && mode != XK_BF16X3) return fail(XK_EINVAL, "xk_setup: unsupported mode");
+  {
+    std::vector<int32_t> s(idx, idx + Naux);
+    std::sort(s.begin(), s.end());
+    if (s.front() < 0 || (int64_t)s.back() >= Ng)
+      return fail(XK_EINVAL, "xk_setup: interp_idx out of range");
+    if (std::adjacent_find(s.begin(), s.end()) != s.end())
+      return fail(XK_EINVAL, "xk_setup: interp_idx has duplicates");
+  }
+  {
+    double wmax = 0.0, asym = 0.0;
+    const size_t na = (size_t)Naux;
+    for (size_t i = 0; i < na; ++i)
+      for (size_t j = 0; j < na; ++j) {
+        const double a = W[i * na + j];
+        if (!std::isfinite(a)) return fail(XK_EINVAL, "xk_setup: W has non-finite entries");
+        wmax = std::max(wmax, std::fabs(a));
+        if (j > i) asym = std::max(asym, std::fabs(a - W[j * na + i]));
+      }
+    if (asym > 1e-12 * wmax) return fail(XK_EINVAL, "xk_setup: W_aux is not symmetric");
+  }
+  size_t need = 0;
+  int rc = xk_footprint(Ng, N, n, Naux, mode, &need);
+  if (rc != XK_OK) return rc;
+
+  int dev = 0;
+  XK_CUDA(cudaGetDevice(&dev));
+  size_t freeb = 0, totalb = 0;
+  XK_CUDA(cudaMemGetInfo(&freeb, &totalb));
+  {
+    std::lock_guard<std::mutex> lk(g_admit_mu);
+    const size_t reserve = (size_t)1 << 30;
+    size_t budget = freeb > reserve ? freeb - reserve : 0;
+    if (const char* env = std::getenv("XK_HBM_BUDGET_BYTES")) {
+      const size_t cap = (size_t)std::strtoull(env, nullptr, 10);
+      const size_t left = cap > g_admitted ? cap - g_admitted : 0;
+      budget = std::min(budget, left);
+    }
+    if (need > budget)
+      return fail(XK_ENOMEM, "xk_setup: footprint " + std::to_string(need) +
+                                 " bytes exceeds the admission budget " + std::to_string(budget));
+    g_admitted += need;
+  }
+
+  xk_handle* h = new xk_handle();
+  h->Ng = Ng; h->N = N; h->n = n; h->Naux = Naux; h->dV = dV; h->mode = mode; h->device = dev;
+  h->footprint = need;
+  auto bail = [&](int code) { free_handle(h); return code; };
+  cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate"));
+
+  const size_t ng = (size_t)Ng, na = (size_t)Naux;
+#define XK_ALLOC(ptr, elems)                                  \
+  do {                                                        \
+    cudaError_t e_ = dalloc(h, &(ptr), (elems));              \
+    if (e_ != cudaSuccess) return bail(cuda_fail(e_, "cudaMalloc " #ptr)); \
+  } while (0)
+  XK_ALLOC(h->C, (size_t)N * n);
+  XK_ALLOC(h->K, (size_t)N * n);
+  XK_ALLOC(h->Ex, 1);
+  XK_ALLOC(h->Kij, (size_t)n * n);
+  XK_ALLOC(h->Lf, (size_t)n * n);
+  XK_ALLOC(h->U, (size_t)n * n);
+  XK_ALLOC(h->Y, (size_t)N * n);
+  XK_ALLOC(h->xi, (size_t)N * n);
+  XK_ALLOC(h->sgn, (size_t)n);
+  XK_ALLOC(h->status, 2);
+  XK_ALLOC(h->red, xk::reduce_work_elems());
+  const size_t work = max_work(Ng, N, n, Naux);
+  XK_ALLOC(h->work, work);
+  if (mode == XK_FP64) {
+    XK_ALLOC(h->phi, ng * N);
+    XK_ALLOC(h->phig, na * N);
+    XK_ALLOC(h->V, na * ng);
+    XK_ALLOC(h->W, na * na);
+    XK_ALLOC(h->idx, na);
+    XK_ALLOC(h->psi, ng * n);
+    XK_ALLOC(h->psig, na * n);
+    XK_ALLOC(h->V2, na * ng);
+    XK_ALLOC(h->M1, (size_t)n * ng);
+    XK_ALLOC(h->M2, na * n);
+    XK_ALLOC(h->Q, na * na);
+    XK_ALLOC(h->M3, na * n);
+    XK_ALLOC(h->L1, (size_t)n * N);
+    XK_ALLOC(h->L2, (size_t)n * N);
+    XK_ALLOC(h->L3, (size_t)n * N);
+    e = cudaMemcpyAsync(h->phi, phi, ng * N * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->V, V, na * ng * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->W, W, na * na * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->idx, idx, na * 4, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = xk::gather_rows_f64(h->phi, N, h->idx, Naux, N, h->phig, N, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "xk_setup upload"));
+  } else {
+    e = xk::mixed_create(Ng, N, n, Naux, phi, idx, V, W, dV, h->stream, &h->mixed);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "xk_setup mixed tables"));
+  }
+#undef XK_ALLOC
+  for (Slot& s : h->slots) {
+    e = cudaHostAlloc((void**)&s.C, (size_t)N * n * 8, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&s.K, (size_t)N * n * 8, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&s.Ex, 8, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "xk_setup slots"));
+  }
+  *out = h;
+  return XK_OK;
+}
+
+int xk_build_device(xk_handle* h, const double* C_dev, double* K_dev, double* Ex_dev,
+                    void* stream) {
+  if (!h || !C_dev || !K_dev || !Ex_dev) return fail(XK_EINVAL, "xk_build_device: NULL argument");
+  std::lock_guard<std::mutex> lk(h->mu);
+  DeviceGuard g(h->device);
+  cudaStream_t us = static_cast<cudaStream_t>(stream);
+  const size_t kb = (size_t)h->N * h->n * 8;
+  // Order the handle's stream after the caller's stream, run, then order back.
+  cudaEvent_t ev;
+  XK_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  XK_CUDA(cudaEventRecord(ev, us));
+  XK_CUDA(cudaStreamWaitEvent(h->stream, ev, 0));
+  XK_CUDA(cudaMemcpyAsync(h->C, C_dev, kb, cudaMemcpyDeviceToDevice, h->stream));
+  int rc = enqueue_build(h);
+  if (rc != XK_OK) { cudaEventDestroy(ev); return rc; }
+  XK_CUDA(cudaMemcpyAsync(K_dev, h->K, kb, cudaMemcpyDeviceToDevice, h->stream));
+  XK_CUDA(cudaMemcpyAsync(Ex_dev, h->Ex, 8, cudaMemcpyDeviceToDevice, h->stream));
+  XK_CUDA(cudaEventRecord(ev, h->stream));
+  XK_CUDA(cudaStreamWaitEvent(us, ev, 0));
+  cudaEventDestroy(ev);
+  h->has_build = true;
+  return XK_OK;
+}
+
+int xk_build(xk_handle* h, const double* C, double* K_out, double* Ex) {
+  if (!h || !C || !K_out || !Ex) return fail(XK_EINVAL, "xk_build: NULL argument");
+  std::lock_guard<std::mutex> lk(h->mu);
+  DeviceGuard g(h->device);
+  const size_t kb = (size_t)h->N * h->n * 8;
+  XK_CUDA(cudaMemcpyAsync(h->C, C, kb, cudaMemcpyHostToDevice, h->stream));
+  int rc = enqueue_build(h);
+  if (rc != XK_OK) return rc;
+  XK_CUDA(cudaMemcpyAsync(K_out, h->K, kb, cudaMemcpyDeviceToHost, h->stream));
+  XK_CUDA(cudaMemcpyAsync(Ex, h->Ex, 8, cudaMemcpyDeviceToHost, h->stream));
+  XK_CUDA(cudaStreamSynchronize(h->stream));
+  h->has_build = true;
+  return XK_OK;
+}
+
+int xk_ace(xk_handle* h, double* Kij_out, double* xi_out, double* sign_out, int* branch) {
+  if (!h || !Kij_out || !xi_out) return fail(XK_EINVAL, "xk_ace: NULL argument");
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (!h->has_build) return fail(XK_EINVAL, "xk_ace: no completed build on this handle");
+  DeviceGuard g(h->device);
+  cudaStream_t s = h->stream;
+  const int N = h->N, n = h->n;
+  xk::DGemm kij{n, n, N, h->C, n, true, h->K, n, false, h->Kij, n, 1.0, nullptr, 0, 0, h->work};
+  XK_CUDA(xk::dgemm(kij, s));
+  XK_CUDA(xk::symmetrize_f64(h->Kij, n, s));
+  XK_CUDA(cudaMemcpyAsync(h->Lf, h->Kij, (size_t)n * n * 8, cudaMemcpyDeviceToDevice, s));
+  XK_CUDA(xk::cholesky_f64(h->Lf, n, h->status, s));
+  int st = 0;
+  XK_CUDA(cudaMemcpyAsync(&st, h->status, 4, cudaMemcpyDeviceToHost, s));
+  XK_CUDA(cudaStreamSynchronize(s));
+  int br = 0;
+  std::vector<double> sg(n, 1.0);
+  if (st == 0) {
+    XK_CUDA(xk::trsm_right_lt_f64(h->Lf, n, h->K, N, h->xi, s));
+  } else {
+    br = 1;
+    XK_CUDA(cudaMemcpyAsync(h->Lf, h->Kij, (size_t)n * n * 8, cudaMemcpyDeviceToDevice, s));
+    XK_CUDA(xk::jacobi_eig_f64(h->Lf, h->U, n, 60, h->status + 1, s));
+    xk::DGemm ku{N, n, n, h->K, n, false, h->U, n, false, h->Y, n, 1.0, nullptr, 0, 0, h->work};
+    XK_CUDA(xk::dgemm(ku, s));
+    XK_CUDA(xk::scale_eigcols_f64(h->Lf, n, h->Y, N, 1e-12, h->xi, h->sgn, s));
+    XK_CUDA(cudaMemcpyAsync(sg.data(), h->sgn, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+  }
+  XK_CUDA(cudaMemcpyAsync(Kij_out, h->Kij, (size_t)n * n * 8, cudaMemcpyDeviceToHost, s));
+  XK_CUDA(cudaMemcpyAsync(xi_out, h->xi, (size_t)N * n * 8, cudaMemcpyDeviceToHost, s));
+  XK_CUDA(cudaStreamSynchronize(s));
+  if (sign_out) std::memcpy(sign_out, sg.data(), (size_t)n * 8);
+  if (branch) *branch = br;
+  return XK_OK;
+}
+
+int xk_submit(xk_handle* h, const double* C, double deadline_ms, xk_ticket* t) {
+  if (!h || !C || !t) return fail(XK_EINVAL, "xk_submit: NULL argument");
+  std::lock_guard<std::mutex> lk(h->mu);
+  DeviceGuard g(h->device);
+  int k = -1;
+  for (int i = 0; i < kSlots; ++i) {
+    Slot& s = h->slots[i];
+    if (s.state == 2 && cudaEventQuery(s.done) == cudaSuccess) s.state = 0;
+    if (s.state == 0 && k < 0) k = i;
+  }
+  if (k < 0) return fail(XK_EBUSY, "xk_submit: every slot of the handle is in flight");
+  Slot& s = h->slots[k];
+  const size_t kb = (size_t)h->N * h->n * 8;
+  std::memcpy(s.C, C, kb);
+  XK_CUDA(cudaMemcpyAsync(h->C, s.C, kb, cudaMemcpyHostToDevice, h->stream));
+  int rc = enqueue_build(h);
+  if (rc != XK_OK) return rc;
+  XK_CUDA(cudaMemcpyAsync(s.K, h->K, kb, cudaMemcpyDeviceToHost, h->stream));
+  XK_CUDA(cudaMemcpyAsync(s.Ex, h->Ex, 8, cudaMemcpyDeviceToHost, h->stream));
+  XK_CUDA(cudaEventRecord(s.done, h->stream));
+  h->has_build = true;
+  s.state = 1;
+  s.has_deadline = deadline_ms > 0;
+  if (s.has_deadline)
+    s.deadline = std::chrono::steady_clock::now() +
+                 std::chrono::microseconds((long long)(deadline_ms * 1000.0));
+  std::lock_guard<std::mutex> tl(g_tickets_mu);
+  s.ticket = g_next_ticket++;
+  g_tickets[s.ticket] = {h, k};
+  *t = s.ticket;
+  return XK_OK;
+}
+
+int xk_poll(xk_ticket t, double* K_out, double* Ex, double* err_bound) {
+  if (!K_out || !Ex) return fail(XK_EINVAL, "xk_poll: NULL argument");
+  xk_handle* h = nullptr;
+  int k = -1;
+  {
+    std::lock_guard<std::mutex> tl(g_tickets_mu);
+    auto it = g_tickets.find(t);
+    if (it == g_tickets.end()) return fail(XK_EINVAL, "xk_poll: unknown ticket");
+    h = it->second.first;
+    k = it->second.second;
+  }
+  std::lock_guard<std::mutex> lk(h->mu);
+  DeviceGuard g(h->device);
+  Slot& s = h->slots[k];
+  cudaError_t q = cudaEventQuery(s.done);
+  auto consume = [&]() {
+    std::lock_guard<std::mutex> tl(g_tickets_mu);
+    g_tickets.erase(t);
+  };
+  if (q == cudaErrorNotReady) {
+    if (s.has_deadline && std::chrono::steady_clock::now() > s.deadline) {
+      s.state = 2;
+      consume();
+      return fail(XK_ETIMEDOUT, "xk_poll: ticket deadline expired");
+    }
+    return XK_PENDING;
+  }
+  if (q != cudaSuccess) {
+    s.state = 0;
+    consume();
+    return cuda_fail(q, "xk_poll");
+  }
+  const size_t kb = (size_t)h->N * h->n * 8;
+  std::memcpy(K_out, s.K, kb);
+  *Ex = *s.Ex;
+  if (err_bound) *err_bound = h->mode == XK_FP64 ? 0.0 : xk::mixed_error_bound(h->mixed);
+  s.state = 0;
+  consume();
+  return XK_OK;
+}
+
+int xk_timing_enable(xk_handle* h, int enable) {
+  if (!h) return fail(XK_EINVAL, "xk_timing_enable: NULL handle");
+  std::lock_guard<std::mutex> lk(h->mu);
+  DeviceGuard g(h->device);
+  XK_CUDA(cudaStreamSynchronize(h->stream));
+  fold_marks(h);
+  for (int i = 0; i < XK_NSTEPS; ++i) {
+    h->step_ms[i] = 0.0;
+    h->step_builds[i] = 0;
+  }
+  h->timing = enable != 0;
+  return XK_OK;
+}
+
+int xk_timing_read(xk_handle* h, int step, double* ms, uint64_t* builds) {
+  if (!h || !ms || step < 0 || step >= XK_NSTEPS)
+    return fail(XK_EINVAL, "xk_timing_read: bad argument");
+  std::lock_guard<std::mutex> lk(h->mu);
+  DeviceGuard g(h->device);
+  XK_CUDA(cudaStreamSynchronize(h->stream));
+  fold_marks(h);
+  *ms = h->step_ms[step];
+  if (builds) *builds = h->step_builds[step];
+  return XK_OK;
+}
+
+int xk_release(xk_handle* h) {
+  if (!h) return fail(XK_EINVAL, "xk_release: NULL handle");
+  {
+    std::lock_guard<std::mutex> tl(g_tickets_mu);
+    for (auto it = g_tickets.begin(); it != g_tickets.end();)
+      it = (it->second.first == h) ? g_tickets.erase(it) : std::next(it);
+  }
+  free_handle(h);
+  return XK_OK;
+}
+
+}  // extern "C"

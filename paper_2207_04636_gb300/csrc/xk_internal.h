@@ -1,0 +1,79 @@
+// Internal declarations shared by the translation units of libxk.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+
+namespace xk {
+
+// Kernel launches issued since load (all translation units).
+extern std::atomic<uint64_t> g_launches;
+inline void count_launch(uint64_t k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------------------
+// FP64 SIMT path (xk_fp64.cu)
+// ---------------------------------------------------------------------------
+
+// C[M x N] = alpha * op(A) op(B) (o H), row-major.  op(A)[m,k] is
+// A[k*lda + m] when transA else A[m*lda + k]; op(B)[k,n] is B[n*ldb + k] when
+// transB else B[k*ldb + n].  H (nullable, ldh) multiplies the result
+// element-wise (the Hadamard epilogue).  ksplit > 1 splits K: partial sums
+// go to `work` (ksplit * M * N doubles) and are summed in split order, so
+// the result does not depend on scheduling.
+struct DGemm {
+  int M, N, K;
+  const double* A; long lda; bool transA;
+  const double* B; long ldb; bool transB;
+  double* C; long ldc;
+  double alpha;
+  const double* H; long ldh;
+  int ksplit;
+  double* work;
+};
+cudaError_t dgemm(const DGemm& g, cudaStream_t s);
+// Split count dgemm picks when DGemm::ksplit == 0 (work needs ksplit*M*N).
+int dgemm_ksplit(int M, int N, int K);
+
+// out[r, c] = in[idx[r] * ld_in + c] for r < rows, c < cols (row gather).
+cudaError_t gather_rows_f64(const double* in, long ld_in, const int32_t* idx, int rows, int cols,
+                            double* out, long ld_out, cudaStream_t s);
+
+// K[mu, i] = dV * (L1[i, mu] + L2[i, mu] - L3[i, mu]); L* are n x N.
+cudaError_t assemble_k_f64(const double* L1, const double* L2, const double* L3, int n, int N,
+                           double dV, double* K, cudaStream_t s);
+
+// *out = -sum_j a[j] * b[j] over `len` doubles, fixed summation order.
+// `work` holds at least reduce_work_elems() doubles.
+cudaError_t neg_dot_f64(const double* a, const double* b, long len, double* work, double* out,
+                        cudaStream_t s);
+size_t reduce_work_elems();
+
+// A <- (A + A^T) / 2 for an n x n matrix.
+cudaError_t symmetrize_f64(double* A, int n, cudaStream_t s);
+
+// In-place Cholesky A = L L^T (lower, n x n, one block).  *status = 0 on
+// success, k + 1 if the k-th pivot is not positive.
+cudaError_t cholesky_f64(double* A, int n, int* status, cudaStream_t s);
+
+// X <- B L^{-T} for L lower n x n and B rows x n (row-major): solves
+// X L^T = B row by row.
+cudaError_t trsm_right_lt_f64(const double* L, int n, const double* B, int rows, double* X,
+                              cudaStream_t s);
+
+// Cyclic Jacobi eigendecomposition of the symmetric n x n matrix A (one
+// block): on return A holds the eigenvalues on its diagonal and U the
+// eigenvectors as columns.  Runs at most max_sweeps sweeps; *sweeps gets the
+// number used.
+cudaError_t jacobi_eig_f64(double* A, double* U, int n, int max_sweeps, int* sweeps,
+                           cudaStream_t s);
+
+// X[r, k] = B[r, k] * f(lambda_k) with f = |lambda|^{-1/2} when
+// |lambda| > cut * max|lambda| else 0; sign[k] = sign(lambda) or 0.
+cudaError_t scale_eigcols_f64(const double* Adiag_src, int n, const double* B, int rows, double cut,
+                              double* X, double* sign, cudaStream_t s);
+
+}  // namespace xk

@@ -1,0 +1,40 @@
+// Mixed-precision (split-BF16x3 on tcgen05 tensor cores) path of the
+// exchange build: tables held in FP32 / BF16 pairs, FP32 accumulation in
+// tensor memory, FP64 cross-tile sums, FP64 K assembly and E_x.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace xk {
+
+struct MixedState;
+
+// Optional callback marking the start (begin = 1) and end (begin = 0) of a
+// build step (the XK_STEP_* numbering of xk.h) on the build's stream.
+struct StepHook {
+  void (*fn)(void* ctx, int step, int begin);
+  void* ctx;
+  void operator()(int step, int begin) const {
+    if (fn) fn(ctx, step, begin);
+  }
+};
+
+// Device bytes of the mixed-precision tables and scratch.
+size_t mixed_footprint(int64_t Ng, int N, int n, int Naux);
+
+// Convert and upload the per-geometry tables (host FP64 inputs).
+cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
+                         const int32_t* idx, const double* V, const double* W, double dV,
+                         cudaStream_t s, MixedState** out);
+void mixed_destroy(MixedState* m);
+
+// Enqueue one build: C_dev (N x n FP64) -> K_dev (N x n FP64), Ex_dev.
+cudaError_t mixed_enqueue(MixedState* m, const double* C_dev, double* K_dev, double* Ex_dev,
+                          cudaStream_t s, const StepHook& hook);
+
+// A-priori bound on |E_x(mixed) - E_x(FP64)| reported with each result.
+double mixed_error_bound(const MixedState* m);
+
+}  // namespace xk

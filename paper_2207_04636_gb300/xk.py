@@ -1,0 +1,176 @@
+"""Python binding of libxk (ctypes): argument marshalling only.
+
+Every step of the exchange build runs in the CUDA kernels of libxk.so; this
+module checks shapes and dtypes, passes pointers and turns return codes into
+exceptions.  The library must have been built (paper_2207_04636_gb300.build);
+importing this module without it raises at once rather than falling back to
+anything else.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+XK_OK, XK_PENDING = 0, 1
+XK_EINVAL, XK_ENOMEM, XK_ETIMEDOUT, XK_ECUDA, XK_EBUSY = -1, -2, -3, -4, -5
+XK_FP64, XK_TF32, XK_BF16X3 = 0, 1, 2
+MODES = {"fp64": XK_FP64, "bf16x3": XK_BF16X3}
+STEPS = ("orbitals", "pair", "m2", "m1", "line1", "line2", "line3", "assemble")
+_NAMES = {XK_EINVAL: "XK_EINVAL", XK_ENOMEM: "XK_ENOMEM", XK_ETIMEDOUT: "XK_ETIMEDOUT",
+          XK_ECUDA: "XK_ECUDA", XK_EBUSY: "XK_EBUSY"}
+
+
+class XKError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libxk.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise ImportError(f"libxk.so is missing ({_build.LIB}); build it with "
+                              "paper_2207_04636_gb300.build.build_library()")
+        L = ctypes.CDLL(_build.LIB)
+        c_d, c_i64, c_i32, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
+        L.xk_footprint.argtypes = [c_i64, c_i32, c_i32, c_i32, c_int, ctypes.POINTER(ctypes.c_size_t)]
+        L.xk_setup.argtypes = [c_i64, c_i32, c_i32, c_i32, c_d, c_d, c_d, c_d, ctypes.c_double,
+                               c_int, ctypes.POINTER(ctypes.c_void_p)]
+        L.xk_build.argtypes = [c_d, c_d, c_d, c_d]
+        L.xk_build_device.argtypes = [c_d, c_d, c_d, c_d, c_d]
+        L.xk_ace.argtypes = [c_d, c_d, c_d, c_d, ctypes.POINTER(c_int)]
+        L.xk_submit.argtypes = [c_d, c_d, ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)]
+        L.xk_poll.argtypes = [ctypes.c_uint64, c_d, c_d, c_d]
+        L.xk_release.argtypes = [c_d]
+        L.xk_timing_enable.argtypes = [c_d, c_int]
+        L.xk_timing_read.argtypes = [c_d, c_int, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_uint64)]
+        L.xk_last_error.restype = ctypes.c_char_p
+        L.xk_kernel_launches.restype = ctypes.c_uint64
+        for f in ("xk_footprint", "xk_setup", "xk_build", "xk_build_device", "xk_ace",
+                  "xk_submit", "xk_poll", "xk_release", "xk_timing_enable", "xk_timing_read"):
+            getattr(L, f).restype = c_int
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().xk_last_error().decode()
+
+
+def kernel_launches() -> int:
+    return int(lib().xk_kernel_launches())
+
+
+def _check(rc):
+    if rc < 0:
+        raise XKError(rc, last_error())
+    return rc
+
+
+def _f64(a, shape, name):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != shape:
+        raise ValueError(f"{name}: expected shape {shape}, got {a.shape}")
+    return a
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def footprint(Ng, N, n, Naux, mode="fp64") -> int:
+    out = ctypes.c_size_t()
+    _check(lib().xk_footprint(Ng, N, n, Naux, MODES[mode], ctypes.byref(out)))
+    return int(out.value)
+
+
+class Handle:
+    """Per-geometry device tables plus build scratch (xk_setup / xk_release)."""
+
+    def __init__(self, phi, idx, V, W, dV, n, mode="fp64"):
+        phi = np.asarray(phi)
+        Ng, N = phi.shape
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        Naux = idx.shape[0]
+        self.Ng, self.N, self.n, self.Naux, self.mode = Ng, N, int(n), Naux, mode
+        phi = _f64(phi, (Ng, N), "phi")
+        V = _f64(V, (Naux, Ng), "V")
+        W = _f64(W, (Naux, Naux), "W")
+        h = ctypes.c_void_p()
+        _check(lib().xk_setup(Ng, N, self.n, Naux, _ptr(phi), _ptr(idx), _ptr(V), _ptr(W),
+                              float(dV), MODES[mode], ctypes.byref(h)))
+        self._h = h
+
+    def build(self, C):
+        """Blocking build from host C (N x n): returns (K_{mu i}, E_x)."""
+        C = _f64(C, (self.N, self.n), "C")
+        K = np.empty((self.N, self.n))
+        Ex = np.empty(1)
+        _check(lib().xk_build(self._h, _ptr(C), _ptr(K), _ptr(Ex)))
+        return K, float(Ex[0])
+
+    def build_device(self, C_dev, K_dev, Ex_dev, stream=0):
+        """Enqueue a build on device buffers (integers: device addresses,
+        e.g. torch tensor .data_ptr()) on the given cudaStream_t handle."""
+        _check(lib().xk_build_device(self._h, ctypes.c_void_p(C_dev), ctypes.c_void_p(K_dev),
+                                     ctypes.c_void_p(Ex_dev), ctypes.c_void_p(stream)))
+
+    def ace(self):
+        """(K_ij, xi, sign, branch) of the last build: branch 'cholesky' or 'eigen'."""
+        Kij = np.empty((self.n, self.n))
+        xi = np.empty((self.N, self.n))
+        sg = np.empty(self.n)
+        br = ctypes.c_int()
+        _check(lib().xk_ace(self._h, _ptr(Kij), _ptr(xi), _ptr(sg), ctypes.byref(br)))
+        return Kij, xi, sg, ("cholesky" if br.value == 0 else "eigen")
+
+    def submit(self, C, deadline_ms=0.0) -> int:
+        C = _f64(C, (self.N, self.n), "C")
+        t = ctypes.c_uint64()
+        _check(lib().xk_submit(self._h, _ptr(C), float(deadline_ms), ctypes.byref(t)))
+        return int(t.value)
+
+    def timing(self, enable=True):
+        """Turn per-step CUDA-event timing on (clearing it) or off."""
+        _check(lib().xk_timing_enable(self._h, 1 if enable else 0))
+
+    def step_times(self):
+        """{step name: (total device ms, builds)} since timing was enabled."""
+        out = {}
+        for i, name in enumerate(STEPS):
+            ms = ctypes.c_double()
+            nb = ctypes.c_uint64()
+            _check(lib().xk_timing_read(self._h, i, ctypes.byref(ms), ctypes.byref(nb)))
+            out[name] = (ms.value, int(nb.value))
+        return out
+
+    def release(self):
+        if getattr(self, "_h", None):
+            lib().xk_release(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+def poll(ticket, N, n):
+    """(status, K, E_x, err_bound); status XK_PENDING while running."""
+    K = np.empty((N, n))
+    Ex = np.empty(1)
+    eb = np.empty(1)
+    rc = lib().xk_poll(ctypes.c_uint64(ticket), _ptr(K), _ptr(Ex), _ptr(eb))
+    if rc == XK_PENDING:
+        return rc, None, None, None
+    _check(rc)
+    return rc, K, float(Ex[0]), float(eb[0])
