@@ -305,7 +305,9 @@ int xk_footprint(int64_t Ng, int32_t N, int32_t n, int32_t Naux, int mode, size_
     return XK_OK;
   }
   if (mode == XK_BF16X3) {
-    *bytes = xk::mixed_footprint(Ng, N, n, Naux) + (size_t)N * n * 8 * 2 + 4096;
+    *bytes = xk::mixed_footprint(Ng, N, n, Naux) + (size_t)N * n * 8 * 2 +
+             (size_t)max_work(Ng, N, n, Naux) * 8 + 4 * (size_t)n * n * 8 + 2 * (size_t)N * n * 8 +
+             65536;
     return XK_OK;
   }
   return fail(XK_EINVAL, "xk_footprint: unknown mode");
@@ -464,6 +466,12 @@ int xk_build(xk_handle* h, const double* C, double* K_out, double* Ex) {
   XK_CUDA(cudaMemcpyAsync(Ex, h->Ex, 8, cudaMemcpyDeviceToHost, h->stream));
   XK_CUDA(cudaStreamSynchronize(h->stream));
   h->has_build = true;
+  if (h->mixed) {
+    const int st = xk::mixed_take_status(h->mixed);
+    if (st != 0)
+      return fail(XK_ETIMEDOUT, "xk_build: a bounded wait inside a kernel gave up (code " +
+                                    std::to_string(st) + ")");
+  }
   return XK_OK;
 }
 
@@ -569,6 +577,15 @@ int xk_poll(xk_ticket t, double* K_out, double* Ex, double* err_bound) {
     return cuda_fail(q, "xk_poll");
   }
   const size_t kb = (size_t)h->N * h->n * 8;
+  if (h->mixed) {
+    const int st = xk::mixed_take_status(h->mixed);
+    if (st != 0) {
+      s.state = 0;
+      consume();
+      return fail(XK_ETIMEDOUT, "xk_poll: a bounded wait inside a kernel gave up (code " +
+                                    std::to_string(st) + ")");
+    }
+  }
   std::memcpy(K_out, s.K, kb);
   *Ex = *s.Ex;
   if (err_bound) *err_bound = h->mode == XK_FP64 ? 0.0 : xk::mixed_error_bound(h->mixed);

@@ -34,6 +34,10 @@ void mixed_destroy(MixedState* m);
 cudaError_t mixed_enqueue(MixedState* m, const double* C_dev, double* K_dev, double* Ex_dev,
                           cudaStream_t s, const StepHook& hook);
 
+// Error code a kernel of the last builds recorded (0 = none; nonzero when a
+// bounded wait inside a kernel gave up), read synchronously and cleared.
+int mixed_take_status(MixedState* m);
+
 // A-priori bound on |E_x(mixed) - E_x(FP64)| reported with each result.
 double mixed_error_bound(const MixedState* m);
 
