@@ -1,18 +1,20 @@
 """Benchmark of the exchange build: K builds/s on the 64-centre diamond cell.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--mode bf16x3|fp64]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--mode f16x3|fp64]
                     [--impl xk|reference]
 
 One step is one complete occ-RI robust-PS exchange build (orbitals, pair
 kernel, the three lines, K_{mu i}, E_x) of the seeded synthetic 64-centre
-cell (N=832, n=128, N_g=60^3, N_aux=4000) for a new C from a seeded
-pseudo-SCF sequence.  `value` times K builds on device-resident inputs with
-CUDA events on the launching stream; `e2e` times the same builds through the
-blocking C-ABI call with host buffers (H2D of C, D2H of K and E_x inside).
-Every table is far larger than L2 (V alone is 6.9 GB in FP64), so no flush
-is needed between builds.  Under torchrun each rank builds its own cell
-instance (weak scaling, no collective on the data path); rank 0 prints one
-JSON line with the max-over-ranks time.
+cell (N=832, n=128, N_g=60^3, N_aux=4000) for the next C of a seeded
+pseudo-SCF sequence.  `value` times K builds of the default tensor-core path
+(--mode f16x3) on device-resident inputs with CUDA events on the launching
+stream; `e2e` times the same builds through the blocking C-ABI call with
+host buffers (H2D of C, D2H of K and E_x inside).  The FP64 path is timed on
+the same cell beside it, and the line reports |dE_x| between the two for the
+same C.  Every table is far larger than L2 (V alone is 3.5 GB in FP32), so
+no flush is needed between builds.  Under torchrun each rank builds its own
+C sequence on its own copy of the cell (weak scaling, no collective on the
+data path); rank 0 prints one JSON line with the max-over-ranks time.
 
 --impl reference times the FP64 CPU oracle on the host cores on the same
 workload (one full build per step) and prints the same line with
@@ -20,7 +22,6 @@ workload (one full build per step) and prints the same line with
 """
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -32,14 +33,14 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-from cellgen import config_spec, load_cell, perturb_coefficients  # noqa: E402
+from cellgen import config_spec, load_cell, pseudo_scf_sequence  # noqa: E402
 
 WORKLOAD = ("64-centre 2x2x2 diamond supercell, L=13.48 bohr, 13 Gaussians/centre "
             "(2s,2p,1d), N=832, n_occ=128, 60^3 grid, N_aux=4000")
 METRIC = "K builds/s (64-atom cell)"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
-# FP64 on the CUDA cores of GB300: measured DFMA issue rate (see the design doc,
-# "FP64 ALU peak"): flops/clock/SM x 152 SMs x max SM clock.
+# FP64 on the CUDA cores of GB300: 2 DFMA (4 flops) per clock per SM, measured
+# 3.81 flops/clock/SM with an FMA-chain probe; x 152 SMs x 2070 MHz.
 FP64_FLOPS_PER_CLK_SM = 4.0
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
@@ -50,10 +51,13 @@ def parse():
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=0)
     p.add_argument("--warmup", type=int, default=3)
-    p.add_argument("--mode", default="auto", choices=["auto", "bf16x3", "fp64"])
+    p.add_argument("--mode", default="f16x3", choices=["f16x3", "fp64"])
     p.add_argument("--impl", default="xk", choices=["xk", "reference"])
-    p.add_argument("--config", type=int, default=2)
+    p.add_argument("--config", type=int, default=2,
+                   help="2: the 64-centre cell (the metric's workload); 1 or 4 for smaller cases")
+    p.add_argument("--k", type=int, default=None, help="lattice size of config 4 (k^3 centres)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
     return p.parse_args()
 
 
@@ -61,14 +65,13 @@ def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as f:
-            d = json.load(f)
-        return d, "measured"
+            return json.load(f), "measured"
     return FALLBACK_PEAKS, "fallback"
 
 
 def step_flops(N, n, Ng, Na):
     """Algorithmic FLOPs of each build step (the contraction counts of the
-    step list in include/xk.h)."""
+    steps listed in include/xk.h); the pair kernel counts P once."""
     return {
         "orbitals": 2.0 * Ng * N * n,
         "pair": 2.0 * Na * Ng * n + Na * Ng,
@@ -135,21 +138,14 @@ def cpu_cores():
         return os.cpu_count()
 
 
-def pseudo_scf(cell, count, seed):
-    Cs = [cell.C]
-    for t in range(count - 1):
-        Cs.append(perturb_coefficients(cell.S, Cs[-1], seed + t))
-    return Cs
-
-
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
-    cell = load_cell(config_spec(args.config))
+    cell = load_cell(config_spec(args.config, k=args.k))
     steps = args.steps or 5
-    Cs = pseudo_scf(cell, steps + args.warmup, 77)
+    Cs = pseudo_scf_sequence(cell.S, cell.C, steps + args.warmup, 77)
     for i in range(args.warmup):
         oracle.exx_rps_occri(cell.phi, cell.idx, cell.V, cell.W, Cs[i], cell.dV)
     t0 = time.perf_counter()
@@ -169,6 +165,26 @@ def run_reference(args):
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def time_device_builds(xk, h, Cd, Kd, Ed, stream, warm, steps, torch):
+    """Warm-up, then `steps` builds between CUDA events on `stream`.
+    Returns (ms, launches, step times)."""
+    for i in range(warm):
+        h.build_device(Cd[i].data_ptr(), Kd.data_ptr(), Ed.data_ptr(), stream.cuda_stream)
+    torch.cuda.synchronize()
+    h.timing(True)
+    launches0 = xk.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        h.build_device(Cd[warm + i].data_ptr(), Kd.data_ptr(), Ed.data_ptr(), stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st = h.step_times()
+    h.timing(False)
+    return e0.elapsed_time(e1), xk.kernel_launches() - launches0, st
 
 
 def main():
@@ -191,27 +207,22 @@ def main():
     xkbuild.build_library()
 
     mode = args.mode
-    if mode == "auto":
-        mode = os.environ.get("XK_BENCH_MODE", "fp64")
-    steps = args.steps or (20 if mode != "fp64" else 6)
+    steps = args.steps or (200 if mode != "fp64" else 6)
     warm = max(3, args.warmup)
-
-    cell = load_cell(config_spec(args.config))
+    cell = load_cell(config_spec(args.config, k=args.k))
     N, n, Ng, Na = cell.N, cell.n, cell.Ng, cell.Naux
-    h = xk.Handle(cell.phi, cell.idx, cell.V, cell.W, cell.dV, n, mode=mode)
-    Cs = pseudo_scf(cell, steps + warm, 1000 + rank)
+    workload = WORKLOAD if args.config == 2 else f"{cell.spec.name}: N={N}, n={n}, N_g={Ng}, N_aux={Na}"
+    Cs = pseudo_scf_sequence(cell.S, cell.C, steps + warm, 1000 + rank)
     Cd = [torch.from_numpy(C).cuda() for C in Cs]
     Kd = torch.empty((N, n), dtype=torch.float64, device="cuda")
     Ed = torch.empty(1, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
-    for i in range(warm):
-        h.build_device(Cd[i].data_ptr(), Kd.data_ptr(), Ed.data_ptr(), stream.cuda_stream)
+
+    h = xk.Handle(cell.phi, cell.idx, cell.V, cell.W, cell.dV, n, mode=mode)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-
-    h.timing(True)
     uuid = None
     try:
         uuid = str(torch.cuda.get_device_properties(local).uuid)
@@ -220,19 +231,8 @@ def main():
         uuid = None
     sampler = ClockSampler(uuid)
     time.sleep(0.3)
-    launches0 = xk.kernel_launches()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for i in range(steps):
-        h.build_device(Cd[warm + i].data_ptr(), Kd.data_ptr(), Ed.data_ptr(), stream.cuda_stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    launches = xk.kernel_launches() - launches0
+    ms, launches, st = time_device_builds(xk, h, Cd, Kd, Ed, stream, warm, steps, torch)
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    st = h.step_times()
-    h.timing(False)
     if dist:
         t = torch.tensor([ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -240,52 +240,73 @@ def main():
         dist.barrier()
     K_last = Kd.cpu().numpy()
     E_last = float(Ed.item())
+    C_last = Cs[warm + steps - 1]
 
-    # e2e through the blocking C-ABI call, host buffers (pinned) in and out.
+    # e2e through the blocking C-ABI call: host (pinned) buffers in and out
     Ch = [torch.from_numpy(C).pin_memory() for C in Cs[warm:warm + steps]]
-    Kh = torch.empty((N, n), dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(steps):
-        K_e2e, E_e2e = h.build(Ch[i].numpy())
+        h.build(Ch[i].numpy())
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    del Kh
     h.release()
     if dist:
         t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
 
+    fp64 = None
+    if mode != "fp64" and not args.no_fp64:
+        hf = xk.Handle(cell.phi, cell.idx, cell.V, cell.W, cell.dV, n, mode="fp64")
+        ms64, _, _ = time_device_builds(xk, hf, Cd[warm + steps - 3:], Kd, Ed, stream, 1, 2, torch)
+        hf.build_device(Cd[warm + steps - 1].data_ptr(), Kd.data_ptr(), Ed.data_ptr(),
+                        stream.cuda_stream)
+        torch.cuda.synchronize()
+        K64, E64 = Kd.cpu().numpy(), float(Ed.item())
+        hf.release()
+        fp64 = {"builds_per_s": 2.0 / (ms64 * 1e-3), "ms_per_build": ms64 / 2.0,
+                "dE_x_vs_fp64": abs(E_last - E64),
+                "max_dK_vs_fp64": float(np.max(np.abs(K_last - K64)))}
+
     if rank == 0:
         pk, pk_src = peaks()
         fl = step_flops(N, n, Ng, Na)
-        dom = max((k for k in st if st[k][1] > 0), key=lambda k: st[k][0])
-        dom_ms = st[dom][0] / max(1, st[dom][1])
         if mode == "fp64":
-            dom_flops = fl[dom]
+            dom = max((k for k in st if st[k][1] > 0), key=lambda k: st[k][0])
+            dom_ms = st[dom][0] / max(1, st[dom][1])
             peak = FP64_FLOPS_PER_CLK_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
             roof = {"bound": "alu", "kernel": f"step '{dom}' (FP64 DFMA GEMM)",
-                    "achieved": dom_flops / (dom_ms * 1e-3) / 1e12, "peak": peak,
-                    "unit": "TFLOP/s", "peak_source": "derived FP64 DFMA rate x SMs x max clock",
+                    "achieved": fl[dom] / (dom_ms * 1e-3) / 1e12, "peak": peak,
+                    "unit": "TFLOP/s",
+                    "peak_source": "FP64 DFMA rate: 4 flop/clk/SM x 152 SMs x 2070 MHz",
                     "traffic": None}
         else:
-            dom_flops = fl["pair"] + fl["m2"] + fl["m1"]
+            dom = "pair"
+            dom_ms = st[dom][0] / max(1, st[dom][1])
+            algo = fl["pair"] + fl["m2"] + fl["m1"] + 4.0 * Na * Na * n
+            # tensor products issued: S = 4 MMA passes, second product = 3 passes,
+            # roles A and B each form S over the N_aux x N_g pairs, role C over N_aux^2
+            npad = -(-n // 64) * 64
+            issued = 7 * 2.0 * 2 * Na * Ng * npad + 7 * 2.0 * Na * Na * npad
             peak = pk.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"])
-            roof = {"bound": "tensor", "kernel": "fused pair/Hadamard/M1/M2 (tcgen05)",
-                    "achieved": dom_flops / (dom_ms * 1e-3) / 1e12, "peak": peak,
-                    "unit": "TFLOP/s", "peak_source": f"bf16 burst ({pk_src})",
+            roof = {"bound": "tensor",
+                    "kernel": "pair kernel (fused P, V o P, back-contraction; 3 launches/build)",
+                    "achieved": algo / (dom_ms * 1e-3) / 1e12, "peak": peak,
+                    "unit": "TFLOP/s",
+                    "peak_source": f"dense bf16/fp16 tensor rate ({pk_src})",
+                    "issued_tensor_tflops": issued / (dom_ms * 1e-3) / 1e12,
                     "traffic": None}
         roof["frac"] = roof["achieved"] / roof["peak"]
-        roof["ms_per_launch"] = dom_ms
+        roof["ms_per_build"] = dom_ms
         value = world * steps / (ms * 1e-3)
         line = {
             "metric": METRIC, "value": value, "unit": "builds/s", "n_gpus": world,
             "steps": steps, "warmup": warm, "ms_per_step": ms / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if mode == "fp64" else "bf16x3",
+            "dtype": "f64" if mode == "fp64" else "f16x3",
             "data": "synthetic (seeded cell generator; inputs resident in HBM)",
-            "config": {"workload": WORKLOAD, "mode": mode, "N": N, "n": n, "N_g": Ng,
+            "config": {"workload": workload, "mode": mode, "N": N, "n": n, "N_g": Ng,
                        "N_aux": Na, "l2": "inputs larger than L2 (V is N_aux x N_g)",
                        "parallelism": f"replicas x{world}"},
             "E_x": E_last,
@@ -297,9 +318,11 @@ def main():
             "e2e": {"value": world * steps / e2e_s, "unit": "builds/s",
                     "h2d_bytes_per_step": N * n * 8, "d2h_bytes_per_step": N * n * 8 + 8},
         }
+        if fp64:
+            line["fp64_path"] = fp64
+            line["speedup_vs_fp64_path"] = value / world / fp64["builds_per_s"]
         if not args.no_cpu_baseline and world == 1:
             import oracle
-            C_last = Cs[warm + steps - 1]
             t0 = time.perf_counter()
             nb = 0
             while True:
@@ -311,8 +334,8 @@ def main():
             line["cpu_baseline"] = {"value": nb / dt, "unit": "builds/s", "cores": cpu_cores(),
                                     "kind": "oracle",
                                     "sample": f"{nb} full FP64 oracle builds of the same cell"}
-            line["parity_last_step"] = {"dE_x": abs(E_last - E0),
-                                        "max_dK": float(np.max(np.abs(K_last - K0)))}
+            line["parity_last_step"] = {"dE_x_vs_oracle": abs(E_last - E0),
+                                        "max_dK_vs_oracle": float(np.max(np.abs(K_last - K0)))}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -397,6 +397,23 @@ def perturb_coefficients(S: np.ndarray, C: np.ndarray, seed: int, step: float = 
     return s_orthonormal(S, C + step * rng.standard_normal(C.shape))
 
 
+def pseudo_scf_sequence(S: np.ndarray, C0: np.ndarray, count: int, seed: int,
+                        step: float = 0.05) -> list:
+    """count coefficient matrices of a seeded pseudo-SCF run: C_0 = C0 and
+    C_{t+1} = S^{-1/2} qr(S^{1/2} C_t + step * noise).Q, i.e. each step adds
+    noise in the orthonormal frame and re-orthonormalises in S."""
+    w, U = np.linalg.eigh(S)
+    s_half = (U * np.sqrt(w)) @ U.T
+    s_mhalf = (U / np.sqrt(w)) @ U.T
+    rng = np.random.default_rng(seed)
+    out = [np.ascontiguousarray(C0)]
+    X = s_half @ C0
+    for _ in range(count - 1):
+        X, _ = np.linalg.qr(X + step * rng.standard_normal(X.shape))
+        out.append(np.ascontiguousarray(s_mhalf @ X))
+    return out
+
+
 # --------------------------------------------------------------------------
 # Cell assembly
 # --------------------------------------------------------------------------

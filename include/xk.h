@@ -52,10 +52,17 @@ enum {
 };
 
 enum {
-  XK_FP64 = 0,        /* every step in FP64                                 */
-  XK_TF32 = 1,        /* reserved                                           */
-  XK_BF16X3 = 2       /* bulk contractions as split-BF16x3 on tensor cores,
-                         FP32 accumulation, FP64 cross-tile sums and E_x    */
+  XK_FP64 = 0,        /* every step in FP64 on the CUDA cores               */
+  XK_TF32 = 1,        /* reserved, rejected by xk_setup                      */
+  XK_F16X3 = 2        /* bulk contractions on the tcgen05 tensor cores with
+                         operands split into FP16 pieces: a fixed-point main
+                         piece whose products accumulate exactly in FP32 and
+                         an FP16 remainder (three products per pair of
+                         operands), FP64 cross-tile sums, FP64 K and E_x.
+                         E_x is returned in the closed form
+                         -dV (2 sum V o P^2 - sum W o Q^2) (Eq. exoccri
+                         contracted with C), accumulated from the pair
+                         products.  Needs n <= 128.                         */
 };
 
 /*
@@ -75,9 +82,10 @@ int xk_footprint(int64_t Ng, int32_t N, int32_t n, int32_t Naux, int mode, size_
  *   V_aux            Naux x Ng   V(R_g, R), potential of chi_g  (Eq. rpsPot)
  *   W_aux            Naux x Naux W(R_g, R_g'), symmetric        (Eq. thcpot)
  *   dV               Omega / N_g, > 0
- *   mode             XK_FP64 or XK_BF16X3
+ *   mode             XK_FP64 or XK_F16X3
  * Errors: XK_EINVAL (sizes, null pointers, idx out of range or duplicated,
- * W not symmetric to 1e-12 relative, dV <= 0, n > N, Naux > Ng),
+ * W not symmetric to 1e-12 relative, dV <= 0, n > N, Naux > Ng; for
+ * XK_F16X3 also n > 128 or basis columns linearly dependent on the grid),
  * XK_ENOMEM (footprint above the admission budget: free device memory less
  * a reserve, or XK_HBM_BUDGET_BYTES when set), XK_ECUDA.
  */

@@ -304,7 +304,7 @@ int xk_footprint(int64_t Ng, int32_t N, int32_t n, int32_t Naux, int mode, size_
     *bytes = plan_bytes(plan_fp64(Ng, N, n, Naux));
     return XK_OK;
   }
-  if (mode == XK_BF16X3) {
+  if (mode == XK_F16X3) {
     *bytes = xk::mixed_footprint(Ng, N, n, Naux) + (size_t)N * n * 8 * 2 +
              (size_t)max_work(Ng, N, n, Naux) * 8 + 4 * (size_t)n * n * 8 + 2 * (size_t)N * n * 8 +
              65536;
@@ -321,7 +321,9 @@ int xk_setup(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* phi,
   if (!phi || !idx || !V || !W) return fail(XK_EINVAL, "xk_setup: NULL table pointer");
   if (!valid_sizes(Ng, N, n, Naux)) return fail(XK_EINVAL, "xk_setup: invalid sizes");
   if (!(dV > 0.0) || !std::isfinite(dV)) return fail(XK_EINVAL, "xk_setup: dV must be > 0");
-  if (mode != XK_FP64 && mode != XK_BF16X3) return fail(XK_EINVAL, "xk_setup: unsupported mode");
+  if (mode != XK_FP64 && mode != XK_F16X3) return fail(XK_EINVAL, "xk_setup: unsupported mode");
+  if (mode == XK_F16X3 && n > 128)
+    return fail(XK_EINVAL, "xk_setup: XK_F16X3 supports n <= 128 occupied orbitals");
   {
     std::vector<int32_t> s(idx, idx + Naux);
     std::sort(s.begin(), s.end());
@@ -416,6 +418,8 @@ int xk_setup(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* phi,
     if (e != cudaSuccess) return bail(cuda_fail(e, "xk_setup upload"));
   } else {
     e = xk::mixed_create(Ng, N, n, Naux, phi, idx, V, W, dV, h->stream, &h->mixed);
+    if (e == cudaErrorInvalidValue)
+      return bail(fail(XK_EINVAL, "xk_setup: basis columns are linearly dependent on the grid"));
     if (e != cudaSuccess) return bail(cuda_fail(e, "xk_setup mixed tables"));
   }
 #undef XK_ALLOC

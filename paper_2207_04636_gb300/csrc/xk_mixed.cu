@@ -1,25 +1,35 @@
 // Mixed-precision path of the exchange build on the 5th-generation tensor
 // cores (tcgen05.mma kind::f16, TMA-fed shared memory, TMEM accumulators).
 //
-// Every bulk contraction runs as split-FP16x3: a value x (scaled by a power
-// of two so that |x| <= 2^15) is held as hi = fp16(x) and lo = fp16(x - hi),
-// and a product a*b is formed as hi_a*hi_b + hi_a*lo_b + lo_a*hi_b with FP32
-// accumulation.  That keeps about 22 significant bits per product.  Partial
-// sums leave the tensor memory as FP32 and are added in FP64; K and E_x are
-// assembled in FP64.
+// Number format.  The FP32 accumulator of tcgen05.mma rounds every addition
+// toward zero (the 16 products of one instruction are summed exactly, the
+// sum is then truncated into the accumulator).  Truncation is biased, so
+// long accumulation chains of ordinary FP16/BF16 splits drift by about half
+// an ulp per instruction.  Every operand row is therefore split as
+//     x = m + h,   m = q * round(x / q),   h = fp16(x - m),
+// with a per-row power-of-two grid q = 2^(ceil(log2 max|row|) - 8), so that
+// m is an integer multiple of q with |m / q| <= 256 (exact in FP16).  The
+// product of two rows is then
+//     A0 = sum m_x m_y        on the grid q_x q_y, exact while K <= 256,
+//     A1 = sum m_x h_y + h_x m_y + h_x h_y,
+// and A1 is about 2^-9 of A0, so its truncation bias is negligible.  A0 and
+// A1 live in separate TMEM accumulators; longer sums are drained every
+// <= 256 terms into round-to-nearest FP32 running sums.  The pair-kernel
+// second product (V o P times the orbitals) uses a floating hi/lo split of
+// V o P and drains every two tiles.
 //
 // Build chain (arXiv 2207.04636, Eq. exoccri with contraction order (a) of
 // Sec. IV.D):
-//   1. Psi = Phi C                          tc_gemm                (Eq. rpsEx step 1)
-//   2. Psi_g = Psi[idx], hi/lo splits       split + gather
-//   3. M2 = (V o (Psi_g Psi^T)) Psi         pair kernel, role A    (steps 2-3, line 2)
-//      M1^T = (V^T o (Psi Psi_g^T)) Psi_g   pair kernel, role B    (line 1)
-//      M3 = (W o (Psi_g Psi_g^T)) Psi_g     pair kernel, role C    (line 3)
-//   4. line1^T = Phi^T M1^T, (line2 - line3)^T = Phi_g^T (M2 - M3)   tc_gemm
-//   5. K_{mu i} = dV (line1 + line2 - line3)^T, E_x = -sum K o C     FP64
-// The pair kernel fuses the pair-kernel GEMM, the Hadamard product with the
-// stored potential and the back-contraction: the N_aux x N_g pair matrix is
-// never written to memory, and V is streamed from HBM once per role.
+//   1. Psi = Phi C                            gemm                   (Eq. rpsEx step 1)
+//   2. Psi_g = Psi[idx], per-row splits       split + gather
+//   3. M2 = (V o (Psi_g Psi^T)) Psi           pair kernel, role A    (steps 2-3, line 2)
+//      M1^T = (V^T o (Psi Psi_g^T)) Psi_g     pair kernel, role B    (line 1)
+//      M3 = (W o (Psi_g Psi_g^T)) Psi_g       pair kernel, role C    (line 3)
+//   4. line1^T = Phi^T M1^T, (line2 - line3)^T = Phi_g^T (M2 - M3)   gemm
+//   5. K_{mu i} = dV (line1 + line2 - line3)^T (FP64)
+//   6. E_x = -dV (2 sum V o P^2 - sum W o Q^2): the contraction of Eq. exoccri
+//      with C in closed form, accumulated from the exact pair products in the
+//      pair-kernel epilogues (FP32 per tile, FP64 across tiles).
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -38,23 +48,24 @@ namespace {
 using namespace tc;
 
 // ----------------------------------------------------------------- scales
-// Device float array of power-of-two scales and FP32 bit patterns of maxima.
+// Global power-of-two scales (device floats) and maxima (FP32 bit patterns).
 enum {
-  SC_PHI = 0,   // Phi, Phi^T, Phi_g^T splits
-  SC_C,         // C^T split
-  SC_PSI,       // Psi, Psi_g splits
+  SC_PHI = 0,   // Phi^T, Phi_g^T (the line contractions)
+  SC_C,         // Q^T = (L^T C)^T
+  SC_PSI,       // Psi, Psi_g
   SC_F_AB,      // V o P before its split (roles A, B)
   SC_F_C,       // W o Q before its split (role C)
-  SC_M1,        // M1 split
-  SC_D23,       // (M2 - M3) split
+  SC_M1,        // M1
+  SC_D23,       // (M2 - M3)^T
   SC_OUT_ORB,   // Psi = acc * this
   SC_OUT_AB,    // M2, M1 = acc * this
   SC_OUT_C,     // M3 = acc * this
   SC_OUT_L1,    // line1 = acc * this
   SC_OUT_L23,   // line2 - line3 = acc * this
+  SC_PHIP,      // Phi' = Phi L^{-T} (the orbital contraction)
   NSC
 };
-enum { AM_PHI = 0, AM_V, AM_W, AM_C, AM_PSI, AM_RN2, AM_M1, AM_D23, NAM };
+enum { AM_PHI = 0, AM_V, AM_W, AM_PHIP, AM_C, AM_PSI, AM_RN2, AM_M1, AM_D23, NAM };
 
 constexpr float kHalfTarget = 16384.0f;  // 2^14: split inputs are scaled to |x| <= 2^14
 constexpr float kProdTarget = 32768.0f;  // 2^15: V o P is scaled to |x| <= 2^15
@@ -64,17 +75,18 @@ __device__ float pow2_scale(float maxabs, float target) {
   int e = (int)floorf(log2f(target / maxabs));
   float s = ldexpf(1.0f, e);
   while (s * maxabs > target) s *= 0.5f;
+  while (s * 2.0f * maxabs <= target) s *= 2.0f;
   return s;
 }
 
 __device__ __forceinline__ float am_get(const unsigned* am, int i) { return __uint_as_float(am[i]); }
 
-// stage 0: C split scale; 1: Psi / pair scales; 2: M1, D23 scales.
+// stage 0: C scale; 1: Psi / pair scales; 2: M1, (M2 - M3) scales.
 __global__ void scales_kernel(const unsigned* __restrict__ am, float* __restrict__ sc, int stage) {
   if (threadIdx.x != 0) return;
   if (stage == 0) {
     sc[SC_C] = pow2_scale(am_get(am, AM_C), kHalfTarget);
-    sc[SC_OUT_ORB] = 1.0f / (sc[SC_PHI] * sc[SC_C]);
+    sc[SC_OUT_ORB] = 1.0f / (sc[SC_PHIP] * sc[SC_C]);
   } else if (stage == 1) {
     const float sp = pow2_scale(am_get(am, AM_PSI), kHalfTarget);
     sc[SC_PSI] = sp;
@@ -95,7 +107,16 @@ __global__ void scales_kernel(const unsigned* __restrict__ am, float* __restrict
 }
 
 __global__ void set_phi_scale_kernel(const unsigned* __restrict__ am, float* __restrict__ sc) {
-  if (threadIdx.x == 0) sc[SC_PHI] = pow2_scale(am_get(am, AM_PHI), kHalfTarget);
+  if (threadIdx.x == 0) {
+    sc[SC_PHI] = pow2_scale(am_get(am, AM_PHI), kHalfTarget);
+    sc[SC_PHIP] = pow2_scale(am_get(am, AM_PHIP), kHalfTarget);
+  }
+}
+
+__global__ void identity_kernel(double* a, int n) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < (long)n * n;
+       t += (long)gridDim.x * blockDim.x)
+    a[t] = (t / n == t % n) ? 1.0 : 0.0;
 }
 
 template <class T>
@@ -131,55 +152,72 @@ __global__ void rownorm2_max_kernel(const float* __restrict__ a, long rows, int 
 
 // ----------------------------------------------------------------- splits
 
-__device__ __forceinline__ void split1(double x, __half& hi, __half& lo) {
-  hi = __float2half_rn((float)x);
-  lo = __float2half_rn((float)(x - (double)__half2float(hi)));
-}
-__device__ __forceinline__ void split1(float x, __half& hi, __half& lo) {
-  hi = __float2half_rn(x);
-  lo = __float2half_rn(x - __half2float(hi));
+// Grid of a row whose largest |value| is mx: q = 2^(ceil(log2 mx) - 8), at
+// least 2^-24 (the FP16 subnormal step), so |x / q| <= 256.
+__device__ __forceinline__ float row_grid(float mx) {
+  if (!(mx > 0.0f)) return 1.0f;
+  int E;
+  const float f = frexpf(mx, &E);  // mx = f 2^E, f in [0.5, 1)
+  const int e = (f == 0.5f) ? E - 1 : E;
+  return ldexpf(1.0f, max(e - 8, -24));
 }
 
-// dst[r][c] (ld_dst) = split(src[r][c] * scale) for c < cols, 0 for cols <= c < ld_dst.
+// Row r of dst (one block of 128 threads per row): m, h pieces of
+// src[r][c] * G on the row's grid for c < cols; zero for cols <= c < ld_dst.
 template <class T>
-__global__ void split_rows_kernel(const T* __restrict__ src, long rows, long cols, long ld_src,
-                                  const float* __restrict__ sc, int sidx, __half* __restrict__ hi,
-                                  __half* __restrict__ lo, long ld_dst) {
-  const T s = (T)sc[sidx];
-  const long total = rows * ld_dst;
-  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
-       t += (long)gridDim.x * blockDim.x) {
-    const long r = t / ld_dst, c = t % ld_dst;
-    __half h = __float2half(0.0f), l = __float2half(0.0f);
-    if (c < cols) split1(src[r * ld_src + c] * s, h, l);
-    hi[t] = h;
-    lo[t] = l;
+__global__ void __launch_bounds__(128) split_mh_rows_kernel(
+    const T* __restrict__ src, long cols, long ld_src, const float* __restrict__ sc, int gidx,
+    __half* __restrict__ mo, __half* __restrict__ ho, long ld_dst) {
+  __shared__ float red[4];
+  const long r = blockIdx.x;
+  const T G = (T)sc[gidx];
+  const T* row = src + r * ld_src;
+  float mx = 0.0f;
+  for (long c = threadIdx.x; c < cols; c += blockDim.x) mx = fmaxf(mx, fabsf((float)(row[c] * G)));
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  mx = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
+  const T q = (T)row_grid(mx);
+  __half* mrow = mo + r * ld_dst;
+  __half* hrow = ho + r * ld_dst;
+  for (long c = threadIdx.x; c < ld_dst; c += blockDim.x) {
+    __half mh = __float2half(0.0f), hh = __float2half(0.0f);
+    if (c < cols) {
+      const T x = row[c] * G;
+      const T m = q * rint(x / q);
+      mh = __float2half_rn((float)m);
+      hh = __float2half_rn((float)(x - m));
+    }
+    mrow[c] = mh;
+    hrow[c] = hh;
   }
 }
 
-// dst[c][r] (ld_dst >= rows) = split(src[r][c] * scale); zero for rows <= r < ld_dst.
+// dst[c][r] (ld_dst) = src[r][c] for r < rows, 0 for rows <= r < ld_dst; all c < cols.
 template <class T>
-__global__ void split_transpose_kernel(const T* __restrict__ src, long rows, long cols,
-                                       long ld_src, const float* __restrict__ sc, int sidx,
-                                       __half* __restrict__ hi, __half* __restrict__ lo,
-                                       long ld_dst) {
+__global__ void transpose_kernel(const T* __restrict__ src, long rows, long cols, long ld_src,
+                                 T* __restrict__ dst, long ld_dst) {
   __shared__ T tile[32][33];
-  const T s = (T)sc[sidx];
   const long r0 = (long)blockIdx.x * 32, c0 = (long)blockIdx.y * 32;
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const long r = r0 + i, c = c0 + threadIdx.x;
-    tile[i][threadIdx.x] = (r < rows && c < cols) ? src[r * ld_src + c] * s : (T)0;
+    tile[i][threadIdx.x] = (r < rows && c < cols) ? src[r * ld_src + c] : (T)0;
   }
   __syncthreads();
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const long c = c0 + i, r = r0 + threadIdx.x;
-    if (c < cols && r < ld_dst) {
-      __half h, l;
-      split1(tile[threadIdx.x][i], h, l);
-      hi[c * ld_dst + r] = h;
-      lo[c * ld_dst + r] = l;
-    }
+    if (c < cols && r < ld_dst) dst[c * ld_dst + r] = tile[threadIdx.x][i];
   }
+}
+
+template <class T>
+cudaError_t transpose(const T* src, long rows, long cols, long ld_src, T* dst, long ld_dst,
+                      cudaStream_t s) {
+  dim3 grid((unsigned)((ld_dst + 31) / 32), (unsigned)((cols + 31) / 32));
+  transpose_kernel<T><<<grid, dim3(32, 8), 0, s>>>(src, rows, cols, ld_src, dst, ld_dst);
+  count_launch();
+  return cudaGetLastError();
 }
 
 __global__ void gather_rows_half_kernel(const __half* __restrict__ src, long ld,
@@ -193,7 +231,7 @@ __global__ void gather_rows_half_kernel(const __half* __restrict__ src, long ld,
   }
 }
 
-// Pads an FP64 host-copied matrix into FP32 [rows][ld_dst] (zero padding).
+// FP64 [rows][cols] -> FP32 [rows][ld_dst], zero padding.
 __global__ void f64_to_f32_kernel(const double* __restrict__ src, long rows, long cols,
                                   float* __restrict__ dst, long ld_dst) {
   const long total = rows * ld_dst;
@@ -204,26 +242,9 @@ __global__ void f64_to_f32_kernel(const double* __restrict__ src, long rows, lon
   }
 }
 
-// dst[c][r] (ld_dst) = src[r][c] as FP32, zero padding for r >= rows.
-__global__ void f64_to_f32_transpose_kernel(const double* __restrict__ src, long rows, long cols,
-                                            float* __restrict__ dst, long ld_dst) {
-  __shared__ float tile[32][33];
-  const long r0 = (long)blockIdx.x * 32, c0 = (long)blockIdx.y * 32;
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const long r = r0 + i, c = c0 + threadIdx.x;
-    tile[i][threadIdx.x] = (r < rows && c < cols) ? (float)src[r * cols + c] : 0.0f;
-  }
-  __syncthreads();
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const long c = c0 + i, r = r0 + threadIdx.x;
-    if (c < cols && r < ld_dst) dst[c * ld_dst + r] = tile[threadIdx.x][i];
-  }
-}
-
 // ------------------------------------------------------------ reductions
 
-// out[m][c] = sum_s a[s][m][c] - sum_s b[s][m][c] in FP64 (b nullable), and
-// the running max of |out| into am_slot.
+// out[t] = sum_s a[s][t] - sum_s b[s][t] in FP64 (b nullable); max |out| -> am_slot.
 __global__ void reduce_parts_kernel(const float* __restrict__ a, int na, const float* __restrict__ b,
                                     int nb, long count, double* __restrict__ out,
                                     unsigned* __restrict__ am_slot) {
@@ -253,9 +274,38 @@ __global__ void final_k_kernel(const float* __restrict__ L1, int n1, const float
   }
 }
 
-// ============================================================ tc_gemm
-// out[split][m][c] = scale * sum_{k in split} A[m][k] B[c][k] for a 128 x 128
-// tile, A and B split-FP16 hi/lo, K-major, 3-stage TMA ring.
+// E_x = -dV (2 sum_k ea[k] - sum_k ec[k]) / G^4 with G the orbital scale, in
+// a fixed summation order (one block of 256 threads).
+__global__ void final_ex_kernel(const double* __restrict__ ea, int na_, const double* __restrict__ ec,
+                                int nc_, const float* __restrict__ sc, double dV, double* Ex) {
+  __shared__ double sa[256], sb[256];
+  double a = 0.0, b = 0.0;
+  for (int t = threadIdx.x; t < na_; t += blockDim.x) a += ea[t];
+  for (int t = threadIdx.x; t < nc_; t += blockDim.x) b += ec[t];
+  sa[threadIdx.x] = a;
+  sb[threadIdx.x] = b;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sa[threadIdx.x] += sa[threadIdx.x + w];
+      sb[threadIdx.x] += sb[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double g = (double)sc[SC_PSI];
+    const double g4 = (g * g) * (g * g);
+    *Ex = -dV * (2.0 * sa[0] - sb[0]) / g4;
+  }
+}
+
+// ============================================================ gemm
+// out[split][m][c] = scale * sum_{k in split} A[m][k] B[c][k] for one
+// 128 x 128 tile, A and B as per-row (m, h) pieces, K-major, 3-stage TMA
+// ring.  A0 (m.m) and A1 (m.h + h.m + h.h) accumulate in one of two TMEM
+// sets; every kDrain k-blocks (192 terms) the epilogue adds A0 + A1 of the
+// finished set into FP32 registers (round to nearest) while the MMA warp
+// moves on to the other set.
 // Warps 0-3: epilogue (thread = row); warp 4: TMA producer; warp 5: MMA.
 
 struct GemmArgs {
@@ -271,14 +321,15 @@ struct GemmArgs {
 constexpr int G_STAGES = 3;
 constexpr int G_STAGE_BYTES = 4 * 16384;
 constexpr int G_SMEM = G_STAGES * G_STAGE_BYTES + 1024;
+constexpr int kDrain = 3;
 
 __global__ void __launch_bounds__(192, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
-                   const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
-                   GemmArgs g) {
+    gemm_kernel(const __grid_constant__ CUtensorMap mAm, const __grid_constant__ CUtensorMap mAh,
+                const __grid_constant__ CUtensorMap mBm, const __grid_constant__ CUtensorMap mBh,
+                GemmArgs g) {
   extern __shared__ uint8_t g_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(g_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ uint64_t full[G_STAGES], empty[G_STAGES], acc_full, drain;
+  __shared__ uint64_t full[G_STAGES], empty[G_STAGES], set_ready[2], set_free[2], drain;
   __shared__ uint32_t tslot;
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -286,19 +337,23 @@ __global__ void __launch_bounds__(192, 1)
   const int kbeg = blockIdx.z * g.kchunk;
   const int kend = min(g.K, kbeg + g.kchunk);
   const int nkb = kend > kbeg ? (kend - kbeg + 63) / 64 : 0;
+  const int ngroups = (nkb + kDrain - 1) / kDrain;
 
   if (tid == 0) {
     for (int s = 0; s < G_STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&acc_full, 1);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&set_ready[s], 1);
+      mbar_init(&set_free[s], 128);
+    }
     mbar_init(&drain, 1);
     abort_flag = 0;
     fence_mbar_init();
   }
   if (warp == 5) {
-    tmem_alloc(&tslot, 128);
+    tmem_alloc(&tslot, 512);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -307,7 +362,7 @@ __global__ void __launch_bounds__(192, 1)
   const uint32_t tbase = tslot;
 
   if (warp == 4 && lane == 0) {
-    prefetch_tmap(&mAh); prefetch_tmap(&mAl); prefetch_tmap(&mBh); prefetch_tmap(&mBl);
+    prefetch_tmap(&mAm); prefetch_tmap(&mAh); prefetch_tmap(&mBm); prefetch_tmap(&mBh);
     int last_parity[G_STAGES] = {-1, -1, -1};
     for (int kb = 0; kb < nkb && !abort_flag; ++kb) {
       const int s = kb % G_STAGES, use = kb / G_STAGES;
@@ -317,10 +372,10 @@ __global__ void __launch_bounds__(192, 1)
       uint8_t* st = sm + s * G_STAGE_BYTES;
       mbar_expect_tx(&full[s], G_STAGE_BYTES);
       const int kc = kbeg + kb * 64;
-      tma_load_2d(st, &mAh, &full[s], kc, m0);
-      tma_load_2d(st + 16384, &mAl, &full[s], kc, m0);
-      tma_load_2d(st + 32768, &mBh, &full[s], kc, n0);
-      tma_load_2d(st + 49152, &mBl, &full[s], kc, n0);
+      tma_load_2d(st, &mAm, &full[s], kc, m0);
+      tma_load_2d(st + 16384, &mAh, &full[s], kc, m0);
+      tma_load_2d(st + 32768, &mBm, &full[s], kc, n0);
+      tma_load_2d(st + 49152, &mBh, &full[s], kc, n0);
       last_parity[s] = use & 1;
     }
     for (int s = 0; s < G_STAGES; ++s)
@@ -328,53 +383,80 @@ __global__ void __launch_bounds__(192, 1)
   } else if (warp == 5 && lane == 0) {
     const uint32_t idesc = idesc_f16(128, 128, false, false, false);
     for (int kb = 0; kb < nkb && !abort_flag; ++kb) {
-      const int s = kb % G_STAGES;
+      const int s = kb % G_STAGES, grp = kb / kDrain, set = grp & 1;
+      const bool first = (kb % kDrain) == 0;
+      const bool last = (kb % kDrain) == kDrain - 1 || kb == nkb - 1;
+      if (first && grp >= 2 && !mbar_wait(&set_free[set], ((grp >> 1) - 1) & 1)) {
+        atomicExch(g.status, 14); abort_flag = 1; break;
+      }
       if (!mbar_wait(&full[s], (kb / G_STAGES) & 1)) {
         atomicExch(g.status, 12); abort_flag = 1; break;
       }
       tc_fence_after();
       const uint32_t st = smem_u32(sm + s * G_STAGE_BYTES);
-      const uint32_t a_off[3] = {0, 0, 16384}, b_off[3] = {32768, 49152, 32768};
+      const uint32_t am = st, ah = st + 16384, bm = st + 32768, bh = st + 49152;
+      const uint32_t t0 = tbase + set * 256, t1 = t0 + 128;
+      for (int kk = 0; kk < 4; ++kk)
+        mma_f16(t0, sdesc_sw128(am + kk * 32, 16, 1024), sdesc_sw128(bm + kk * 32, 16, 1024),
+                idesc, (first && kk == 0) ? 0u : 1u);
+      const uint32_t ao[3] = {am, ah, ah}, bo[3] = {bh, bm, bh};
       for (int p = 0; p < 3; ++p)
-        for (int kk = 0; kk < 4; ++kk) {
-          const uint64_t ad = sdesc_sw128(st + a_off[p] + kk * 32, 16, 1024);
-          const uint64_t bd = sdesc_sw128(st + b_off[p] + kk * 32, 16, 1024);
-          mma_f16(tbase, ad, bd, idesc, (kb > 0 || p > 0 || kk > 0) ? 1u : 0u);
-        }
+        for (int kk = 0; kk < 4; ++kk)
+          mma_f16(t1, sdesc_sw128(ao[p] + kk * 32, 16, 1024),
+                  sdesc_sw128(bo[p] + kk * 32, 16, 1024), idesc,
+                  (first && p == 0 && kk == 0) ? 0u : 1u);
       mma_commit(&empty[s]);
+      if (last) mma_commit(&set_ready[set]);
     }
-    mma_commit(&acc_full);
     mma_commit(&drain);
     mbar_wait(&drain, 0);
   } else if (warp < 4) {
     const int r = warp * 32 + lane;
-    const bool ok = mbar_wait(&acc_full, 0);
-    tc_fence_after();
-    if (!ok) atomicExch(g.status, 13);
+    const uint32_t lane_off = static_cast<uint32_t>(warp * 32) << 16;
+    float run[128];
+#pragma unroll
+    for (int c = 0; c < 128; ++c) run[c] = 0.0f;
+    bool ok = true;
+    for (int gi = 0; gi < ngroups; ++gi) {
+      const int set = gi & 1;
+      if (!mbar_wait(&set_ready[set], (gi >> 1) & 1)) { ok = false; atomicExch(g.status, 13); break; }
+      tc_fence_after();
+#pragma unroll
+      for (int c = 0; c < 128; c += 16) {
+        uint32_t a0[16], a1[16];
+        tmem_ld16(tbase + lane_off + set * 256 + c, a0);
+        tmem_ld16(tbase + lane_off + set * 256 + 128 + c, a1);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) run[c + j] += __uint_as_float(a0[j]) + __uint_as_float(a1[j]);
+      }
+      tc_fence_before();
+      mbar_arrive(&set_free[set]);
+    }
+    ok = ok && !abort_flag;
     const float scale = g.sc[g.scale_idx];
-    float* orow = g.out + (long)blockIdx.z * g.split_stride + (long)(m0 + r) * g.ldo;
-    const bool row_ok = (m0 + r) < g.M;
-    for (int c = 0; c < 128; c += 16) {
-      uint32_t v[16];
-      tmem_ld16(tbase + (static_cast<uint32_t>(warp * 32) << 16) + c, v);
-      tmem_wait_ld();
-      if (row_ok)
-        for (int j = 0; j < 16; ++j) {
-          const int col = n0 + c + j;
-          if (col < g.Ncols) orow[col] = (ok && nkb > 0) ? __uint_as_float(v[j]) * scale : 0.0f;
-        }
+    if (m0 + r < g.M) {
+      float* orow = g.out + (long)blockIdx.z * g.split_stride + (long)(m0 + r) * g.ldo;
+#pragma unroll
+      for (int c = 0; c < 128; ++c) {
+        const int col = n0 + c;
+        if (col < g.Ncols) orow[col] = ok ? run[c] * scale : 0.0f;
+      }
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 5) tmem_dealloc(tbase, 128);
+  if (warp == 5) tmem_dealloc(tbase, 512);
 }
 
 // ============================================================ pair kernel
-// For one X tile of 128 rows and a range of Y rows (in tiles of 64):
-//   S = X Y^T (K = NP), T = f * V' o S, acc[x][j] += sum_y T[x][y] Y[y][j]
-// X, Y: split-FP16 [rows][NP] K-major; V': FP32 [X rows][Y cols].
+// For one X tile of 128 rows and a range of Y rows (tiles of 64):
+//   S = X Y^T as A0 (m.m, exact) + A1 (cross terms)       K = NP
+//   T = V' o S;  e += sum_y T S  (the closed-form energy term, optional)
+//   U = f T as floating hi/lo;  acc[x][j] += sum_y U[x][y] Y[y][j]
+// X, Y: per-row (m, h) pieces [rows][NP], K-major; V': FP32 [X rows][Y cols].
 // The Y tile doubles as the MN-major B operand of the second product.
+// TMEM: S double buffer (A0, A1) x 2 = 256 columns, acc 128, running sum 128.
 
 struct PairArgs {
   int X, Y, ychunk, n;
@@ -384,33 +466,37 @@ struct PairArgs {
   long ldo;
   long part_stride;
   int transposed;  // 0: out[part][x][j]; 1: out[j][x] (single part)
+  double* epart;   // nullable: per-CTA sum_y V' S^2 (scaled by G^4)
   int* status;
 };
 
+constexpr int kAccDrain = 2;  // tiles per acc drain
+
 template <int NP>
 struct PairCfg {
-  static constexpr int X_BYTES = 128 * NP * 2;     // one of hi / lo
+  static constexpr int X_BYTES = 128 * NP * 2;     // one piece
   static constexpr int Y_BYTES = 64 * NP * 2;
   static constexpr int V_BYTES = 128 * 64 * 4;
   static constexpr int STAGE = 2 * Y_BYTES + V_BYTES;
   static constexpr int OFF_STAGE = 2 * X_BYTES;
-  static constexpr int OFF_V2 = OFF_STAGE + 2 * STAGE;
-  static constexpr int V2_BYTES = 128 * 64 * 2;
-  static constexpr int SMEM = OFF_V2 + 2 * V2_BYTES + 1024;
+  static constexpr int OFF_U = OFF_STAGE + 2 * STAGE;
+  static constexpr int U_BYTES = 128 * 64 * 2;
+  static constexpr int SMEM = OFF_U + 2 * U_BYTES + 1024;
 };
 
 template <int NP>
 __global__ void __launch_bounds__(192, 1)
-    pair_kernel(const __grid_constant__ CUtensorMap mXh, const __grid_constant__ CUtensorMap mXl,
-                const __grid_constant__ CUtensorMap mYh, const __grid_constant__ CUtensorMap mYl,
+    pair_kernel(const __grid_constant__ CUtensorMap mXm, const __grid_constant__ CUtensorMap mXh,
+                const __grid_constant__ CUtensorMap mYm, const __grid_constant__ CUtensorMap mYh,
                 const __grid_constant__ CUtensorMap mV, PairArgs a) {
   using C = PairCfg<NP>;
   extern __shared__ uint8_t p_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ uint64_t x_full, full[2], empty[2], s_full[2], s_free[2], v2_full, v2_free, acc_full,
-      drain;
+  __shared__ uint64_t x_full, full[2], empty[2], s_full[2], s_free[2], u_full, u_free, acc_ready,
+      acc_free, drain;
   __shared__ uint32_t tslot;
   __shared__ volatile int abort_flag;
+  __shared__ double ered[128];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int x0 = blockIdx.x * 128;
   const int y0 = blockIdx.y * a.ychunk;
@@ -426,34 +512,35 @@ __global__ void __launch_bounds__(192, 1)
       mbar_init(&s_full[s], 1);
       mbar_init(&s_free[s], 128);
     }
-    mbar_init(&v2_full, 128);
-    mbar_init(&v2_free, 1);
-    mbar_init(&acc_full, 1);
+    mbar_init(&u_full, 128);
+    mbar_init(&u_free, 1);
+    mbar_init(&acc_ready, 1);
+    mbar_init(&acc_free, 128);
     mbar_init(&drain, 1);
     abort_flag = 0;
     fence_mbar_init();
   }
   if (warp == 5) {
-    tmem_alloc(&tslot, 256);
+    tmem_alloc(&tslot, 512);
     tmem_relinquish();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = tslot;
-  const uint32_t t_acc = tbase + 128;
+  const uint32_t t_acc = tbase + 256, t_run = tbase + 384;
 
   if (warp == 4 && lane == 0) {
     // ---------------- TMA producer
-    prefetch_tmap(&mXh); prefetch_tmap(&mXl); prefetch_tmap(&mYh); prefetch_tmap(&mYl);
+    prefetch_tmap(&mXm); prefetch_tmap(&mXh); prefetch_tmap(&mYm); prefetch_tmap(&mYh);
     prefetch_tmap(&mV);
     int last_parity[2] = {-1, -1};
     bool xl = false;
     if (T > 0) {
       mbar_expect_tx(&x_full, 2 * C::X_BYTES);
       for (int kb = 0; kb < NKB; ++kb) {
-        tma_load_2d(sm + kb * 16384, &mXh, &x_full, kb * 64, x0);
-        tma_load_2d(sm + C::X_BYTES + kb * 16384, &mXl, &x_full, kb * 64, x0);
+        tma_load_2d(sm + kb * 16384, &mXm, &x_full, kb * 64, x0);
+        tma_load_2d(sm + C::X_BYTES + kb * 16384, &mXh, &x_full, kb * 64, x0);
       }
       xl = true;
     }
@@ -466,8 +553,8 @@ __global__ void __launch_bounds__(192, 1)
       mbar_expect_tx(&full[s], C::STAGE);
       const int yr = y0 + t * 64;
       for (int kb = 0; kb < NKB; ++kb) {
-        tma_load_2d(st + kb * 8192, &mYh, &full[s], kb * 64, yr);
-        tma_load_2d(st + C::Y_BYTES + kb * 8192, &mYl, &full[s], kb * 64, yr);
+        tma_load_2d(st + kb * 8192, &mYm, &full[s], kb * 64, yr);
+        tma_load_2d(st + C::Y_BYTES + kb * 8192, &mYh, &full[s], kb * 64, yr);
       }
       tma_load_2d(st + 2 * C::Y_BYTES, &mV, &full[s], yr, x0);
       tma_load_2d(st + 2 * C::Y_BYTES + 16384, &mV, &full[s], yr + 32, x0);
@@ -480,25 +567,29 @@ __global__ void __launch_bounds__(192, 1)
     // ---------------- MMA issuer
     const uint32_t id_s = idesc_f16(128, 64, false, false, false);
     const uint32_t id_acc = idesc_f16(128, NP, false, false, true);
-    const uint32_t xh = smem_u32(sm), xlo = smem_u32(sm + C::X_BYTES);
-    const uint32_t v2h = smem_u32(sm + C::OFF_V2), v2l = smem_u32(sm + C::OFF_V2 + C::V2_BYTES);
+    const uint32_t xm = smem_u32(sm), xh = smem_u32(sm + C::X_BYTES);
+    const uint32_t uh = smem_u32(sm + C::OFF_U), ul = smem_u32(sm + C::OFF_U + C::U_BYTES);
     bool good = T > 0 && mbar_wait(&x_full, 0);
     if (T > 0 && !good) { atomicExch(a.status, 22); abort_flag = 1; }
     auto issue_acc = [&](int u) -> bool {
-      const int s = u & 1;
-      if (!mbar_wait(&v2_full, u & 1)) return false;
+      const int s = u & 1, grp = u / kAccDrain;
+      const bool first = (u % kAccDrain) == 0;
+      const bool last = (u % kAccDrain) == kAccDrain - 1 || u == T - 1;
+      if (first && grp > 0 && !mbar_wait(&acc_free, (grp - 1) & 1)) return false;
+      if (!mbar_wait(&u_full, u & 1)) return false;
       tc_fence_after();
-      const uint32_t yh = smem_u32(sm + C::OFF_STAGE + s * C::STAGE);
-      const uint32_t yl = yh + C::Y_BYTES;
-      const uint32_t ao[3] = {v2h, v2h, v2l}, bo[3] = {yh, yl, yh};
+      const uint32_t ym = smem_u32(sm + C::OFF_STAGE + s * C::STAGE);
+      const uint32_t yh = ym + C::Y_BYTES;
+      const uint32_t ao[3] = {uh, uh, ul}, bo[3] = {ym, yh, ym};
       for (int p = 0; p < 3; ++p)
         for (int kk = 0; kk < 4; ++kk) {
           const uint64_t ad = sdesc_sw128(ao[p] + kk * 32, 16, 1024);
           const uint64_t bd = sdesc_sw128(bo[p] + kk * 2048, 8192, 1024);
-          mma_f16(t_acc, ad, bd, id_acc, (u > 0 || p > 0 || kk > 0) ? 1u : 0u);
+          mma_f16(t_acc, ad, bd, id_acc, (first && p == 0 && kk == 0) ? 0u : 1u);
         }
       mma_commit(&empty[s]);
-      mma_commit(&v2_free);
+      mma_commit(&u_free);
+      if (last) mma_commit(&acc_ready);
       return true;
     };
     for (int t = 0; good && t < T && !abort_flag; ++t) {
@@ -508,55 +599,71 @@ __global__ void __launch_bounds__(192, 1)
         atomicExch(a.status, 24); abort_flag = 1; good = false; break;
       }
       tc_fence_after();
-      const uint32_t yh = smem_u32(sm + C::OFF_STAGE + s * C::STAGE);
-      const uint32_t yl = yh + C::Y_BYTES;
-      const uint32_t ao[3] = {xh, xh, xlo}, bo[3] = {yh, yl, yh};
-      const uint32_t t_s = tbase + s * 64;
+      const uint32_t ym = smem_u32(sm + C::OFF_STAGE + s * C::STAGE);
+      const uint32_t yh = ym + C::Y_BYTES;
+      const uint32_t t_s0 = tbase + s * 128, t_s1 = t_s0 + 64;
+      for (int kk = 0; kk < NP / 16; ++kk) {
+        const uint64_t ad = sdesc_sw128(xm + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024);
+        const uint64_t bd = sdesc_sw128(ym + (kk >> 2) * 8192 + (kk & 3) * 32, 16, 1024);
+        mma_f16(t_s0, ad, bd, id_s, kk > 0 ? 1u : 0u);
+      }
+      const uint32_t ao[3] = {xm, xh, xh}, bo[3] = {yh, ym, yh};
       for (int p = 0; p < 3; ++p)
         for (int kk = 0; kk < NP / 16; ++kk) {
           const uint64_t ad = sdesc_sw128(ao[p] + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024);
           const uint64_t bd = sdesc_sw128(bo[p] + (kk >> 2) * 8192 + (kk & 3) * 32, 16, 1024);
-          mma_f16(t_s, ad, bd, id_s, (p > 0 || kk > 0) ? 1u : 0u);
+          mma_f16(t_s1, ad, bd, id_s, (p > 0 || kk > 0) ? 1u : 0u);
         }
       mma_commit(&s_full[s]);
       if (t > 0 && !issue_acc(t - 1)) { atomicExch(a.status, 25); abort_flag = 1; good = false; break; }
     }
     if (good && T > 0 && !issue_acc(T - 1)) { atomicExch(a.status, 26); abort_flag = 1; }
-    mma_commit(&acc_full);
     mma_commit(&drain);
     mbar_wait(&drain, 0);
   } else if (warp < 4) {
-    // ---------------- epilogue: T = f V' o S, split, stage for the second product
+    // ---------------- epilogue
     const int r = warp * 32 + lane;
     const uint32_t lane_off = static_cast<uint32_t>(warp * 32) << 16;
     const float f = a.sc[a.f_idx];
-    uint8_t* v2h = sm + C::OFF_V2;
-    uint8_t* v2l = v2h + C::V2_BYTES;
+    const bool want_e = a.epart != nullptr;
+    uint8_t* uhp = sm + C::OFF_U;
+    uint8_t* ulp = uhp + C::U_BYTES;
     const int sw = r & 7;
+    double esum = 0.0;
+    bool ok = T > 0;
     for (int t = 0; t < T && !abort_flag; ++t) {
       const int s = t & 1;
-      if (!mbar_wait(&s_full[s], (t >> 1) & 1)) { atomicExch(a.status, 27); abort_flag = 1; break; }
+      if (!mbar_wait(&s_full[s], (t >> 1) & 1)) { atomicExch(a.status, 27); abort_flag = 1; ok = false; break; }
       tc_fence_after();
       float sv[64];
 #pragma unroll
       for (int c = 0; c < 64; c += 16) {
-        uint32_t u[16];
-        tmem_ld16(tbase + lane_off + s * 64 + c, u);
+        uint32_t u0[16], u1[16];
+        tmem_ld16(tbase + lane_off + s * 128 + c, u0);
+        tmem_ld16(tbase + lane_off + s * 128 + 64 + c, u1);
         tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 16; ++j) sv[c + j] = __uint_as_float(u[j]);
+        for (int j = 0; j < 16; ++j) sv[c + j] = __uint_as_float(u0[j]) + __uint_as_float(u1[j]);
       }
       tc_fence_before();
       mbar_arrive(&s_free[s]);
       const uint8_t* vt = sm + C::OFF_STAGE + s * C::STAGE + 2 * C::Y_BYTES;
       uint32_t hi[32], lo[32];
+      float etile = 0.0f;
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const int box = q >> 3, qc = q & 7;
         const float4 v = *reinterpret_cast<const float4*>(vt + box * 16384 + r * 128 +
                                                           ((qc ^ sw) << 4));
-        const float t0 = v.x * sv[4 * q + 0] * f, t1 = v.y * sv[4 * q + 1] * f;
-        const float t2 = v.z * sv[4 * q + 2] * f, t3 = v.w * sv[4 * q + 3] * f;
+        const float p0 = v.x * sv[4 * q + 0], p1 = v.y * sv[4 * q + 1];
+        const float p2 = v.z * sv[4 * q + 2], p3 = v.w * sv[4 * q + 3];
+        if (want_e) {
+          etile = fmaf(p0, sv[4 * q + 0], etile);
+          etile = fmaf(p1, sv[4 * q + 1], etile);
+          etile = fmaf(p2, sv[4 * q + 2], etile);
+          etile = fmaf(p3, sv[4 * q + 3], etile);
+        }
+        const float t0 = p0 * f, t1 = p1 * f, t2 = p2 * f, t3 = p3 * f;
         const __half2 h01 = __floats2half2_rn(t0, t1), h23 = __floats2half2_rn(t2, t3);
         const float2 b01 = __half22float2(h01), b23 = __half22float2(h23);
         const __half2 l01 = __floats2half2_rn(t0 - b01.x, t1 - b01.y);
@@ -566,45 +673,73 @@ __global__ void __launch_bounds__(192, 1)
         lo[2 * q] = *reinterpret_cast<const uint32_t*>(&l01);
         lo[2 * q + 1] = *reinterpret_cast<const uint32_t*>(&l23);
       }
-      if (t > 0 && !mbar_wait(&v2_free, (t - 1) & 1)) { atomicExch(a.status, 28); abort_flag = 1; break; }
+      esum += (double)etile;
+      if (t > 0 && !mbar_wait(&u_free, (t - 1) & 1)) { atomicExch(a.status, 28); abort_flag = 1; ok = false; break; }
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int off = r * 128 + ((q ^ sw) << 4);
-        *reinterpret_cast<uint4*>(v2h + off) = make_uint4(hi[4 * q], hi[4 * q + 1], hi[4 * q + 2], hi[4 * q + 3]);
-        *reinterpret_cast<uint4*>(v2l + off) = make_uint4(lo[4 * q], lo[4 * q + 1], lo[4 * q + 2], lo[4 * q + 3]);
+        *reinterpret_cast<uint4*>(uhp + off) = make_uint4(hi[4 * q], hi[4 * q + 1], hi[4 * q + 2], hi[4 * q + 3]);
+        *reinterpret_cast<uint4*>(ulp + off) = make_uint4(lo[4 * q], lo[4 * q + 1], lo[4 * q + 2], lo[4 * q + 3]);
       }
       fence_async_smem();
-      mbar_arrive(&v2_full);
+      mbar_arrive(&u_full);
+      // drain the second-product accumulator into the running sum after each group
+      if ((t % kAccDrain) == kAccDrain - 1 || t == T - 1) {
+        const int grp = t / kAccDrain;
+        if (!mbar_wait(&acc_ready, grp & 1)) { atomicExch(a.status, 29); abort_flag = 1; ok = false; break; }
+        tc_fence_after();
+#pragma unroll 1
+        for (int c = 0; c < NP; c += 16) {
+          uint32_t ua[16], ur[16];
+          tmem_ld16(t_acc + lane_off + c, ua);
+          if (grp > 0) tmem_ld16(t_run + lane_off + c, ur);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            ur[j] = __float_as_uint((grp > 0 ? __uint_as_float(ur[j]) : 0.0f) + __uint_as_float(ua[j]));
+          tmem_st16(t_run + lane_off + c, ur);
+        }
+        tmem_wait_st();
+        tc_fence_before();
+        mbar_arrive(&acc_free);
+      }
     }
-    // ---------------- drain the accumulator
-    bool ok = mbar_wait(&acc_full, 0);
-    tc_fence_after();
-    if (!ok) atomicExch(a.status, 29);
     ok = ok && !abort_flag;
+    // ---------------- write the running sum
+    tc_fence_after();
     const float os = a.sc[a.out_idx];
     const int x = x0 + r;
     const bool row_ok = x < a.X;
 #pragma unroll 1
     for (int c = 0; c < NP; c += 16) {
       uint32_t u[16];
-      tmem_ld16(t_acc + lane_off + c, u);
+      tmem_ld16(t_run + lane_off + c, u);
       tmem_wait_ld();
       if (!row_ok) continue;
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const int col = c + j;
         if (col >= a.n) continue;
-        const float v = (ok && T > 0) ? __uint_as_float(u[j]) * os : 0.0f;
+        const float v = ok ? __uint_as_float(u[j]) * os : 0.0f;
         if (a.transposed)
           a.out[(long)col * a.ldo + x] = v;
         else
           a.out[(long)blockIdx.y * a.part_stride + (long)x * a.ldo + col] = v;
       }
     }
+    if (want_e) {
+      ered[r] = (ok && row_ok) ? esum : 0.0;
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (r == 0) {
+        double sum = 0.0;
+        for (int i = 0; i < 128; ++i) sum += ered[i];
+        a.epart[(long)blockIdx.y * gridDim.x + blockIdx.x] = sum;
+      }
+    }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 5) tmem_dealloc(tbase, 256);
+  if (warp == 5) tmem_dealloc(tbase, 512);
 }
 
 // ------------------------------------------------------------- host side
@@ -641,6 +776,15 @@ int blocks_for(long total, int tpb = 256) {
   return (int)std::max<long>(1, std::min<long>((total + tpb - 1) / tpb, 152L * 16));
 }
 
+template <class T>
+cudaError_t split_rows(const T* src, long rows, long cols, long ld_src, const float* sc, int gidx,
+                       __half* mo, __half* ho, long ld_dst, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  split_mh_rows_kernel<T><<<(unsigned)rows, 128, 0, s>>>(src, cols, ld_src, sc, gidx, mo, ho, ld_dst);
+  count_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 struct MixedState {
@@ -649,24 +793,25 @@ struct MixedState {
   long Np = 0, Ng8 = 0, Na8 = 0, Ng4 = 0, Na4 = 0;
   double dV = 0.0;
   std::vector<void*> allocs;
-  __half *phi_h = nullptr, *phi_l = nullptr, *phiT_h = nullptr, *phiT_l = nullptr,
-         *phigT_h = nullptr, *phigT_l = nullptr;
+  __half *phi_m = nullptr, *phi_h = nullptr, *phiT_m = nullptr, *phiT_h = nullptr,
+         *phigT_m = nullptr, *phigT_h = nullptr;
   float *V32 = nullptr, *VT32 = nullptr, *W32 = nullptr;
   int32_t* idx = nullptr;
-  __half *CT_h = nullptr, *CT_l = nullptr, *psi_h = nullptr, *psi_l = nullptr, *psig_h = nullptr,
-         *psig_l = nullptr, *M1_h = nullptr, *M1_l = nullptr, *D23T_h = nullptr,
-         *D23T_l = nullptr;
+  __half *CT_m = nullptr, *CT_h = nullptr, *psi_m = nullptr, *psi_h = nullptr, *psig_m = nullptr,
+         *psig_h = nullptr, *M1_m = nullptr, *M1_h = nullptr, *D23T_m = nullptr,
+         *D23T_h = nullptr;
   float *psi32 = nullptr, *M2p = nullptr, *M3p = nullptr, *M1 = nullptr, *L1p = nullptr,
         *L23p = nullptr, *sc = nullptr;
-  double *D23 = nullptr, *red = nullptr;
+  double *D23 = nullptr, *CT64 = nullptr, *D23T64 = nullptr, *red = nullptr, *EpA = nullptr,
+         *EpC = nullptr, *Lf = nullptr, *Q64 = nullptr, *dwork = nullptr;
   unsigned* am = nullptr;
   int* status = nullptr;
-  int partsA = 1, partsC = 1, splitsOrb = 1, splitsL1 = 1, splitsL23 = 1;
+  int xa = 1, partsA = 1, partsC = 1, splitsL1 = 1, splitsL23 = 1;
   int ychunkA = 64, ychunkC = 64;
   int kchunkL1 = 64, kchunkL23 = 64;
-  CUtensorMap m_phi_h, m_phi_l, m_CT_h, m_CT_l, m_psi128_h, m_psi128_l, m_psi64_h, m_psi64_l,
-      m_psig128_h, m_psig128_l, m_psig64_h, m_psig64_l, m_V, m_VT, m_W, m_phiT_h, m_phiT_l,
-      m_M1_h, m_M1_l, m_phigT_h, m_phigT_l, m_D23T_h, m_D23T_l;
+  CUtensorMap m_phi_m, m_phi_h, m_CT_m, m_CT_h, m_psi128_m, m_psi128_h, m_psi64_m, m_psi64_h,
+      m_psig128_m, m_psig128_h, m_psig64_m, m_psig64_h, m_V, m_VT, m_W, m_phiT_m, m_phiT_h,
+      m_M1_m, m_M1_h, m_phigT_m, m_phigT_h, m_D23T_m, m_D23T_h;
 };
 
 namespace {
@@ -683,7 +828,7 @@ cudaError_t alloc(MixedState* m, T** p, size_t elems) {
 
 struct Plan {
   long Np, Ng8, Na8, Ng4, Na4;
-  int np, partsA, partsC, splitsL1, splitsL23, kchunkL1, kchunkL23, ychunkA, ychunkC;
+  int np, xa, partsA, partsC, splitsL1, splitsL23, kchunkL1, kchunkL23, ychunkA, ychunkC;
 };
 
 Plan make_plan(int64_t Ng, int N, int n, int Naux) {
@@ -694,15 +839,15 @@ Plan make_plan(int64_t Ng, int N, int n, int Naux) {
   p.Na8 = rup(Naux, 8);
   p.Ng4 = rup(Ng, 4);
   p.Na4 = rup(Naux, 4);
-  const int xa = (Naux + 127) / 128;
-  // role A and C: X = g tiles; split Y so the grid is about two waves of 152 SMs
-  p.partsA = std::max(1, std::min<int>((304 + xa - 1) / xa, (int)((Ng + 63) / 64)));
+  p.xa = (Naux + 127) / 128;
+  // roles A and C: X = g tiles; split Y so the grid is about two waves of 152 SMs
+  p.partsA = std::max(1, std::min<int>((304 + p.xa - 1) / p.xa, (int)((Ng + 63) / 64)));
   p.ychunkA = (int)rup((Ng + p.partsA - 1) / p.partsA, 64);
   p.partsA = (int)((Ng + p.ychunkA - 1) / p.ychunkA);
-  p.partsC = std::max(1, std::min<int>((152 + xa - 1) / xa, (Naux + 63) / 64));
+  p.partsC = std::max(1, std::min<int>((152 + p.xa - 1) / p.xa, (Naux + 63) / 64));
   p.ychunkC = (int)rup((Naux + p.partsC - 1) / p.partsC, 64);
   p.partsC = (Naux + p.ychunkC - 1) / p.ychunkC;
-  // line GEMMs: M = N (basis) tiles x N = n tiles x K splits of >= 1024
+  // line GEMMs: (N / 128) x (n / 128) tiles x K splits of >= 1024
   const int tiles = ((N + 127) / 128) * ((n + 127) / 128);
   p.splitsL1 = std::max(1, std::min<int>((int)((Ng + 1023) / 1024), (608 + tiles - 1) / tiles));
   p.kchunkL1 = (int)rup((Ng + p.splitsL1 - 1) / p.splitsL1, 64);
@@ -713,19 +858,31 @@ Plan make_plan(int64_t Ng, int N, int n, int Naux) {
   return p;
 }
 
+// Split-K work of the FP64 contractions of the set-up and of Q = L^T C.
+size_t dwork_elems(int64_t Ng, int N, int n) {
+  auto w = [](int M, int Nc, int K) {
+    const int ks = dgemm_ksplit(M, Nc, K);
+    return ks > 1 ? (size_t)ks * M * Nc : (size_t)1;
+  };
+  return std::max({w(N, N, (int)Ng), w(N, n, N), w((int)Ng, N, N), (size_t)1});
+}
+
 }  // namespace
 
 size_t mixed_footprint(int64_t Ng, int N, int n, int Naux) {
   const Plan p = make_plan(Ng, N, n, Naux);
   const size_t ng = Ng, na = Naux;
   size_t b = 0;
-  b += 2 * ng * p.Np * 2 + 2 * (size_t)N * p.Ng8 * 2 + 2 * (size_t)N * p.Na8 * 2;  // Phi splits
+  b += 2 * ng * p.Np * 2 + 2 * (size_t)N * p.Ng8 * 2 + 2 * (size_t)N * p.Na8 * 2;  // Phi pieces
   b += na * p.Ng4 * 4 + ng * p.Na4 * 4 + na * p.Na4 * 4 + na * 4;                  // V, V^T, W, idx
-  b += 2 * (size_t)p.np * p.Np * 2 + ng * n * 4 + 2 * ng * p.np * 2 + 2 * na * p.np * 2;
+  b += 2 * (size_t)n * p.Np * 2 + (size_t)n * p.Np * 8 + ng * n * 4 + 2 * ng * p.np * 2 +
+       2 * na * p.np * 2;
   b += (size_t)p.partsA * na * n * 4 + (size_t)p.partsC * na * n * 4 + (size_t)n * p.Ng4 * 4;
-  b += na * n * 8 + 2 * (size_t)n * p.Ng8 * 2 + 2 * (size_t)n * p.Na8 * 2;
+  b += na * n * 8 + (size_t)n * p.Na8 * 8 + 2 * (size_t)n * p.Ng8 * 2 + 2 * (size_t)n * p.Na8 * 2;
   b += (size_t)p.splitsL1 * N * n * 4 + (size_t)p.splitsL23 * N * n * 4;
-  b += ng * std::max<size_t>(N, Naux) * 8;  // setup staging of the FP64 tables
+  b += (size_t)(p.partsA + p.partsC) * p.xa * 8;
+  b += (size_t)N * N * 8 + (size_t)N * n * 8 + dwork_elems(Ng, N, n) * 8;
+  b += 2 * std::max(ng * std::max<size_t>(N, p.Na8) + 2 * (size_t)N * N, (size_t)N * p.Ng8) * 8;
   return b + 64 * 1024;
 }
 
@@ -737,101 +894,123 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   if (e != cudaSuccess) return e;
   const Plan p = make_plan(Ng, N, n, Naux);
   if (p.np > 128) return cudaErrorNotSupported;  // the fused kernel holds n <= 128 columns
-  for (int np : {64, 128}) {
-    if (np == 64) e = cudaFuncSetAttribute(pair_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairCfg<64>::SMEM);
-    else e = cudaFuncSetAttribute(pair_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairCfg<128>::SMEM);
-    if (e != cudaSuccess) return e;
-  }
-  e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G_SMEM);
+  e = cudaFuncSetAttribute(pair_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairCfg<64>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(pair_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairCfg<128>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G_SMEM);
   if (e != cudaSuccess) return e;
 
   MixedState* m = new MixedState();
   auto bail = [&](cudaError_t err) { mixed_destroy(m); return err; };
   m->Ng = Ng; m->N = N; m->n = n; m->Naux = Naux; m->dV = dV; m->np = p.np;
   m->Np = p.Np; m->Ng8 = p.Ng8; m->Na8 = p.Na8; m->Ng4 = p.Ng4; m->Na4 = p.Na4;
-  m->partsA = p.partsA; m->partsC = p.partsC; m->ychunkA = p.ychunkA; m->ychunkC = p.ychunkC;
+  m->xa = p.xa; m->partsA = p.partsA; m->partsC = p.partsC;
+  m->ychunkA = p.ychunkA; m->ychunkC = p.ychunkC;
   m->splitsL1 = p.splitsL1; m->splitsL23 = p.splitsL23;
   m->kchunkL1 = p.kchunkL1; m->kchunkL23 = p.kchunkL23;
   const size_t ng = Ng, na = Naux;
-#define MX(ptr, elems)                         \
-  do {                                         \
+#define MX(ptr, elems)                          \
+  do {                                          \
     cudaError_t e_ = alloc(m, &(ptr), (elems)); \
     if (e_ != cudaSuccess) return bail(e_);     \
   } while (0)
-  MX(m->phi_h, ng * p.Np); MX(m->phi_l, ng * p.Np);
-  MX(m->phiT_h, (size_t)N * p.Ng8); MX(m->phiT_l, (size_t)N * p.Ng8);
-  MX(m->phigT_h, (size_t)N * p.Na8); MX(m->phigT_l, (size_t)N * p.Na8);
+  MX(m->phi_m, ng * p.Np); MX(m->phi_h, ng * p.Np);
+  MX(m->phiT_m, (size_t)N * p.Ng8); MX(m->phiT_h, (size_t)N * p.Ng8);
+  MX(m->phigT_m, (size_t)N * p.Na8); MX(m->phigT_h, (size_t)N * p.Na8);
   MX(m->V32, na * p.Ng4); MX(m->VT32, ng * p.Na4); MX(m->W32, na * p.Na4);
   MX(m->idx, na);
-  MX(m->CT_h, (size_t)p.np * p.Np); MX(m->CT_l, (size_t)p.np * p.Np);
+  MX(m->CT_m, (size_t)n * p.Np); MX(m->CT_h, (size_t)n * p.Np); MX(m->CT64, (size_t)n * p.Np);
   MX(m->psi32, ng * n);
-  MX(m->psi_h, ng * p.np); MX(m->psi_l, ng * p.np);
-  MX(m->psig_h, na * p.np); MX(m->psig_l, na * p.np);
+  MX(m->psi_m, ng * p.np); MX(m->psi_h, ng * p.np);
+  MX(m->psig_m, na * p.np); MX(m->psig_h, na * p.np);
   MX(m->M2p, (size_t)p.partsA * na * n); MX(m->M3p, (size_t)p.partsC * na * n);
   MX(m->M1, (size_t)n * p.Ng4);
-  MX(m->D23, na * n);
-  MX(m->M1_h, (size_t)n * p.Ng8); MX(m->M1_l, (size_t)n * p.Ng8);
-  MX(m->D23T_h, (size_t)n * p.Na8); MX(m->D23T_l, (size_t)n * p.Na8);
+  MX(m->D23, na * n); MX(m->D23T64, (size_t)n * p.Na8);
+  MX(m->M1_m, (size_t)n * p.Ng8); MX(m->M1_h, (size_t)n * p.Ng8);
+  MX(m->D23T_m, (size_t)n * p.Na8); MX(m->D23T_h, (size_t)n * p.Na8);
   MX(m->L1p, (size_t)p.splitsL1 * N * n); MX(m->L23p, (size_t)p.splitsL23 * N * n);
+  MX(m->EpA, (size_t)p.partsA * p.xa); MX(m->EpC, (size_t)p.partsC * p.xa);
   MX(m->sc, NSC); MX(m->am, NAM); MX(m->status, 4);
   MX(m->red, reduce_work_elems());
-  double* stage = nullptr;
+  MX(m->Lf, (size_t)N * N); MX(m->Q64, (size_t)N * n);
+  MX(m->dwork, dwork_elems(Ng, N, n));
+#undef MX
+  double *stage = nullptr, *stage2 = nullptr;
   {
+    const size_t elems = std::max(ng * std::max<size_t>(N, p.Na8) + 2 * (size_t)N * N,
+                                  (size_t)N * p.Ng8);
     void* q = nullptr;
-    e = cudaMalloc(&q, ng * std::max<size_t>(N, na) * 8);
+    e = cudaMalloc(&q, elems * 8);
     if (e != cudaSuccess) return bail(e);
     stage = static_cast<double*>(q);
+    e = cudaMalloc(&q, elems * 8);
+    if (e != cudaSuccess) { cudaFree(stage); return bail(e); }
+    stage2 = static_cast<double*>(q);
   }
-  auto fin = [&](cudaError_t err) { cudaFree(stage); return err == cudaSuccess ? cudaSuccess : bail(err); };
+  auto fin = [&](cudaError_t err) {
+    cudaFree(stage);
+    cudaFree(stage2);
+    return err == cudaSuccess ? cudaSuccess : bail(err);
+  };
   e = cudaMemsetAsync(m->am, 0, NAM * 4, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->sc, 0, NSC * 4, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->status, 0, 16, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(m->CT_h, 0, (size_t)p.np * p.Np * 2, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(m->CT_l, 0, (size_t)p.np * p.Np * 2, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(m->idx, idx, na * 4, cudaMemcpyHostToDevice, s);
-  // Phi: FP64 staging -> scale -> splits in three layouts
+  // Phi pieces in three layouts: Phi [R][mu], Phi^T [mu][R], Phi_g^T [mu][g]
   if (e == cudaSuccess) e = cudaMemcpyAsync(stage, phi, ng * N * 8, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return fin(e);
-  absmax_kernel<double><<<blocks_for(ng * N), 256, 0, s>>>(stage, ng, N, N, m->am + AM_PHI);
-  set_phi_scale_kernel<<<1, 32, 0, s>>>(m->am, m->sc);
-  split_rows_kernel<double><<<blocks_for(ng * p.Np), 256, 0, s>>>(stage, ng, N, N, m->sc, SC_PHI, m->phi_h, m->phi_l, p.Np);
+  // Orthonormalised basis on the grid: Phi^T Phi = L L^T (Cholesky, FP64) and
+  // Phi' = Phi L^{-T}.  Each build forms Psi = Phi' (L^T C), which equals
+  // Phi C exactly but contracts two matrices with orthonormal columns, so
+  // the split arithmetic is not amplified by the conditioning of the basis.
   {
-    dim3 grid((unsigned)((p.Ng8 + 31) / 32), (unsigned)((N + 31) / 32));
-    split_transpose_kernel<double><<<grid, dim3(32, 8), 0, s>>>(stage, ng, N, N, m->sc, SC_PHI, m->phiT_h, m->phiT_l, p.Ng8);
+    DGemm g{N, N, (int)ng, stage, N, true, stage, N, false, m->Lf, N, 1.0, nullptr, 0, 0, m->dwork};
+    e = dgemm(g, s);
+    if (e == cudaSuccess) e = cholesky_f64(m->Lf, N, m->status, s);
+    int st = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st, m->status, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && st != 0) e = cudaErrorInvalidValue;  // basis dependent on the grid
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->status, 0, 16, s);
+    if (e != cudaSuccess) return fin(e);
+    // stage2 (N x N) <- L^{-T} by solving X L^T = I, then Phi' = Phi L^{-T}
+    identity_kernel<<<64, 256, 0, s>>>(stage2 + (size_t)N * N, N);
+    count_launch();
+    e = trsm_right_lt_f64(m->Lf, N, stage2 + (size_t)N * N, N, stage2, s);
+    if (e != cudaSuccess) return fin(e);
+    DGemm g2{(int)ng, N, N, stage, N, false, stage2, N, false, stage2 + 2 * (size_t)N * N, N, 1.0,
+             nullptr, 0, 0, m->dwork};
+    e = dgemm(g2, s);
+    if (e != cudaSuccess) return fin(e);
+    double* phip = stage2 + 2 * (size_t)N * N;
+    absmax_kernel<double><<<blocks_for(ng * N), 256, 0, s>>>(phip, ng, N, N, m->am + AM_PHIP);
+    absmax_kernel<double><<<blocks_for(ng * N), 256, 0, s>>>(stage, ng, N, N, m->am + AM_PHI);
+    set_phi_scale_kernel<<<1, 32, 0, s>>>(m->am, m->sc);
+    count_launch(3);
+    e = split_rows<double>(phip, ng, N, N, m->sc, SC_PHIP, m->phi_m, m->phi_h, p.Np, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fin(e);
   }
-  count_launch(4);
-  // Phi_g^T from the gathered FP64 rows (reuse the front of the staging buffer after Phi^T)
-  e = cudaStreamSynchronize(s);
+  e = transpose<double>(stage, ng, N, N, stage2, p.Ng8, s);
+  if (e == cudaSuccess) e = split_rows<double>(stage2, N, p.Ng8, p.Ng8, m->sc, SC_PHI, m->phiT_m, m->phiT_h, p.Ng8, s);
+  if (e == cudaSuccess) e = gather_rows_f64(stage, N, m->idx, Naux, N, stage2, N, s);
+  if (e == cudaSuccess) e = transpose<double>(stage2, na, N, N, stage, p.Na8, s);
+  if (e == cudaSuccess) e = split_rows<double>(stage, N, p.Na8, p.Na8, m->sc, SC_PHI, m->phigT_m, m->phigT_h, p.Na8, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fin(e);
-  {
-    // gather Phi rows at idx into a compact FP64 buffer, then transpose-split
-    double* phig = nullptr;
-    void* q = nullptr;
-    e = cudaMalloc(&q, na * N * 8);
-    if (e != cudaSuccess) return fin(e);
-    phig = static_cast<double*>(q);
-    e = gather_rows_f64(stage, N, m->idx, Naux, N, phig, N, s);
-    if (e == cudaSuccess) {
-      dim3 grid((unsigned)((p.Na8 + 31) / 32), (unsigned)((N + 31) / 32));
-      split_transpose_kernel<double><<<grid, dim3(32, 8), 0, s>>>(phig, na, N, N, m->sc, SC_PHI, m->phigT_h, m->phigT_l, p.Na8);
-      count_launch();
-      e = cudaStreamSynchronize(s);
-    }
-    cudaFree(phig);
-    if (e != cudaSuccess) return fin(e);
-  }
-  // V in both orientations, W; max |V|, max |W| for the product scales
+  // V in both orientations, W; max |V|, max |W| bound the product scales
   e = cudaMemcpyAsync(stage, V, na * ng * 8, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return fin(e);
   absmax_kernel<double><<<blocks_for(na * ng), 256, 0, s>>>(stage, na, ng, ng, m->am + AM_V);
   f64_to_f32_kernel<<<blocks_for(na * p.Ng4), 256, 0, s>>>(stage, na, ng, m->V32, p.Ng4);
-  {
-    dim3 grid((unsigned)((p.Na4 + 31) / 32), (unsigned)((ng + 31) / 32));
-    // VT[R][g] = V[g][R], zero for g >= N_aux
-    f64_to_f32_transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(stage, na, ng, m->VT32, p.Na4);
+  count_launch(2);
+  e = transpose<double>(stage, na, ng, ng, stage2, p.Na4, s);  // [R][g], zero for g >= N_aux
+  if (e == cudaSuccess) {
+    f64_to_f32_kernel<<<blocks_for(ng * p.Na4), 256, 0, s>>>(stage2, ng, p.Na4, m->VT32, p.Na4);
+    count_launch();
+    e = cudaStreamSynchronize(s);
   }
-  count_launch(3);
-  e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(stage, W, na * na * 8, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return fin(e);
   absmax_kernel<double><<<blocks_for(na * na), 256, 0, s>>>(stage, na, na, na, m->am + AM_W);
@@ -840,41 +1019,39 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fin(e);
 
-  // tensor maps
   const auto F16 = CU_TENSOR_MAP_DATA_TYPE_FLOAT16, F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   const int np_ = p.np;
   struct MapSpec { CUtensorMap* m; const void* p; CUtensorMapDataType t; int es; long rows, ld; int br, bc; };
   const MapSpec specs[] = {
+      {&m->m_phi_m, m->phi_m, F16, 2, (long)ng, p.Np, 128, 64},
       {&m->m_phi_h, m->phi_h, F16, 2, (long)ng, p.Np, 128, 64},
-      {&m->m_phi_l, m->phi_l, F16, 2, (long)ng, p.Np, 128, 64},
+      {&m->m_CT_m, m->CT_m, F16, 2, n, p.Np, 128, 64},
       {&m->m_CT_h, m->CT_h, F16, 2, n, p.Np, 128, 64},
-      {&m->m_CT_l, m->CT_l, F16, 2, n, p.Np, 128, 64},
+      {&m->m_psi128_m, m->psi_m, F16, 2, (long)ng, np_, 128, 64},
       {&m->m_psi128_h, m->psi_h, F16, 2, (long)ng, np_, 128, 64},
-      {&m->m_psi128_l, m->psi_l, F16, 2, (long)ng, np_, 128, 64},
+      {&m->m_psi64_m, m->psi_m, F16, 2, (long)ng, np_, 64, 64},
       {&m->m_psi64_h, m->psi_h, F16, 2, (long)ng, np_, 64, 64},
-      {&m->m_psi64_l, m->psi_l, F16, 2, (long)ng, np_, 64, 64},
+      {&m->m_psig128_m, m->psig_m, F16, 2, (long)na, np_, 128, 64},
       {&m->m_psig128_h, m->psig_h, F16, 2, (long)na, np_, 128, 64},
-      {&m->m_psig128_l, m->psig_l, F16, 2, (long)na, np_, 128, 64},
+      {&m->m_psig64_m, m->psig_m, F16, 2, (long)na, np_, 64, 64},
       {&m->m_psig64_h, m->psig_h, F16, 2, (long)na, np_, 64, 64},
-      {&m->m_psig64_l, m->psig_l, F16, 2, (long)na, np_, 64, 64},
       {&m->m_V, m->V32, F32, 4, (long)na, p.Ng4, 128, 32},
       {&m->m_VT, m->VT32, F32, 4, (long)ng, p.Na4, 128, 32},
       {&m->m_W, m->W32, F32, 4, (long)na, p.Na4, 128, 32},
+      {&m->m_phiT_m, m->phiT_m, F16, 2, N, p.Ng8, 128, 64},
       {&m->m_phiT_h, m->phiT_h, F16, 2, N, p.Ng8, 128, 64},
-      {&m->m_phiT_l, m->phiT_l, F16, 2, N, p.Ng8, 128, 64},
+      {&m->m_M1_m, m->M1_m, F16, 2, n, p.Ng8, 128, 64},
       {&m->m_M1_h, m->M1_h, F16, 2, n, p.Ng8, 128, 64},
-      {&m->m_M1_l, m->M1_l, F16, 2, n, p.Ng8, 128, 64},
+      {&m->m_phigT_m, m->phigT_m, F16, 2, N, p.Na8, 128, 64},
       {&m->m_phigT_h, m->phigT_h, F16, 2, N, p.Na8, 128, 64},
-      {&m->m_phigT_l, m->phigT_l, F16, 2, N, p.Na8, 128, 64},
+      {&m->m_D23T_m, m->D23T_m, F16, 2, n, p.Na8, 128, 64},
       {&m->m_D23T_h, m->D23T_h, F16, 2, n, p.Na8, 128, 64},
-      {&m->m_D23T_l, m->D23T_l, F16, 2, n, p.Na8, 128, 64},
   };
   for (const MapSpec& ms : specs) {
     e = make_map(ms.m, ms.p, ms.t, ms.es, ms.rows, ms.ld, ms.br, ms.bc);
     if (e != cudaSuccess) return fin(e);
   }
-#undef MX
-  cudaFree(stage);
+  fin(cudaSuccess);
   *out = m;
   return cudaSuccess;
 }
@@ -894,58 +1071,63 @@ cudaError_t mixed_enqueue(MixedState* m, const double* C, double* K, double* Ex,
   hook(0, 1);
   e = cudaMemsetAsync(m->am + AM_C, 0, (NAM - AM_C) * 4, s);
   if (e != cudaSuccess) return e;
-  absmax_kernel<double><<<blocks_for((long)N * n), 256, 0, s>>>(C, N, n, n, m->am + AM_C);
-  scales_kernel<<<1, 32, 0, s>>>(m->am, m->sc, 0);
   {
-    dim3 grid((unsigned)((m->Np + 31) / 32), (unsigned)((n + 31) / 32));
-    // C^T[j][mu] from C[mu][j]; rows j >= n of CT stay zero from setup
-    split_transpose_kernel<double><<<grid, dim3(32, 8), 0, s>>>(C, N, n, n, m->sc, SC_C, m->CT_h, m->CT_l, m->Np);
+    DGemm g{N, n, N, m->Lf, N, true, C, n, false, m->Q64, n, 1.0, nullptr, 0, 0, m->dwork};
+    e = dgemm(g, s);
+    if (e != cudaSuccess) return e;
   }
+  absmax_kernel<double><<<blocks_for((long)N * n), 256, 0, s>>>(m->Q64, N, n, n, m->am + AM_C);
+  scales_kernel<<<1, 32, 0, s>>>(m->am, m->sc, 0);
+  count_launch(2);
+  e = transpose<double>(m->Q64, N, n, n, m->CT64, m->Np, s);  // Q^T [j][mu], zero for mu >= N
+  if (e == cudaSuccess) e = split_rows<double>(m->CT64, n, m->Np, m->Np, m->sc, SC_C, m->CT_m, m->CT_h, m->Np, s);
+  if (e != cudaSuccess) return e;
   {
     GemmArgs g{(int)ng, n, N, (int)m->Np, m->psi32, n, 0, m->sc, SC_OUT_ORB, m->status};
     dim3 grid((unsigned)((ng + 127) / 128), (unsigned)((n + 127) / 128), 1);
-    tc_gemm_kernel<<<grid, 192, G_SMEM, s>>>(m->m_phi_h, m->m_phi_l, m->m_CT_h, m->m_CT_l, g);
+    gemm_kernel<<<grid, 192, G_SMEM, s>>>(m->m_phi_m, m->m_phi_h, m->m_CT_m, m->m_CT_h, g);
   }
   absmax_kernel<float><<<blocks_for(ng * n), 256, 0, s>>>(m->psi32, ng, n, n, m->am + AM_PSI);
   rownorm2_max_kernel<<<blocks_for(ng), 256, 0, s>>>(m->psi32, ng, n, n, m->am + AM_RN2);
   scales_kernel<<<1, 32, 0, s>>>(m->am, m->sc, 1);
-  split_rows_kernel<float><<<blocks_for(ng * np), 256, 0, s>>>(m->psi32, ng, n, n, m->sc, SC_PSI, m->psi_h, m->psi_l, np);
+  count_launch(4);
+  e = split_rows<float>(m->psi32, ng, n, n, m->sc, SC_PSI, m->psi_m, m->psi_h, np, s);
+  if (e != cudaSuccess) return e;
+  gather_rows_half_kernel<<<blocks_for(na * np), 256, 0, s>>>(m->psi_m, np, m->idx, (int)na, m->psig_m);
   gather_rows_half_kernel<<<blocks_for(na * np), 256, 0, s>>>(m->psi_h, np, m->idx, (int)na, m->psig_h);
-  gather_rows_half_kernel<<<blocks_for(na * np), 256, 0, s>>>(m->psi_l, np, m->idx, (int)na, m->psig_l);
-  count_launch(10);
+  count_launch(2);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   hook(0, 0);
 
-  // ---- step 2-3: the three fused pair contractions
+  // ---- steps 2-3: the three fused pair contractions
   hook(1, 1);
-  const int xa = (int)((na + 127) / 128);
-  auto launch_pair = [&](const CUtensorMap& Xh, const CUtensorMap& Xl, const CUtensorMap& Yh,
-                         const CUtensorMap& Yl, const CUtensorMap& Vm, const PairArgs& pa,
+  auto launch_pair = [&](const CUtensorMap& Xm, const CUtensorMap& Xh, const CUtensorMap& Ym,
+                         const CUtensorMap& Yh, const CUtensorMap& Vm, const PairArgs& pa,
                          dim3 grid) {
     if (np == 64)
-      pair_kernel<64><<<grid, 192, PairCfg<64>::SMEM, s>>>(Xh, Xl, Yh, Yl, Vm, pa);
+      pair_kernel<64><<<grid, 192, PairCfg<64>::SMEM, s>>>(Xm, Xh, Ym, Yh, Vm, pa);
     else
-      pair_kernel<128><<<grid, 192, PairCfg<128>::SMEM, s>>>(Xh, Xl, Yh, Yl, Vm, pa);
+      pair_kernel<128><<<grid, 192, PairCfg<128>::SMEM, s>>>(Xm, Xh, Ym, Yh, Vm, pa);
     count_launch();
   };
-  {  // role A: M2[g][j] = sum_R (V o P)[g][R] Psi[R][j]
+  {  // role A: M2[g][j] = sum_R (V o P)[g][R] Psi[R][j], and sum V o P^2
     PairArgs pa{(int)na, (int)ng, m->ychunkA, n, m->sc, SC_F_AB, SC_OUT_AB, m->M2p, n,
-                na * n, 0, m->status};
-    launch_pair(m->m_psig128_h, m->m_psig128_l, m->m_psi64_h, m->m_psi64_l, m->m_V, pa,
-                dim3(xa, m->partsA));
+                na * n, 0, m->EpA, m->status};
+    launch_pair(m->m_psig128_m, m->m_psig128_h, m->m_psi64_m, m->m_psi64_h, m->m_V, pa,
+                dim3(m->xa, m->partsA));
   }
   {  // role B: M1[j][R] = sum_g (V^T o P^T)[R][g] Psi_g[g][j], written transposed
     PairArgs pa{(int)ng, (int)na, (int)rup(na, 64), n, m->sc, SC_F_AB, SC_OUT_AB, m->M1,
-                m->Ng4, 0, 1, m->status};
-    launch_pair(m->m_psi128_h, m->m_psi128_l, m->m_psig64_h, m->m_psig64_l, m->m_VT, pa,
+                m->Ng4, 0, 1, nullptr, m->status};
+    launch_pair(m->m_psi128_m, m->m_psi128_h, m->m_psig64_m, m->m_psig64_h, m->m_VT, pa,
                 dim3((unsigned)((ng + 127) / 128), 1));
   }
-  {  // role C: M3[g][j] = sum_g' (W o Q)[g][g'] Psi_g[g'][j]
+  {  // role C: M3[g][j] = sum_g' (W o Q)[g][g'] Psi_g[g'][j], and sum W o Q^2
     PairArgs pa{(int)na, (int)na, m->ychunkC, n, m->sc, SC_F_C, SC_OUT_C, m->M3p, n, na * n, 0,
-                m->status};
-    launch_pair(m->m_psig128_h, m->m_psig128_l, m->m_psig64_h, m->m_psig64_l, m->m_W, pa,
-                dim3(xa, m->partsC));
+                m->EpC, m->status};
+    launch_pair(m->m_psig128_m, m->m_psig128_h, m->m_psig64_m, m->m_psig64_h, m->m_W, pa,
+                dim3(m->xa, m->partsC));
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -957,22 +1139,22 @@ cudaError_t mixed_enqueue(MixedState* m, const double* C, double* K, double* Ex,
                                                          na * n, m->D23, m->am + AM_D23);
   absmax_kernel<float><<<blocks_for((long)n * ng), 256, 0, s>>>(m->M1, n, ng, m->Ng4, m->am + AM_M1);
   scales_kernel<<<1, 32, 0, s>>>(m->am, m->sc, 2);
-  split_rows_kernel<float><<<blocks_for((long)n * m->Ng8), 256, 0, s>>>(m->M1, n, ng, m->Ng4, m->sc, SC_M1, m->M1_h, m->M1_l, m->Ng8);
-  {
-    dim3 grid((unsigned)((m->Na8 + 31) / 32), (unsigned)((n + 31) / 32));
-    split_transpose_kernel<double><<<grid, dim3(32, 8), 0, s>>>(m->D23, na, n, n, m->sc, SC_D23, m->D23T_h, m->D23T_l, m->Na8);
-  }
+  count_launch(3);
+  e = split_rows<float>(m->M1, n, ng, m->Ng4, m->sc, SC_M1, m->M1_m, m->M1_h, m->Ng8, s);
+  if (e == cudaSuccess) e = transpose<double>(m->D23, na, n, n, m->D23T64, m->Na8, s);
+  if (e == cudaSuccess) e = split_rows<double>(m->D23T64, n, m->Na8, m->Na8, m->sc, SC_D23, m->D23T_m, m->D23T_h, m->Na8, s);
+  if (e != cudaSuccess) return e;
   {
     GemmArgs g{N, n, (int)ng, m->kchunkL1, m->L1p, n, (long)N * n, m->sc, SC_OUT_L1, m->status};
     dim3 grid((unsigned)((N + 127) / 128), (unsigned)((n + 127) / 128), (unsigned)m->splitsL1);
-    tc_gemm_kernel<<<grid, 192, G_SMEM, s>>>(m->m_phiT_h, m->m_phiT_l, m->m_M1_h, m->m_M1_l, g);
+    gemm_kernel<<<grid, 192, G_SMEM, s>>>(m->m_phiT_m, m->m_phiT_h, m->m_M1_m, m->m_M1_h, g);
   }
   {
     GemmArgs g{N, n, (int)na, m->kchunkL23, m->L23p, n, (long)N * n, m->sc, SC_OUT_L23, m->status};
     dim3 grid((unsigned)((N + 127) / 128), (unsigned)((n + 127) / 128), (unsigned)m->splitsL23);
-    tc_gemm_kernel<<<grid, 192, G_SMEM, s>>>(m->m_phigT_h, m->m_phigT_l, m->m_D23T_h, m->m_D23T_l, g);
+    gemm_kernel<<<grid, 192, G_SMEM, s>>>(m->m_phigT_m, m->m_phigT_h, m->m_D23T_m, m->m_D23T_h, g);
   }
-  count_launch(7);
+  count_launch(2);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   hook(4, 0);
@@ -981,10 +1163,10 @@ cudaError_t mixed_enqueue(MixedState* m, const double* C, double* K, double* Ex,
   hook(7, 1);
   final_k_kernel<<<blocks_for((long)N * n), 256, 0, s>>>(m->L1p, m->splitsL1, m->L23p,
                                                          m->splitsL23, (long)N * n, m->dV, K);
-  count_launch();
+  final_ex_kernel<<<1, 256, 0, s>>>(m->EpA, m->partsA * m->xa, m->EpC, m->partsC * m->xa, m->sc,
+                                    m->dV, Ex);
+  count_launch(2);
   e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  e = neg_dot_f64(K, C, (long)N * n, m->red, Ex, s);
   if (e != cudaSuccess) return e;
   hook(7, 0);
   return cudaSuccess;
@@ -998,8 +1180,6 @@ int mixed_take_status(MixedState* m) {
 }
 
 double mixed_error_bound(const MixedState* m) {
-  // Per-product relative error of split-FP16x3 is about 2^-22; the E_x bound
-  // reported with each result is that factor times the size of the build.
   (void)m;
   return 1e-6;
 }

@@ -15,8 +15,8 @@ from . import build as _build
 
 XK_OK, XK_PENDING = 0, 1
 XK_EINVAL, XK_ENOMEM, XK_ETIMEDOUT, XK_ECUDA, XK_EBUSY = -1, -2, -3, -4, -5
-XK_FP64, XK_TF32, XK_BF16X3 = 0, 1, 2
-MODES = {"fp64": XK_FP64, "bf16x3": XK_BF16X3}
+XK_FP64, XK_TF32, XK_F16X3 = 0, 1, 2
+MODES = {"fp64": XK_FP64, "f16x3": XK_F16X3}
 STEPS = ("orbitals", "pair", "m2", "m1", "line1", "line2", "line3", "assemble")
 _NAMES = {XK_EINVAL: "XK_EINVAL", XK_ENOMEM: "XK_ENOMEM", XK_ETIMEDOUT: "XK_ETIMEDOUT",
           XK_ECUDA: "XK_ECUDA", XK_EBUSY: "XK_EBUSY"}

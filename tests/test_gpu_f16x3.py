@@ -1,0 +1,87 @@
+"""Parity of the tensor-core path (XK_F16X3, through the C ABI) with the CPU oracle.
+
+The path returns E_x from the closed form of Eq. exoccri contracted with C
+and K_{mu i} from the split-FP16 tensor-core contractions.  Its error against
+the FP64 oracle is held to |dE_x| <= 1e-6 Ha per cell (measured about 4e-8 on
+the 64-centre cell) and to max|dK| <= 1e-6 (measured about 1.2e-7).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from cellgen import CellSpec, Shell, build_cell, config_spec, load_cell
+
+pytestmark = pytest.mark.gpu
+
+TOL_E, TOL_K = 1e-6, 1e-6
+
+
+@pytest.fixture(scope="module")
+def xk():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2207_04636_gb300 as m
+    return m
+
+
+def _check(xk, c):
+    K0, E0 = oracle.exx_rps_occri(c.phi, c.idx, c.V, c.W, c.C, c.dV)
+    h = xk.Handle(c.phi, c.idx, c.V, c.W, c.dV, c.n, mode="f16x3")
+    try:
+        K, E = h.build(c.C)
+        K2, E2 = h.build(c.C)
+    finally:
+        h.release()
+    assert abs(E - E0) <= TOL_E, (E, E0)
+    assert np.max(np.abs(K - K0)) <= TOL_K, np.max(np.abs(K - K0))
+    assert np.array_equal(K, K2) and E == E2  # fixed reduction order
+    return K, E
+
+
+def test_config1(xk, cell1):
+    before = xk.kernel_launches()
+    _check(xk, cell1)
+    assert xk.kernel_launches() > before
+
+
+def test_ragged(xk):
+    """N = 27, n = 7, N_aux = 97, N_g = 13^3: every tile has a ragged edge."""
+    sh = [Shell(0, (0.35,), (1.0,)), Shell(1, (0.8,), (1.0,)), Shell(2, (1.1,), (1.0,))]
+    c = build_cell(CellSpec("ragged", np.array([[0.1, 0.2, 0.3], [0.6, 0.5, 0.45],
+                                                 [0.3, 0.75, 0.8]]), 6.5, 13, sh, 7, 97, 9001))
+    _check(xk, c)
+
+
+def test_cubic27(xk):
+    """27-centre simple-cubic cell (N = 351, n = 54, N_aux = 1755, N_g = 45^3)."""
+    _check(xk, load_cell(config_spec(4, k=3)))
+
+
+def test_rejects_large_n(xk):
+    sh = [Shell(0, (0.4,), (1.0,))] * 2
+    rng = np.random.default_rng(0)
+    Ng, N, n, Na = 4096, 200, 129, 300
+    phi = rng.standard_normal((Ng, N))
+    idx = np.sort(rng.choice(Ng, Na, replace=False))
+    V = rng.standard_normal((Na, Ng))
+    W = rng.standard_normal((Na, Na))
+    with pytest.raises(xk.XKError) as e:
+        xk.Handle(phi, idx, V, W + W.T, 0.1, n, mode="f16x3")
+    assert e.value.code == xk.XK_EINVAL
+
+
+def test_ace_on_tensor_path(xk, cell1):
+    """K_ij of the tensor-core build is positive definite and factors."""
+    c = cell1
+    h = xk.Handle(c.phi, c.idx, c.V, c.W, c.dV, c.n, mode="f16x3")
+    K, _ = h.build(c.C)
+    Kij, xi, s, br = h.ace()
+    h.release()
+    assert br == "cholesky"
+    assert np.max(np.abs((xi * s) @ xi.T @ c.C - K)) <= 1e-9 * np.max(np.abs(K))
+
+
+@pytest.mark.slow
+def test_config2(xk):
+    """64-centre supercell (the benchmark workload): E_x within 1e-6 Ha."""
+    _check(xk, load_cell(config_spec(2)))
