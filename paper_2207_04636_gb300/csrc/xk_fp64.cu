@@ -106,7 +106,7 @@ int choose_ksplit(int M, int N, int K) {
   const long target = 4L * 152;  // about four waves of CTAs over 152 SMs
   if (tiles >= target) return 1;
   long ks = (target + tiles - 1) / tiles;
-  ks = std::min<long>(ks, std::max(1, K / 256));
+  ks = std::min<long>(ks, std::max(1, K / 64));
   return (int)std::max<long>(1, std::min<long>(ks, 64));
 }
 

@@ -65,7 +65,8 @@ enum {
   SC_PHIP,      // Phi' = Phi L^{-T} (the orbital contraction)
   NSC
 };
-enum { AM_PHI = 0, AM_V, AM_W, AM_PHIP, AM_C, AM_PSI, AM_RN2, AM_M1, AM_D23, NAM };
+enum { AM_PHI = 0, AM_V, AM_W, AM_PHIP, AM_PHIP_RN, AM_C, AM_QCN, AM_PSI, AM_RN2, AM_M1, AM_D23,
+       NAM };
 
 constexpr float kHalfTarget = 16384.0f;  // 2^14: split inputs are scaled to |x| <= 2^14
 constexpr float kProdTarget = 32768.0f;  // 2^15: V o P is scaled to |x| <= 2^15
@@ -87,9 +88,11 @@ __global__ void scales_kernel(const unsigned* __restrict__ am, float* __restrict
   if (stage == 0) {
     sc[SC_C] = pow2_scale(am_get(am, AM_C), kHalfTarget);
     sc[SC_OUT_ORB] = 1.0f / (sc[SC_PHIP] * sc[SC_C]);
+    // |Psi(R,j)| <= |Phi'(R,:)| |Q(:,j)| (Cauchy-Schwarz) bounds the orbital scale
+    sc[SC_PSI] = pow2_scale(sqrtf(am_get(am, AM_PHIP_RN)) * sqrtf(am_get(am, AM_QCN)) * 1.0001f,
+                            kHalfTarget);
   } else if (stage == 1) {
-    const float sp = pow2_scale(am_get(am, AM_PSI), kHalfTarget);
-    sc[SC_PSI] = sp;
+    const float sp = sc[SC_PSI];
     // |P(g,R)| <= max_R sum_i psi_i(R)^2 (Cauchy-Schwarz), so |V o P| <= max|V| rn2
     const float rn2 = am_get(am, AM_RN2) * sp * sp;
     const float fab = pow2_scale(am_get(am, AM_V) * rn2, kProdTarget);
@@ -133,21 +136,59 @@ __global__ void absmax_kernel(const T* __restrict__ a, long rows, long cols, lon
   if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
-// max over rows of sum_c a[r][c]^2 (rows of Psi: the orbital density at R).
-__global__ void rownorm2_max_kernel(const float* __restrict__ a, long rows, int cols, long ld,
+// max over rows of sum_c a[r][c]^2.
+template <class T>
+__global__ void rownorm2_max_kernel(const T* __restrict__ a, long rows, int cols, long ld,
                                     unsigned* __restrict__ out) {
   float m = 0.0f;
   for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < rows;
        r += (long)gridDim.x * blockDim.x) {
     float s = 0.0f;
     for (int c = 0; c < cols; ++c) {
-      const float v = a[r * ld + c];
+      const float v = (float)a[r * ld + c];
       s = fmaf(v, v, s);
     }
     m = fmaxf(m, s);
   }
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m * 1.0001f));
+}
+
+// max over columns of sum_r a[r][c]^2 (one block per column).
+__global__ void colnorm2_max_kernel(const double* __restrict__ a, long rows, long ld,
+                                    unsigned* __restrict__ out) {
+  __shared__ float red[8];
+  const long c = blockIdx.x;
+  float s = 0.0f;
+  for (long r = threadIdx.x; r < rows; r += blockDim.x) {
+    const float v = (float)a[r * ld + c];
+    s = fmaf(v, v, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    atomicMax(out, __float_as_uint(t * 1.0001f));
+  }
+}
+
+// rowmax[r] = max_c |a[r][c]| and glob = max over all, for long rows (2-D grid:
+// x = column chunks, y = rows).
+template <class T>
+__global__ void rowmax2d_kernel(const T* __restrict__ a, long cols, long ld,
+                                unsigned* __restrict__ rowmax, unsigned* __restrict__ glob) {
+  const long r = blockIdx.y;
+  float m = 0.0f;
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < cols;
+       c += (long)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf((float)a[r * ld + c]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(rowmax + r, __float_as_uint(m));
+    atomicMax(glob, __float_as_uint(m));
+  }
 }
 
 // ----------------------------------------------------------------- splits
@@ -191,6 +232,32 @@ __global__ void __launch_bounds__(128) split_mh_rows_kernel(
     }
     mrow[c] = mh;
     hrow[c] = hh;
+  }
+}
+
+// As split_mh_rows_kernel with the row maxima (of |src|, unscaled) given:
+// 2-D grid, x = column chunks of ld_dst, y = rows.
+template <class T>
+__global__ void split_mh_rows_pre_kernel(const T* __restrict__ src, long cols, long ld_src,
+                                         const unsigned* __restrict__ rowmax,
+                                         const float* __restrict__ sc, int gidx,
+                                         __half* __restrict__ mo, __half* __restrict__ ho,
+                                         long ld_dst) {
+  const long r = blockIdx.y;
+  const T G = (T)sc[gidx];
+  const T q = (T)row_grid(__uint_as_float(rowmax[r]) * (float)G);
+  const T* row = src + r * ld_src;
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < ld_dst;
+       c += (long)gridDim.x * blockDim.x) {
+    __half mh = __float2half(0.0f), hh = __float2half(0.0f);
+    if (c < cols) {
+      const T x = row[c] * G;
+      const T m = q * rint(x / q);
+      mh = __float2half_rn((float)m);
+      hh = __float2half_rn((float)(x - m));
+    }
+    mo[r * ld_dst + c] = mh;
+    ho[r * ld_dst + c] = hh;
   }
 }
 
@@ -316,6 +383,14 @@ struct GemmArgs {
   const float* sc;
   int scale_idx;
   int* status;
+  // When pm is set (one N tile, no split): write each output row as per-row
+  // (m, h) pieces of (row * sc[piece_idx]) into pm / ph [M][ld_p] instead of
+  // out, and fold max_r sum_c row[c]^2 into rn2.
+  __half* pm;
+  __half* ph;
+  long ld_p;
+  int piece_idx;
+  unsigned* rn2;
 };
 
 constexpr int G_STAGES = 3;
@@ -382,6 +457,7 @@ __global__ void __launch_bounds__(192, 1)
       if (last_parity[s] >= 0) mbar_wait(&full[s], last_parity[s]);
   } else if (warp == 5 && lane == 0) {
     const uint32_t idesc = idesc_f16(128, 128, false, false, false);
+    const uint64_t dst0 = sdesc_sw128(smem_u32(sm), 16, 1024);
     for (int kb = 0; kb < nkb && !abort_flag; ++kb) {
       const int s = kb % G_STAGES, grp = kb / kDrain, set = grp & 1;
       const bool first = (kb % kDrain) == 0;
@@ -393,18 +469,21 @@ __global__ void __launch_bounds__(192, 1)
         atomicExch(g.status, 12); abort_flag = 1; break;
       }
       tc_fence_after();
-      const uint32_t st = smem_u32(sm + s * G_STAGE_BYTES);
-      const uint32_t am = st, ah = st + 16384, bm = st + 32768, bh = st + 49152;
+      // stage s: A m-piece at +0, A h at +16 KB, B m at +32 KB, B h at +48 KB; the
+      // descriptor address field counts 16-byte units (1024 per 16 KB, 2 per K step)
+      const uint64_t dam = dst0 + s * (G_STAGE_BYTES >> 4), dah = dam + 1024;
+      const uint64_t dbm = dam + 2048, dbh = dam + 3072;
       const uint32_t t0 = tbase + set * 256, t1 = t0 + 128;
+#pragma unroll
       for (int kk = 0; kk < 4; ++kk)
-        mma_f16(t0, sdesc_sw128(am + kk * 32, 16, 1024), sdesc_sw128(bm + kk * 32, 16, 1024),
-                idesc, (first && kk == 0) ? 0u : 1u);
-      const uint32_t ao[3] = {am, ah, ah}, bo[3] = {bh, bm, bh};
-      for (int p = 0; p < 3; ++p)
-        for (int kk = 0; kk < 4; ++kk)
-          mma_f16(t1, sdesc_sw128(ao[p] + kk * 32, 16, 1024),
-                  sdesc_sw128(bo[p] + kk * 32, 16, 1024), idesc,
-                  (first && p == 0 && kk == 0) ? 0u : 1u);
+        mma_f16(t0, dam + kk * 2, dbm + kk * 2, idesc, (first && kk == 0) ? 0u : 1u);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        mma_f16(t1, dam + kk * 2, dbh + kk * 2, idesc, (first && kk == 0) ? 0u : 1u);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) mma_f16(t1, dah + kk * 2, dbm + kk * 2, idesc, 1u);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) mma_f16(t1, dah + kk * 2, dbh + kk * 2, idesc, 1u);
       mma_commit(&empty[s]);
       if (last) mma_commit(&set_ready[set]);
     }
@@ -435,7 +514,40 @@ __global__ void __launch_bounds__(192, 1)
     }
     ok = ok && !abort_flag;
     const float scale = g.sc[g.scale_idx];
-    if (m0 + r < g.M) {
+    if (g.pm) {
+      // orbital rows: values, row norm, per-row grid, pieces
+      float mx = 0.0f, nrm = 0.0f;
+      const float G = g.sc[g.piece_idx];
+#pragma unroll
+      for (int c = 0; c < 128; ++c) {
+        const float v = (ok && c < g.Ncols) ? run[c] * scale : 0.0f;
+        run[c] = v;
+        nrm = fmaf(v, v, nrm);
+        mx = fmaxf(mx, fabsf(v * G));
+      }
+      if (m0 + r < g.M) {
+        atomicMax(g.rn2, __float_as_uint(nrm * 1.0001f));
+        const float q = row_grid(mx);
+        __half* mrow = g.pm + (long)(m0 + r) * g.ld_p;
+        __half* hrow = g.ph + (long)(m0 + r) * g.ld_p;
+#pragma unroll
+        for (int c0 = 0; c0 < 128; c0 += 8) {
+          if (c0 >= g.ld_p) break;
+          uint32_t mw[4], hw[4];
+#pragma unroll
+          for (int j = 0; j < 8; j += 2) {
+            const float x0 = run[c0 + j] * G, x1 = run[c0 + j + 1] * G;
+            const float m0v = q * rintf(x0 / q), m1v = q * rintf(x1 / q);
+            const __half2 hm = __floats2half2_rn(m0v, m1v);
+            const __half2 hh = __floats2half2_rn(x0 - m0v, x1 - m1v);
+            mw[j / 2] = *reinterpret_cast<const uint32_t*>(&hm);
+            hw[j / 2] = *reinterpret_cast<const uint32_t*>(&hh);
+          }
+          *reinterpret_cast<uint4*>(mrow + c0) = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+          *reinterpret_cast<uint4*>(hrow + c0) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        }
+      }
+    } else if (m0 + r < g.M) {
       float* orow = g.out + (long)blockIdx.z * g.split_stride + (long)(m0 + r) * g.ldo;
 #pragma unroll
       for (int c = 0; c < 128; ++c) {
@@ -473,6 +585,8 @@ struct PairArgs {
 constexpr int kAccDrain = 2;  // tiles per acc drain
 
 template <int NP>
+struct PairCfg;
+template <int NP>
 struct PairCfg {
   static constexpr int X_BYTES = 128 * NP * 2;     // one piece
   static constexpr int Y_BYTES = 64 * NP * 2;
@@ -484,20 +598,25 @@ struct PairCfg {
   static constexpr int SMEM = OFF_U + 2 * U_BYTES + 1024;
 };
 
+constexpr int kEpiWarps = 8;                 // two warpgroups split each row's columns
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kPairThreads = kEpiThreads + 64; // + TMA producer warp + MMA warp
+
 template <int NP>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kPairThreads, 1)
     pair_kernel(const __grid_constant__ CUtensorMap mXm, const __grid_constant__ CUtensorMap mXh,
                 const __grid_constant__ CUtensorMap mYm, const __grid_constant__ CUtensorMap mYh,
                 const __grid_constant__ CUtensorMap mV, PairArgs a) {
   using C = PairCfg<NP>;
   extern __shared__ uint8_t p_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ uint64_t x_full, full[2], empty[2], s_full[2], s_free[2], u_full, u_free, acc_ready,
-      acc_free, drain;
+  __shared__ uint64_t x_full, full[2], empty[2], s_full, s_free, u_full, u_free, acc_ready[2],
+      acc_free[2], drain;
   __shared__ uint32_t tslot;
   __shared__ volatile int abort_flag;
-  __shared__ double ered[128];
+  __shared__ double ered[kEpiWarps];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int prod_warp = kEpiWarps, mma_warp = kEpiWarps + 1;
   const int x0 = blockIdx.x * 128;
   const int y0 = blockIdx.y * a.ychunk;
   const int y1 = min(a.Y, y0 + a.ychunk);
@@ -509,28 +628,31 @@ __global__ void __launch_bounds__(192, 1)
     for (int s = 0; s < 2; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
-      mbar_init(&s_full[s], 1);
-      mbar_init(&s_free[s], 128);
+      mbar_init(&acc_ready[s], 1);
+      mbar_init(&acc_free[s], kEpiThreads);
     }
-    mbar_init(&u_full, 128);
+    mbar_init(&s_full, 1);
+    mbar_init(&s_free, kEpiThreads);
+    mbar_init(&u_full, kEpiThreads);
     mbar_init(&u_free, 1);
-    mbar_init(&acc_ready, 1);
-    mbar_init(&acc_free, 128);
     mbar_init(&drain, 1);
     abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == 5) {
+  if (warp == mma_warp) {
     tmem_alloc(&tslot, 512);
     tmem_relinquish();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  // TMEM columns: S = A0 [0, 64) + A1 [64, 128); second-product accumulators
+  // acc[0] [128, 256) and acc[1] [256, 384) alternate by drain group; the
+  // running sum [384, 512).
   const uint32_t tbase = tslot;
-  const uint32_t t_acc = tbase + 256, t_run = tbase + 384;
+  const uint32_t t_run = tbase + 384;
 
-  if (warp == 4 && lane == 0) {
+  if (warp == prod_warp && lane == 0) {
     // ---------------- TMA producer
     prefetch_tmap(&mXm); prefetch_tmap(&mXh); prefetch_tmap(&mYm); prefetch_tmap(&mYh);
     prefetch_tmap(&mV);
@@ -563,98 +685,132 @@ __global__ void __launch_bounds__(192, 1)
     if (xl) mbar_wait(&x_full, 0);
     for (int s = 0; s < 2; ++s)
       if (last_parity[s] >= 0) mbar_wait(&full[s], last_parity[s]);
-  } else if (warp == 5 && lane == 0) {
+  } else if (warp == mma_warp && lane == 0) {
     // ---------------- MMA issuer
     const uint32_t id_s = idesc_f16(128, 64, false, false, false);
     const uint32_t id_acc = idesc_f16(128, NP, false, false, true);
-    const uint32_t xm = smem_u32(sm), xh = smem_u32(sm + C::X_BYTES);
+    const uint32_t xm = smem_u32(sm), xh = smem_u32(sm + C::X_BYTES);  // 1024-aligned tile bases
     const uint32_t uh = smem_u32(sm + C::OFF_U), ul = smem_u32(sm + C::OFF_U + C::U_BYTES);
     bool good = T > 0 && mbar_wait(&x_full, 0);
     if (T > 0 && !good) { atomicExch(a.status, 22); abort_flag = 1; }
+    // Descriptors of every operand tile start from one base descriptor; the
+    // address field counts 16-byte units, so tile offsets add as immediates.
+    const uint64_t dxm = sdesc_sw128(xm, 16, 1024), dxh = sdesc_sw128(xh, 16, 1024);
+    const uint64_t duh = sdesc_sw128(uh, 16, 1024), dul = sdesc_sw128(ul, 16, 1024);
+    const uint64_t dy0 = sdesc_sw128(smem_u32(sm + C::OFF_STAGE), 16, 1024);
+    const uint64_t dy0mn = sdesc_sw128(smem_u32(sm + C::OFF_STAGE), 8192, 1024);
+    constexpr uint64_t kStage16 = C::STAGE >> 4, kYh16 = C::Y_BYTES >> 4;
     auto issue_acc = [&](int u) -> bool {
-      const int s = u & 1, grp = u / kAccDrain;
+      const int s = u & 1, grp = u / kAccDrain, buf = grp & 1;
       const bool first = (u % kAccDrain) == 0;
       const bool last = (u % kAccDrain) == kAccDrain - 1 || u == T - 1;
-      if (first && grp > 0 && !mbar_wait(&acc_free, (grp - 1) & 1)) return false;
+      // acc[buf] was last used by group grp - 2; its drain must be done
+      if (first && grp >= 2 && !mbar_wait(&acc_free[buf], ((grp >> 1) - 1) & 1)) return false;
       if (!mbar_wait(&u_full, u & 1)) return false;
       tc_fence_after();
-      const uint32_t ym = smem_u32(sm + C::OFF_STAGE + s * C::STAGE);
-      const uint32_t yh = ym + C::Y_BYTES;
-      const uint32_t ao[3] = {uh, uh, ul}, bo[3] = {ym, yh, ym};
-      for (int p = 0; p < 3; ++p)
-        for (int kk = 0; kk < 4; ++kk) {
-          const uint64_t ad = sdesc_sw128(ao[p] + kk * 32, 16, 1024);
-          const uint64_t bd = sdesc_sw128(bo[p] + kk * 2048, 8192, 1024);
-          mma_f16(t_acc, ad, bd, id_acc, (first && p == 0 && kk == 0) ? 0u : 1u);
-        }
+      const uint64_t bym = dy0mn + s * kStage16, byh = bym + kYh16;
+      const uint32_t t_acc = tbase + 128 + buf * 128;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        mma_f16(t_acc, duh + kk * 2, bym + kk * 128, id_acc, (first && kk == 0) ? 0u : 1u);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) mma_f16(t_acc, duh + kk * 2, byh + kk * 128, id_acc, 1u);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) mma_f16(t_acc, dul + kk * 2, bym + kk * 128, id_acc, 1u);
       mma_commit(&empty[s]);
       mma_commit(&u_free);
-      if (last) mma_commit(&acc_ready);
+      if (last) mma_commit(&acc_ready[buf]);
       return true;
     };
     for (int t = 0; good && t < T && !abort_flag; ++t) {
       const int s = t & 1, use = t >> 1;
       if (!mbar_wait(&full[s], use & 1)) { atomicExch(a.status, 23); abort_flag = 1; good = false; break; }
-      if (use > 0 && !mbar_wait(&s_free[s], (use - 1) & 1)) {
+      if (t > 0 && !mbar_wait(&s_free, (t - 1) & 1)) {
         atomicExch(a.status, 24); abort_flag = 1; good = false; break;
       }
       tc_fence_after();
-      const uint32_t ym = smem_u32(sm + C::OFF_STAGE + s * C::STAGE);
-      const uint32_t yh = ym + C::Y_BYTES;
-      const uint32_t t_s0 = tbase + s * 128, t_s1 = t_s0 + 64;
-      for (int kk = 0; kk < NP / 16; ++kk) {
-        const uint64_t ad = sdesc_sw128(xm + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024);
-        const uint64_t bd = sdesc_sw128(ym + (kk >> 2) * 8192 + (kk & 3) * 32, 16, 1024);
-        mma_f16(t_s0, ad, bd, id_s, kk > 0 ? 1u : 0u);
-      }
-      const uint32_t ao[3] = {xm, xh, xh}, bo[3] = {yh, ym, yh};
-      for (int p = 0; p < 3; ++p)
-        for (int kk = 0; kk < NP / 16; ++kk) {
-          const uint64_t ad = sdesc_sw128(ao[p] + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024);
-          const uint64_t bd = sdesc_sw128(bo[p] + (kk >> 2) * 8192 + (kk & 3) * 32, 16, 1024);
-          mma_f16(t_s1, ad, bd, id_s, (p > 0 || kk > 0) ? 1u : 0u);
-        }
-      mma_commit(&s_full[s]);
+      const uint64_t dym = dy0 + s * kStage16, dyh = dym + kYh16;
+      const uint32_t t_s0 = tbase, t_s1 = tbase + 64;
+      // K step kk: X tile offset (kk/4)*16384 + (kk%4)*32 bytes, Y tile (kk/4)*8192 + (kk%4)*32
+#pragma unroll
+      for (int kk = 0; kk < NP / 16; ++kk)
+        mma_f16(t_s0, dxm + (kk >> 2) * 1024 + (kk & 3) * 2, dym + (kk >> 2) * 512 + (kk & 3) * 2,
+                id_s, kk > 0 ? 1u : 0u);
+#pragma unroll
+      for (int kk = 0; kk < NP / 16; ++kk)
+        mma_f16(t_s1, dxm + (kk >> 2) * 1024 + (kk & 3) * 2, dyh + (kk >> 2) * 512 + (kk & 3) * 2,
+                id_s, kk > 0 ? 1u : 0u);
+#pragma unroll
+      for (int kk = 0; kk < NP / 16; ++kk)
+        mma_f16(t_s1, dxh + (kk >> 2) * 1024 + (kk & 3) * 2, dym + (kk >> 2) * 512 + (kk & 3) * 2,
+                id_s, 1u);
+#pragma unroll
+      for (int kk = 0; kk < NP / 16; ++kk)
+        mma_f16(t_s1, dxh + (kk >> 2) * 1024 + (kk & 3) * 2, dyh + (kk >> 2) * 512 + (kk & 3) * 2,
+                id_s, 1u);
+      mma_commit(&s_full);
       if (t > 0 && !issue_acc(t - 1)) { atomicExch(a.status, 25); abort_flag = 1; good = false; break; }
     }
     if (good && T > 0 && !issue_acc(T - 1)) { atomicExch(a.status, 26); abort_flag = 1; }
     mma_commit(&drain);
     mbar_wait(&drain, 0);
-  } else if (warp < 4) {
-    // ---------------- epilogue
-    const int r = warp * 32 + lane;
-    const uint32_t lane_off = static_cast<uint32_t>(warp * 32) << 16;
+  } else if (warp < kEpiWarps) {
+    // ---------------- epilogue: warp quadrant = TMEM lanes (rows), half = columns
+    const int quad = warp & 3, half = warp >> 2;
+    const int r = quad * 32 + lane;
+    const uint32_t lane_off = static_cast<uint32_t>(quad * 32) << 16;
     const float f = a.sc[a.f_idx];
     const bool want_e = a.epart != nullptr;
     uint8_t* uhp = sm + C::OFF_U;
     uint8_t* ulp = uhp + C::U_BYTES;
     const int sw = r & 7;
+    constexpr int ACOLS = NP / 2;  // accumulator columns per epilogue half
     double esum = 0.0;
     bool ok = T > 0;
-    for (int t = 0; t < T && !abort_flag; ++t) {
-      const int s = t & 1;
-      if (!mbar_wait(&s_full[s], (t >> 1) & 1)) { atomicExch(a.status, 27); abort_flag = 1; ok = false; break; }
+    const int ngroups = (T + kAccDrain - 1) / kAccDrain;
+    // Adds acc[grp & 1] into the running sum (drain group grp), then frees it.
+    auto drain_group = [&](int grp) -> bool {
+      const int buf = grp & 1;
+      if (!mbar_wait(&acc_ready[buf], (grp >> 1) & 1)) return false;
       tc_fence_after();
-      float sv[64];
-#pragma unroll
-      for (int c = 0; c < 64; c += 16) {
-        uint32_t u0[16], u1[16];
-        tmem_ld16(tbase + lane_off + s * 128 + c, u0);
-        tmem_ld16(tbase + lane_off + s * 128 + 64 + c, u1);
+      const uint32_t t_acc = tbase + 128 + buf * 128;
+#pragma unroll 1
+      for (int c = 0; c < ACOLS; c += 32) {
+        uint32_t ua[32], ur[32];
+        tmem_ld32(t_acc + lane_off + half * ACOLS + c, ua);
+        if (grp > 0) tmem_ld32(t_run + lane_off + half * ACOLS + c, ur);
         tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 16; ++j) sv[c + j] = __uint_as_float(u0[j]) + __uint_as_float(u1[j]);
+        for (int j = 0; j < 32; ++j)
+          ur[j] = __float_as_uint((grp > 0 ? __uint_as_float(ur[j]) : 0.0f) + __uint_as_float(ua[j]));
+        tmem_st32(t_run + lane_off + half * ACOLS + c, ur);
+      }
+      tmem_wait_st();
+      tc_fence_before();
+      mbar_arrive(&acc_free[buf]);
+      return true;
+    };
+    for (int t = 0; t < T && !abort_flag; ++t) {
+      const int s = t & 1;
+      if (!mbar_wait(&s_full, t & 1)) { atomicExch(a.status, 27); abort_flag = 1; ok = false; break; }
+      tc_fence_after();
+      float sv[32];
+      {
+        uint32_t u0[32], u1[32];
+        tmem_ld32(tbase + lane_off + half * 32, u0);
+        tmem_ld32(tbase + lane_off + 64 + half * 32, u1);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) sv[j] = __uint_as_float(u0[j]) + __uint_as_float(u1[j]);
       }
       tc_fence_before();
-      mbar_arrive(&s_free[s]);
-      const uint8_t* vt = sm + C::OFF_STAGE + s * C::STAGE + 2 * C::Y_BYTES;
-      uint32_t hi[32], lo[32];
+      mbar_arrive(&s_free);
+      const uint8_t* vt = sm + C::OFF_STAGE + s * C::STAGE + 2 * C::Y_BYTES + half * 16384;
+      uint32_t hi[16], lo[16];
       float etile = 0.0f;
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int box = q >> 3, qc = q & 7;
-        const float4 v = *reinterpret_cast<const float4*>(vt + box * 16384 + r * 128 +
-                                                          ((qc ^ sw) << 4));
+      for (int q = 0; q < 8; ++q) {
+        const float4 v = *reinterpret_cast<const float4*>(vt + r * 128 + ((q ^ sw) << 4));
         const float p0 = v.x * sv[4 * q + 0], p1 = v.y * sv[4 * q + 1];
         const float p2 = v.z * sv[4 * q + 2], p3 = v.w * sv[4 * q + 3];
         if (want_e) {
@@ -676,33 +832,20 @@ __global__ void __launch_bounds__(192, 1)
       esum += (double)etile;
       if (t > 0 && !mbar_wait(&u_free, (t - 1) & 1)) { atomicExch(a.status, 28); abort_flag = 1; ok = false; break; }
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int off = r * 128 + ((q ^ sw) << 4);
+      for (int q = 0; q < 4; ++q) {
+        const int off = r * 128 + (((4 * half + q) ^ sw) << 4);
         *reinterpret_cast<uint4*>(uhp + off) = make_uint4(hi[4 * q], hi[4 * q + 1], hi[4 * q + 2], hi[4 * q + 3]);
         *reinterpret_cast<uint4*>(ulp + off) = make_uint4(lo[4 * q], lo[4 * q + 1], lo[4 * q + 2], lo[4 * q + 3]);
       }
       fence_async_smem();
       mbar_arrive(&u_full);
-      // drain the second-product accumulator into the running sum after each group
-      if ((t % kAccDrain) == kAccDrain - 1 || t == T - 1) {
-        const int grp = t / kAccDrain;
-        if (!mbar_wait(&acc_ready, grp & 1)) { atomicExch(a.status, 29); abort_flag = 1; ok = false; break; }
-        tc_fence_after();
-#pragma unroll 1
-        for (int c = 0; c < NP; c += 16) {
-          uint32_t ua[16], ur[16];
-          tmem_ld16(t_acc + lane_off + c, ua);
-          if (grp > 0) tmem_ld16(t_run + lane_off + c, ur);
-          tmem_wait_ld();
-#pragma unroll
-          for (int j = 0; j < 16; ++j)
-            ur[j] = __float_as_uint((grp > 0 ? __uint_as_float(ur[j]) : 0.0f) + __uint_as_float(ua[j]));
-          tmem_st16(t_run + lane_off + c, ur);
-        }
-        tmem_wait_st();
-        tc_fence_before();
-        mbar_arrive(&acc_free);
+      // drain the previous group one tile late, while the MMA fills the other buffer
+      if ((t % kAccDrain) == 0 && t > 0 && !drain_group(t / kAccDrain - 1)) {
+        atomicExch(a.status, 29); abort_flag = 1; ok = false; break;
       }
+    }
+    if (ok && !abort_flag && ngroups > 0 && !drain_group(ngroups - 1)) {
+      atomicExch(a.status, 30); abort_flag = 1; ok = false;
     }
     ok = ok && !abort_flag;
     // ---------------- write the running sum
@@ -711,14 +854,14 @@ __global__ void __launch_bounds__(192, 1)
     const int x = x0 + r;
     const bool row_ok = x < a.X;
 #pragma unroll 1
-    for (int c = 0; c < NP; c += 16) {
-      uint32_t u[16];
-      tmem_ld16(t_run + lane_off + c, u);
+    for (int c = 0; c < ACOLS; c += 32) {
+      uint32_t u[32];
+      tmem_ld32(t_run + lane_off + half * ACOLS + c, u);
       tmem_wait_ld();
       if (!row_ok) continue;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int col = c + j;
+      for (int j = 0; j < 32; ++j) {
+        const int col = half * ACOLS + c + j;
         if (col >= a.n) continue;
         const float v = ok ? __uint_as_float(u[j]) * os : 0.0f;
         if (a.transposed)
@@ -728,18 +871,20 @@ __global__ void __launch_bounds__(192, 1)
       }
     }
     if (want_e) {
-      ered[r] = (ok && row_ok) ? esum : 0.0;
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (r == 0) {
+      double e = (ok && row_ok) ? esum : 0.0;
+      for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+      if (lane == 0) ered[warp] = e;
+      asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory");
+      if (tid == 0) {
         double sum = 0.0;
-        for (int i = 0; i < 128; ++i) sum += ered[i];
+        for (int i = 0; i < kEpiWarps; ++i) sum += ered[i];
         a.epart[(long)blockIdx.y * gridDim.x + blockIdx.x] = sum;
       }
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 5) tmem_dealloc(tbase, 512);
+  if (warp == mma_warp) tmem_dealloc(tbase, 512);
 }
 
 // ------------------------------------------------------------- host side
@@ -800,11 +945,12 @@ struct MixedState {
   __half *CT_m = nullptr, *CT_h = nullptr, *psi_m = nullptr, *psi_h = nullptr, *psig_m = nullptr,
          *psig_h = nullptr, *M1_m = nullptr, *M1_h = nullptr, *D23T_m = nullptr,
          *D23T_h = nullptr;
-  float *psi32 = nullptr, *M2p = nullptr, *M3p = nullptr, *M1 = nullptr, *L1p = nullptr,
-        *L23p = nullptr, *sc = nullptr;
+  float *M2p = nullptr, *M3p = nullptr, *M1 = nullptr, *L1p = nullptr, *L23p = nullptr,
+        *sc = nullptr;
   double *D23 = nullptr, *CT64 = nullptr, *D23T64 = nullptr, *red = nullptr, *EpA = nullptr,
          *EpC = nullptr, *Lf = nullptr, *Q64 = nullptr, *dwork = nullptr;
   unsigned* am = nullptr;
+  unsigned* rowmax = nullptr;
   int* status = nullptr;
   int xa = 1, partsA = 1, partsC = 1, splitsL1 = 1, splitsL23 = 1;
   int ychunkA = 64, ychunkC = 64;
@@ -841,10 +987,10 @@ Plan make_plan(int64_t Ng, int N, int n, int Naux) {
   p.Na4 = rup(Naux, 4);
   p.xa = (Naux + 127) / 128;
   // roles A and C: X = g tiles; split Y so the grid is about two waves of 152 SMs
-  p.partsA = std::max(1, std::min<int>((304 + p.xa - 1) / p.xa, (int)((Ng + 63) / 64)));
+  p.partsA = std::max(1, std::min<int>((608 + p.xa - 1) / p.xa, (int)((Ng + 63) / 64)));
   p.ychunkA = (int)rup((Ng + p.partsA - 1) / p.partsA, 64);
   p.partsA = (int)((Ng + p.ychunkA - 1) / p.ychunkA);
-  p.partsC = std::max(1, std::min<int>((152 + p.xa - 1) / p.xa, (Naux + 63) / 64));
+  p.partsC = std::max(1, std::min<int>((608 + p.xa - 1) / p.xa, (Naux + 63) / 64));
   p.ychunkC = (int)rup((Naux + p.partsC - 1) / p.partsC, 64);
   p.partsC = (Naux + p.ychunkC - 1) / p.ychunkC;
   // line GEMMs: (N / 128) x (n / 128) tiles x K splits of >= 1024
@@ -875,8 +1021,7 @@ size_t mixed_footprint(int64_t Ng, int N, int n, int Naux) {
   size_t b = 0;
   b += 2 * ng * p.Np * 2 + 2 * (size_t)N * p.Ng8 * 2 + 2 * (size_t)N * p.Na8 * 2;  // Phi pieces
   b += na * p.Ng4 * 4 + ng * p.Na4 * 4 + na * p.Na4 * 4 + na * 4;                  // V, V^T, W, idx
-  b += 2 * (size_t)n * p.Np * 2 + (size_t)n * p.Np * 8 + ng * n * 4 + 2 * ng * p.np * 2 +
-       2 * na * p.np * 2;
+  b += 2 * (size_t)n * p.Np * 2 + (size_t)n * p.Np * 8 + 2 * ng * p.np * 2 + 2 * na * p.np * 2;
   b += (size_t)p.partsA * na * n * 4 + (size_t)p.partsC * na * n * 4 + (size_t)n * p.Ng4 * 4;
   b += na * n * 8 + (size_t)n * p.Na8 * 8 + 2 * (size_t)n * p.Ng8 * 2 + 2 * (size_t)n * p.Na8 * 2;
   b += (size_t)p.splitsL1 * N * n * 4 + (size_t)p.splitsL23 * N * n * 4;
@@ -921,7 +1066,6 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   MX(m->V32, na * p.Ng4); MX(m->VT32, ng * p.Na4); MX(m->W32, na * p.Na4);
   MX(m->idx, na);
   MX(m->CT_m, (size_t)n * p.Np); MX(m->CT_h, (size_t)n * p.Np); MX(m->CT64, (size_t)n * p.Np);
-  MX(m->psi32, ng * n);
   MX(m->psi_m, ng * p.np); MX(m->psi_h, ng * p.np);
   MX(m->psig_m, na * p.np); MX(m->psig_h, na * p.np);
   MX(m->M2p, (size_t)p.partsA * na * n); MX(m->M3p, (size_t)p.partsC * na * n);
@@ -931,7 +1075,7 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   MX(m->D23T_m, (size_t)n * p.Na8); MX(m->D23T_h, (size_t)n * p.Na8);
   MX(m->L1p, (size_t)p.splitsL1 * N * n); MX(m->L23p, (size_t)p.splitsL23 * N * n);
   MX(m->EpA, (size_t)p.partsA * p.xa); MX(m->EpC, (size_t)p.partsC * p.xa);
-  MX(m->sc, NSC); MX(m->am, NAM); MX(m->status, 4);
+  MX(m->sc, NSC); MX(m->am, NAM); MX(m->status, 4); MX(m->rowmax, (size_t)n);
   MX(m->red, reduce_work_elems());
   MX(m->Lf, (size_t)N * N); MX(m->Q64, (size_t)N * n);
   MX(m->dwork, dwork_elems(Ng, N, n));
@@ -985,9 +1129,10 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
     if (e != cudaSuccess) return fin(e);
     double* phip = stage2 + 2 * (size_t)N * N;
     absmax_kernel<double><<<blocks_for(ng * N), 256, 0, s>>>(phip, ng, N, N, m->am + AM_PHIP);
+    rownorm2_max_kernel<double><<<blocks_for(ng), 256, 0, s>>>(phip, ng, N, N, m->am + AM_PHIP_RN);
     absmax_kernel<double><<<blocks_for(ng * N), 256, 0, s>>>(stage, ng, N, N, m->am + AM_PHI);
     set_phi_scale_kernel<<<1, 32, 0, s>>>(m->am, m->sc);
-    count_launch(3);
+    count_launch(4);
     e = split_rows<double>(phip, ng, N, N, m->sc, SC_PHIP, m->phi_m, m->phi_h, p.Np, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fin(e);
@@ -1077,25 +1222,22 @@ cudaError_t mixed_enqueue(MixedState* m, const double* C, double* K, double* Ex,
     if (e != cudaSuccess) return e;
   }
   absmax_kernel<double><<<blocks_for((long)N * n), 256, 0, s>>>(m->Q64, N, n, n, m->am + AM_C);
+  colnorm2_max_kernel<<<n, 256, 0, s>>>(m->Q64, N, n, m->am + AM_QCN);
   scales_kernel<<<1, 32, 0, s>>>(m->am, m->sc, 0);
-  count_launch(2);
+  count_launch(3);
   e = transpose<double>(m->Q64, N, n, n, m->CT64, m->Np, s);  // Q^T [j][mu], zero for mu >= N
   if (e == cudaSuccess) e = split_rows<double>(m->CT64, n, m->Np, m->Np, m->sc, SC_C, m->CT_m, m->CT_h, m->Np, s);
   if (e != cudaSuccess) return e;
-  {
-    GemmArgs g{(int)ng, n, N, (int)m->Np, m->psi32, n, 0, m->sc, SC_OUT_ORB, m->status};
-    dim3 grid((unsigned)((ng + 127) / 128), (unsigned)((n + 127) / 128), 1);
+  {  // Psi = Phi' Q, written directly as per-row pieces
+    GemmArgs g{(int)ng, n, N, (int)m->Np, nullptr, 0, 0, m->sc, SC_OUT_ORB, m->status,
+               m->psi_m, m->psi_h, np, SC_PSI, m->am + AM_RN2};
+    dim3 grid((unsigned)((ng + 127) / 128), 1, 1);
     gemm_kernel<<<grid, 192, G_SMEM, s>>>(m->m_phi_m, m->m_phi_h, m->m_CT_m, m->m_CT_h, g);
   }
-  absmax_kernel<float><<<blocks_for(ng * n), 256, 0, s>>>(m->psi32, ng, n, n, m->am + AM_PSI);
-  rownorm2_max_kernel<<<blocks_for(ng), 256, 0, s>>>(m->psi32, ng, n, n, m->am + AM_RN2);
   scales_kernel<<<1, 32, 0, s>>>(m->am, m->sc, 1);
-  count_launch(4);
-  e = split_rows<float>(m->psi32, ng, n, n, m->sc, SC_PSI, m->psi_m, m->psi_h, np, s);
-  if (e != cudaSuccess) return e;
   gather_rows_half_kernel<<<blocks_for(na * np), 256, 0, s>>>(m->psi_m, np, m->idx, (int)na, m->psig_m);
   gather_rows_half_kernel<<<blocks_for(na * np), 256, 0, s>>>(m->psi_h, np, m->idx, (int)na, m->psig_h);
-  count_launch(2);
+  count_launch(4);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   hook(0, 0);
@@ -1106,9 +1248,9 @@ cudaError_t mixed_enqueue(MixedState* m, const double* C, double* K, double* Ex,
                          const CUtensorMap& Yh, const CUtensorMap& Vm, const PairArgs& pa,
                          dim3 grid) {
     if (np == 64)
-      pair_kernel<64><<<grid, 192, PairCfg<64>::SMEM, s>>>(Xm, Xh, Ym, Yh, Vm, pa);
+      pair_kernel<64><<<grid, kPairThreads, PairCfg<64>::SMEM, s>>>(Xm, Xh, Ym, Yh, Vm, pa);
     else
-      pair_kernel<128><<<grid, 192, PairCfg<128>::SMEM, s>>>(Xm, Xh, Ym, Yh, Vm, pa);
+      pair_kernel<128><<<grid, kPairThreads, PairCfg<128>::SMEM, s>>>(Xm, Xh, Ym, Yh, Vm, pa);
     count_launch();
   };
   {  // role A: M2[g][j] = sum_R (V o P)[g][R] Psi[R][j], and sum V o P^2
@@ -1137,20 +1279,29 @@ cudaError_t mixed_enqueue(MixedState* m, const double* C, double* K, double* Ex,
   hook(4, 1);
   reduce_parts_kernel<<<blocks_for(na * n), 256, 0, s>>>(m->M2p, m->partsA, m->M3p, m->partsC,
                                                          na * n, m->D23, m->am + AM_D23);
-  absmax_kernel<float><<<blocks_for((long)n * ng), 256, 0, s>>>(m->M1, n, ng, m->Ng4, m->am + AM_M1);
-  scales_kernel<<<1, 32, 0, s>>>(m->am, m->sc, 2);
-  count_launch(3);
-  e = split_rows<float>(m->M1, n, ng, m->Ng4, m->sc, SC_M1, m->M1_m, m->M1_h, m->Ng8, s);
-  if (e == cudaSuccess) e = transpose<double>(m->D23, na, n, n, m->D23T64, m->Na8, s);
+  e = cudaMemsetAsync(m->rowmax, 0, (size_t)n * 4, s);
+  if (e != cudaSuccess) return e;
+  {
+    const unsigned chunks = (unsigned)std::min<long>(64, (ng + 1023) / 1024);
+    rowmax2d_kernel<float><<<dim3(chunks, n), 256, 0, s>>>(m->M1, ng, m->Ng4, m->rowmax, m->am + AM_M1);
+    scales_kernel<<<1, 32, 0, s>>>(m->am, m->sc, 2);
+    const unsigned schunks = (unsigned)std::min<long>(128, (m->Ng8 + 1023) / 1024);
+    split_mh_rows_pre_kernel<float><<<dim3(schunks, n), 256, 0, s>>>(
+        m->M1, ng, m->Ng4, m->rowmax, m->sc, SC_M1, m->M1_m, m->M1_h, m->Ng8);
+  }
+  count_launch(4);
+  e = transpose<double>(m->D23, na, n, n, m->D23T64, m->Na8, s);
   if (e == cudaSuccess) e = split_rows<double>(m->D23T64, n, m->Na8, m->Na8, m->sc, SC_D23, m->D23T_m, m->D23T_h, m->Na8, s);
   if (e != cudaSuccess) return e;
   {
-    GemmArgs g{N, n, (int)ng, m->kchunkL1, m->L1p, n, (long)N * n, m->sc, SC_OUT_L1, m->status};
+    GemmArgs g{N, n, (int)ng, m->kchunkL1, m->L1p, n, (long)N * n, m->sc, SC_OUT_L1, m->status,
+               nullptr, nullptr, 0, 0, nullptr};
     dim3 grid((unsigned)((N + 127) / 128), (unsigned)((n + 127) / 128), (unsigned)m->splitsL1);
     gemm_kernel<<<grid, 192, G_SMEM, s>>>(m->m_phiT_m, m->m_phiT_h, m->m_M1_m, m->m_M1_h, g);
   }
   {
-    GemmArgs g{N, n, (int)na, m->kchunkL23, m->L23p, n, (long)N * n, m->sc, SC_OUT_L23, m->status};
+    GemmArgs g{N, n, (int)na, m->kchunkL23, m->L23p, n, (long)N * n, m->sc, SC_OUT_L23, m->status,
+               nullptr, nullptr, 0, 0, nullptr};
     dim3 grid((unsigned)((N + 127) / 128), (unsigned)((n + 127) / 128), (unsigned)m->splitsL23);
     gemm_kernel<<<grid, 192, G_SMEM, s>>>(m->m_phigT_m, m->m_phigT_h, m->m_D23T_m, m->m_D23T_h, g);
   }
