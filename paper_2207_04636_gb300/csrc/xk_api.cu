@@ -15,7 +15,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "../../include/xk.h"
+#include "xk.h"
 
 namespace {
 
