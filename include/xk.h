@@ -180,6 +180,29 @@ int xk_timing_enable(xk_handle* h, int enable);
 int xk_timing_read(xk_handle* h, int step, double* ms, uint64_t* builds);
 
 /*
+ * Exchange energy E_x = -sum_t K[t] C[t] over `count` doubles of device
+ * memory (K = K_{mu i}, C the occupied coefficients, both N x n, count = N*n),
+ * enqueued on `stream` (a cudaStream_t, NULL = legacy default stream); the
+ * result is written to the device double *Ex_dev.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory at the time of the call -- code running inside a CUDA graph
+ * capture, or a host that owns the whole device heap through its own pool
+ * and forbids libraries to call cudaMalloc.  It allocates nothing: its
+ * partial sums live in a fixed file-scope device array of 2048 doubles
+ * (16 KiB), which every device that loads the library holds until the
+ * process exits, so count may be at most 2048 * 2048 = 4194304 elements;
+ * larger counts return XK_EINVAL.  Every call overwrites the partials it
+ * reads, so nothing has to be cleared between calls, but all calls share the
+ * one array: calls that overlap on the GPU (different streams, different
+ * threads) race and must be serialised by the caller, e.g. on one stream.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * Errors: XK_EINVAL (NULL pointer, count < 0 or above the maximum), XK_ECUDA.
+ */
+int xk_exchange_energy_noalloc(const double* K_dev, const double* C_dev, int64_t count,
+                               double* Ex_dev, void* stream);
+
+/*
  * Kernel launches issued by the library since load (counts every kernel of
  * every build): lets a caller confirm the device path ran.
  */

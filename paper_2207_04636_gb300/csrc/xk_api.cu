@@ -624,6 +624,19 @@ int xk_timing_read(xk_handle* h, int step, double* ms, uint64_t* builds) {
   return XK_OK;
 }
 
+int xk_exchange_energy_noalloc(const double* K_dev, const double* C_dev, int64_t count,
+                               double* Ex_dev, void* stream) {
+  if (!K_dev || !C_dev || !Ex_dev)
+    return fail(XK_EINVAL, "xk_exchange_energy_noalloc: NULL pointer");
+  if (count < 0 || count > xk::noalloc_max_count())
+    return fail(XK_EINVAL, "xk_exchange_energy_noalloc: count " + std::to_string(count) +
+                               " is outside [0, " + std::to_string(xk::noalloc_max_count()) + "]");
+  cudaError_t e = xk::exchange_energy_noalloc(K_dev, C_dev, count, Ex_dev,
+                                              static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "xk_exchange_energy_noalloc");
+  return XK_OK;
+}
+
 int xk_release(xk_handle* h) {
   if (!h) return fail(XK_EINVAL, "xk_release: NULL handle");
   {

@@ -76,4 +76,10 @@ cudaError_t jacobi_eig_f64(double* A, double* U, int n, int max_sweeps, int* swe
 cudaError_t scale_eigcols_f64(const double* Adiag_src, int n, const double* B, int rows, double cut,
                               double* X, double* sign, cudaStream_t s);
 
+// Allocation-free E_x = -sum K[t] C[t] with partial sums in a fixed
+// file-scope device array (xk_noalloc.cu); count <= noalloc_max_count().
+int64_t noalloc_max_count();
+cudaError_t exchange_energy_noalloc(const double* K, const double* C, int64_t count, double* Ex,
+                                    cudaStream_t s);
+
 }  // namespace xk

@@ -52,10 +52,12 @@ def lib():
         L.xk_timing_enable.argtypes = [c_d, c_int]
         L.xk_timing_read.argtypes = [c_d, c_int, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_uint64)]
+        L.xk_exchange_energy_noalloc.argtypes = [c_d, c_d, c_i64, c_d, c_d]
         L.xk_last_error.restype = ctypes.c_char_p
         L.xk_kernel_launches.restype = ctypes.c_uint64
         for f in ("xk_footprint", "xk_setup", "xk_build", "xk_build_device", "xk_ace",
-                  "xk_submit", "xk_poll", "xk_release", "xk_timing_enable", "xk_timing_read"):
+                  "xk_submit", "xk_poll", "xk_release", "xk_timing_enable", "xk_timing_read",
+                  "xk_exchange_energy_noalloc"):
             getattr(L, f).restype = c_int
         _lib = L
     return _lib
@@ -162,6 +164,14 @@ class Handle:
             self.release()
         except Exception:
             pass
+
+
+def exchange_energy_noalloc(K_dev, C_dev, count, Ex_dev, stream=0):
+    """E_x = -sum K*C over `count` device doubles into the device double at
+    Ex_dev, without any allocation (integers: device addresses)."""
+    _check(lib().xk_exchange_energy_noalloc(ctypes.c_void_p(K_dev), ctypes.c_void_p(C_dev),
+                                            int(count), ctypes.c_void_p(Ex_dev),
+                                            ctypes.c_void_p(stream)))
 
 
 def poll(ticket, N, n):
