@@ -58,6 +58,7 @@ def parse():
     p.add_argument("--k", type=int, default=None, help="lattice size of config 4 (k^3 centres)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
+    p.add_argument("--no-serve", action="store_true", help="skip the serving-latency loop")
     return p.parse_args()
 
 
@@ -167,6 +168,22 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(value, dist, device):
+    """The largest `value` over all ranks (the whole-job time of a step loop)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, steps, ms):
+    """Whole-job builds/s: every rank runs `steps` builds; the job takes the
+    slowest rank's `ms` (weak scaling, no data-path collective)."""
+    return world * steps / (ms * 1e-3)
+
+
 def time_device_builds(xk, h, Cd, Kd, Ed, stream, warm, steps, torch):
     """Warm-up, then `steps` builds between CUDA events on `stream`.
     Returns (ms, launches, step times)."""
@@ -185,6 +202,45 @@ def time_device_builds(xk, h, Cd, Kd, Ed, stream, warm, steps, torch):
     st = h.step_times()
     h.timing(False)
     return e0.elapsed_time(e1), xk.kernel_launches() - launches0, st
+
+
+def serve_latency(xk, cell, handles, Cs, rate, count, seed):
+    """Serving loop: `count` build requests arrive as a Poisson process of
+    `rate` per second, each from one of the SCF runs (handles) in turn, and
+    are submitted with xk_submit as soon as they arrive and a slot of their
+    run is free; completions are found with xk_poll.  Returns latencies
+    (arrival to completion, ms) and the achieved builds/s."""
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=count))
+    N, n = cell.N, cell.n
+    pending = []          # (arrival time, handle index, request index)
+    inflight = {}         # ticket -> arrival time
+    lat = []
+    t0 = time.perf_counter()
+    nxt = 0
+    while len(lat) < count:
+        now = time.perf_counter() - t0
+        while nxt < count and arrivals[nxt] <= now:
+            pending.append((arrivals[nxt], nxt % len(handles), nxt))
+            nxt += 1
+        still = []
+        for arr, hi, ri in pending:
+            try:
+                tk = handles[hi].submit(Cs[ri % len(Cs)])
+                inflight[tk] = arr
+            except xk.XKError as e:
+                if e.code != xk.XK_EBUSY:
+                    raise
+                still.append((arr, hi, ri))
+        pending = still
+        for tk in list(inflight):
+            st, _, _, _ = xk.poll(tk, N, n)
+            if st == xk.XK_OK:
+                lat.append(1e3 * (time.perf_counter() - t0 - inflight.pop(tk)))
+        if not inflight and not pending and nxt < count:
+            time.sleep(max(0.0, min(0.001, arrivals[nxt] - (time.perf_counter() - t0))))
+    total = time.perf_counter() - t0
+    return np.array(lat), count / total
 
 
 def main():
@@ -233,10 +289,8 @@ def main():
     time.sleep(0.3)
     ms, launches, st = time_device_builds(xk, h, Cd, Kd, Ed, stream, warm, steps, torch)
     clocks = sampler.stop()
+    ms = max_over_ranks(ms, dist, "cuda")
     if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     K_last = Kd.cpu().numpy()
     E_last = float(Ed.item())
@@ -251,10 +305,21 @@ def main():
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     h.release()
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
+
+    serving = None
+    if mode != "fp64" and not args.no_serve and world == 1:
+        runs = [xk.Handle(cell.phi, cell.idx, cell.V, cell.W, cell.dV, n, mode=mode)
+                for _ in range(2)]
+        rate = 0.7 * steps / (ms * 1e-3)
+        lat, got = serve_latency(xk, cell, runs, Cs[warm:], rate, 400, 7)
+        for r in runs:
+            r.release()
+        serving = {"runs": len(runs), "requests": int(lat.size), "arrival_rate_per_s": rate,
+                   "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                   "builds_per_s": got,
+                   "note": "Poisson arrivals at 0.7x the measured throughput, xk_submit/xk_poll, "
+                           "host buffers in and out"}
 
     fp64 = None
     if mode != "fp64" and not args.no_fp64:
@@ -299,7 +364,7 @@ def main():
                     "traffic": None}
         roof["frac"] = roof["achieved"] / roof["peak"]
         roof["ms_per_build"] = dom_ms
-        value = world * steps / (ms * 1e-3)
+        value = job_throughput(world, steps, ms)
         line = {
             "metric": METRIC, "value": value, "unit": "builds/s", "n_gpus": world,
             "steps": steps, "warmup": warm, "ms_per_step": ms / steps,
@@ -315,9 +380,11 @@ def main():
             "roofline": roof,
             "gpu_launches": int(launches),
             "clocks": clocks,
-            "e2e": {"value": world * steps / e2e_s, "unit": "builds/s",
+            "e2e": {"value": job_throughput(world, steps, e2e_s * 1e3), "unit": "builds/s",
                     "h2d_bytes_per_step": N * n * 8, "d2h_bytes_per_step": N * n * 8 + 8},
         }
+        if serving:
+            line["serving"] = serving
         if fp64:
             line["fp64_path"] = fp64
             line["speedup_vs_fp64_path"] = value / world / fp64["builds_per_s"]
