@@ -566,12 +566,19 @@ __global__ void __launch_bounds__(192, 1)
 //   S = X Y^T as A0 (m.m, exact) + A1 (cross terms)       K = NP
 //   T = V' o S;  e += sum_y T S  (the closed-form energy term, optional)
 //   U = f T as floating hi/lo;  acc[x][j] += sum_y U[x][y] Y[y][j]
-// X, Y: per-row (m, h) pieces [rows][NP], K-major; V': FP32 [X rows][Y cols].
-// The Y tile doubles as the MN-major B operand of the second product.
-// TMEM: S double buffer (A0, A1) x 2 = 256 columns, acc 128, running sum 128.
+// X: per-row (m, h) pieces, copied once per CTA into tensor memory and used
+// there as the A operand of S; Y: per-row (m, h) pieces [rows][NP], K-major,
+// streamed by TMA, and reused as the MN-major B operand of the second product;
+// V': FP32 [X rows][Y cols].  Three TMA stages of (Y, V') keep about 128 KB of
+// loads in flight per SM.
+// TMEM: X pieces [0, NP), S = A0 [128, 192) + A1 [192, 256), acc [256, 384),
+// running sum [384, 512).
 
 struct PairArgs {
   int X, Y, ychunk, n;
+  const __half* xm;  // X pieces [X rows][ldx]
+  const __half* xh;
+  long ldx;
   const float* sc;
   int f_idx, out_idx;
   float* out;
@@ -582,36 +589,33 @@ struct PairArgs {
   int* status;
 };
 
-constexpr int kAccDrain = 2;  // tiles per acc drain
-
-template <int NP>
-struct PairCfg;
-template <int NP>
-struct PairCfg {
-  static constexpr int X_BYTES = 128 * NP * 2;     // one piece
-  static constexpr int Y_BYTES = 64 * NP * 2;
-  static constexpr int V_BYTES = 128 * 64 * 4;
-  static constexpr int STAGE = 2 * Y_BYTES + V_BYTES;
-  static constexpr int OFF_STAGE = 2 * X_BYTES;
-  static constexpr int OFF_U = OFF_STAGE + 2 * STAGE;
-  static constexpr int U_BYTES = 128 * 64 * 2;
-  static constexpr int SMEM = OFF_U + 2 * U_BYTES + 1024;
-};
-
-constexpr int kEpiWarps = 8;                 // two warpgroups split each row's columns
+constexpr int kAccDrain = 2;                   // tiles per second-product drain
+constexpr int kStages = 3;                     // TMA stages of (Y, V')
+constexpr int kEpiWarps = 8;                   // two warpgroups split each row's columns
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kPairThreads = kEpiThreads + 64; // + TMA producer warp + MMA warp
 
 template <int NP>
+struct PairCfg {
+  static constexpr int Y_BYTES = 64 * NP * 2;  // one piece
+  static constexpr int V_BYTES = 128 * 64 * 4;
+  static constexpr int STAGE = 2 * Y_BYTES + V_BYTES;
+  static constexpr int OFF_U = kStages * STAGE;
+  static constexpr int U_BYTES = 128 * 64 * 2;
+  static constexpr int SMEM = OFF_U + 2 * U_BYTES + 1024;
+  static constexpr uint32_t T_XM = 0, T_XH = NP / 2, T_S0 = 128, T_S1 = 192, T_ACC = 256,
+                            T_RUN = 384;
+};
+
+template <int NP>
 __global__ void __launch_bounds__(kPairThreads, 1)
-    pair_kernel(const __grid_constant__ CUtensorMap mXm, const __grid_constant__ CUtensorMap mXh,
-                const __grid_constant__ CUtensorMap mYm, const __grid_constant__ CUtensorMap mYh,
+    pair_kernel(const __grid_constant__ CUtensorMap mYm, const __grid_constant__ CUtensorMap mYh,
                 const __grid_constant__ CUtensorMap mV, PairArgs a) {
   using C = PairCfg<NP>;
   extern __shared__ uint8_t p_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ uint64_t x_full, full[2], empty[2], s_full, s_free, u_full, u_free, acc_ready[2],
-      acc_free[2], drain;
+  __shared__ uint64_t full[kStages], empty[kStages], s_full, s_free, u_full, u_free, acc_ready,
+      acc_free, drain;
   __shared__ uint32_t tslot;
   __shared__ volatile int abort_flag;
   __shared__ double ered[kEpiWarps];
@@ -624,17 +628,16 @@ __global__ void __launch_bounds__(kPairThreads, 1)
   constexpr int NKB = NP / 64;
 
   if (tid == 0) {
-    mbar_init(&x_full, 1);
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
-      mbar_init(&acc_ready[s], 1);
-      mbar_init(&acc_free[s], kEpiThreads);
     }
     mbar_init(&s_full, 1);
     mbar_init(&s_free, kEpiThreads);
     mbar_init(&u_full, kEpiThreads);
     mbar_init(&u_free, 1);
+    mbar_init(&acc_ready, 1);
+    mbar_init(&acc_free, kEpiThreads);
     mbar_init(&drain, 1);
     abort_flag = 0;
     fence_mbar_init();
@@ -646,32 +649,42 @@ __global__ void __launch_bounds__(kPairThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  // TMEM columns: S = A0 [0, 64) + A1 [64, 128); second-product accumulators
-  // acc[0] [128, 256) and acc[1] [256, 384) alternate by drain group; the
-  // running sum [384, 512).
   const uint32_t tbase = tslot;
-  const uint32_t t_run = tbase + 384;
+
+  // ---------------- X tile -> tensor memory (lane = row; warpgroup 0 the m
+  // piece, warpgroup 1 the h piece; fp16 pairs as stored in memory)
+  if (warp < kEpiWarps) {
+    const int quad = warp & 3, half = warp >> 2;
+    const int r = quad * 32 + lane;
+    const long x = (long)x0 + r;
+    const uint32_t lane_off = static_cast<uint32_t>(quad * 32) << 16;
+    const uint4* src = reinterpret_cast<const uint4*>((half ? a.xh : a.xm) + x * a.ldx);
+#pragma unroll
+    for (int c0 = 0; c0 < NP / 2; c0 += 32) {
+      uint32_t w[32];
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        const uint4 q = (x < a.X) ? src[c0 / 4 + v] : make_uint4(0u, 0u, 0u, 0u);
+        w[4 * v] = q.x; w[4 * v + 1] = q.y; w[4 * v + 2] = q.z; w[4 * v + 3] = q.w;
+      }
+      tmem_st32(tbase + lane_off + (half ? C::T_XH : C::T_XM) + c0, w);
+    }
+    tmem_wait_st();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
 
   if (warp == prod_warp && lane == 0) {
     // ---------------- TMA producer
-    prefetch_tmap(&mXm); prefetch_tmap(&mXh); prefetch_tmap(&mYm); prefetch_tmap(&mYh);
-    prefetch_tmap(&mV);
-    int last_parity[2] = {-1, -1};
-    bool xl = false;
-    if (T > 0) {
-      mbar_expect_tx(&x_full, 2 * C::X_BYTES);
-      for (int kb = 0; kb < NKB; ++kb) {
-        tma_load_2d(sm + kb * 16384, &mXm, &x_full, kb * 64, x0);
-        tma_load_2d(sm + C::X_BYTES + kb * 16384, &mXh, &x_full, kb * 64, x0);
-      }
-      xl = true;
-    }
+    prefetch_tmap(&mYm); prefetch_tmap(&mYh); prefetch_tmap(&mV);
+    int last_parity[kStages] = {-1, -1, -1};
     for (int t = 0; t < T && !abort_flag; ++t) {
-      const int s = t & 1, use = t >> 1;
+      const int s = t % kStages, use = t / kStages;
       if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) {
         atomicExch(a.status, 21); abort_flag = 1; break;
       }
-      uint8_t* st = sm + C::OFF_STAGE + s * C::STAGE;
+      uint8_t* st = sm + s * C::STAGE;
       mbar_expect_tx(&full[s], C::STAGE);
       const int yr = y0 + t * 64;
       for (int kb = 0; kb < NKB; ++kb) {
@@ -682,72 +695,63 @@ __global__ void __launch_bounds__(kPairThreads, 1)
       tma_load_2d(st + 2 * C::Y_BYTES + 16384, &mV, &full[s], yr + 32, x0);
       last_parity[s] = use & 1;
     }
-    if (xl) mbar_wait(&x_full, 0);
-    for (int s = 0; s < 2; ++s)
+    for (int s = 0; s < kStages; ++s)
       if (last_parity[s] >= 0) mbar_wait(&full[s], last_parity[s]);
   } else if (warp == mma_warp && lane == 0) {
     // ---------------- MMA issuer
     const uint32_t id_s = idesc_f16(128, 64, false, false, false);
     const uint32_t id_acc = idesc_f16(128, NP, false, false, true);
-    const uint32_t xm = smem_u32(sm), xh = smem_u32(sm + C::X_BYTES);  // 1024-aligned tile bases
-    const uint32_t uh = smem_u32(sm + C::OFF_U), ul = smem_u32(sm + C::OFF_U + C::U_BYTES);
-    bool good = T > 0 && mbar_wait(&x_full, 0);
-    if (T > 0 && !good) { atomicExch(a.status, 22); abort_flag = 1; }
-    // Descriptors of every operand tile start from one base descriptor; the
-    // address field counts 16-byte units, so tile offsets add as immediates.
-    const uint64_t dxm = sdesc_sw128(xm, 16, 1024), dxh = sdesc_sw128(xh, 16, 1024);
-    const uint64_t duh = sdesc_sw128(uh, 16, 1024), dul = sdesc_sw128(ul, 16, 1024);
-    const uint64_t dy0 = sdesc_sw128(smem_u32(sm + C::OFF_STAGE), 16, 1024);
-    const uint64_t dy0mn = sdesc_sw128(smem_u32(sm + C::OFF_STAGE), 8192, 1024);
+    // Descriptors start from one base; the address field counts 16-byte units,
+    // so tile offsets add as immediates.
+    const uint64_t duh = sdesc_sw128(smem_u32(sm + C::OFF_U), 16, 1024);
+    const uint64_t dul = duh + (C::U_BYTES >> 4);
+    const uint64_t dy0 = sdesc_sw128(smem_u32(sm), 16, 1024);
+    const uint64_t dy0mn = sdesc_sw128(smem_u32(sm), 8192, 1024);
     constexpr uint64_t kStage16 = C::STAGE >> 4, kYh16 = C::Y_BYTES >> 4;
+    const uint32_t txm = tbase + C::T_XM, txh = tbase + C::T_XH;
+    const uint32_t ts0 = tbase + C::T_S0, ts1 = tbase + C::T_S1, tacc = tbase + C::T_ACC;
+    bool good = T > 0;
     auto issue_acc = [&](int u) -> bool {
-      const int s = u & 1, grp = u / kAccDrain, buf = grp & 1;
+      const int s = u % kStages, grp = u / kAccDrain;
       const bool first = (u % kAccDrain) == 0;
       const bool last = (u % kAccDrain) == kAccDrain - 1 || u == T - 1;
-      // acc[buf] was last used by group grp - 2; its drain must be done
-      if (first && grp >= 2 && !mbar_wait(&acc_free[buf], ((grp >> 1) - 1) & 1)) return false;
+      if (first && grp > 0 && !mbar_wait(&acc_free, (grp - 1) & 1)) return false;
       if (!mbar_wait(&u_full, u & 1)) return false;
       tc_fence_after();
       const uint64_t bym = dy0mn + s * kStage16, byh = bym + kYh16;
-      const uint32_t t_acc = tbase + 128 + buf * 128;
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
-        mma_f16(t_acc, duh + kk * 2, bym + kk * 128, id_acc, (first && kk == 0) ? 0u : 1u);
+        mma_f16(tacc, duh + kk * 2, bym + kk * 128, id_acc, (first && kk == 0) ? 0u : 1u);
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) mma_f16(t_acc, duh + kk * 2, byh + kk * 128, id_acc, 1u);
+      for (int kk = 0; kk < 4; ++kk) mma_f16(tacc, duh + kk * 2, byh + kk * 128, id_acc, 1u);
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) mma_f16(t_acc, dul + kk * 2, bym + kk * 128, id_acc, 1u);
+      for (int kk = 0; kk < 4; ++kk) mma_f16(tacc, dul + kk * 2, bym + kk * 128, id_acc, 1u);
       mma_commit(&empty[s]);
       mma_commit(&u_free);
-      if (last) mma_commit(&acc_ready[buf]);
+      if (last) mma_commit(&acc_ready);
       return true;
     };
     for (int t = 0; good && t < T && !abort_flag; ++t) {
-      const int s = t & 1, use = t >> 1;
+      const int s = t % kStages, use = t / kStages;
       if (!mbar_wait(&full[s], use & 1)) { atomicExch(a.status, 23); abort_flag = 1; good = false; break; }
       if (t > 0 && !mbar_wait(&s_free, (t - 1) & 1)) {
         atomicExch(a.status, 24); abort_flag = 1; good = false; break;
       }
       tc_fence_after();
       const uint64_t dym = dy0 + s * kStage16, dyh = dym + kYh16;
-      const uint32_t t_s0 = tbase, t_s1 = tbase + 64;
-      // K step kk: X tile offset (kk/4)*16384 + (kk%4)*32 bytes, Y tile (kk/4)*8192 + (kk%4)*32
+      // K step kk: 8 TMEM columns of X; Y tile offset (kk/4)*8192 + (kk%4)*32 bytes
 #pragma unroll
       for (int kk = 0; kk < NP / 16; ++kk)
-        mma_f16(t_s0, dxm + (kk >> 2) * 1024 + (kk & 3) * 2, dym + (kk >> 2) * 512 + (kk & 3) * 2,
-                id_s, kk > 0 ? 1u : 0u);
+        mma_f16_ts(ts0, txm + kk * 8, dym + (kk >> 2) * 512 + (kk & 3) * 2, id_s, kk > 0 ? 1u : 0u);
 #pragma unroll
       for (int kk = 0; kk < NP / 16; ++kk)
-        mma_f16(t_s1, dxm + (kk >> 2) * 1024 + (kk & 3) * 2, dyh + (kk >> 2) * 512 + (kk & 3) * 2,
-                id_s, kk > 0 ? 1u : 0u);
+        mma_f16_ts(ts1, txm + kk * 8, dyh + (kk >> 2) * 512 + (kk & 3) * 2, id_s, kk > 0 ? 1u : 0u);
 #pragma unroll
       for (int kk = 0; kk < NP / 16; ++kk)
-        mma_f16(t_s1, dxh + (kk >> 2) * 1024 + (kk & 3) * 2, dym + (kk >> 2) * 512 + (kk & 3) * 2,
-                id_s, 1u);
+        mma_f16_ts(ts1, txh + kk * 8, dym + (kk >> 2) * 512 + (kk & 3) * 2, id_s, 1u);
 #pragma unroll
       for (int kk = 0; kk < NP / 16; ++kk)
-        mma_f16(t_s1, dxh + (kk >> 2) * 1024 + (kk & 3) * 2, dyh + (kk >> 2) * 512 + (kk & 3) * 2,
-                id_s, 1u);
+        mma_f16_ts(ts1, txh + kk * 8, dyh + (kk >> 2) * 512 + (kk & 3) * 2, id_s, 1u);
       mma_commit(&s_full);
       if (t > 0 && !issue_acc(t - 1)) { atomicExch(a.status, 25); abort_flag = 1; good = false; break; }
     }
@@ -765,47 +769,25 @@ __global__ void __launch_bounds__(kPairThreads, 1)
     uint8_t* ulp = uhp + C::U_BYTES;
     const int sw = r & 7;
     constexpr int ACOLS = NP / 2;  // accumulator columns per epilogue half
+    const uint32_t t_acc = tbase + C::T_ACC, t_run = tbase + C::T_RUN;
     double esum = 0.0;
     bool ok = T > 0;
-    const int ngroups = (T + kAccDrain - 1) / kAccDrain;
-    // Adds acc[grp & 1] into the running sum (drain group grp), then frees it.
-    auto drain_group = [&](int grp) -> bool {
-      const int buf = grp & 1;
-      if (!mbar_wait(&acc_ready[buf], (grp >> 1) & 1)) return false;
-      tc_fence_after();
-      const uint32_t t_acc = tbase + 128 + buf * 128;
-#pragma unroll 1
-      for (int c = 0; c < ACOLS; c += 32) {
-        uint32_t ua[32], ur[32];
-        tmem_ld32(t_acc + lane_off + half * ACOLS + c, ua);
-        if (grp > 0) tmem_ld32(t_run + lane_off + half * ACOLS + c, ur);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          ur[j] = __float_as_uint((grp > 0 ? __uint_as_float(ur[j]) : 0.0f) + __uint_as_float(ua[j]));
-        tmem_st32(t_run + lane_off + half * ACOLS + c, ur);
-      }
-      tmem_wait_st();
-      tc_fence_before();
-      mbar_arrive(&acc_free[buf]);
-      return true;
-    };
     for (int t = 0; t < T && !abort_flag; ++t) {
-      const int s = t & 1;
+      const int s = t % kStages;
       if (!mbar_wait(&s_full, t & 1)) { atomicExch(a.status, 27); abort_flag = 1; ok = false; break; }
       tc_fence_after();
       float sv[32];
       {
         uint32_t u0[32], u1[32];
-        tmem_ld32(tbase + lane_off + half * 32, u0);
-        tmem_ld32(tbase + lane_off + 64 + half * 32, u1);
+        tmem_ld32(tbase + lane_off + C::T_S0 + half * 32, u0);
+        tmem_ld32(tbase + lane_off + C::T_S1 + half * 32, u1);
         tmem_wait_ld();
 #pragma unroll
         for (int j = 0; j < 32; ++j) sv[j] = __uint_as_float(u0[j]) + __uint_as_float(u1[j]);
       }
       tc_fence_before();
       mbar_arrive(&s_free);
-      const uint8_t* vt = sm + C::OFF_STAGE + s * C::STAGE + 2 * C::Y_BYTES + half * 16384;
+      const uint8_t* vt = sm + s * C::STAGE + 2 * C::Y_BYTES + half * 16384;
       uint32_t hi[16], lo[16];
       float etile = 0.0f;
 #pragma unroll
@@ -839,13 +821,26 @@ __global__ void __launch_bounds__(kPairThreads, 1)
       }
       fence_async_smem();
       mbar_arrive(&u_full);
-      // drain the previous group one tile late, while the MMA fills the other buffer
-      if ((t % kAccDrain) == 0 && t > 0 && !drain_group(t / kAccDrain - 1)) {
-        atomicExch(a.status, 29); abort_flag = 1; ok = false; break;
+      // drain the second-product accumulator into the running sum after each group
+      if ((t % kAccDrain) == kAccDrain - 1 || t == T - 1) {
+        const int grp = t / kAccDrain;
+        if (!mbar_wait(&acc_ready, grp & 1)) { atomicExch(a.status, 29); abort_flag = 1; ok = false; break; }
+        tc_fence_after();
+#pragma unroll 1
+        for (int c = 0; c < ACOLS; c += 32) {
+          uint32_t ua[32], ur[32];
+          tmem_ld32(t_acc + lane_off + half * ACOLS + c, ua);
+          if (grp > 0) tmem_ld32(t_run + lane_off + half * ACOLS + c, ur);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            ur[j] = __float_as_uint((grp > 0 ? __uint_as_float(ur[j]) : 0.0f) + __uint_as_float(ua[j]));
+          tmem_st32(t_run + lane_off + half * ACOLS + c, ur);
+        }
+        tmem_wait_st();
+        tc_fence_before();
+        mbar_arrive(&acc_free);
       }
-    }
-    if (ok && !abort_flag && ngroups > 0 && !drain_group(ngroups - 1)) {
-      atomicExch(a.status, 30); abort_flag = 1; ok = false;
     }
     ok = ok && !abort_flag;
     // ---------------- write the running sum
@@ -1244,32 +1239,28 @@ cudaError_t mixed_enqueue(MixedState* m, const double* C, double* K, double* Ex,
 
   // ---- steps 2-3: the three fused pair contractions
   hook(1, 1);
-  auto launch_pair = [&](const CUtensorMap& Xm, const CUtensorMap& Xh, const CUtensorMap& Ym,
-                         const CUtensorMap& Yh, const CUtensorMap& Vm, const PairArgs& pa,
-                         dim3 grid) {
+  auto launch_pair = [&](const CUtensorMap& Ym, const CUtensorMap& Yh, const CUtensorMap& Vm,
+                         const PairArgs& pa, dim3 grid) {
     if (np == 64)
-      pair_kernel<64><<<grid, kPairThreads, PairCfg<64>::SMEM, s>>>(Xm, Xh, Ym, Yh, Vm, pa);
+      pair_kernel<64><<<grid, kPairThreads, PairCfg<64>::SMEM, s>>>(Ym, Yh, Vm, pa);
     else
-      pair_kernel<128><<<grid, kPairThreads, PairCfg<128>::SMEM, s>>>(Xm, Xh, Ym, Yh, Vm, pa);
+      pair_kernel<128><<<grid, kPairThreads, PairCfg<128>::SMEM, s>>>(Ym, Yh, Vm, pa);
     count_launch();
   };
   {  // role A: M2[g][j] = sum_R (V o P)[g][R] Psi[R][j], and sum V o P^2
-    PairArgs pa{(int)na, (int)ng, m->ychunkA, n, m->sc, SC_F_AB, SC_OUT_AB, m->M2p, n,
-                na * n, 0, m->EpA, m->status};
-    launch_pair(m->m_psig128_m, m->m_psig128_h, m->m_psi64_m, m->m_psi64_h, m->m_V, pa,
-                dim3(m->xa, m->partsA));
+    PairArgs pa{(int)na, (int)ng, m->ychunkA, n, m->psig_m, m->psig_h, np, m->sc, SC_F_AB,
+                SC_OUT_AB, m->M2p, n, na * n, 0, m->EpA, m->status};
+    launch_pair(m->m_psi64_m, m->m_psi64_h, m->m_V, pa, dim3(m->xa, m->partsA));
   }
   {  // role B: M1[j][R] = sum_g (V^T o P^T)[R][g] Psi_g[g][j], written transposed
-    PairArgs pa{(int)ng, (int)na, (int)rup(na, 64), n, m->sc, SC_F_AB, SC_OUT_AB, m->M1,
-                m->Ng4, 0, 1, nullptr, m->status};
-    launch_pair(m->m_psi128_m, m->m_psi128_h, m->m_psig64_m, m->m_psig64_h, m->m_VT, pa,
-                dim3((unsigned)((ng + 127) / 128), 1));
+    PairArgs pa{(int)ng, (int)na, (int)rup(na, 64), n, m->psi_m, m->psi_h, np, m->sc, SC_F_AB,
+                SC_OUT_AB, m->M1, m->Ng4, 0, 1, nullptr, m->status};
+    launch_pair(m->m_psig64_m, m->m_psig64_h, m->m_VT, pa, dim3((unsigned)((ng + 127) / 128), 1));
   }
   {  // role C: M3[g][j] = sum_g' (W o Q)[g][g'] Psi_g[g'][j], and sum W o Q^2
-    PairArgs pa{(int)na, (int)na, m->ychunkC, n, m->sc, SC_F_C, SC_OUT_C, m->M3p, n, na * n, 0,
-                m->EpC, m->status};
-    launch_pair(m->m_psig128_m, m->m_psig128_h, m->m_psig64_m, m->m_psig64_h, m->m_W, pa,
-                dim3(m->xa, m->partsC));
+    PairArgs pa{(int)na, (int)na, m->ychunkC, n, m->psig_m, m->psig_h, np, m->sc, SC_F_C,
+                SC_OUT_C, m->M3p, n, na * n, 0, m->EpC, m->status};
+    launch_pair(m->m_psig64_m, m->m_psig64_h, m->m_W, pa, dim3(m->xa, m->partsC));
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
