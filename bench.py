@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--config", type=int, default=2,
                    help="2: the 64-centre cell (the metric's workload); 1 or 4 for smaller cases")
     p.add_argument("--k", type=int, default=None, help="lattice size of config 4 (k^3 centres)")
+    p.add_argument("--n-occ", type=int, default=None,
+                   help="override the number of occupied orbitals (profiling cases only)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
     p.add_argument("--no-serve", action="store_true", help="skip the serving-latency loop")
@@ -265,7 +267,10 @@ def main():
     mode = args.mode
     steps = args.steps or (200 if mode != "fp64" else 6)
     warm = max(3, args.warmup)
-    cell = load_cell(config_spec(args.config, k=args.k))
+    spec = config_spec(args.config, k=args.k)
+    if args.n_occ:
+        spec.n_occ = args.n_occ
+    cell = load_cell(spec)
     N, n, Ng, Na = cell.N, cell.n, cell.Ng, cell.Naux
     workload = WORKLOAD if args.config == 2 else f"{cell.spec.name}: N={N}, n={n}, N_g={Ng}, N_aux={Na}"
     Cs = pseudo_scf_sequence(cell.S, cell.C, steps + warm, 1000 + rank)
