@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(&set_ready[s], 1);
-      mbar_init(&set_free[s], 128);
+      mbar_init(&set_free[s], 4);  // one arrival per epilogue warp
     }
     mbar_init(&drain, 1);
     abort_flag = 0;
@@ -455,19 +455,22 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int s = 0; s < G_STAGES; ++s)
       if (last_parity[s] >= 0) mbar_wait(&full[s], last_parity[s]);
-  } else if (warp == 5 && lane == 0) {
+  } else if (warp == 5) {
+    // whole warp runs the loop; one elected lane issues each MMA and commit
     const uint32_t idesc = idesc_f16(128, 128, false, false, false);
     const uint64_t dst0 = sdesc_sw128(smem_u32(sm), 16, 1024);
-    for (int kb = 0; kb < nkb && !abort_flag; ++kb) {
+    auto fail = [&](int code) {
+      if (lane == 0) { atomicExch(g.status, code); abort_flag = 1; }
+      __syncwarp();
+    };
+    for (int kb = 0; kb < nkb && !__shfl_sync(0xffffffffu, (int)abort_flag, 0); ++kb) {
       const int s = kb % G_STAGES, grp = kb / kDrain, set = grp & 1;
       const bool first = (kb % kDrain) == 0;
       const bool last = (kb % kDrain) == kDrain - 1 || kb == nkb - 1;
-      if (first && grp >= 2 && !mbar_wait(&set_free[set], ((grp >> 1) - 1) & 1)) {
-        atomicExch(g.status, 14); abort_flag = 1; break;
+      if (first && grp >= 2 && !mbar_wait_warp(&set_free[set], ((grp >> 1) - 1) & 1)) {
+        fail(14); break;
       }
-      if (!mbar_wait(&full[s], (kb / G_STAGES) & 1)) {
-        atomicExch(g.status, 12); abort_flag = 1; break;
-      }
+      if (!mbar_wait_warp(&full[s], (kb / G_STAGES) & 1)) { fail(12); break; }
       tc_fence_after();
       // stage s: A m-piece at +0, A h at +16 KB, B m at +32 KB, B h at +48 KB; the
       // descriptor address field counts 16-byte units (1024 per 16 KB, 2 per K step)
@@ -476,19 +479,25 @@ __global__ void __launch_bounds__(192, 1)
       const uint32_t t0 = tbase + set * 256, t1 = t0 + 128;
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
-        mma_f16(t0, dam + kk * 2, dbm + kk * 2, idesc, (first && kk == 0) ? 0u : 1u);
+        if (elect_one()) mma_f16(t0, dam + kk * 2, dbm + kk * 2, idesc, (first && kk == 0) ? 0u : 1u);
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
-        mma_f16(t1, dam + kk * 2, dbh + kk * 2, idesc, (first && kk == 0) ? 0u : 1u);
+        if (elect_one()) mma_f16(t1, dam + kk * 2, dbh + kk * 2, idesc, (first && kk == 0) ? 0u : 1u);
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) mma_f16(t1, dah + kk * 2, dbm + kk * 2, idesc, 1u);
+      for (int kk = 0; kk < 4; ++kk)
+        if (elect_one()) mma_f16(t1, dah + kk * 2, dbm + kk * 2, idesc, 1u);
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) mma_f16(t1, dah + kk * 2, dbh + kk * 2, idesc, 1u);
-      mma_commit(&empty[s]);
-      if (last) mma_commit(&set_ready[set]);
+      for (int kk = 0; kk < 4; ++kk)
+        if (elect_one()) mma_f16(t1, dah + kk * 2, dbh + kk * 2, idesc, 1u);
+      if (elect_one()) {
+        mma_commit(&empty[s]);
+        if (last) mma_commit(&set_ready[set]);
+      }
+      __syncwarp();
     }
-    mma_commit(&drain);
-    mbar_wait(&drain, 0);
+    if (elect_one()) mma_commit(&drain);
+    __syncwarp();
+    mbar_wait_warp(&drain, 0);
   } else if (warp < 4) {
     const int r = warp * 32 + lane;
     const uint32_t lane_off = static_cast<uint32_t>(warp * 32) << 16;
@@ -498,7 +507,11 @@ __global__ void __launch_bounds__(192, 1)
     bool ok = true;
     for (int gi = 0; gi < ngroups; ++gi) {
       const int set = gi & 1;
-      if (!mbar_wait(&set_ready[set], (gi >> 1) & 1)) { ok = false; atomicExch(g.status, 13); break; }
+      if (!mbar_wait_warp(&set_ready[set], (gi >> 1) & 1)) {
+        ok = false;
+        if (lane == 0) atomicExch(g.status, 13);
+        break;
+      }
       tc_fence_after();
 #pragma unroll
       for (int c = 0; c < 128; c += 16) {
@@ -510,7 +523,8 @@ __global__ void __launch_bounds__(192, 1)
         for (int j = 0; j < 16; ++j) run[c + j] += __uint_as_float(a0[j]) + __uint_as_float(a1[j]);
       }
       tc_fence_before();
-      mbar_arrive(&set_free[set]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&set_free[set]);
     }
     ok = ok && !abort_flag;
     const float scale = g.sc[g.scale_idx];
@@ -633,11 +647,11 @@ __global__ void __launch_bounds__(kPairThreads, 1)
       mbar_init(&empty[s], 1);
     }
     mbar_init(&s_full, 1);
-    mbar_init(&s_free, kEpiThreads);
-    mbar_init(&u_full, kEpiThreads);
+    mbar_init(&s_free, kEpiWarps);  // epilogue barriers: one arrival per warp
+    mbar_init(&u_full, kEpiWarps);
     mbar_init(&u_free, 1);
     mbar_init(&acc_ready, 1);
-    mbar_init(&acc_free, kEpiThreads);
+    mbar_init(&acc_free, kEpiWarps);
     mbar_init(&drain, 1);
     abort_flag = 0;
     fence_mbar_init();
@@ -697,8 +711,9 @@ __global__ void __launch_bounds__(kPairThreads, 1)
     }
     for (int s = 0; s < kStages; ++s)
       if (last_parity[s] >= 0) mbar_wait(&full[s], last_parity[s]);
-  } else if (warp == mma_warp && lane == 0) {
-    // ---------------- MMA issuer
+  } else if (warp == mma_warp) {
+    // ---------------- MMA issuer: the whole warp runs the loop (warp-uniform
+    // descriptors and waits); one elected lane issues each MMA and commit.
     const uint32_t id_s = idesc_f16(128, 64, false, false, false);
     const uint32_t id_acc = idesc_f16(128, NP, false, false, true);
     // Descriptors start from one base; the address field counts 16-byte units,
@@ -710,54 +725,64 @@ __global__ void __launch_bounds__(kPairThreads, 1)
     constexpr uint64_t kStage16 = C::STAGE >> 4, kYh16 = C::Y_BYTES >> 4;
     const uint32_t txm = tbase + C::T_XM, txh = tbase + C::T_XH;
     const uint32_t ts0 = tbase + C::T_S0, ts1 = tbase + C::T_S1, tacc = tbase + C::T_ACC;
+    auto aborted = [&]() { return __shfl_sync(0xffffffffu, (int)abort_flag, 0) != 0; };
+    auto fail = [&](int code) {
+      if (lane == 0) { atomicExch(a.status, code); abort_flag = 1; }
+      __syncwarp();
+    };
     bool good = T > 0;
     auto issue_acc = [&](int u) -> bool {
       const int s = u % kStages, grp = u / kAccDrain;
       const bool first = (u % kAccDrain) == 0;
       const bool last = (u % kAccDrain) == kAccDrain - 1 || u == T - 1;
-      if (first && grp > 0 && !mbar_wait(&acc_free, (grp - 1) & 1)) return false;
-      if (!mbar_wait(&u_full, u & 1)) return false;
+      if (first && grp > 0 && !mbar_wait_warp(&acc_free, (grp - 1) & 1)) return false;
+      if (!mbar_wait_warp(&u_full, u & 1)) return false;
       tc_fence_after();
       const uint64_t bym = dy0mn + s * kStage16, byh = bym + kYh16;
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
-        mma_f16(tacc, duh + kk * 2, bym + kk * 128, id_acc, (first && kk == 0) ? 0u : 1u);
+        if (elect_one()) mma_f16(tacc, duh + kk * 2, bym + kk * 128, id_acc, (first && kk == 0) ? 0u : 1u);
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) mma_f16(tacc, duh + kk * 2, byh + kk * 128, id_acc, 1u);
+      for (int kk = 0; kk < 4; ++kk)
+        if (elect_one()) mma_f16(tacc, duh + kk * 2, byh + kk * 128, id_acc, 1u);
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) mma_f16(tacc, dul + kk * 2, bym + kk * 128, id_acc, 1u);
-      mma_commit(&empty[s]);
-      mma_commit(&u_free);
-      if (last) mma_commit(&acc_ready);
+      for (int kk = 0; kk < 4; ++kk)
+        if (elect_one()) mma_f16(tacc, dul + kk * 2, bym + kk * 128, id_acc, 1u);
+      if (elect_one()) {
+        mma_commit(&empty[s]);
+        mma_commit(&u_free);
+        if (last) mma_commit(&acc_ready);
+      }
+      __syncwarp();
       return true;
     };
-    for (int t = 0; good && t < T && !abort_flag; ++t) {
+    for (int t = 0; good && t < T && !aborted(); ++t) {
       const int s = t % kStages, use = t / kStages;
-      if (!mbar_wait(&full[s], use & 1)) { atomicExch(a.status, 23); abort_flag = 1; good = false; break; }
-      if (t > 0 && !mbar_wait(&s_free, (t - 1) & 1)) {
-        atomicExch(a.status, 24); abort_flag = 1; good = false; break;
-      }
+      if (!mbar_wait_warp(&full[s], use & 1)) { fail(23); good = false; break; }
+      if (t > 0 && !mbar_wait_warp(&s_free, (t - 1) & 1)) { fail(24); good = false; break; }
       tc_fence_after();
       const uint64_t dym = dy0 + s * kStage16, dyh = dym + kYh16;
       // K step kk: 8 TMEM columns of X; Y tile offset (kk/4)*8192 + (kk%4)*32 bytes
 #pragma unroll
       for (int kk = 0; kk < NP / 16; ++kk)
-        mma_f16_ts(ts0, txm + kk * 8, dym + (kk >> 2) * 512 + (kk & 3) * 2, id_s, kk > 0 ? 1u : 0u);
+        if (elect_one()) mma_f16_ts(ts0, txm + kk * 8, dym + (kk >> 2) * 512 + (kk & 3) * 2, id_s, kk > 0 ? 1u : 0u);
 #pragma unroll
       for (int kk = 0; kk < NP / 16; ++kk)
-        mma_f16_ts(ts1, txm + kk * 8, dyh + (kk >> 2) * 512 + (kk & 3) * 2, id_s, kk > 0 ? 1u : 0u);
+        if (elect_one()) mma_f16_ts(ts1, txm + kk * 8, dyh + (kk >> 2) * 512 + (kk & 3) * 2, id_s, kk > 0 ? 1u : 0u);
 #pragma unroll
       for (int kk = 0; kk < NP / 16; ++kk)
-        mma_f16_ts(ts1, txh + kk * 8, dym + (kk >> 2) * 512 + (kk & 3) * 2, id_s, 1u);
+        if (elect_one()) mma_f16_ts(ts1, txh + kk * 8, dym + (kk >> 2) * 512 + (kk & 3) * 2, id_s, 1u);
 #pragma unroll
       for (int kk = 0; kk < NP / 16; ++kk)
-        mma_f16_ts(ts1, txh + kk * 8, dyh + (kk >> 2) * 512 + (kk & 3) * 2, id_s, 1u);
-      mma_commit(&s_full);
-      if (t > 0 && !issue_acc(t - 1)) { atomicExch(a.status, 25); abort_flag = 1; good = false; break; }
+        if (elect_one()) mma_f16_ts(ts1, txh + kk * 8, dyh + (kk >> 2) * 512 + (kk & 3) * 2, id_s, 1u);
+      if (elect_one()) mma_commit(&s_full);
+      __syncwarp();
+      if (t > 0 && !issue_acc(t - 1)) { fail(25); good = false; break; }
     }
-    if (good && T > 0 && !issue_acc(T - 1)) { atomicExch(a.status, 26); abort_flag = 1; }
-    mma_commit(&drain);
-    mbar_wait(&drain, 0);
+    if (good && T > 0 && !issue_acc(T - 1)) fail(26);
+    if (elect_one()) mma_commit(&drain);
+    __syncwarp();
+    mbar_wait_warp(&drain, 0);
   } else if (warp < kEpiWarps) {
     // ---------------- epilogue: warp quadrant = TMEM lanes (rows), half = columns
     const int quad = warp & 3, half = warp >> 2;
@@ -772,9 +797,16 @@ __global__ void __launch_bounds__(kPairThreads, 1)
     const uint32_t t_acc = tbase + C::T_ACC, t_run = tbase + C::T_RUN;
     double esum = 0.0;
     bool ok = T > 0;
-    for (int t = 0; t < T && !abort_flag; ++t) {
+    // waits and the abort test are warp-uniform: the tensor-memory loads and
+    // stores below are warp-collective
+    auto aborted = [&]() { return __shfl_sync(0xffffffffu, (int)abort_flag, 0) != 0; };
+    auto fail = [&](int code) {
+      if (lane == 0) { atomicExch(a.status, code); abort_flag = 1; }
+      __syncwarp();
+    };
+    for (int t = 0; t < T && !aborted(); ++t) {
       const int s = t % kStages;
-      if (!mbar_wait(&s_full, t & 1)) { atomicExch(a.status, 27); abort_flag = 1; ok = false; break; }
+      if (!mbar_wait_warp(&s_full, t & 1)) { fail(27); ok = false; break; }
       tc_fence_after();
       float sv[32];
       {
@@ -786,7 +818,8 @@ __global__ void __launch_bounds__(kPairThreads, 1)
         for (int j = 0; j < 32; ++j) sv[j] = __uint_as_float(u0[j]) + __uint_as_float(u1[j]);
       }
       tc_fence_before();
-      mbar_arrive(&s_free);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&s_free);
       const uint8_t* vt = sm + s * C::STAGE + 2 * C::Y_BYTES + half * 16384;
       uint32_t hi[16], lo[16];
       float etile = 0.0f;
@@ -812,7 +845,7 @@ __global__ void __launch_bounds__(kPairThreads, 1)
         lo[2 * q + 1] = *reinterpret_cast<const uint32_t*>(&l23);
       }
       esum += (double)etile;
-      if (t > 0 && !mbar_wait(&u_free, (t - 1) & 1)) { atomicExch(a.status, 28); abort_flag = 1; ok = false; break; }
+      if (t > 0 && !mbar_wait_warp(&u_free, (t - 1) & 1)) { fail(28); ok = false; break; }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int off = r * 128 + (((4 * half + q) ^ sw) << 4);
@@ -820,11 +853,12 @@ __global__ void __launch_bounds__(kPairThreads, 1)
         *reinterpret_cast<uint4*>(ulp + off) = make_uint4(lo[4 * q], lo[4 * q + 1], lo[4 * q + 2], lo[4 * q + 3]);
       }
       fence_async_smem();
-      mbar_arrive(&u_full);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&u_full);
       // drain the second-product accumulator into the running sum after each group
       if ((t % kAccDrain) == kAccDrain - 1 || t == T - 1) {
         const int grp = t / kAccDrain;
-        if (!mbar_wait(&acc_ready, grp & 1)) { atomicExch(a.status, 29); abort_flag = 1; ok = false; break; }
+        if (!mbar_wait_warp(&acc_ready, grp & 1)) { fail(29); ok = false; break; }
         tc_fence_after();
 #pragma unroll 1
         for (int c = 0; c < ACOLS; c += 32) {
@@ -839,10 +873,11 @@ __global__ void __launch_bounds__(kPairThreads, 1)
         }
         tmem_wait_st();
         tc_fence_before();
-        mbar_arrive(&acc_free);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_free);
       }
     }
-    ok = ok && !abort_flag;
+    ok = ok && !aborted();
     // ---------------- write the running sum
     tc_fence_after();
     const float os = a.sc[a.out_idx];
