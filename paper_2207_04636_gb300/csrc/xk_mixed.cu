@@ -580,13 +580,18 @@ __global__ void __launch_bounds__(192, 1)
 //   S = X Y^T as A0 (m.m, exact) + A1 (cross terms)       K = NP
 //   T = V' o S;  e += sum_y T S  (the closed-form energy term, optional)
 //   U = f T as floating hi/lo;  acc[x][j] += sum_y U[x][y] Y[y][j]
-// X: per-row (m, h) pieces, copied once per CTA into tensor memory and used
-// there as the A operand of S; Y: per-row (m, h) pieces [rows][NP], K-major,
-// streamed by TMA, and reused as the MN-major B operand of the second product;
-// V': FP32 [X rows][Y cols].  Three TMA stages of (Y, V') keep about 128 KB of
-// loads in flight per SM.
-// TMEM: X pieces [0, NP), S = A0 [128, 192) + A1 [192, 256), acc [256, 384),
-// running sum [384, 512).
+// X: per-row (m, h) pieces, copied once per CTA into tensor memory (A operand
+// of S); Y: per-row (m, h) pieces [rows][NP], K-major, streamed by TMA and
+// reused as the MN-major B operand of the second product; V': FP32 [X rows][Y
+// cols] tiles streamed by TMA beside Y.  U is written by the epilogue into
+// tensor memory and is the A operand of the second product, so shared memory
+// carries only the TMA streams, the MMA operand reads and the V' reads.
+// Tensor memory: X pieces [0, NP), S = A0 [128, 192) + A1 [192, 256),
+// U buffers [256, 320) and [320, 384) (hi 32 + lo 32 columns each),
+// second-product accumulator [384, 384 + NP).  16 epilogue warps: warp w
+// serves lanes 32 (w % 4) .. +31 and a quarter (w / 4) of the S, U and
+// accumulator columns; the accumulator drains every kAccDrain tiles into
+// round-to-nearest FP32 sums held in registers.
 
 struct PairArgs {
   int X, Y, ychunk, n;
@@ -604,21 +609,20 @@ struct PairArgs {
 };
 
 constexpr int kAccDrain = 2;                   // tiles per second-product drain
-constexpr int kStages = 3;                     // TMA stages of (Y, V')
-constexpr int kEpiWarps = 8;                   // two warpgroups split each row's columns
+constexpr int kStages = 3;                     // TMA stages of (Y pieces, V')
+constexpr int kEpiWarps = 16;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kPairThreads = kEpiThreads + 64; // + TMA producer warp + MMA warp
 
 template <int NP>
 struct PairCfg {
-  static constexpr int Y_BYTES = 64 * NP * 2;  // one piece
-  static constexpr int V_BYTES = 128 * 64 * 4;
+  static constexpr int Y_BYTES = 64 * NP * 2;  // one piece of a 64-row tile
+  static constexpr int V_BYTES = 128 * 64 * 4;  // V' tile: two [128][32] FP32 boxes
   static constexpr int STAGE = 2 * Y_BYTES + V_BYTES;
-  static constexpr int OFF_U = kStages * STAGE;
-  static constexpr int U_BYTES = 128 * 64 * 2;
-  static constexpr int SMEM = OFF_U + 2 * U_BYTES + 1024;
-  static constexpr uint32_t T_XM = 0, T_XH = NP / 2, T_S0 = 128, T_S1 = 192, T_ACC = 256,
-                            T_RUN = 384;
+  static constexpr int SMEM = kStages * STAGE + 1024;
+  static constexpr uint32_t T_XM = 0, T_XH = NP / 2, T_S0 = 128, T_S1 = 192, T_U = 256,
+                            T_ACC = 384;
+  static constexpr int AC = NP / 4;            // accumulator columns per epilogue warp
 };
 
 template <int NP>
@@ -628,7 +632,7 @@ __global__ void __launch_bounds__(kPairThreads, 1)
   using C = PairCfg<NP>;
   extern __shared__ uint8_t p_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ uint64_t full[kStages], empty[kStages], s_full, s_free, u_full, u_free, acc_ready,
+  __shared__ uint64_t full[kStages], empty[kStages], s_full, s_free, u_full[2], u_free[2], acc_ready,
       acc_free, drain;
   __shared__ uint32_t tslot;
   __shared__ volatile int abort_flag;
@@ -648,8 +652,10 @@ __global__ void __launch_bounds__(kPairThreads, 1)
     }
     mbar_init(&s_full, 1);
     mbar_init(&s_free, kEpiWarps);  // epilogue barriers: one arrival per warp
-    mbar_init(&u_full, kEpiWarps);
-    mbar_init(&u_free, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&u_full[b], kEpiWarps);
+      mbar_init(&u_free[b], 1);
+    }
     mbar_init(&acc_ready, 1);
     mbar_init(&acc_free, kEpiWarps);
     mbar_init(&drain, 1);
@@ -665,24 +671,24 @@ __global__ void __launch_bounds__(kPairThreads, 1)
   tc_fence_after();
   const uint32_t tbase = tslot;
 
-  // ---------------- X tile -> tensor memory (lane = row; warpgroup 0 the m
-  // piece, warpgroup 1 the h piece; fp16 pairs as stored in memory)
+  // ---------------- X tile -> tensor memory (lane = row; warp w / 4 picks the
+  // piece (m, h) and the half of its NP / 2 columns; fp16 pairs as in memory)
   if (warp < kEpiWarps) {
-    const int quad = warp & 3, half = warp >> 2;
+    const int quad = warp & 3, c = warp >> 2;
+    const int piece = c >> 1, part = c & 1;
     const int r = quad * 32 + lane;
     const long x = (long)x0 + r;
     const uint32_t lane_off = static_cast<uint32_t>(quad * 32) << 16;
-    const uint4* src = reinterpret_cast<const uint4*>((half ? a.xh : a.xm) + x * a.ldx);
+    const uint4* src = reinterpret_cast<const uint4*>((piece ? a.xh : a.xm) + x * a.ldx + part * (NP / 2));
+    uint32_t w[C::AC];
 #pragma unroll
-    for (int c0 = 0; c0 < NP / 2; c0 += 32) {
-      uint32_t w[32];
-#pragma unroll
-      for (int v = 0; v < 8; ++v) {
-        const uint4 q = (x < a.X) ? src[c0 / 4 + v] : make_uint4(0u, 0u, 0u, 0u);
-        w[4 * v] = q.x; w[4 * v + 1] = q.y; w[4 * v + 2] = q.z; w[4 * v + 3] = q.w;
-      }
-      tmem_st32(tbase + lane_off + (half ? C::T_XH : C::T_XM) + c0, w);
+    for (int v = 0; v < C::AC / 4; ++v) {
+      const uint4 q = (x < a.X) ? src[v] : make_uint4(0u, 0u, 0u, 0u);
+      w[4 * v] = q.x; w[4 * v + 1] = q.y; w[4 * v + 2] = q.z; w[4 * v + 3] = q.w;
     }
+    const uint32_t col = (piece ? C::T_XH : C::T_XM) + part * C::AC;
+    if constexpr (C::AC == 32) tmem_st32(tbase + lane_off + col, w);
+    else tmem_st16(tbase + lane_off + col, w);
     tmem_wait_st();
   }
   tc_fence_before();
@@ -692,7 +698,8 @@ __global__ void __launch_bounds__(kPairThreads, 1)
   if (warp == prod_warp && lane == 0) {
     // ---------------- TMA producer
     prefetch_tmap(&mYm); prefetch_tmap(&mYh); prefetch_tmap(&mV);
-    int last_parity[kStages] = {-1, -1, -1};
+    int last_parity[kStages];
+    for (int s = 0; s < kStages; ++s) last_parity[s] = -1;
     for (int t = 0; t < T && !abort_flag; ++t) {
       const int s = t % kStages, use = t / kStages;
       if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) {
@@ -718,8 +725,6 @@ __global__ void __launch_bounds__(kPairThreads, 1)
     const uint32_t id_acc = idesc_f16(128, NP, false, false, true);
     // Descriptors start from one base; the address field counts 16-byte units,
     // so tile offsets add as immediates.
-    const uint64_t duh = sdesc_sw128(smem_u32(sm + C::OFF_U), 16, 1024);
-    const uint64_t dul = duh + (C::U_BYTES >> 4);
     const uint64_t dy0 = sdesc_sw128(smem_u32(sm), 16, 1024);
     const uint64_t dy0mn = sdesc_sw128(smem_u32(sm), 8192, 1024);
     constexpr uint64_t kStage16 = C::STAGE >> 4, kYh16 = C::Y_BYTES >> 4;
@@ -732,25 +737,27 @@ __global__ void __launch_bounds__(kPairThreads, 1)
     };
     bool good = T > 0;
     auto issue_acc = [&](int u) -> bool {
-      const int s = u % kStages, grp = u / kAccDrain;
+      const int s = u % kStages, b = u & 1, grp = u / kAccDrain;
       const bool first = (u % kAccDrain) == 0;
       const bool last = (u % kAccDrain) == kAccDrain - 1 || u == T - 1;
       if (first && grp > 0 && !mbar_wait_warp(&acc_free, (grp - 1) & 1)) return false;
-      if (!mbar_wait_warp(&u_full, u & 1)) return false;
+      if (!mbar_wait_warp(&u_full[b], (u >> 1) & 1)) return false;
       tc_fence_after();
       const uint64_t bym = dy0mn + s * kStage16, byh = bym + kYh16;
+      const uint32_t tuh = tbase + C::T_U + b * 64, tul = tuh + 32;
+      // K step kk: 16 Y rows = 8 TMEM columns of U, 2048 bytes of the MN-major Y tile
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
-        if (elect_one()) mma_f16(tacc, duh + kk * 2, bym + kk * 128, id_acc, (first && kk == 0) ? 0u : 1u);
+        if (elect_one()) mma_f16_ts(tacc, tuh + kk * 8, bym + kk * 128, id_acc, (first && kk == 0) ? 0u : 1u);
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
-        if (elect_one()) mma_f16(tacc, duh + kk * 2, byh + kk * 128, id_acc, 1u);
+        if (elect_one()) mma_f16_ts(tacc, tuh + kk * 8, byh + kk * 128, id_acc, 1u);
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
-        if (elect_one()) mma_f16(tacc, dul + kk * 2, bym + kk * 128, id_acc, 1u);
+        if (elect_one()) mma_f16_ts(tacc, tul + kk * 8, bym + kk * 128, id_acc, 1u);
       if (elect_one()) {
         mma_commit(&empty[s]);
-        mma_commit(&u_free);
+        mma_commit(&u_free[b]);
         if (last) mma_commit(&acc_ready);
       }
       __syncwarp();
@@ -784,17 +791,25 @@ __global__ void __launch_bounds__(kPairThreads, 1)
     __syncwarp();
     mbar_wait_warp(&drain, 0);
   } else if (warp < kEpiWarps) {
-    // ---------------- epilogue: warp quadrant = TMEM lanes (rows), half = columns
-    const int quad = warp & 3, half = warp >> 2;
+    // ---------------- epilogue: warp w % 4 = TMEM lane quadrant (rows),
+    // w / 4 = quarter of the columns
+    const int quad = warp & 3, c = warp >> 2;
     const int r = quad * 32 + lane;
     const uint32_t lane_off = static_cast<uint32_t>(quad * 32) << 16;
+    const long x = (long)x0 + r;
+    const bool xok = x < a.X;
     const float f = a.sc[a.f_idx];
     const bool want_e = a.epart != nullptr;
-    uint8_t* uhp = sm + C::OFF_U;
-    uint8_t* ulp = uhp + C::U_BYTES;
-    const int sw = r & 7;
-    constexpr int ACOLS = NP / 2;  // accumulator columns per epilogue half
-    const uint32_t t_acc = tbase + C::T_ACC, t_run = tbase + C::T_RUN;
+    const uint32_t t_s0 = tbase + lane_off + C::T_S0 + 16 * c, t_s1 = t_s0 + (C::T_S1 - C::T_S0);
+    const uint32_t t_u = tbase + lane_off + C::T_U + 8 * c;
+    const uint32_t t_acc = tbase + lane_off + C::T_ACC + C::AC * c;
+    // V' of this thread's 16 columns: box c / 2 of the stage, 16-byte chunks
+    // 4 (c % 2) .. +3 of row r (128-byte swizzle: chunk q sits at q ^ (r % 8))
+    const int vbox_off = 2 * C::Y_BYTES + (c >> 1) * 16384 + r * 128;
+    const int sw = r & 7, q0 = (c & 1) * 4;
+    float run[C::AC];
+#pragma unroll
+    for (int j = 0; j < C::AC; ++j) run[j] = 0.0f;
     double esum = 0.0;
     bool ok = T > 0;
     // waits and the abort test are warp-uniform: the tensor-memory loads and
@@ -804,104 +819,93 @@ __global__ void __launch_bounds__(kPairThreads, 1)
       if (lane == 0) { atomicExch(a.status, code); abort_flag = 1; }
       __syncwarp();
     };
-    for (int t = 0; t < T && !aborted(); ++t) {
-      const int s = t % kStages;
-      if (!mbar_wait_warp(&s_full, t & 1)) { fail(27); ok = false; break; }
-      tc_fence_after();
-      float sv[32];
-      {
-        uint32_t u0[32], u1[32];
-        tmem_ld32(tbase + lane_off + C::T_S0 + half * 32, u0);
-        tmem_ld32(tbase + lane_off + C::T_S1 + half * 32, u1);
+    // Per tile: read S(t) and release it first, so that the next S product is
+    // queued while this warp drains the accumulator (group ending at t - 1)
+    // and forms U(t).
+    for (int t = 0; t <= T && !aborted(); ++t) {
+      const int b = t & 1;
+      float sv[16];
+      if (t < T) {
+        if (!mbar_wait_warp(&s_full, t & 1)) { fail(27); ok = false; break; }
+        tc_fence_after();
+        uint32_t u0[16], u1[16];
+        tmem_ld16(t_s0, u0);
+        tmem_ld16(t_s1, u1);
         tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 32; ++j) sv[j] = __uint_as_float(u0[j]) + __uint_as_float(u1[j]);
+        for (int j = 0; j < 16; ++j) sv[j] = __uint_as_float(u0[j]) + __uint_as_float(u1[j]);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s_free);
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&s_free);
-      const uint8_t* vt = sm + s * C::STAGE + 2 * C::Y_BYTES + half * 16384;
-      uint32_t hi[16], lo[16];
-      float etile = 0.0f;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float4 v = *reinterpret_cast<const float4*>(vt + r * 128 + ((q ^ sw) << 4));
-        const float p0 = v.x * sv[4 * q + 0], p1 = v.y * sv[4 * q + 1];
-        const float p2 = v.z * sv[4 * q + 2], p3 = v.w * sv[4 * q + 3];
-        if (want_e) {
-          etile = fmaf(p0, sv[4 * q + 0], etile);
-          etile = fmaf(p1, sv[4 * q + 1], etile);
-          etile = fmaf(p2, sv[4 * q + 2], etile);
-          etile = fmaf(p3, sv[4 * q + 3], etile);
-        }
-        const float t0 = p0 * f, t1 = p1 * f, t2 = p2 * f, t3 = p3 * f;
-        const __half2 h01 = __floats2half2_rn(t0, t1), h23 = __floats2half2_rn(t2, t3);
-        const float2 b01 = __half22float2(h01), b23 = __half22float2(h23);
-        const __half2 l01 = __floats2half2_rn(t0 - b01.x, t1 - b01.y);
-        const __half2 l23 = __floats2half2_rn(t2 - b23.x, t3 - b23.y);
-        hi[2 * q] = *reinterpret_cast<const uint32_t*>(&h01);
-        hi[2 * q + 1] = *reinterpret_cast<const uint32_t*>(&h23);
-        lo[2 * q] = *reinterpret_cast<const uint32_t*>(&l01);
-        lo[2 * q + 1] = *reinterpret_cast<const uint32_t*>(&l23);
-      }
-      esum += (double)etile;
-      if (t > 0 && !mbar_wait_warp(&u_free, (t - 1) & 1)) { fail(28); ok = false; break; }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int off = r * 128 + (((4 * half + q) ^ sw) << 4);
-        *reinterpret_cast<uint4*>(uhp + off) = make_uint4(hi[4 * q], hi[4 * q + 1], hi[4 * q + 2], hi[4 * q + 3]);
-        *reinterpret_cast<uint4*>(ulp + off) = make_uint4(lo[4 * q], lo[4 * q + 1], lo[4 * q + 2], lo[4 * q + 3]);
-      }
-      fence_async_smem();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&u_full);
-      // drain the second-product accumulator into the running sum after each group
-      if ((t % kAccDrain) == kAccDrain - 1 || t == T - 1) {
-        const int grp = t / kAccDrain;
+      // drain the second-product accumulator into the running sums after each group
+      if (t > 0 && (((t - 1) % kAccDrain) == kAccDrain - 1 || t == T)) {
+        const int grp = (t - 1) / kAccDrain;
         if (!mbar_wait_warp(&acc_ready, grp & 1)) { fail(29); ok = false; break; }
         tc_fence_after();
-#pragma unroll 1
-        for (int c = 0; c < ACOLS; c += 32) {
-          uint32_t ua[32], ur[32];
-          tmem_ld32(t_acc + lane_off + half * ACOLS + c, ua);
-          if (grp > 0) tmem_ld32(t_run + lane_off + half * ACOLS + c, ur);
+#pragma unroll
+        for (int h = 0; h < C::AC; h += 16) {  // 16 columns at a time (register budget)
+          uint32_t ua[16];
+          tmem_ld16(t_acc + h, ua);
           tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
-            ur[j] = __float_as_uint((grp > 0 ? __uint_as_float(ur[j]) : 0.0f) + __uint_as_float(ua[j]));
-          tmem_st32(t_run + lane_off + half * ACOLS + c, ur);
+          for (int j = 0; j < 16; ++j) run[h + j] += __uint_as_float(ua[j]);
         }
-        tmem_wait_st();
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&acc_free);
       }
+      if (t == T) break;
+      uint32_t hi[8], lo[8];
+      float etile = 0.0f;
+      const uint8_t* vrow = sm + (t % kStages) * C::STAGE + vbox_off;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        float vv[2];
+        {
+          const float4 v4 = *reinterpret_cast<const float4*>(vrow + (((q0 + (q >> 1)) ^ sw) << 4));
+          vv[0] = (q & 1) ? v4.z : v4.x;
+          vv[1] = (q & 1) ? v4.w : v4.y;
+        }
+        const float p0 = vv[0] * sv[2 * q], p1 = vv[1] * sv[2 * q + 1];
+        if (want_e) {
+          etile = fmaf(p0, sv[2 * q], etile);
+          etile = fmaf(p1, sv[2 * q + 1], etile);
+        }
+        const float t0 = p0 * f, t1 = p1 * f;
+        const __half2 h01 = __floats2half2_rn(t0, t1);
+        const float2 b01 = __half22float2(h01);
+        const __half2 l01 = __floats2half2_rn(t0 - b01.x, t1 - b01.y);
+        hi[q] = *reinterpret_cast<const uint32_t*>(&h01);
+        lo[q] = *reinterpret_cast<const uint32_t*>(&l01);
+      }
+      esum += (double)etile;
+      if (t >= 2 && !mbar_wait_warp(&u_free[b], ((t - 2) >> 1) & 1)) { fail(28); ok = false; break; }
+      tc_fence_after();
+      tmem_st8(t_u + b * 64, hi);
+      tmem_st8(t_u + b * 64 + 32, lo);
+      tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&u_full[b]);
     }
     ok = ok && !aborted();
-    // ---------------- write the running sum
-    tc_fence_after();
+    // ---------------- write the running sums
     const float os = a.sc[a.out_idx];
-    const int x = x0 + r;
-    const bool row_ok = x < a.X;
-#pragma unroll 1
-    for (int c = 0; c < ACOLS; c += 32) {
-      uint32_t u[32];
-      tmem_ld32(t_run + lane_off + half * ACOLS + c, u);
-      tmem_wait_ld();
-      if (!row_ok) continue;
+    if (xok) {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int col = half * ACOLS + c + j;
+      for (int j = 0; j < C::AC; ++j) {
+        const int col = C::AC * c + j;
         if (col >= a.n) continue;
-        const float v = ok ? __uint_as_float(u[j]) * os : 0.0f;
+        const float v = ok ? run[j] * os : 0.0f;
         if (a.transposed)
           a.out[(long)col * a.ldo + x] = v;
         else
-          a.out[(long)blockIdx.y * a.part_stride + (long)x * a.ldo + col] = v;
+          a.out[(long)blockIdx.y * a.part_stride + x * a.ldo + col] = v;
       }
     }
     if (want_e) {
-      double e = (ok && row_ok) ? esum : 0.0;
+      double e = (ok && xok) ? esum : 0.0;
       for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
       if (lane == 0) ered[warp] = e;
       asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory");
@@ -935,13 +939,14 @@ cudaError_t get_encode() {
 
 // 2-D map of a row-major [rows][ld] array, box [box_rows][box_cols], 128-B swizzle.
 cudaError_t make_map(CUtensorMap* m, const void* ptr, CUtensorMapDataType dt, int esize, long rows,
-                     long ld, int box_rows, int box_cols) {
+                     long ld, int box_rows, int box_cols,
+                     CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(ld), static_cast<cuuint64_t>(rows)};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * esize};
   cuuint32_t box[2] = {static_cast<cuuint32_t>(box_cols), static_cast<cuuint32_t>(box_rows)};
   cuuint32_t es[2] = {1, 1};
   CUresult r = g_encode(m, dt, 2, const_cast<void*>(ptr), dims, strides, box, es,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -986,7 +991,7 @@ struct MixedState {
   int ychunkA = 64, ychunkC = 64;
   int kchunkL1 = 64, kchunkL23 = 64;
   CUtensorMap m_phi_m, m_phi_h, m_CT_m, m_CT_h, m_psi128_m, m_psi128_h, m_psi64_m, m_psi64_h,
-      m_psig128_m, m_psig128_h, m_psig64_m, m_psig64_h, m_V, m_VT, m_W, m_phiT_m, m_phiT_h,
+      m_psig128_m, m_psig128_h, m_psig64_m, m_psig64_h, m_VA, m_VB, m_VC, m_phiT_m, m_phiT_h,
       m_M1_m, m_M1_h, m_phigT_m, m_phigT_h, m_D23T_m, m_D23T_h;
 };
 
@@ -1194,7 +1199,7 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fin(e);
 
-  const auto F16 = CU_TENSOR_MAP_DATA_TYPE_FLOAT16, F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const auto F16 = CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   const int np_ = p.np;
   struct MapSpec { CUtensorMap* m; const void* p; CUtensorMapDataType t; int es; long rows, ld; int br, bc; };
   const MapSpec specs[] = {
@@ -1210,9 +1215,6 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
       {&m->m_psig128_h, m->psig_h, F16, 2, (long)na, np_, 128, 64},
       {&m->m_psig64_m, m->psig_m, F16, 2, (long)na, np_, 64, 64},
       {&m->m_psig64_h, m->psig_h, F16, 2, (long)na, np_, 64, 64},
-      {&m->m_V, m->V32, F32, 4, (long)na, p.Ng4, 128, 32},
-      {&m->m_VT, m->VT32, F32, 4, (long)ng, p.Na4, 128, 32},
-      {&m->m_W, m->W32, F32, 4, (long)na, p.Na4, 128, 32},
       {&m->m_phiT_m, m->phiT_m, F16, 2, N, p.Ng8, 128, 64},
       {&m->m_phiT_h, m->phiT_h, F16, 2, N, p.Ng8, 128, 64},
       {&m->m_M1_m, m->M1_m, F16, 2, n, p.Ng8, 128, 64},
@@ -1224,6 +1226,13 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   };
   for (const MapSpec& ms : specs) {
     e = make_map(ms.m, ms.p, ms.t, ms.es, ms.rows, ms.ld, ms.br, ms.bc);
+    if (e != cudaSuccess) return fin(e);
+  }
+  {  // V' tiles [X rows][Y cols] in FP32: [128][32] boxes, 128-byte swizzle
+    const auto F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    e = make_map(&m->m_VA, m->V32, F32, 4, (long)na, p.Ng4, 128, 32);
+    if (e == cudaSuccess) e = make_map(&m->m_VB, m->VT32, F32, 4, (long)ng, p.Na4, 128, 32);
+    if (e == cudaSuccess) e = make_map(&m->m_VC, m->W32, F32, 4, (long)na, p.Na4, 128, 32);
     if (e != cudaSuccess) return fin(e);
   }
   fin(cudaSuccess);
@@ -1283,19 +1292,16 @@ cudaError_t mixed_enqueue(MixedState* m, const double* C, double* K, double* Ex,
     count_launch();
   };
   {  // role A: M2[g][j] = sum_R (V o P)[g][R] Psi[R][j], and sum V o P^2
-    PairArgs pa{(int)na, (int)ng, m->ychunkA, n, m->psig_m, m->psig_h, np, m->sc, SC_F_AB,
-                SC_OUT_AB, m->M2p, n, na * n, 0, m->EpA, m->status};
-    launch_pair(m->m_psi64_m, m->m_psi64_h, m->m_V, pa, dim3(m->xa, m->partsA));
+    PairArgs pa{(int)na, (int)ng, m->ychunkA, n, m->psig_m, m->psig_h, np, m->sc, SC_F_AB, SC_OUT_AB, m->M2p, n, na * n, 0, m->EpA, m->status};
+    launch_pair(m->m_psi64_m, m->m_psi64_h, m->m_VA, pa, dim3(m->xa, m->partsA));
   }
   {  // role B: M1[j][R] = sum_g (V^T o P^T)[R][g] Psi_g[g][j], written transposed
-    PairArgs pa{(int)ng, (int)na, (int)rup(na, 64), n, m->psi_m, m->psi_h, np, m->sc, SC_F_AB,
-                SC_OUT_AB, m->M1, m->Ng4, 0, 1, nullptr, m->status};
-    launch_pair(m->m_psig64_m, m->m_psig64_h, m->m_VT, pa, dim3((unsigned)((ng + 127) / 128), 1));
+    PairArgs pa{(int)ng, (int)na, (int)rup(na, 64), n, m->psi_m, m->psi_h, np, m->sc, SC_F_AB, SC_OUT_AB, m->M1, m->Ng4, 0, 1, nullptr, m->status};
+    launch_pair(m->m_psig64_m, m->m_psig64_h, m->m_VB, pa, dim3((unsigned)((ng + 127) / 128), 1));
   }
   {  // role C: M3[g][j] = sum_g' (W o Q)[g][g'] Psi_g[g'][j], and sum W o Q^2
-    PairArgs pa{(int)na, (int)na, m->ychunkC, n, m->psig_m, m->psig_h, np, m->sc, SC_F_C,
-                SC_OUT_C, m->M3p, n, na * n, 0, m->EpC, m->status};
-    launch_pair(m->m_psig64_m, m->m_psig64_h, m->m_W, pa, dim3(m->xa, m->partsC));
+    PairArgs pa{(int)na, (int)na, m->ychunkC, n, m->psig_m, m->psig_h, np, m->sc, SC_F_C, SC_OUT_C, m->M3p, n, na * n, 0, m->EpC, m->status};
+    launch_pair(m->m_psig64_m, m->m_psig64_h, m->m_VC, pa, dim3(m->xa, m->partsC));
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
