@@ -23,8 +23,9 @@ __global__ void __launch_bounds__(TPB) dgemm_kernel(DGemm g, int kchunk) {
   __shared__ double Bs[BK][BN + 1];
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   const long m0 = (long)blockIdx.y * BM, n0 = (long)blockIdx.x * BN;
-  const long kbeg = (long)blockIdx.z * kchunk;
-  const long kend = min((long)g.K, kbeg + kchunk);
+  const long kend = min((long)g.K, (long)blockIdx.z * kchunk + kchunk);
+  // rows m0.. of an upper-triangular op(A) vanish for k < m0
+  const long kbeg = g.upperA ? max((long)blockIdx.z * kchunk, m0) : (long)blockIdx.z * kchunk;
   double acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)

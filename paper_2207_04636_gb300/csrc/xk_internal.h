@@ -33,6 +33,7 @@ struct DGemm {
   const double* H; long ldh;
   int ksplit;
   double* work;
+  bool upperA;  // op(A) is upper triangular: K steps below a row tile are skipped
 };
 cudaError_t dgemm(const DGemm& g, cudaStream_t s);
 // Split count dgemm picks when DGemm::ksplit == 0 (work needs ksplit*M*N).

@@ -174,24 +174,40 @@ __global__ void colnorm2_max_kernel(const double* __restrict__ a, long rows, lon
   }
 }
 
-// rowmax[r] = max_c |a[r][c]| and glob = max over all, for long rows (2-D grid:
-// x = column chunks, y = rows).
-template <class T>
-__global__ void rowmax2d_kernel(const T* __restrict__ a, long cols, long ld,
+// rowmax[r] = max_c |a[r][c]| and glob = max over all, for long FP32 rows whose
+// stride is a multiple of 4 (2-D grid: x = column chunks, y = rows; float4 loads).
+__global__ void rowmax2d_kernel(const float* __restrict__ a, long cols, long ld,
                                 unsigned* __restrict__ rowmax, unsigned* __restrict__ glob) {
   const long r = blockIdx.y;
+  const float4* row = reinterpret_cast<const float4*>(a + r * ld);
+  const long n4 = cols / 4;
   float m = 0.0f;
-  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < cols;
-       c += (long)gridDim.x * blockDim.x)
-    m = fmaxf(m, fabsf((float)a[r * ld + c]));
+  const long step = (long)gridDim.x * blockDim.x;
+  long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  for (; c + 3 * step < n4; c += 4 * step) {
+    float4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = row[c + u * step];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      m = fmaxf(m, fmaxf(fmaxf(fabsf(v[u].x), fabsf(v[u].y)), fmaxf(fabsf(v[u].z), fabsf(v[u].w))));
+  }
+  for (; c < n4; c += step) {
+    const float4 v = row[c];
+    m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+  }
+  if (blockIdx.x == 0)
+    for (long t = n4 * 4 + threadIdx.x; t < cols; t += blockDim.x) m = fmaxf(m, fabsf(a[r * ld + t]));
+  __shared__ float red[32];
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) {
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
     atomicMax(rowmax + r, __float_as_uint(m));
     atomicMax(glob, __float_as_uint(m));
   }
 }
-
-// ----------------------------------------------------------------- splits
 
 // Grid of a row whose largest |value| is mx: q = 2^(ceil(log2 mx) - 8), at
 // least 2^-24 (the FP16 subnormal step), so |x / q| <= 256.
@@ -219,45 +235,61 @@ __global__ void __launch_bounds__(128) split_mh_rows_kernel(
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
   mx = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
-  const T q = (T)row_grid(mx);
+  // FP32 from here: rounding x to FP32 (2^-24) is far below the FP16 step of h
+  const float q = row_grid(mx), qi = 1.0f / q;  // q a power of two: x * qi == x / q
   __half* mrow = mo + r * ld_dst;
   __half* hrow = ho + r * ld_dst;
   for (long c = threadIdx.x; c < ld_dst; c += blockDim.x) {
     __half mh = __float2half(0.0f), hh = __float2half(0.0f);
     if (c < cols) {
-      const T x = row[c] * G;
-      const T m = q * rint(x / q);
-      mh = __float2half_rn((float)m);
-      hh = __float2half_rn((float)(x - m));
+      const float x = (float)(row[c] * G);
+      const float m = q * rintf(x * qi);
+      mh = __float2half_rn(m);
+      hh = __float2half_rn(x - m);
     }
     mrow[c] = mh;
     hrow[c] = hh;
   }
 }
 
-// As split_mh_rows_kernel with the row maxima (of |src|, unscaled) given:
-// 2-D grid, x = column chunks of ld_dst, y = rows.
-template <class T>
-__global__ void split_mh_rows_pre_kernel(const T* __restrict__ src, long cols, long ld_src,
+// As split_mh_rows_kernel with the row maxima (of |src|, unscaled) given, for
+// FP32 rows (stride a multiple of 4) into pieces of stride a multiple of 8:
+// 2-D grid, x = chunks of 8 columns, y = rows.
+__global__ void split_mh_rows_pre_kernel(const float* __restrict__ src, long cols, long ld_src,
                                          const unsigned* __restrict__ rowmax,
                                          const float* __restrict__ sc, int gidx,
                                          __half* __restrict__ mo, __half* __restrict__ ho,
                                          long ld_dst) {
   const long r = blockIdx.y;
-  const T G = (T)sc[gidx];
-  const T q = (T)row_grid(__uint_as_float(rowmax[r]) * (float)G);
-  const T* row = src + r * ld_src;
-  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < ld_dst;
-       c += (long)gridDim.x * blockDim.x) {
-    __half mh = __float2half(0.0f), hh = __float2half(0.0f);
-    if (c < cols) {
-      const T x = row[c] * G;
-      const T m = q * rint(x / q);
-      mh = __float2half_rn((float)m);
-      hh = __float2half_rn((float)(x - m));
+  const float G = sc[gidx];
+  const float q = row_grid(__uint_as_float(rowmax[r]) * G);
+  const float qi = 1.0f / q;  // q is a power of two: x * qi == x / q
+  const float* row = src + r * ld_src;
+  for (long c8 = blockIdx.x * (long)blockDim.x + threadIdx.x; c8 * 8 < ld_dst;
+       c8 += (long)gridDim.x * blockDim.x) {
+    const long c = c8 * 8;
+    float x[8];
+    if (c + 8 <= cols) {
+      const float4 v0 = *reinterpret_cast<const float4*>(row + c);
+      const float4 v1 = *reinterpret_cast<const float4*>(row + c + 4);
+      x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
+      x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x[j] = (c + j < cols) ? row[c + j] : 0.0f;
     }
-    mo[r * ld_dst + c] = mh;
-    ho[r * ld_dst + c] = hh;
+    uint32_t mw[4], hw[4];
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      const float x0 = x[j] * G, x1 = x[j + 1] * G;
+      const float m0 = q * rintf(x0 * qi), m1 = q * rintf(x1 * qi);
+      const __half2 hm = __floats2half2_rn(m0, m1);
+      const __half2 hh = __floats2half2_rn(x0 - m0, x1 - m1);
+      mw[j / 2] = *reinterpret_cast<const uint32_t*>(&hm);
+      hw[j / 2] = *reinterpret_cast<const uint32_t*>(&hh);
+    }
+    *reinterpret_cast<uint4*>(mo + r * ld_dst + c) = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+    *reinterpret_cast<uint4*>(ho + r * ld_dst + c) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
   }
 }
 
@@ -312,16 +344,29 @@ __global__ void f64_to_f32_kernel(const double* __restrict__ src, long rows, lon
 // ------------------------------------------------------------ reductions
 
 // out[t] = sum_s a[s][t] - sum_s b[s][t] in FP64 (b nullable); max |out| -> am_slot.
+// Error-free accumulation of FP32 terms into an unevaluated sum hi + lo
+// (two-sum), in a fixed order; about 2^-44 relative, on the FP32 pipes.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  lo += (hi - (s - bp)) + (x - bp);
+  hi = s;
+}
+
 __global__ void reduce_parts_kernel(const float* __restrict__ a, int na, const float* __restrict__ b,
                                     int nb, long count, double* __restrict__ out,
                                     unsigned* __restrict__ am_slot) {
   float m = 0.0f;
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count;
        t += (long)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int p = 0; p < na; ++p) s += (double)a[(long)p * count + t];
-    if (b)
-      for (int p = 0; p < nb; ++p) s -= (double)b[(long)p * count + t];
+    float hi = 0.0f, lo = 0.0f;
+#pragma unroll 8
+    for (int p = 0; p < na; ++p) ff_add(hi, lo, a[(long)p * count + t]);
+    if (b) {
+#pragma unroll 8
+      for (int p = 0; p < nb; ++p) ff_add(hi, lo, -b[(long)p * count + t]);
+    }
+    const double s = (double)hi + (double)lo;
     out[t] = s;
     m = fmaxf(m, fabsf((float)s));
   }
@@ -334,9 +379,12 @@ __global__ void final_k_kernel(const float* __restrict__ L1, int n1, const float
                                int n23, long count, double dV, double* __restrict__ K) {
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count;
        t += (long)gridDim.x * blockDim.x) {
-    double s1 = 0.0, s2 = 0.0;
-    for (int p = 0; p < n1; ++p) s1 += (double)L1[(long)p * count + t];
-    for (int p = 0; p < n23; ++p) s2 += (double)L23[(long)p * count + t];
+    float h1 = 0.0f, l1 = 0.0f, h2 = 0.0f, l2 = 0.0f;
+#pragma unroll 8
+    for (int p = 0; p < n1; ++p) ff_add(h1, l1, L1[(long)p * count + t]);
+#pragma unroll 8
+    for (int p = 0; p < n23; ++p) ff_add(h2, l2, L23[(long)p * count + t]);
+    const double s1 = (double)h1 + (double)l1, s2 = (double)h2 + (double)l2;
     K[t] = dV * (s1 + s2);
   }
 }
@@ -1039,13 +1087,18 @@ Plan make_plan(int64_t Ng, int N, int n, int Naux) {
   return p;
 }
 
+// Split of Q = L^T C into K steps of 16: the product is bound by the FP64
+// pipe, and one 64 x 64 x 16 step per CTA spreads the triangle's uneven row
+// work evenly over the SMs.
+int q_ksplit(int N) { return std::max(1, std::min(64, (N + 15) / 16)); }
+
 // Split-K work of the FP64 contractions of the set-up and of Q = L^T C.
 size_t dwork_elems(int64_t Ng, int N, int n) {
   auto w = [](int M, int Nc, int K) {
     const int ks = dgemm_ksplit(M, Nc, K);
     return ks > 1 ? (size_t)ks * M * Nc : (size_t)1;
   };
-  return std::max({w(N, N, (int)Ng), w(N, n, N), w((int)Ng, N, N), (size_t)1});
+  return std::max({w(N, N, (int)Ng), (size_t)q_ksplit(N) * N * n, w((int)Ng, N, N), (size_t)1});
 }
 
 }  // namespace
@@ -1256,7 +1309,9 @@ cudaError_t mixed_enqueue(MixedState* m, const double* C, double* K, double* Ex,
   e = cudaMemsetAsync(m->am + AM_C, 0, (NAM - AM_C) * 4, s);
   if (e != cudaSuccess) return e;
   {
-    DGemm g{N, n, N, m->Lf, N, true, C, n, false, m->Q64, n, 1.0, nullptr, 0, 0, m->dwork};
+    // L^T is upper triangular: each row tile of Q only needs K >= its first row
+    DGemm g{N, n, N, m->Lf, N, true, C, n, false, m->Q64, n, 1.0, nullptr, 0, q_ksplit(N), m->dwork,
+            true};
     e = dgemm(g, s);
     if (e != cudaSuccess) return e;
   }
@@ -1314,11 +1369,11 @@ cudaError_t mixed_enqueue(MixedState* m, const double* C, double* K, double* Ex,
   e = cudaMemsetAsync(m->rowmax, 0, (size_t)n * 4, s);
   if (e != cudaSuccess) return e;
   {
-    const unsigned chunks = (unsigned)std::min<long>(64, (ng + 1023) / 1024);
-    rowmax2d_kernel<float><<<dim3(chunks, n), 256, 0, s>>>(m->M1, ng, m->Ng4, m->rowmax, m->am + AM_M1);
+    const unsigned chunks = (unsigned)std::min<long>(16, (ng + 1023) / 1024);
+    rowmax2d_kernel<<<dim3(chunks, n), 256, 0, s>>>(m->M1, ng, m->Ng4, m->rowmax, m->am + AM_M1);
     scales_kernel<<<1, 32, 0, s>>>(m->am, m->sc, 2);
-    const unsigned schunks = (unsigned)std::min<long>(128, (m->Ng8 + 1023) / 1024);
-    split_mh_rows_pre_kernel<float><<<dim3(schunks, n), 256, 0, s>>>(
+    const unsigned schunks = (unsigned)std::min<long>(64, (m->Ng8 / 8 + 255) / 256);
+    split_mh_rows_pre_kernel<<<dim3(schunks, n), 256, 0, s>>>(
         m->M1, ng, m->Ng4, m->rowmax, m->sc, SC_M1, m->M1_m, m->M1_h, m->Ng8);
   }
   count_launch(4);
