@@ -662,6 +662,20 @@ constexpr int kEpiWarps = 16;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kPairThreads = kEpiThreads + 64; // + TMA producer warp + MMA warp
 
+// The three contractions of one build run as one launch (roles in order A, B,
+// C; the grid is their concatenation), so the short role-C CTAs fill the tail
+// of the long ones.
+struct PairRole {
+  PairArgs a;
+  int gx;    // the role's own grid is gx x (nblk / gx)
+  int nblk;
+};
+struct PairJob {
+  CUtensorMap ym[3], yh[3], v[3];
+  PairRole role[3];
+  int nroles;
+};
+
 template <int NP>
 struct PairCfg {
   static constexpr int Y_BYTES = 64 * NP * 2;  // one piece of a 64-row tile
@@ -675,9 +689,17 @@ struct PairCfg {
 
 template <int NP>
 __global__ void __launch_bounds__(kPairThreads, 1)
-    pair_kernel(const __grid_constant__ CUtensorMap mYm, const __grid_constant__ CUtensorMap mYh,
-                const __grid_constant__ CUtensorMap mV, PairArgs a) {
+    pair_kernel(const __grid_constant__ PairJob job) {
   using C = PairCfg<NP>;
+  int ri = 0, blk = blockIdx.x;
+  while (ri + 1 < job.nroles && blk >= job.role[ri].nblk) blk -= job.role[ri].nblk, ++ri;
+  // constant-index selection keeps the tensor maps in parameter space
+  const CUtensorMap* mYm = ri == 0 ? &job.ym[0] : ri == 1 ? &job.ym[1] : &job.ym[2];
+  const CUtensorMap* mYh = ri == 0 ? &job.yh[0] : ri == 1 ? &job.yh[1] : &job.yh[2];
+  const CUtensorMap* mV = ri == 0 ? &job.v[0] : ri == 1 ? &job.v[1] : &job.v[2];
+  const PairArgs& a = ri == 0 ? job.role[0].a : ri == 1 ? job.role[1].a : job.role[2].a;
+  const int gx = ri == 0 ? job.role[0].gx : ri == 1 ? job.role[1].gx : job.role[2].gx;
+  const int bx = blk % gx, by = blk / gx;
   extern __shared__ uint8_t p_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p_raw) + 1023) & ~uintptr_t(1023));
   __shared__ uint64_t full[kStages], empty[kStages], s_full, s_free, u_full[2], u_free[2], acc_ready,
@@ -687,8 +709,8 @@ __global__ void __launch_bounds__(kPairThreads, 1)
   __shared__ double ered[kEpiWarps];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int prod_warp = kEpiWarps, mma_warp = kEpiWarps + 1;
-  const int x0 = blockIdx.x * 128;
-  const int y0 = blockIdx.y * a.ychunk;
+  const int x0 = bx * 128;
+  const int y0 = by * a.ychunk;
   const int y1 = min(a.Y, y0 + a.ychunk);
   const int T = y1 > y0 ? (y1 - y0 + 63) / 64 : 0;
   constexpr int NKB = NP / 64;
@@ -745,7 +767,7 @@ __global__ void __launch_bounds__(kPairThreads, 1)
 
   if (warp == prod_warp && lane == 0) {
     // ---------------- TMA producer
-    prefetch_tmap(&mYm); prefetch_tmap(&mYh); prefetch_tmap(&mV);
+    prefetch_tmap(mYm); prefetch_tmap(mYh); prefetch_tmap(mV);
     int last_parity[kStages];
     for (int s = 0; s < kStages; ++s) last_parity[s] = -1;
     for (int t = 0; t < T && !abort_flag; ++t) {
@@ -757,11 +779,11 @@ __global__ void __launch_bounds__(kPairThreads, 1)
       mbar_expect_tx(&full[s], C::STAGE);
       const int yr = y0 + t * 64;
       for (int kb = 0; kb < NKB; ++kb) {
-        tma_load_2d(st + kb * 8192, &mYm, &full[s], kb * 64, yr);
-        tma_load_2d(st + C::Y_BYTES + kb * 8192, &mYh, &full[s], kb * 64, yr);
+        tma_load_2d(st + kb * 8192, mYm, &full[s], kb * 64, yr);
+        tma_load_2d(st + C::Y_BYTES + kb * 8192, mYh, &full[s], kb * 64, yr);
       }
-      tma_load_2d(st + 2 * C::Y_BYTES, &mV, &full[s], yr, x0);
-      tma_load_2d(st + 2 * C::Y_BYTES + 16384, &mV, &full[s], yr + 32, x0);
+      tma_load_2d(st + 2 * C::Y_BYTES, mV, &full[s], yr, x0);
+      tma_load_2d(st + 2 * C::Y_BYTES + 16384, mV, &full[s], yr + 32, x0);
       last_parity[s] = use & 1;
     }
     for (int s = 0; s < kStages; ++s)
@@ -949,7 +971,7 @@ __global__ void __launch_bounds__(kPairThreads, 1)
         if (a.transposed)
           a.out[(long)col * a.ldo + x] = v;
         else
-          a.out[(long)blockIdx.y * a.part_stride + x * a.ldo + col] = v;
+          a.out[(long)by * a.part_stride + x * a.ldo + col] = v;
       }
     }
     if (want_e) {
@@ -960,7 +982,7 @@ __global__ void __launch_bounds__(kPairThreads, 1)
       if (tid == 0) {
         double sum = 0.0;
         for (int i = 0; i < kEpiWarps; ++i) sum += ered[i];
-        a.epart[(long)blockIdx.y * gridDim.x + blockIdx.x] = sum;
+        a.epart[(long)by * gx + bx] = sum;
       }
     }
   }
@@ -1338,25 +1360,31 @@ cudaError_t mixed_enqueue(MixedState* m, const double* C, double* K, double* Ex,
 
   // ---- steps 2-3: the three fused pair contractions
   hook(1, 1);
-  auto launch_pair = [&](const CUtensorMap& Ym, const CUtensorMap& Yh, const CUtensorMap& Vm,
-                         const PairArgs& pa, dim3 grid) {
+  {
+    // role A: M2[g][j] = sum_R (V o P)[g][R] Psi[R][j], and sum V o P^2
+    // role B: M1[j][R] = sum_g (V^T o P^T)[R][g] Psi_g[g][j], written transposed
+    // role C: M3[g][j] = sum_g' (W o Q)[g][g'] Psi_g[g'][j], and sum W o Q^2
+    PairJob job;
+    job.ym[0] = m->m_psi64_m; job.yh[0] = m->m_psi64_h; job.v[0] = m->m_VA;
+    job.ym[1] = m->m_psig64_m; job.yh[1] = m->m_psig64_h; job.v[1] = m->m_VB;
+    job.ym[2] = m->m_psig64_m; job.yh[2] = m->m_psig64_h; job.v[2] = m->m_VC;
+    job.role[0] = {PairArgs{(int)na, (int)ng, m->ychunkA, n, m->psig_m, m->psig_h, np, m->sc,
+                            SC_F_AB, SC_OUT_AB, m->M2p, n, na * n, 0, m->EpA, m->status},
+                   m->xa, m->xa * m->partsA};
+    const int gB = (int)((ng + 127) / 128);
+    job.role[1] = {PairArgs{(int)ng, (int)na, (int)rup(na, 64), n, m->psi_m, m->psi_h, np, m->sc,
+                            SC_F_AB, SC_OUT_AB, m->M1, m->Ng4, 0, 1, nullptr, m->status},
+                   gB, gB};
+    job.role[2] = {PairArgs{(int)na, (int)na, m->ychunkC, n, m->psig_m, m->psig_h, np, m->sc,
+                            SC_F_C, SC_OUT_C, m->M3p, n, na * n, 0, m->EpC, m->status},
+                   m->xa, m->xa * m->partsC};
+    job.nroles = 3;
+    const unsigned blocks = (unsigned)(job.role[0].nblk + job.role[1].nblk + job.role[2].nblk);
     if (np == 64)
-      pair_kernel<64><<<grid, kPairThreads, PairCfg<64>::SMEM, s>>>(Ym, Yh, Vm, pa);
+      pair_kernel<64><<<blocks, kPairThreads, PairCfg<64>::SMEM, s>>>(job);
     else
-      pair_kernel<128><<<grid, kPairThreads, PairCfg<128>::SMEM, s>>>(Ym, Yh, Vm, pa);
+      pair_kernel<128><<<blocks, kPairThreads, PairCfg<128>::SMEM, s>>>(job);
     count_launch();
-  };
-  {  // role A: M2[g][j] = sum_R (V o P)[g][R] Psi[R][j], and sum V o P^2
-    PairArgs pa{(int)na, (int)ng, m->ychunkA, n, m->psig_m, m->psig_h, np, m->sc, SC_F_AB, SC_OUT_AB, m->M2p, n, na * n, 0, m->EpA, m->status};
-    launch_pair(m->m_psi64_m, m->m_psi64_h, m->m_VA, pa, dim3(m->xa, m->partsA));
-  }
-  {  // role B: M1[j][R] = sum_g (V^T o P^T)[R][g] Psi_g[g][j], written transposed
-    PairArgs pa{(int)ng, (int)na, (int)rup(na, 64), n, m->psi_m, m->psi_h, np, m->sc, SC_F_AB, SC_OUT_AB, m->M1, m->Ng4, 0, 1, nullptr, m->status};
-    launch_pair(m->m_psig64_m, m->m_psig64_h, m->m_VB, pa, dim3((unsigned)((ng + 127) / 128), 1));
-  }
-  {  // role C: M3[g][j] = sum_g' (W o Q)[g][g'] Psi_g[g'][j], and sum W o Q^2
-    PairArgs pa{(int)na, (int)na, m->ychunkC, n, m->psig_m, m->psig_h, np, m->sc, SC_F_C, SC_OUT_C, m->M3p, n, na * n, 0, m->EpC, m->status};
-    launch_pair(m->m_psig64_m, m->m_psig64_h, m->m_VC, pa, dim3(m->xa, m->partsC));
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
