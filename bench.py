@@ -39,6 +39,9 @@ WORKLOAD = ("64-centre 2x2x2 diamond supercell, L=13.48 bohr, 13 Gaussians/centr
             "(2s,2p,1d), N=832, n_occ=128, 60^3 grid, N_aux=4000")
 METRIC = "K builds/s (64-atom cell)"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# DRAM bytes per (X row, Y row) pair of the pair kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum = 1496 MB over 3.2316e8 pairs)
+PAIR_DRAM_BYTES_PER_PAIR = 1496e6 / (2.0 * 1755 * 91125 + 1755.0 * 1755)
 # FP64 on the CUDA cores of GB300: 2 DFMA (4 flops) per clock per SM, measured
 # 3.81 flops/clock/SM with an FMA-chain probe; x 152 SMs x 2070 MHz.
 FP64_FLOPS_PER_CLK_SM = 4.0
@@ -366,7 +369,15 @@ def main():
                     "unit": "TFLOP/s",
                     "peak_source": f"dense bf16/fp16 tensor rate ({pk_src})",
                     "issued_tensor_tflops": issued / (dom_ms * 1e-3) / 1e12,
-                    "traffic": None}
+                    # tensor-pipe fraction: MMA FLOPs issued (7 split passes) over the
+                    # same peak; the algorithmic 'frac' counts each product once
+                    "issued_frac": issued / (dom_ms * 1e-3) / 1e12 / peak,
+                    # DRAM bytes of the pair launch: dram__bytes_read + write of one ncu
+                    # capture (27-centre cell, n = 128: 1496 MB for 3.23e8 pairs), scaled
+                    # to this cell by its pair count (the traffic is per pair)
+                    "traffic": PAIR_DRAM_BYTES_PER_PAIR * (2.0 * Na * Ng + float(Na) * Na),
+                    "traffic_source": "ncu capture of the pair kernel on the 27-centre cell "
+                                      "(n = 128), scaled by pair count"}
         roof["frac"] = roof["achieved"] / roof["peak"]
         roof["ms_per_build"] = dom_ms
         value = job_throughput(world, steps, ms)
