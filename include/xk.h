@@ -62,7 +62,10 @@ enum {
                          E_x is returned in the closed form
                          -dV (2 sum V o P^2 - sum W o Q^2) (Eq. exoccri
                          contracted with C), accumulated from the pair
-                         products.  Needs n <= 128.                         */
+                         products.  n <= 128: one fused kernel, P never
+                         stored; n > 128: T = V o P stored as FP16 hi/lo
+                         (4 N_aux (N_g + N_aux) bytes more) and contracted
+                         by three tensor-core GEMMs.                        */
 };
 
 /*
@@ -85,7 +88,7 @@ int xk_footprint(int64_t Ng, int32_t N, int32_t n, int32_t Naux, int mode, size_
  *   mode             XK_FP64 or XK_F16X3
  * Errors: XK_EINVAL (sizes, null pointers, idx out of range or duplicated,
  * W not symmetric to 1e-12 relative, dV <= 0, n > N, Naux > Ng; for
- * XK_F16X3 also n > 128 or basis columns linearly dependent on the grid),
+ * XK_F16X3 also basis columns linearly dependent on the grid),
  * XK_ENOMEM (footprint above the admission budget: free device memory less
  * a reserve, or XK_HBM_BUDGET_BYTES when set), XK_ECUDA.
  */

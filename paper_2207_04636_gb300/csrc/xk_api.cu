@@ -322,8 +322,6 @@ int xk_setup(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* phi,
   if (!valid_sizes(Ng, N, n, Naux)) return fail(XK_EINVAL, "xk_setup: invalid sizes");
   if (!(dV > 0.0) || !std::isfinite(dV)) return fail(XK_EINVAL, "xk_setup: dV must be > 0");
   if (mode != XK_FP64 && mode != XK_F16X3) return fail(XK_EINVAL, "xk_setup: unsupported mode");
-  if (mode == XK_F16X3 && n > 128)
-    return fail(XK_EINVAL, "xk_setup: XK_F16X3 supports n <= 128 occupied orbitals");
   {
     std::vector<int32_t> s(idx, idx + Naux);
     std::sort(s.begin(), s.end());

@@ -319,6 +319,71 @@ cudaError_t transpose(const T* src, long rows, long cols, long ld_src, T* dst, l
   return cudaGetLastError();
 }
 
+// dst[c][r] (stride ld_dst) = float(src[r][c]) for r < rows, c < cols.
+__global__ void transpose_f64_f32_kernel(const double* __restrict__ src, long rows, long cols,
+                                         long ld_src, float* __restrict__ dst, long ld_dst) {
+  __shared__ float tile[32][33];
+  const long r0 = (long)blockIdx.y * 32, c0 = (long)blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const long r = r0 + i, c = c0 + threadIdx.x;
+    tile[i][threadIdx.x] = (r < rows && c < cols) ? (float)src[r * ld_src + c] : 0.0f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const long c = c0 + i, r = r0 + threadIdx.x;
+    if (c < cols && r < rows) dst[c * ld_dst + r] = tile[threadIdx.x][i];
+  }
+}
+
+// Per-row pieces of FP32 rows, one warp per row (grid-stride): m, h of
+// src[r][c] * G on the row's grid for c < cols, zero for cols <= c < ld_dst
+// (a multiple of 8); max_r sum_c src[r][c]^2 folded into rn2 once per block.
+__global__ void split_rows_f32_kernel(const float* __restrict__ src, long rows, int cols,
+                                      long ld_src, const float* __restrict__ sc, int gidx,
+                                      __half* __restrict__ mo, __half* __restrict__ ho,
+                                      long ld_dst, unsigned* __restrict__ rn2) {
+  __shared__ float red[32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const float G = sc[gidx];
+  float wn = 0.0f;
+  for (long r = (long)blockIdx.x * nw + wib; r < rows; r += (long)gridDim.x * nw) {
+    const float* row = src + r * ld_src;
+    float mx = 0.0f, nrm = 0.0f;
+    for (int c = lane; c < cols; c += 32) {
+      const float v = row[c];
+      nrm = fmaf(v, v, nrm);
+      mx = fmaxf(mx, fabsf(v * G));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+    }
+    wn = fmaxf(wn, nrm);
+    const float q = row_grid(mx), qi = 1.0f / q;
+    for (long c = (long)lane * 8; c < ld_dst; c += 256) {
+      uint32_t mw[4], hw[4];
+#pragma unroll
+      for (int j = 0; j < 8; j += 2) {
+        const float x0 = c + j < cols ? row[c + j] * G : 0.0f;
+        const float x1 = c + j + 1 < cols ? row[c + j + 1] * G : 0.0f;
+        const float m0 = q * rintf(x0 * qi), m1 = q * rintf(x1 * qi);
+        const __half2 hm = __floats2half2_rn(m0, m1);
+        const __half2 hh = __floats2half2_rn(x0 - m0, x1 - m1);
+        mw[j / 2] = *reinterpret_cast<const uint32_t*>(&hm);
+        hw[j / 2] = *reinterpret_cast<const uint32_t*>(&hh);
+      }
+      *reinterpret_cast<uint4*>(mo + r * ld_dst + c) = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+      *reinterpret_cast<uint4*>(ho + r * ld_dst + c) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    }
+  }
+  if (lane == 0) red[wib] = wn;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < nw; ++w) wn = fmaxf(wn, red[w]);
+    atomicMax(rn2, __float_as_uint(wn * 1.0001f));
+  }
+}
+
 __global__ void gather_rows_half_kernel(const __half* __restrict__ src, long ld,
                                         const int32_t* __restrict__ idx, int rows,
                                         __half* __restrict__ dst) {
@@ -439,6 +504,22 @@ struct GemmArgs {
   long ld_p;
   int piece_idx;
   unsigned* rn2;
+  // Operands stored MN-major ([K][M], [K][N]; 64 x 64 TMA boxes) instead of
+  // K-major ([M][K], [N][K]; 128 x 64 boxes).
+  int a_mn, b_mn;
+  int transposed;  // write out[col][row] (stride ldo) instead of out[row][col]
+  // T mode (tv set, one split): the tile is S = A B^T (both in piece units);
+  // write the hi/lo FP16 split of f V'[row][col] S into th / tl [M][ld_t]
+  // (zero for Ncols <= col < ld_t) and the tile's sum V' S^2 into
+  // epart[blockIdx.y * gridDim.x + blockIdx.x].
+  const float* tv;
+  long ldv;
+  int f_idx;
+  __half* th;
+  __half* tl;
+  long ld_t;
+  double* epart;
+  int kdrain;  // k-blocks per accumulator drain (0: kDrain)
 };
 
 constexpr int G_STAGES = 3;
@@ -460,7 +541,8 @@ __global__ void __launch_bounds__(192, 1)
   const int kbeg = blockIdx.z * g.kchunk;
   const int kend = min(g.K, kbeg + g.kchunk);
   const int nkb = kend > kbeg ? (kend - kbeg + 63) / 64 : 0;
-  const int ngroups = (nkb + kDrain - 1) / kDrain;
+  const int kd = g.kdrain > 0 ? g.kdrain : kDrain;
+  const int ngroups = (nkb + kd - 1) / kd;
 
   if (tid == 0) {
     for (int s = 0; s < G_STAGES; ++s) {
@@ -495,26 +577,45 @@ __global__ void __launch_bounds__(192, 1)
       uint8_t* st = sm + s * G_STAGE_BYTES;
       mbar_expect_tx(&full[s], G_STAGE_BYTES);
       const int kc = kbeg + kb * 64;
-      tma_load_2d(st, &mAm, &full[s], kc, m0);
-      tma_load_2d(st + 16384, &mAh, &full[s], kc, m0);
-      tma_load_2d(st + 32768, &mBm, &full[s], kc, n0);
-      tma_load_2d(st + 49152, &mBh, &full[s], kc, n0);
+      if (!g.a_mn) {
+        tma_load_2d(st, &mAm, &full[s], kc, m0);
+        tma_load_2d(st + 16384, &mAh, &full[s], kc, m0);
+      } else {  // [64 K rows][64 M] boxes, M halves 8 KB apart
+        tma_load_2d(st, &mAm, &full[s], m0, kc);
+        tma_load_2d(st + 8192, &mAm, &full[s], m0 + 64, kc);
+        tma_load_2d(st + 16384, &mAh, &full[s], m0, kc);
+        tma_load_2d(st + 24576, &mAh, &full[s], m0 + 64, kc);
+      }
+      if (!g.b_mn) {
+        tma_load_2d(st + 32768, &mBm, &full[s], kc, n0);
+        tma_load_2d(st + 49152, &mBh, &full[s], kc, n0);
+      } else {
+        tma_load_2d(st + 32768, &mBm, &full[s], n0, kc);
+        tma_load_2d(st + 40960, &mBm, &full[s], n0 + 64, kc);
+        tma_load_2d(st + 49152, &mBh, &full[s], n0, kc);
+        tma_load_2d(st + 57344, &mBh, &full[s], n0 + 64, kc);
+      }
       last_parity[s] = use & 1;
     }
     for (int s = 0; s < G_STAGES; ++s)
       if (last_parity[s] >= 0) mbar_wait(&full[s], last_parity[s]);
   } else if (warp == 5) {
     // whole warp runs the loop; one elected lane issues each MMA and commit
-    const uint32_t idesc = idesc_f16(128, 128, false, false, false);
-    const uint64_t dst0 = sdesc_sw128(smem_u32(sm), 16, 1024);
+    const uint32_t idesc = idesc_f16(128, 128, false, g.a_mn != 0, g.b_mn != 0);
+    // K-major tiles step 32 B per K = 16; MN-major tiles step 16 rows (2 KB)
+    // and keep their two 64-wide halves 8 KB apart (LBO)
+    const uint64_t dkm = sdesc_sw128(smem_u32(sm), 16, 1024);
+    const uint64_t dmn = sdesc_sw128(smem_u32(sm), 8192, 1024);
+    const uint64_t da0 = g.a_mn ? dmn : dkm, db0 = g.b_mn ? dmn : dkm;
+    const uint32_t ast = g.a_mn ? 128 : 2, bst = g.b_mn ? 128 : 2;
     auto fail = [&](int code) {
       if (lane == 0) { atomicExch(g.status, code); abort_flag = 1; }
       __syncwarp();
     };
     for (int kb = 0; kb < nkb && !__shfl_sync(0xffffffffu, (int)abort_flag, 0); ++kb) {
-      const int s = kb % G_STAGES, grp = kb / kDrain, set = grp & 1;
-      const bool first = (kb % kDrain) == 0;
-      const bool last = (kb % kDrain) == kDrain - 1 || kb == nkb - 1;
+      const int s = kb % G_STAGES, grp = kb / kd, set = grp & 1;
+      const bool first = (kb % kd) == 0;
+      const bool last = (kb % kd) == kd - 1 || kb == nkb - 1;
       if (first && grp >= 2 && !mbar_wait_warp(&set_free[set], ((grp >> 1) - 1) & 1)) {
         fail(14); break;
       }
@@ -522,21 +623,21 @@ __global__ void __launch_bounds__(192, 1)
       tc_fence_after();
       // stage s: A m-piece at +0, A h at +16 KB, B m at +32 KB, B h at +48 KB; the
       // descriptor address field counts 16-byte units (1024 per 16 KB, 2 per K step)
-      const uint64_t dam = dst0 + s * (G_STAGE_BYTES >> 4), dah = dam + 1024;
-      const uint64_t dbm = dam + 2048, dbh = dam + 3072;
+      const uint64_t dam = da0 + s * (G_STAGE_BYTES >> 4), dah = dam + 1024;
+      const uint64_t dbm = db0 + s * (G_STAGE_BYTES >> 4) + 2048, dbh = dbm + 1024;
       const uint32_t t0 = tbase + set * 256, t1 = t0 + 128;
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
-        if (elect_one()) mma_f16(t0, dam + kk * 2, dbm + kk * 2, idesc, (first && kk == 0) ? 0u : 1u);
+        if (elect_one()) mma_f16(t0, dam + kk * ast, dbm + kk * bst, idesc, (first && kk == 0) ? 0u : 1u);
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
-        if (elect_one()) mma_f16(t1, dam + kk * 2, dbh + kk * 2, idesc, (first && kk == 0) ? 0u : 1u);
+        if (elect_one()) mma_f16(t1, dam + kk * ast, dbh + kk * bst, idesc, (first && kk == 0) ? 0u : 1u);
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
-        if (elect_one()) mma_f16(t1, dah + kk * 2, dbm + kk * 2, idesc, 1u);
+        if (elect_one()) mma_f16(t1, dah + kk * ast, dbm + kk * bst, idesc, 1u);
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
-        if (elect_one()) mma_f16(t1, dah + kk * 2, dbh + kk * 2, idesc, 1u);
+        if (elect_one()) mma_f16(t1, dah + kk * ast, dbh + kk * bst, idesc, 1u);
       if (elect_one()) {
         mma_commit(&empty[s]);
         if (last) mma_commit(&set_ready[set]);
@@ -587,8 +688,12 @@ __global__ void __launch_bounds__(192, 1)
         nrm = fmaf(v, v, nrm);
         mx = fmaxf(mx, fabsf(v * G));
       }
+      {
+        float wn = (m0 + r < g.M) ? nrm : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) wn = fmaxf(wn, __shfl_xor_sync(0xffffffffu, wn, o));
+        if (lane == 0) atomicMax(g.rn2, __float_as_uint(wn * 1.0001f));
+      }
       if (m0 + r < g.M) {
-        atomicMax(g.rn2, __float_as_uint(nrm * 1.0001f));
         const float q = row_grid(mx);
         __half* mrow = g.pm + (long)(m0 + r) * g.ld_p;
         __half* hrow = g.ph + (long)(m0 + r) * g.ld_p;
@@ -607,6 +712,65 @@ __global__ void __launch_bounds__(192, 1)
           }
           *reinterpret_cast<uint4*>(mrow + c0) = make_uint4(mw[0], mw[1], mw[2], mw[3]);
           *reinterpret_cast<uint4*>(hrow + c0) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        }
+      }
+    } else if (g.tv) {
+      // T mode: V' o S and its hi/lo split, 8 columns at a time
+      const long x = (long)m0 + r;
+      const bool xok = x < g.M;
+      const float f = g.sc[g.f_idx];
+      const float* vrow = g.tv + x * g.ldv;
+      double esum = 0.0;
+#pragma unroll
+      for (int c0 = 0; c0 < 128; c0 += 8) {
+        const long col = (long)n0 + c0;
+        if (col >= g.ld_t) break;
+        float v[8];
+        if (xok && col + 8 <= g.Ncols) {
+          const float4 v0 = *reinterpret_cast<const float4*>(vrow + col);
+          const float4 v1 = *reinterpret_cast<const float4*>(vrow + col + 4);
+          v[0] = v0.x; v[1] = v0.y; v[2] = v0.z; v[3] = v0.w;
+          v[4] = v1.x; v[5] = v1.y; v[6] = v1.z; v[7] = v1.w;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) v[j] = (xok && col + j < g.Ncols) ? vrow[col + j] : 0.0f;
+        }
+        uint32_t hw[4], lw[4];
+        float e = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+          const float s0 = ok ? run[c0 + j] : 0.0f, s1 = ok ? run[c0 + j + 1] : 0.0f;
+          const float p0 = v[j] * s0, p1 = v[j + 1] * s1;
+          e = fmaf(p0, s0, e);
+          e = fmaf(p1, s1, e);
+          const float t0 = p0 * f, t1 = p1 * f;
+          const __half2 h01 = __floats2half2_rn(t0, t1);
+          const float2 b01 = __half22float2(h01);
+          const __half2 l01 = __floats2half2_rn(t0 - b01.x, t1 - b01.y);
+          hw[j / 2] = *reinterpret_cast<const uint32_t*>(&h01);
+          lw[j / 2] = *reinterpret_cast<const uint32_t*>(&l01);
+        }
+        esum += (double)e;
+        if (xok) {
+          *reinterpret_cast<uint4*>(g.th + x * g.ld_t + col) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          *reinterpret_cast<uint4*>(g.tl + x * g.ld_t + col) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+      }
+      if (g.epart) {
+        __shared__ double ered[4];
+        for (int o = 16; o > 0; o >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, o);
+        if (lane == 0) ered[warp] = esum;
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (r == 0)
+          g.epart[(long)blockIdx.y * gridDim.x + blockIdx.x] = ered[0] + ered[1] + ered[2] + ered[3];
+      }
+    } else if (g.transposed) {
+      const long row = (long)m0 + r;
+      if (row < g.M) {
+#pragma unroll
+        for (int c = 0; c < 128; ++c) {
+          const int col = n0 + c;
+          if (col < g.Ncols) g.out[(long)col * g.ldo + row] = ok ? run[c] * scale : 0.0f;
         }
       }
     } else if (m0 + r < g.M) {
@@ -1059,6 +1223,13 @@ struct MixedState {
   int* status = nullptr;
   int xa = 1, partsA = 1, partsC = 1, splitsL1 = 1, splitsL23 = 1;
   int ychunkA = 64, ychunkC = 64;
+  // n > 128: the pair contractions run through a stored T = f V o P (hi/lo
+  // FP16, [N_aux][N_g] and [N_aux][N_aux]) and three GEMMs over it
+  bool large = false;
+  int nt = 1;
+  long epA = 1, epC = 1;
+  __half *TA_h = nullptr, *TA_l = nullptr, *TC_h = nullptr, *TC_l = nullptr;
+  CUtensorMap m_TA_h, m_TA_l, m_TAmn_h, m_TAmn_l, m_TC_h, m_TC_l;
   int kchunkL1 = 64, kchunkL23 = 64;
   CUtensorMap m_phi_m, m_phi_h, m_CT_m, m_CT_h, m_psi128_m, m_psi128_h, m_psi64_m, m_psi64_h,
       m_psig128_m, m_psig128_h, m_psig64_m, m_psig64_h, m_VA, m_VB, m_VC, m_phiT_m, m_phiT_h,
@@ -1080,6 +1251,9 @@ cudaError_t alloc(MixedState* m, T** p, size_t elems) {
 struct Plan {
   long Np, Ng8, Na8, Ng4, Na4;
   int np, xa, partsA, partsC, splitsL1, splitsL23, kchunkL1, kchunkL23, ychunkA, ychunkC;
+  bool large;
+  int nt;
+  long epA, epC;
 };
 
 Plan make_plan(int64_t Ng, int N, int n, int Naux) {
@@ -1091,13 +1265,30 @@ Plan make_plan(int64_t Ng, int N, int n, int Naux) {
   p.Ng4 = rup(Ng, 4);
   p.Na4 = rup(Naux, 4);
   p.xa = (Naux + 127) / 128;
-  // roles A and C: X = g tiles; split Y so the grid is about two waves of 152 SMs
-  p.partsA = std::max(1, std::min<int>((608 + p.xa - 1) / p.xa, (int)((Ng + 63) / 64)));
-  p.ychunkA = (int)rup((Ng + p.partsA - 1) / p.partsA, 64);
-  p.partsA = (int)((Ng + p.ychunkA - 1) / p.ychunkA);
-  p.partsC = std::max(1, std::min<int>((608 + p.xa - 1) / p.xa, (Naux + 63) / 64));
-  p.ychunkC = (int)rup((Naux + p.partsC - 1) / p.partsC, 64);
-  p.partsC = (Naux + p.ychunkC - 1) / p.ychunkC;
+  p.large = p.np > 128;
+  p.nt = (n + 127) / 128;
+  if (!p.large) {
+    // roles A and C: X = g tiles; split Y so the grid is about four waves of 152 SMs
+    p.partsA = std::max(1, std::min<int>((608 + p.xa - 1) / p.xa, (int)((Ng + 63) / 64)));
+    p.ychunkA = (int)rup((Ng + p.partsA - 1) / p.partsA, 64);
+    p.partsA = (int)((Ng + p.ychunkA - 1) / p.ychunkA);
+    p.partsC = std::max(1, std::min<int>((608 + p.xa - 1) / p.xa, (Naux + 63) / 64));
+    p.ychunkC = (int)rup((Naux + p.partsC - 1) / p.partsC, 64);
+    p.partsC = (Naux + p.ychunkC - 1) / p.ychunkC;
+    p.epA = (long)p.partsA * p.xa;
+    p.epC = (long)p.partsC * p.xa;
+  } else {
+    // M2 = T_A Psi and M3 = T_C Psi_g: (xa x nt) tiles, K split to about four waves
+    const int t2 = p.xa * p.nt;
+    p.partsA = std::max(1, std::min<int>((608 + t2 - 1) / t2, (int)((Ng + 4095) / 4096)));
+    p.ychunkA = (int)rup((Ng + p.partsA - 1) / p.partsA, 64);
+    p.partsA = (int)((Ng + p.ychunkA - 1) / p.ychunkA);
+    p.partsC = std::max(1, std::min<int>((304 + t2 - 1) / t2, (Naux + 1023) / 1024));
+    p.ychunkC = (int)rup((Naux + p.partsC - 1) / p.partsC, 64);
+    p.partsC = (Naux + p.ychunkC - 1) / p.ychunkC;
+    p.epA = (long)p.xa * ((Ng + 127) / 128);
+    p.epC = (long)p.xa * ((Naux + 127) / 128);
+  }
   // line GEMMs: (N / 128) x (n / 128) tiles x K splits of >= 1024
   const int tiles = ((N + 127) / 128) * ((n + 127) / 128);
   p.splitsL1 = std::max(1, std::min<int>((int)((Ng + 1023) / 1024), (608 + tiles - 1) / tiles));
@@ -1115,6 +1306,14 @@ Plan make_plan(int64_t Ng, int N, int n, int Naux) {
 int q_ksplit(int N) { return std::max(1, std::min(64, (N + 15) / 16)); }
 
 // Split-K work of the FP64 contractions of the set-up and of Q = L^T C.
+// Device staging for the set-up (two buffers): Phi and its layouts, W, and V
+// in row chunks of at most N rows.
+size_t stage_elems(int64_t Ng, int N, int Naux, long Ng8) {
+  const size_t ng = Ng, na = Naux;
+  return std::max({ng * N + 2 * (size_t)N * N, (size_t)N * Ng8, na * na, ng * std::min<size_t>(na, N),
+                   na * (size_t)N});
+}
+
 size_t dwork_elems(int64_t Ng, int N, int n) {
   auto w = [](int M, int Nc, int K) {
     const int ks = dgemm_ksplit(M, Nc, K);
@@ -1130,14 +1329,15 @@ size_t mixed_footprint(int64_t Ng, int N, int n, int Naux) {
   const size_t ng = Ng, na = Naux;
   size_t b = 0;
   b += 2 * ng * p.Np * 2 + 2 * (size_t)N * p.Ng8 * 2 + 2 * (size_t)N * p.Na8 * 2;  // Phi pieces
-  b += na * p.Ng4 * 4 + ng * p.Na4 * 4 + na * p.Na4 * 4 + na * 4;                  // V, V^T, W, idx
+  b += na * p.Ng4 * 4 + (p.large ? 0 : ng * p.Na4 * 4) + na * p.Na4 * 4 + na * 4;  // V, V^T, W, idx
+  if (p.large) b += 2 * na * p.Ng8 * 2 + 2 * na * p.Na8 * 2;                      // T_A, T_C
   b += 2 * (size_t)n * p.Np * 2 + (size_t)n * p.Np * 8 + 2 * ng * p.np * 2 + 2 * na * p.np * 2;
   b += (size_t)p.partsA * na * n * 4 + (size_t)p.partsC * na * n * 4 + (size_t)n * p.Ng4 * 4;
   b += na * n * 8 + (size_t)n * p.Na8 * 8 + 2 * (size_t)n * p.Ng8 * 2 + 2 * (size_t)n * p.Na8 * 2;
   b += (size_t)p.splitsL1 * N * n * 4 + (size_t)p.splitsL23 * N * n * 4;
-  b += (size_t)(p.partsA + p.partsC) * p.xa * 8;
+  b += (size_t)(p.epA + p.epC) * 8;
   b += (size_t)N * N * 8 + (size_t)N * n * 8 + dwork_elems(Ng, N, n) * 8;
-  b += 2 * std::max(ng * std::max<size_t>(N, p.Na8) + 2 * (size_t)N * N, (size_t)N * p.Ng8) * 8;
+  b += 2 * stage_elems(Ng, N, Naux, p.Ng8) * 8;
   return b + 64 * 1024;
 }
 
@@ -1148,7 +1348,6 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   cudaError_t e = get_encode();
   if (e != cudaSuccess) return e;
   const Plan p = make_plan(Ng, N, n, Naux);
-  if (p.np > 128) return cudaErrorNotSupported;  // the fused kernel holds n <= 128 columns
   e = cudaFuncSetAttribute(pair_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairCfg<64>::SMEM);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(pair_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairCfg<128>::SMEM);
@@ -1164,6 +1363,7 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   m->ychunkA = p.ychunkA; m->ychunkC = p.ychunkC;
   m->splitsL1 = p.splitsL1; m->splitsL23 = p.splitsL23;
   m->kchunkL1 = p.kchunkL1; m->kchunkL23 = p.kchunkL23;
+  m->large = p.large; m->nt = p.nt; m->epA = p.epA; m->epC = p.epC;
   const size_t ng = Ng, na = Naux;
 #define MX(ptr, elems)                          \
   do {                                          \
@@ -1173,7 +1373,12 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   MX(m->phi_m, ng * p.Np); MX(m->phi_h, ng * p.Np);
   MX(m->phiT_m, (size_t)N * p.Ng8); MX(m->phiT_h, (size_t)N * p.Ng8);
   MX(m->phigT_m, (size_t)N * p.Na8); MX(m->phigT_h, (size_t)N * p.Na8);
-  MX(m->V32, na * p.Ng4); MX(m->VT32, ng * p.Na4); MX(m->W32, na * p.Na4);
+  MX(m->V32, na * p.Ng4); MX(m->W32, na * p.Na4);
+  if (!p.large) MX(m->VT32, ng * p.Na4);
+  if (p.large) {
+    MX(m->TA_h, na * p.Ng8); MX(m->TA_l, na * p.Ng8);
+    MX(m->TC_h, na * p.Na8); MX(m->TC_l, na * p.Na8);
+  }
   MX(m->idx, na);
   MX(m->CT_m, (size_t)n * p.Np); MX(m->CT_h, (size_t)n * p.Np); MX(m->CT64, (size_t)n * p.Np);
   MX(m->psi_m, ng * p.np); MX(m->psi_h, ng * p.np);
@@ -1184,7 +1389,7 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   MX(m->M1_m, (size_t)n * p.Ng8); MX(m->M1_h, (size_t)n * p.Ng8);
   MX(m->D23T_m, (size_t)n * p.Na8); MX(m->D23T_h, (size_t)n * p.Na8);
   MX(m->L1p, (size_t)p.splitsL1 * N * n); MX(m->L23p, (size_t)p.splitsL23 * N * n);
-  MX(m->EpA, (size_t)p.partsA * p.xa); MX(m->EpC, (size_t)p.partsC * p.xa);
+  MX(m->EpA, (size_t)p.epA); MX(m->EpC, (size_t)p.epC);
   MX(m->sc, NSC); MX(m->am, NAM); MX(m->status, 4); MX(m->rowmax, (size_t)n);
   MX(m->red, reduce_work_elems());
   MX(m->Lf, (size_t)N * N); MX(m->Q64, (size_t)N * n);
@@ -1192,8 +1397,7 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
 #undef MX
   double *stage = nullptr, *stage2 = nullptr;
   {
-    const size_t elems = std::max(ng * std::max<size_t>(N, p.Na8) + 2 * (size_t)N * N,
-                                  (size_t)N * p.Ng8);
+    const size_t elems = stage_elems(Ng, N, Naux, p.Ng8);
     void* q = nullptr;
     e = cudaMalloc(&q, elems * 8);
     if (e != cudaSuccess) return bail(e);
@@ -1254,17 +1458,25 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   if (e == cudaSuccess) e = split_rows<double>(stage, N, p.Na8, p.Na8, m->sc, SC_PHI, m->phigT_m, m->phigT_h, p.Na8, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fin(e);
-  // V in both orientations, W; max |V|, max |W| bound the product scales
-  e = cudaMemcpyAsync(stage, V, na * ng * 8, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return fin(e);
-  absmax_kernel<double><<<blocks_for(na * ng), 256, 0, s>>>(stage, na, ng, ng, m->am + AM_V);
-  f64_to_f32_kernel<<<blocks_for(na * p.Ng4), 256, 0, s>>>(stage, na, ng, m->V32, p.Ng4);
-  count_launch(2);
-  e = transpose<double>(stage, na, ng, ng, stage2, p.Na4, s);  // [R][g], zero for g >= N_aux
-  if (e == cudaSuccess) {
-    f64_to_f32_kernel<<<blocks_for(ng * p.Na4), 256, 0, s>>>(stage2, ng, p.Na4, m->VT32, p.Na4);
-    count_launch();
-    e = cudaStreamSynchronize(s);
+  // V (and, for n <= 128, V^T) in FP32, converted in chunks of rows; max |V|
+  // and max |W| bound the product scales
+  if (m->VT32) e = cudaMemsetAsync(m->VT32, 0, ng * p.Na4 * 4, s);
+  {
+    const long chunk = std::max<long>(1, std::min<long>((long)na, N));
+    for (long r0 = 0; r0 < (long)na && e == cudaSuccess; r0 += chunk) {
+      const long rows = std::min<long>(chunk, (long)na - r0);
+      e = cudaMemcpyAsync(stage, V + (size_t)r0 * ng, rows * ng * 8, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) break;
+      absmax_kernel<double><<<blocks_for(rows * ng), 256, 0, s>>>(stage, rows, ng, ng, m->am + AM_V);
+      f64_to_f32_kernel<<<blocks_for(rows * p.Ng4), 256, 0, s>>>(stage, rows, ng, m->V32 + r0 * p.Ng4, p.Ng4);
+      count_launch(2);
+      if (m->VT32) {  // V^T [g][R]
+        dim3 grid((unsigned)((ng + 31) / 32), (unsigned)((rows + 31) / 32));
+        transpose_f64_f32_kernel<<<grid, dim3(32, 8), 0, s>>>(stage, rows, ng, ng, m->VT32 + r0, p.Na4);
+        count_launch();
+      }
+      e = cudaStreamSynchronize(s);  // the next chunk reuses the staging buffer
+    }
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(stage, W, na * na * 8, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return fin(e);
@@ -1303,10 +1515,24 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
     e = make_map(ms.m, ms.p, ms.t, ms.es, ms.rows, ms.ld, ms.br, ms.bc);
     if (e != cudaSuccess) return fin(e);
   }
+  if (p.large) {  // T_A, T_C as K-major [rows][K] and T_A as MN-major [K = R][M = g]
+    const MapSpec tspecs[] = {
+        {&m->m_TA_h, m->TA_h, F16, 2, (long)na, p.Ng8, 128, 64},
+        {&m->m_TA_l, m->TA_l, F16, 2, (long)na, p.Ng8, 128, 64},
+        {&m->m_TAmn_h, m->TA_h, F16, 2, (long)na, p.Ng8, 64, 64},
+        {&m->m_TAmn_l, m->TA_l, F16, 2, (long)na, p.Ng8, 64, 64},
+        {&m->m_TC_h, m->TC_h, F16, 2, (long)na, p.Na8, 128, 64},
+        {&m->m_TC_l, m->TC_l, F16, 2, (long)na, p.Na8, 128, 64},
+    };
+    for (const MapSpec& ms : tspecs) {
+      e = make_map(ms.m, ms.p, ms.t, ms.es, ms.rows, ms.ld, ms.br, ms.bc);
+      if (e != cudaSuccess) return fin(e);
+    }
+  }
   {  // V' tiles [X rows][Y cols] in FP32: [128][32] boxes, 128-byte swizzle
     const auto F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     e = make_map(&m->m_VA, m->V32, F32, 4, (long)na, p.Ng4, 128, 32);
-    if (e == cudaSuccess) e = make_map(&m->m_VB, m->VT32, F32, 4, (long)ng, p.Na4, 128, 32);
+    if (e == cudaSuccess && m->VT32) e = make_map(&m->m_VB, m->VT32, F32, 4, (long)ng, p.Na4, 128, 32);
     if (e == cudaSuccess) e = make_map(&m->m_VC, m->W32, F32, 4, (long)na, p.Na4, 128, 32);
     if (e != cudaSuccess) return fin(e);
   }
@@ -1344,11 +1570,20 @@ cudaError_t mixed_enqueue(MixedState* m, const double* C, double* K, double* Ex,
   e = transpose<double>(m->Q64, N, n, n, m->CT64, m->Np, s);  // Q^T [j][mu], zero for mu >= N
   if (e == cudaSuccess) e = split_rows<double>(m->CT64, n, m->Np, m->Np, m->sc, SC_C, m->CT_m, m->CT_h, m->Np, s);
   if (e != cudaSuccess) return e;
-  {  // Psi = Phi' Q, written directly as per-row pieces
+  if (!m->large) {  // Psi = Phi' Q, written directly as per-row pieces
     GemmArgs g{(int)ng, n, N, (int)m->Np, nullptr, 0, 0, m->sc, SC_OUT_ORB, m->status,
                m->psi_m, m->psi_h, np, SC_PSI, m->am + AM_RN2};
     dim3 grid((unsigned)((ng + 127) / 128), 1, 1);
     gemm_kernel<<<grid, 192, G_SMEM, s>>>(m->m_phi_m, m->m_phi_h, m->m_CT_m, m->m_CT_h, g);
+  } else {  // n > 128: Psi in FP32 (the M1 buffer, free until step 3), then per-row pieces
+    GemmArgs g{};
+    g.M = (int)ng; g.Ncols = n; g.K = N; g.kchunk = (int)m->Np;
+    g.out = m->M1; g.ldo = n; g.sc = m->sc; g.scale_idx = SC_OUT_ORB; g.status = m->status;
+    dim3 grid((unsigned)((ng + 127) / 128), (unsigned)m->nt, 1);
+    gemm_kernel<<<grid, 192, G_SMEM, s>>>(m->m_phi_m, m->m_phi_h, m->m_CT_m, m->m_CT_h, g);
+    split_rows_f32_kernel<<<152 * 4, 256, 0, s>>>(m->M1, ng, n, n, m->sc, SC_PSI, m->psi_m,
+                                                  m->psi_h, np, m->am + AM_RN2);
+    count_launch();
   }
   scales_kernel<<<1, 32, 0, s>>>(m->am, m->sc, 1);
   gather_rows_half_kernel<<<blocks_for(na * np), 256, 0, s>>>(m->psi_m, np, m->idx, (int)na, m->psig_m);
@@ -1360,7 +1595,39 @@ cudaError_t mixed_enqueue(MixedState* m, const double* C, double* K, double* Ex,
 
   // ---- steps 2-3: the three fused pair contractions
   hook(1, 1);
-  {
+  if (m->large) {
+    // n > 128: T_A = f_AB V o (Psi_g Psi^T) and T_C = f_C W o (Psi_g Psi_g^T)
+    // as hi/lo FP16 with their energy sums, then M2 = T_A Psi, M3 = T_C Psi_g
+    // and M1^T = T_A^T Psi_g (written transposed) on the tensor cores.
+    GemmArgs t{};
+    t.M = (int)na; t.Ncols = (int)ng; t.K = np; t.kchunk = np; t.sc = m->sc; t.status = m->status;
+    t.tv = m->V32; t.ldv = m->Ng4; t.f_idx = SC_F_AB; t.th = m->TA_h; t.tl = m->TA_l;
+    t.ld_t = m->Ng8; t.epart = m->EpA;
+    gemm_kernel<<<dim3((unsigned)m->xa, (unsigned)((ng + 127) / 128), 1), 192, G_SMEM, s>>>(
+        m->m_psig128_m, m->m_psig128_h, m->m_psi128_m, m->m_psi128_h, t);
+    GemmArgs tc = t;
+    tc.Ncols = (int)na; tc.tv = m->W32; tc.ldv = m->Na4; tc.f_idx = SC_F_C; tc.th = m->TC_h;
+    tc.tl = m->TC_l; tc.ld_t = m->Na8; tc.epart = m->EpC;
+    gemm_kernel<<<dim3((unsigned)m->xa, (unsigned)((na + 127) / 128), 1), 192, G_SMEM, s>>>(
+        m->m_psig128_m, m->m_psig128_h, m->m_psig128_m, m->m_psig128_h, tc);
+    GemmArgs g2{};
+    g2.M = (int)na; g2.Ncols = n; g2.K = (int)ng; g2.kchunk = m->ychunkA; g2.out = m->M2p;
+    g2.ldo = n; g2.split_stride = na * n; g2.sc = m->sc; g2.scale_idx = SC_OUT_AB;
+    g2.status = m->status; g2.b_mn = 1;
+    gemm_kernel<<<dim3((unsigned)m->xa, (unsigned)m->nt, (unsigned)m->partsA), 192, G_SMEM, s>>>(
+        m->m_TA_h, m->m_TA_l, m->m_psi64_m, m->m_psi64_h, g2);
+    GemmArgs g3 = g2;
+    g3.K = (int)na; g3.kchunk = m->ychunkC; g3.out = m->M3p; g3.scale_idx = SC_OUT_C;
+    gemm_kernel<<<dim3((unsigned)m->xa, (unsigned)m->nt, (unsigned)m->partsC), 192, G_SMEM, s>>>(
+        m->m_TC_h, m->m_TC_l, m->m_psig64_m, m->m_psig64_h, g3);
+    GemmArgs g1{};
+    g1.M = (int)ng; g1.Ncols = n; g1.K = (int)na; g1.kchunk = (int)rup(na, 64); g1.out = m->M1;
+    g1.ldo = m->Ng4; g1.sc = m->sc; g1.scale_idx = SC_OUT_AB; g1.status = m->status;
+    g1.a_mn = 1; g1.b_mn = 1; g1.transposed = 1;
+    gemm_kernel<<<dim3((unsigned)((ng + 127) / 128), (unsigned)m->nt, 1), 192, G_SMEM, s>>>(
+        m->m_TAmn_h, m->m_TAmn_l, m->m_psig64_m, m->m_psig64_h, g1);
+    count_launch(5);
+  } else {
     // role A: M2[g][j] = sum_R (V o P)[g][R] Psi[R][j], and sum V o P^2
     // role B: M1[j][R] = sum_g (V^T o P^T)[R][g] Psi_g[g][j], written transposed
     // role C: M3[g][j] = sum_g' (W o Q)[g][g'] Psi_g[g'][j], and sum W o Q^2
@@ -1429,8 +1696,7 @@ cudaError_t mixed_enqueue(MixedState* m, const double* C, double* K, double* Ex,
   hook(7, 1);
   final_k_kernel<<<blocks_for((long)N * n), 256, 0, s>>>(m->L1p, m->splitsL1, m->L23p,
                                                          m->splitsL23, (long)N * n, m->dV, K);
-  final_ex_kernel<<<1, 256, 0, s>>>(m->EpA, m->partsA * m->xa, m->EpC, m->partsC * m->xa, m->sc,
-                                    m->dV, Ex);
+  final_ex_kernel<<<1, 256, 0, s>>>(m->EpA, (int)m->epA, m->EpC, (int)m->epC, m->sc, m->dV, Ex);
   count_launch(2);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
