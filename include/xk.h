@@ -150,6 +150,28 @@ int xk_poll(xk_ticket t, double* K_out, double* Ex, double* err_bound);
 /* Free every device and host resource of the handle (waits for its work). */
 int xk_release(xk_handle* h);
 
+/*
+ * Batches: one exchange build for each of several handles (cells of
+ * different sizes, different SCF runs) as one unit of device work.  The
+ * paper builds one cell at a time; a batch is the grouped, launch-bound
+ * form of the same per-iteration step (Eq. exoccri for every member).
+ *   xk_batch_create   handles: count distinct XK_F16X3 handles on one device;
+ *                     the batch keeps pointers to them (release the batch
+ *                     before any of its handles).
+ *   xk_batch_build    C[i] (host, N_i x n_i) -> K_out[i] (host, N_i x n_i),
+ *                     Ex_out[i]; blocking.  The device work of the whole
+ *                     batch (every member's orbitals, one grouped pair launch
+ *                     over all members with n <= 128, the line steps) is
+ *                     captured into a CUDA graph on the first call and
+ *                     replayed afterwards; results equal xk_build's bitwise.
+ * Errors: XK_EINVAL (NULL pointers, empty or repeated handles, FP64 handles,
+ * handles on different devices), XK_ETIMEDOUT, XK_ECUDA.
+ */
+typedef struct xk_batch xk_batch;
+int xk_batch_create(xk_handle* const* handles, int count, xk_batch** out);
+int xk_batch_build(xk_batch* b, const double* const* C, double* const* K_out, double* Ex_out);
+int xk_batch_release(xk_batch* b);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* xk_last_error(void);
 

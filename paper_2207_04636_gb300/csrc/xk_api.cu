@@ -646,4 +646,129 @@ int xk_release(xk_handle* h) {
   return XK_OK;
 }
 
+// ---------------------------------------------------------------- batches
+
+struct xk_batch {
+  std::vector<xk_handle*> hs;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  xk::PairGroup* group = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t launches = 0;  // kernels in one replay of the graph
+};
+
+int xk_batch_create(xk_handle* const* handles, int count, xk_batch** out) {
+  if (!out) return fail(XK_EINVAL, "xk_batch_create: out is NULL");
+  *out = nullptr;
+  if (!handles || count <= 0) return fail(XK_EINVAL, "xk_batch_create: no handles");
+  std::vector<xk_handle*> hs(handles, handles + count);
+  for (xk_handle* h : hs) {
+    if (!h) return fail(XK_EINVAL, "xk_batch_create: NULL handle");
+    if (h->mode != XK_F16X3 || !h->mixed)
+      return fail(XK_EINVAL, "xk_batch_create: every handle must use XK_F16X3");
+    if (h->device != hs[0]->device)
+      return fail(XK_EINVAL, "xk_batch_create: handles on different devices");
+  }
+  {
+    std::vector<xk_handle*> t = hs;
+    std::sort(t.begin(), t.end());
+    if (std::adjacent_find(t.begin(), t.end()) != t.end())
+      return fail(XK_EINVAL, "xk_batch_create: a handle appears twice");
+  }
+  DeviceGuard g(hs[0]->device);
+  xk_batch* b = new xk_batch();
+  b->hs = hs;
+  b->device = hs[0]->device;
+  cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  std::vector<xk::MixedState*> ms;
+  for (xk_handle* h : hs) ms.push_back(h->mixed);
+  if (e == cudaSuccess) e = xk::mixed_group_create(ms.data(), count, &b->group);
+  if (e != cudaSuccess) {
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return cuda_fail(e, "xk_batch_create");
+  }
+  *out = b;
+  return XK_OK;
+}
+
+int xk_batch_build(xk_batch* b, const double* const* C, double* const* K_out, double* Ex_out) {
+  if (!b || !C || !K_out || !Ex_out) return fail(XK_EINVAL, "xk_batch_build: NULL argument");
+  const size_t count = b->hs.size();
+  for (size_t i = 0; i < count; ++i)
+    if (!C[i] || !K_out[i]) return fail(XK_EINVAL, "xk_batch_build: NULL coefficient or K pointer");
+  // lock the members in address order (no lock-order cycles with other batches)
+  std::vector<xk_handle*> order = b->hs;
+  std::sort(order.begin(), order.end());
+  std::vector<std::unique_lock<std::mutex>> locks;
+  for (xk_handle* h : order) locks.emplace_back(h->mu);
+  DeviceGuard g(b->device);
+  // after any work still queued on the members' own streams, then the inputs
+  for (xk_handle* h : b->hs) {
+    cudaEvent_t ev;
+    XK_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    XK_CUDA(cudaEventRecord(ev, h->stream));
+    XK_CUDA(cudaStreamWaitEvent(b->stream, ev, 0));
+    cudaEventDestroy(ev);
+  }
+  for (size_t i = 0; i < count; ++i) {
+    xk_handle* h = b->hs[i];
+    XK_CUDA(cudaMemcpyAsync(h->C, C[i], (size_t)h->N * h->n * 8, cudaMemcpyHostToDevice, b->stream));
+  }
+  if (!b->exec) {
+    // the whole batch, device work only, captured once into a graph: the
+    // orbitals of every member, one grouped pair launch, the line steps
+    const uint64_t l0 = xk::g_launches.load();
+    XK_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    xk::StepHook none{nullptr, nullptr};
+    cudaError_t e = cudaSuccess;
+    for (xk_handle* h : b->hs)
+      if (e == cudaSuccess) e = xk::mixed_enqueue_pre(h->mixed, h->C, b->stream, none);
+    if (e == cudaSuccess) e = xk::mixed_group_enqueue_pair(b->group, b->stream);
+    for (xk_handle* h : b->hs)
+      if (e == cudaSuccess) e = xk::mixed_enqueue_post(h->mixed, h->K, h->Ex, b->stream, none);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(b->stream, &graph);
+    if (e == cudaSuccess) e = ec;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+    if (e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      b->exec = nullptr;
+      return cuda_fail(e, "xk_batch_build: graph capture");
+    }
+    b->graph = graph;
+    b->launches = xk::g_launches.load() - l0;
+    xk::g_launches.fetch_sub(b->launches);  // counted again per replay below
+  }
+  XK_CUDA(cudaGraphLaunch(b->exec, b->stream));
+  xk::g_launches.fetch_add(b->launches);
+  for (size_t i = 0; i < count; ++i) {
+    xk_handle* h = b->hs[i];
+    XK_CUDA(cudaMemcpyAsync(K_out[i], h->K, (size_t)h->N * h->n * 8, cudaMemcpyDeviceToHost, b->stream));
+    XK_CUDA(cudaMemcpyAsync(Ex_out + i, h->Ex, 8, cudaMemcpyDeviceToHost, b->stream));
+  }
+  XK_CUDA(cudaStreamSynchronize(b->stream));
+  for (xk_handle* h : b->hs) {
+    h->has_build = true;
+    const int st = xk::mixed_take_status(h->mixed);
+    if (st != 0)
+      return fail(XK_ETIMEDOUT, "xk_batch_build: a bounded wait inside a kernel gave up (code " +
+                                    std::to_string(st) + ")");
+  }
+  return XK_OK;
+}
+
+int xk_batch_release(xk_batch* b) {
+  if (!b) return fail(XK_EINVAL, "xk_batch_release: NULL batch");
+  DeviceGuard g(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  xk::mixed_group_destroy(b->group);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return XK_OK;
+}
+
 }  // extern "C"

@@ -820,26 +820,25 @@ struct PairArgs {
   int* status;
 };
 
+// One role of a pair launch (host record; copied into the launch parameters).
+struct PairRole {
+  CUtensorMap ym, yh, v;  // Y pieces (m, h) and the V' tiles
+  PairArgs a;
+  int gx;     // the role's own grid is gx x (nblk / gx)
+  int nblk;
+  int tiles;  // Y tiles per block (longest roles are placed first)
+};
+
 constexpr int kAccDrain = 2;                   // tiles per second-product drain
 constexpr int kStages = 3;                     // TMA stages of (Y pieces, V')
 constexpr int kEpiWarps = 16;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kPairThreads = kEpiThreads + 64; // + TMA producer warp + MMA warp
 
-// The three contractions of one build run as one launch (roles in order A, B,
-// C; the grid is their concatenation), so the short role-C CTAs fill the tail
-// of the long ones.
-struct PairRole {
-  PairArgs a;
-  int gx;    // the role's own grid is gx x (nblk / gx)
-  int nblk;
-};
-struct PairJob {
-  CUtensorMap ym[3], yh[3], v[3];
-  PairRole role[3];
-  int nroles;
-};
-
+// One launch runs several roles (the three contractions of one build, or
+// those of many builds grouped together): the roles' blocks are concatenated
+// in the grid, and their tensor maps and arguments are kernel parameters.
+// Long roles go first, so the short ones fill the tail of the grid.
 template <int NP>
 struct PairCfg {
   static constexpr int Y_BYTES = 64 * NP * 2;  // one piece of a 64-row tile
@@ -851,19 +850,12 @@ struct PairCfg {
   static constexpr int AC = NP / 4;            // accumulator columns per epilogue warp
 };
 
+// The kernel body: one X tile against a range of Y tiles for one role.
 template <int NP>
-__global__ void __launch_bounds__(kPairThreads, 1)
-    pair_kernel(const __grid_constant__ PairJob job) {
+__device__ __forceinline__ void pair_body(const CUtensorMap* mYm, const CUtensorMap* mYh,
+                                          const CUtensorMap* mV, const PairArgs& a, int bx, int by,
+                                          int gx) {
   using C = PairCfg<NP>;
-  int ri = 0, blk = blockIdx.x;
-  while (ri + 1 < job.nroles && blk >= job.role[ri].nblk) blk -= job.role[ri].nblk, ++ri;
-  // constant-index selection keeps the tensor maps in parameter space
-  const CUtensorMap* mYm = ri == 0 ? &job.ym[0] : ri == 1 ? &job.ym[1] : &job.ym[2];
-  const CUtensorMap* mYh = ri == 0 ? &job.yh[0] : ri == 1 ? &job.yh[1] : &job.yh[2];
-  const CUtensorMap* mV = ri == 0 ? &job.v[0] : ri == 1 ? &job.v[1] : &job.v[2];
-  const PairArgs& a = ri == 0 ? job.role[0].a : ri == 1 ? job.role[1].a : job.role[2].a;
-  const int gx = ri == 0 ? job.role[0].gx : ri == 1 ? job.role[1].gx : job.role[2].gx;
-  const int bx = blk % gx, by = blk / gx;
   extern __shared__ uint8_t p_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p_raw) + 1023) & ~uintptr_t(1023));
   __shared__ uint64_t full[kStages], empty[kStages], s_full, s_free, u_full[2], u_free[2], acc_ready,
@@ -1155,7 +1147,83 @@ __global__ void __launch_bounds__(kPairThreads, 1)
   if (warp == mma_warp) tmem_dealloc(tbase, 512);
 }
 
+// The three roles of one build; arguments and tensor maps in parameter space
+// (selected with constant indices, so they stay operands of the instructions).
+struct PairJob3 {
+  CUtensorMap ym[3], yh[3], v[3];
+  PairArgs a[3];
+  int gx[3], nblk[3];
+};
+
+template <int NP>
+__global__ void __launch_bounds__(kPairThreads, 1) pair_kernel(const __grid_constant__ PairJob3 job) {
+  int ri = 0, blk = blockIdx.x;
+  if (blk >= job.nblk[0]) {
+    blk -= job.nblk[0];
+    ri = 1;
+    if (blk >= job.nblk[1]) { blk -= job.nblk[1]; ri = 2; }
+  }
+  const CUtensorMap* mYm = ri == 0 ? &job.ym[0] : ri == 1 ? &job.ym[1] : &job.ym[2];
+  const CUtensorMap* mYh = ri == 0 ? &job.yh[0] : ri == 1 ? &job.yh[1] : &job.yh[2];
+  const CUtensorMap* mV = ri == 0 ? &job.v[0] : ri == 1 ? &job.v[1] : &job.v[2];
+  const PairArgs& a = ri == 0 ? job.a[0] : ri == 1 ? job.a[1] : job.a[2];
+  const int gx = ri == 0 ? job.gx[0] : ri == 1 ? job.gx[1] : job.gx[2];
+  pair_body<NP>(mYm, mYh, mV, a, blk % gx, blk / gx, gx);
+}
+
+// Up to kGroupRoles roles of several builds in one launch, all in parameter
+// space (a grouped batch is split into launches of at most this many roles).
+constexpr int kGroupRoles = 16;
+struct PairJobN {
+  CUtensorMap ym[kGroupRoles], yh[kGroupRoles], v[kGroupRoles];
+  PairArgs a[kGroupRoles];
+  int gx[kGroupRoles], first[kGroupRoles];
+  int nroles;
+};
+
+template <int NP>
+__global__ void __launch_bounds__(kPairThreads, 1)
+    pair_kernel_group(const __grid_constant__ PairJobN job) {
+  int ri = 0;
+  while (ri + 1 < job.nroles && (int)blockIdx.x >= job.first[ri + 1]) ++ri;
+  const int gx = job.gx[ri], blk = (int)blockIdx.x - job.first[ri];
+  pair_body<NP>(&job.ym[ri], &job.yh[ri], &job.v[ri], job.a[ri], blk % gx, blk / gx, gx);
+}
+
 // ------------------------------------------------------------- host side
+
+// Launches the roles (sorted, longest first) in chunks of at most kGroupRoles.
+void launch_pair_roles(const std::vector<PairRole>& rs, int np, cudaStream_t s) {
+  for (size_t c0 = 0; c0 < rs.size(); c0 += kGroupRoles) {
+    PairJobN job;
+    int blocks = 0, k = 0;
+    for (size_t i = c0; i < rs.size() && k < kGroupRoles; ++i, ++k) {
+      job.ym[k] = rs[i].ym; job.yh[k] = rs[i].yh; job.v[k] = rs[i].v;
+      job.a[k] = rs[i].a; job.gx[k] = rs[i].gx; job.first[k] = blocks;
+      blocks += rs[i].nblk;
+    }
+    job.nroles = k;
+    if (np == 64)
+      pair_kernel_group<64><<<blocks, kPairThreads, PairCfg<64>::SMEM, s>>>(job);
+    else
+      pair_kernel_group<128><<<blocks, kPairThreads, PairCfg<128>::SMEM, s>>>(job);
+    count_launch();
+  }
+}
+
+void launch_pair3(const PairRole* r, int np, cudaStream_t s) {
+  PairJob3 job;
+  for (int k = 0; k < 3; ++k) {
+    job.ym[k] = r[k].ym; job.yh[k] = r[k].yh; job.v[k] = r[k].v;
+    job.a[k] = r[k].a; job.gx[k] = r[k].gx; job.nblk[k] = r[k].nblk;
+  }
+  const unsigned blocks = (unsigned)(r[0].nblk + r[1].nblk + r[2].nblk);
+  if (np == 64)
+    pair_kernel<64><<<blocks, kPairThreads, PairCfg<64>::SMEM, s>>>(job);
+  else
+    pair_kernel<128><<<blocks, kPairThreads, PairCfg<128>::SMEM, s>>>(job);
+  count_launch();
+}
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
@@ -1230,6 +1298,8 @@ struct MixedState {
   long epA = 1, epC = 1;
   __half *TA_h = nullptr, *TA_l = nullptr, *TC_h = nullptr, *TC_l = nullptr;
   CUtensorMap m_TA_h, m_TA_l, m_TAmn_h, m_TAmn_l, m_TC_h, m_TC_l;
+  // n <= 128: the three roles of the fused pair launch
+  PairRole roles[3];
   int kchunkL1 = 64, kchunkL23 = 64;
   CUtensorMap m_phi_m, m_phi_h, m_CT_m, m_CT_h, m_psi128_m, m_psi128_h, m_psi64_m, m_psi64_h,
       m_psig128_m, m_psig128_h, m_psig64_m, m_psig64_h, m_VA, m_VB, m_VC, m_phiT_m, m_phiT_h,
@@ -1351,6 +1421,10 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   e = cudaFuncSetAttribute(pair_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairCfg<64>::SMEM);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(pair_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairCfg<128>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(pair_kernel_group<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairCfg<64>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(pair_kernel_group<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairCfg<128>::SMEM);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G_SMEM);
   if (e != cudaSuccess) return e;
@@ -1536,6 +1610,25 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
     if (e == cudaSuccess) e = make_map(&m->m_VC, m->W32, F32, 4, (long)na, p.Na4, 128, 32);
     if (e != cudaSuccess) return fin(e);
   }
+  if (!p.large) {
+    // role A: M2[g][j] = sum_R (V o P)[g][R] Psi[R][j], and sum V o P^2
+    // role B: M1[j][R] = sum_g (V^T o P^T)[R][g] Psi_g[g][j], written transposed
+    // role C: M3[g][j] = sum_g' (W o Q)[g][g'] Psi_g[g'][j], and sum W o Q^2
+    PairRole* r = m->roles;
+    r[0].ym = m->m_psi64_m; r[0].yh = m->m_psi64_h; r[0].v = m->m_VA;
+    r[0].a = PairArgs{(int)na, (int)ng, m->ychunkA, n, m->psig_m, m->psig_h, np_, m->sc, SC_F_AB,
+                      SC_OUT_AB, m->M2p, n, (long)(na * n), 0, m->EpA, m->status};
+    r[0].gx = m->xa; r[0].nblk = m->xa * m->partsA; r[0].tiles = m->ychunkA / 64;
+    const int gB = (int)((ng + 127) / 128);
+    r[1].ym = m->m_psig64_m; r[1].yh = m->m_psig64_h; r[1].v = m->m_VB;
+    r[1].a = PairArgs{(int)ng, (int)na, (int)rup(na, 64), n, m->psi_m, m->psi_h, np_, m->sc,
+                      SC_F_AB, SC_OUT_AB, m->M1, m->Ng4, 0, 1, nullptr, m->status};
+    r[1].gx = gB; r[1].nblk = gB; r[1].tiles = (int)(rup(na, 64) / 64);
+    r[2].ym = m->m_psig64_m; r[2].yh = m->m_psig64_h; r[2].v = m->m_VC;
+    r[2].a = PairArgs{(int)na, (int)na, m->ychunkC, n, m->psig_m, m->psig_h, np_, m->sc, SC_F_C,
+                      SC_OUT_C, m->M3p, n, (long)(na * n), 0, m->EpC, m->status};
+    r[2].gx = m->xa; r[2].nblk = m->xa * m->partsC; r[2].tiles = m->ychunkC / 64;
+  }
   fin(cudaSuccess);
   *out = m;
   return cudaSuccess;
@@ -1547,8 +1640,7 @@ void mixed_destroy(MixedState* m) {
   delete m;
 }
 
-cudaError_t mixed_enqueue(MixedState* m, const double* C, double* K, double* Ex, cudaStream_t s,
-                          const StepHook& hook) {
+cudaError_t mixed_enqueue_pre(MixedState* m, const double* C, cudaStream_t s, const StepHook& hook) {
   const long ng = m->Ng, na = m->Naux;
   const int N = m->N, n = m->n, np = m->np;
   cudaError_t e;
@@ -1592,7 +1684,13 @@ cudaError_t mixed_enqueue(MixedState* m, const double* C, double* K, double* Ex,
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   hook(0, 0);
+  return cudaSuccess;
+}
 
+cudaError_t mixed_enqueue_pair(MixedState* m, cudaStream_t s, const StepHook& hook) {
+  const long ng = m->Ng, na = m->Naux;
+  const int n = m->n, np = m->np;
+  cudaError_t e;
   // ---- steps 2-3: the three fused pair contractions
   hook(1, 1);
   if (m->large) {
@@ -1628,35 +1726,19 @@ cudaError_t mixed_enqueue(MixedState* m, const double* C, double* K, double* Ex,
         m->m_TAmn_h, m->m_TAmn_l, m->m_psig64_m, m->m_psig64_h, g1);
     count_launch(5);
   } else {
-    // role A: M2[g][j] = sum_R (V o P)[g][R] Psi[R][j], and sum V o P^2
-    // role B: M1[j][R] = sum_g (V^T o P^T)[R][g] Psi_g[g][j], written transposed
-    // role C: M3[g][j] = sum_g' (W o Q)[g][g'] Psi_g[g'][j], and sum W o Q^2
-    PairJob job;
-    job.ym[0] = m->m_psi64_m; job.yh[0] = m->m_psi64_h; job.v[0] = m->m_VA;
-    job.ym[1] = m->m_psig64_m; job.yh[1] = m->m_psig64_h; job.v[1] = m->m_VB;
-    job.ym[2] = m->m_psig64_m; job.yh[2] = m->m_psig64_h; job.v[2] = m->m_VC;
-    job.role[0] = {PairArgs{(int)na, (int)ng, m->ychunkA, n, m->psig_m, m->psig_h, np, m->sc,
-                            SC_F_AB, SC_OUT_AB, m->M2p, n, na * n, 0, m->EpA, m->status},
-                   m->xa, m->xa * m->partsA};
-    const int gB = (int)((ng + 127) / 128);
-    job.role[1] = {PairArgs{(int)ng, (int)na, (int)rup(na, 64), n, m->psi_m, m->psi_h, np, m->sc,
-                            SC_F_AB, SC_OUT_AB, m->M1, m->Ng4, 0, 1, nullptr, m->status},
-                   gB, gB};
-    job.role[2] = {PairArgs{(int)na, (int)na, m->ychunkC, n, m->psig_m, m->psig_h, np, m->sc,
-                            SC_F_C, SC_OUT_C, m->M3p, n, na * n, 0, m->EpC, m->status},
-                   m->xa, m->xa * m->partsC};
-    job.nroles = 3;
-    const unsigned blocks = (unsigned)(job.role[0].nblk + job.role[1].nblk + job.role[2].nblk);
-    if (np == 64)
-      pair_kernel<64><<<blocks, kPairThreads, PairCfg<64>::SMEM, s>>>(job);
-    else
-      pair_kernel<128><<<blocks, kPairThreads, PairCfg<128>::SMEM, s>>>(job);
-    count_launch();
+    launch_pair3(m->roles, np, s);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   hook(1, 0);
+  return cudaSuccess;
+}
 
+cudaError_t mixed_enqueue_post(MixedState* m, double* K, double* Ex, cudaStream_t s,
+                               const StepHook& hook) {
+  const long ng = m->Ng, na = m->Naux;
+  const int N = m->N, n = m->n;
+  cudaError_t e;
   // ---- step 4: line1^T = Phi^T M1^T and (line2 - line3)^T = Phi_g^T (M2 - M3)
   hook(4, 1);
   reduce_parts_kernel<<<blocks_for(na * n), 256, 0, s>>>(m->M2p, m->partsA, m->M3p, m->partsC,
@@ -1703,6 +1785,47 @@ cudaError_t mixed_enqueue(MixedState* m, const double* C, double* K, double* Ex,
   hook(7, 0);
   return cudaSuccess;
 }
+
+cudaError_t mixed_enqueue(MixedState* m, const double* C, double* K, double* Ex, cudaStream_t s,
+                          const StepHook& hook) {
+  cudaError_t e = mixed_enqueue_pre(m, C, s, hook);
+  if (e == cudaSuccess) e = mixed_enqueue_pair(m, s, hook);
+  if (e == cudaSuccess) e = mixed_enqueue_post(m, K, Ex, s, hook);
+  return e;
+}
+
+// ---- grouped pair launches over several handles (n <= 128 members)
+struct PairGroup {
+  int np[2] = {64, 128};
+  std::vector<PairRole> roles[2];
+  std::vector<MixedState*> large;  // members with n > 128 run their own pair step
+};
+
+cudaError_t mixed_group_create(MixedState* const* ms, int count, PairGroup** out) {
+  PairGroup* g = new PairGroup();
+  for (int t = 0; t < 2; ++t) {
+    for (int i = 0; i < count; ++i)
+      if (!ms[i]->large && ms[i]->np == g->np[t])
+        for (int k = 0; k < 3; ++k) g->roles[t].push_back(ms[i]->roles[k]);
+    std::stable_sort(g->roles[t].begin(), g->roles[t].end(),
+                     [](const PairRole& x, const PairRole& y) { return x.tiles > y.tiles; });
+  }
+  for (int i = 0; i < count; ++i)
+    if (ms[i]->large) g->large.push_back(ms[i]);
+  *out = g;
+  return cudaSuccess;
+}
+
+cudaError_t mixed_group_enqueue_pair(PairGroup* g, cudaStream_t s) {
+  for (int t = 0; t < 2; ++t) launch_pair_roles(g->roles[t], g->np[t], s);
+  cudaError_t e = cudaGetLastError();
+  StepHook none{nullptr, nullptr};
+  for (MixedState* m : g->large)
+    if (e == cudaSuccess) e = mixed_enqueue_pair(m, s, none);
+  return e;
+}
+
+void mixed_group_destroy(PairGroup* g) { delete g; }
 
 int mixed_take_status(MixedState* m) {
   int st[4] = {0, 0, 0, 0};

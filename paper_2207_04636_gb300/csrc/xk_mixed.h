@@ -34,6 +34,22 @@ void mixed_destroy(MixedState* m);
 cudaError_t mixed_enqueue(MixedState* m, const double* C_dev, double* K_dev, double* Ex_dev,
                           cudaStream_t s, const StepHook& hook);
 
+// The same build in three parts: orbitals (step 1), the pair contractions
+// (steps 2-3), and the line contractions with K and E_x (steps 4-5).
+cudaError_t mixed_enqueue_pre(MixedState* m, const double* C_dev, cudaStream_t s,
+                              const StepHook& hook);
+cudaError_t mixed_enqueue_pair(MixedState* m, cudaStream_t s, const StepHook& hook);
+cudaError_t mixed_enqueue_post(MixedState* m, double* K_dev, double* Ex_dev, cudaStream_t s,
+                               const StepHook& hook);
+
+// Pair contractions of several handles as one grouped launch per piece width
+// (64 or 128 columns): the roles of every n <= 128 member, longest first, in
+// launches of up to 16 roles; members with n > 128 run their own pair step.
+struct PairGroup;
+cudaError_t mixed_group_create(MixedState* const* ms, int count, PairGroup** out);
+cudaError_t mixed_group_enqueue_pair(PairGroup* g, cudaStream_t s);
+void mixed_group_destroy(PairGroup* g);
+
 // Error code a kernel of the last builds recorded (0 = none; nonzero when a
 // bounded wait inside a kernel gave up), read synchronously and cleared.
 int mixed_take_status(MixedState* m);

@@ -53,11 +53,15 @@ def lib():
         L.xk_timing_read.argtypes = [c_d, c_int, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_uint64)]
         L.xk_exchange_energy_noalloc.argtypes = [c_d, c_d, c_i64, c_d, c_d]
+        L.xk_batch_create.argtypes = [c_d, c_int, ctypes.POINTER(ctypes.c_void_p)]
+        L.xk_batch_build.argtypes = [c_d, c_d, c_d, c_d]
+        L.xk_batch_release.argtypes = [c_d]
         L.xk_last_error.restype = ctypes.c_char_p
         L.xk_kernel_launches.restype = ctypes.c_uint64
         for f in ("xk_footprint", "xk_setup", "xk_build", "xk_build_device", "xk_ace",
                   "xk_submit", "xk_poll", "xk_release", "xk_timing_enable", "xk_timing_read",
-                  "xk_exchange_energy_noalloc"):
+                  "xk_exchange_energy_noalloc", "xk_batch_create", "xk_batch_build",
+                  "xk_batch_release"):
             getattr(L, f).restype = c_int
         _lib = L
     return _lib
@@ -158,6 +162,40 @@ class Handle:
         if getattr(self, "_h", None):
             lib().xk_release(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+class Batch:
+    """One build of each of several XK_F16X3 handles per call, captured into
+    a CUDA graph (xk_batch_create / xk_batch_build / xk_batch_release).  The
+    handles must outlive the batch."""
+
+    def __init__(self, handles):
+        self.handles = list(handles)
+        arr = (ctypes.c_void_p * len(self.handles))(*[h._h for h in self.handles])
+        b = ctypes.c_void_p()
+        _check(lib().xk_batch_create(arr, len(self.handles), ctypes.byref(b)))
+        self._b = b
+
+    def build(self, Cs):
+        """Cs: one host C (N_i x n_i) per handle; returns ([K_i], [E_i])."""
+        Cs = [_f64(C, (h.N, h.n), "C") for C, h in zip(Cs, self.handles)]
+        Ks = [np.empty((h.N, h.n)) for h in self.handles]
+        Ex = np.empty(len(self.handles))
+        cp = (ctypes.c_void_p * len(Cs))(*[C.ctypes.data for C in Cs])
+        kp = (ctypes.c_void_p * len(Ks))(*[K.ctypes.data for K in Ks])
+        _check(lib().xk_batch_build(self._b, cp, kp, _ptr(Ex)))
+        return Ks, [float(e) for e in Ex]
+
+    def release(self):
+        if getattr(self, "_b", None):
+            lib().xk_batch_release(self._b)
+            self._b = None
 
     def __del__(self):
         try:

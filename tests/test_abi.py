@@ -98,3 +98,8 @@ def test_null_handles_and_tickets(L):
     t = ctypes.c_uint64()
     assert L.xk_submit(None, p, 0.0, ctypes.byref(t)) == xk.XK_EINVAL
     assert L.xk_ace(None, p, p, None, None) == xk.XK_EINVAL
+    b = ctypes.c_void_p()
+    assert L.xk_batch_create(None, 0, ctypes.byref(b)) == xk.XK_EINVAL
+    assert L.xk_batch_create(None, 1, None) == xk.XK_EINVAL
+    assert L.xk_batch_build(None, p, p, p) == xk.XK_EINVAL
+    assert L.xk_batch_release(None) == xk.XK_EINVAL
