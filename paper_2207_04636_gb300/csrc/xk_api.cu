@@ -111,12 +111,18 @@ struct Plan {
   size_t work = 0;  // doubles of split-K work
 };
 
-size_t max_work(int64_t Ng, int N, int n, int Naux) {
+// Doubles of split-K work the FP64 contractions need (a contraction that
+// runs unsplit needs none); with ace_only, only the occ-RI K_ij products.
+size_t max_work(int64_t Ng, int N, int n, int Naux, bool ace_only = false) {
   const int ng = (int)Ng;
-  size_t w = 0;
+  size_t w = 1;
   auto acc = [&](int M, int Nc, int K) {
-    w = std::max(w, (size_t)xk::dgemm_ksplit(M, Nc, K) * (size_t)M * (size_t)Nc);
+    const size_t ks = (size_t)xk::dgemm_ksplit(M, Nc, K);
+    if (ks > 1) w = std::max(w, ks * (size_t)M * (size_t)Nc);
   };
+  acc(n, n, N);         // K_ij
+  acc(N, n, n);         // K U
+  if (ace_only) return w;
   acc(ng, n, N);        // Psi = Phi C
   acc(Naux, ng, n);     // V2 = V o (Psi_g Psi^T)
   acc(Naux, n, ng);     // M2 = V2 Psi
@@ -125,8 +131,6 @@ size_t max_work(int64_t Ng, int N, int n, int Naux) {
   acc(n, N, Naux);      // line2, line3
   acc(Naux, Naux, n);   // W o Q
   acc(Naux, n, Naux);   // M3
-  acc(n, n, N);         // K_ij
-  acc(N, n, n);         // K U
   return w;
 }
 
@@ -306,7 +310,7 @@ int xk_footprint(int64_t Ng, int32_t N, int32_t n, int32_t Naux, int mode, size_
   }
   if (mode == XK_F16X3) {
     *bytes = xk::mixed_footprint(Ng, N, n, Naux) + (size_t)N * n * 8 * 2 +
-             (size_t)max_work(Ng, N, n, Naux) * 8 + 4 * (size_t)n * n * 8 + 2 * (size_t)N * n * 8 +
+             (size_t)max_work(Ng, N, n, Naux, true) * 8 + 4 * (size_t)n * n * 8 + 2 * (size_t)N * n * 8 +
              65536;
     return XK_OK;
   }
@@ -389,7 +393,7 @@ int xk_setup(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* phi,
   XK_ALLOC(h->sgn, (size_t)n);
   XK_ALLOC(h->status, 2);
   XK_ALLOC(h->red, xk::reduce_work_elems());
-  const size_t work = max_work(Ng, N, n, Naux);
+  const size_t work = max_work(Ng, N, n, Naux, mode != XK_FP64);
   XK_ALLOC(h->work, work);
   if (mode == XK_FP64) {
     XK_ALLOC(h->phi, ng * N);
