@@ -1300,6 +1300,7 @@ struct MixedState {
   CUtensorMap m_TA_h, m_TA_l, m_TAmn_h, m_TAmn_l, m_TC_h, m_TC_l;
   // n <= 128: the three roles of the fused pair launch
   PairRole roles[3];
+  float tuned_ms = 0.0f;  // pair launch time of the split the autotuner kept
   int kchunkL1 = 64, kchunkL23 = 64;
   CUtensorMap m_phi_m, m_phi_h, m_CT_m, m_CT_h, m_psi128_m, m_psi128_h, m_psi64_m, m_psi64_h,
       m_psig128_m, m_psig128_h, m_psig64_m, m_psig64_h, m_VA, m_VB, m_VC, m_phiT_m, m_phiT_h,
@@ -1324,7 +1325,22 @@ struct Plan {
   bool large;
   int nt;
   long epA, epC;
+  int partsA_max;  // largest role-A split the autotuner may pick (buffer sizes)
 };
+
+// Role-A splits the autotuner tries for n <= 128: the X tiles times the
+// split fill about 2, 3, 4, 6 or 8 waves of CTAs over the 152 SMs.
+std::vector<int> tune_candidates(int64_t Ng, int xa) {
+  std::vector<int> c;
+  const int cap = (int)std::max<int64_t>(1, (Ng + 63) / 64);
+  for (int w : {2, 3, 4, 6, 8}) {
+    const int parts = std::max(1, std::min(cap, (w * 152 + xa / 2) / xa));
+    const int chunk = (int)(((Ng + parts - 1) / parts + 63) / 64 * 64);
+    const int real = (int)((Ng + chunk - 1) / chunk);
+    if (std::find(c.begin(), c.end(), real) == c.end()) c.push_back(real);
+  }
+  return c;
+}
 
 Plan make_plan(int64_t Ng, int N, int n, int Naux) {
   Plan p;
@@ -1345,7 +1361,9 @@ Plan make_plan(int64_t Ng, int N, int n, int Naux) {
     p.partsC = std::max(1, std::min<int>((608 + p.xa - 1) / p.xa, (Naux + 63) / 64));
     p.ychunkC = (int)rup((Naux + p.partsC - 1) / p.partsC, 64);
     p.partsC = (Naux + p.ychunkC - 1) / p.ychunkC;
-    p.epA = (long)p.partsA * p.xa;
+    p.partsA_max = p.partsA;
+    for (int c : tune_candidates(Ng, p.xa)) p.partsA_max = std::max(p.partsA_max, c);
+    p.epA = (long)p.partsA_max * p.xa;
     p.epC = (long)p.partsC * p.xa;
   } else {
     // M2 = T_A Psi and M3 = T_C Psi_g: (xa x nt) tiles, K split to about four waves
@@ -1358,6 +1376,7 @@ Plan make_plan(int64_t Ng, int N, int n, int Naux) {
     p.partsC = (Naux + p.ychunkC - 1) / p.ychunkC;
     p.epA = (long)p.xa * ((Ng + 127) / 128);
     p.epC = (long)p.xa * ((Naux + 127) / 128);
+    p.partsA_max = p.partsA;
   }
   // line GEMMs: (N / 128) x (n / 128) tiles x K splits of >= 1024
   const int tiles = ((N + 127) / 128) * ((n + 127) / 128);
@@ -1402,13 +1421,93 @@ size_t mixed_footprint(int64_t Ng, int N, int n, int Naux) {
   b += na * p.Ng4 * 4 + (p.large ? 0 : ng * p.Na4 * 4) + na * p.Na4 * 4 + na * 4;  // V, V^T, W, idx
   if (p.large) b += 2 * na * p.Ng8 * 2 + 2 * na * p.Na8 * 2;                      // T_A, T_C
   b += 2 * (size_t)n * p.Np * 2 + (size_t)n * p.Np * 8 + 2 * ng * p.np * 2 + 2 * na * p.np * 2;
-  b += (size_t)p.partsA * na * n * 4 + (size_t)p.partsC * na * n * 4 + (size_t)n * p.Ng4 * 4;
+  b += (size_t)p.partsA_max * na * n * 4 + (size_t)p.partsC * na * n * 4 + (size_t)n * p.Ng4 * 4;
   b += na * n * 8 + (size_t)n * p.Na8 * 8 + 2 * (size_t)n * p.Ng8 * 2 + 2 * (size_t)n * p.Na8 * 2;
   b += (size_t)p.splitsL1 * N * n * 4 + (size_t)p.splitsL23 * N * n * 4;
   b += (size_t)(p.epA + p.epC) * 8;
   b += (size_t)N * N * 8 + (size_t)N * n * 8 + dwork_elems(Ng, N, n) * 8;
   b += 2 * stage_elems(Ng, N, Naux, p.Ng8) * 8;
   return b + 64 * 1024;
+}
+
+// Role A with its Y range split into `parts` chunks of whole 64-row tiles.
+void set_split_a(MixedState* m, int parts) {
+  const long ng = m->Ng, na = m->Naux;
+  m->ychunkA = (int)rup((ng + parts - 1) / parts, 64);
+  m->partsA = (int)((ng + m->ychunkA - 1) / m->ychunkA);
+  m->epA = (long)m->partsA * m->xa;
+  PairRole& r = m->roles[0];
+  r.a = PairArgs{(int)na, (int)ng, m->ychunkA, m->n, m->psig_m, m->psig_h, m->np, m->sc, SC_F_AB,
+                 SC_OUT_AB, m->M2p, m->n, (long)(na * m->n), 0, m->EpA, m->status};
+  r.gx = m->xa;
+  r.nblk = m->xa * m->partsA;
+  r.tiles = m->ychunkA / 64;
+}
+
+__global__ void fill_pieces_kernel(__half* a, long count, uint32_t seed) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count;
+       t += (long)gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)t * 2654435761u ^ seed;
+    h ^= h >> 13; h *= 0x5bd1e995u; h ^= h >> 15;
+    a[t] = __float2half_rn(((float)(h & 0xffff) / 32768.0f - 1.0f) * 0.0625f);
+  }
+}
+
+__global__ void set_tune_scales_kernel(float* sc) {
+  if (threadIdx.x == 0) {
+    sc[SC_F_AB] = 1.0f; sc[SC_F_C] = 1.0f; sc[SC_OUT_AB] = 1.0f; sc[SC_OUT_C] = 1.0f;
+  }
+}
+
+// Autotuner of the pair launch's role-A split: with pseudo-random orbital
+// pieces (full switching activity, like real data) and the handle's own V
+// and W, time one pair launch per candidate split (best of two) and keep the
+// fastest; the heuristic split stays unless another is 3 % faster.  The
+// choice fixes the summation order of the role-A partial sums: results are
+// bitwise repeatable for the handle, and agree within the stated tolerance
+// between handles that chose differently.
+cudaError_t autotune_split_a(MixedState* m, cudaStream_t s) {
+  const std::vector<int> cands = tune_candidates(m->Ng, m->xa);
+  const long ng = m->Ng, na = m->Naux;
+  fill_pieces_kernel<<<blocks_for(ng * m->np), 256, 0, s>>>(m->psi_m, ng * m->np, 1u);
+  fill_pieces_kernel<<<blocks_for(ng * m->np), 256, 0, s>>>(m->psi_h, ng * m->np, 2u);
+  fill_pieces_kernel<<<blocks_for(na * m->np), 256, 0, s>>>(m->psig_m, na * m->np, 3u);
+  fill_pieces_kernel<<<blocks_for(na * m->np), 256, 0, s>>>(m->psig_h, na * m->np, 4u);
+  set_tune_scales_kernel<<<1, 32, 0, s>>>(m->sc);
+  count_launch(5);
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return e;
+  e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) { cudaEventDestroy(e0); return e; }
+  const int base = m->partsA;
+  int best = base;
+  float best_ms = 0.0f, base_ms = 0.0f;
+  launch_pair3(m->roles, m->np, s);  // warm-up
+  for (int c : cands) {
+    set_split_a(m, c);
+    float ms = 1e30f;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+      e = cudaEventRecord(e0, s);
+      launch_pair3(m->roles, m->np, s);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float t = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+      ms = std::min(ms, t);
+    }
+    if (e != cudaSuccess) break;
+    if (m->partsA == base) base_ms = ms;
+    if (best_ms == 0.0f || ms < best_ms) { best_ms = ms; best = m->partsA; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e == cudaSuccess && base_ms > 0.0f && best_ms > 0.97f * base_ms) best = base;
+  set_split_a(m, best);
+  m->tuned_ms = best_ms;
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->status, 0, 16, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
 }
 
 cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
@@ -1457,7 +1556,7 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   MX(m->CT_m, (size_t)n * p.Np); MX(m->CT_h, (size_t)n * p.Np); MX(m->CT64, (size_t)n * p.Np);
   MX(m->psi_m, ng * p.np); MX(m->psi_h, ng * p.np);
   MX(m->psig_m, na * p.np); MX(m->psig_h, na * p.np);
-  MX(m->M2p, (size_t)p.partsA * na * n); MX(m->M3p, (size_t)p.partsC * na * n);
+  MX(m->M2p, (size_t)p.partsA_max * na * n); MX(m->M3p, (size_t)p.partsC * na * n);
   MX(m->M1, (size_t)n * p.Ng4);
   MX(m->D23, na * n); MX(m->D23T64, (size_t)n * p.Na8);
   MX(m->M1_m, (size_t)n * p.Ng8); MX(m->M1_h, (size_t)n * p.Ng8);
@@ -1616,9 +1715,7 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
     // role C: M3[g][j] = sum_g' (W o Q)[g][g'] Psi_g[g'][j], and sum W o Q^2
     PairRole* r = m->roles;
     r[0].ym = m->m_psi64_m; r[0].yh = m->m_psi64_h; r[0].v = m->m_VA;
-    r[0].a = PairArgs{(int)na, (int)ng, m->ychunkA, n, m->psig_m, m->psig_h, np_, m->sc, SC_F_AB,
-                      SC_OUT_AB, m->M2p, n, (long)(na * n), 0, m->EpA, m->status};
-    r[0].gx = m->xa; r[0].nblk = m->xa * m->partsA; r[0].tiles = m->ychunkA / 64;
+    set_split_a(m, m->partsA);
     const int gB = (int)((ng + 127) / 128);
     r[1].ym = m->m_psig64_m; r[1].yh = m->m_psig64_h; r[1].v = m->m_VB;
     r[1].a = PairArgs{(int)ng, (int)na, (int)rup(na, 64), n, m->psi_m, m->psi_h, np_, m->sc,
@@ -1628,6 +1725,8 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
     r[2].a = PairArgs{(int)na, (int)na, m->ychunkC, n, m->psig_m, m->psig_h, np_, m->sc, SC_F_C,
                       SC_OUT_C, m->M3p, n, (long)(na * n), 0, m->EpC, m->status};
     r[2].gx = m->xa; r[2].nblk = m->xa * m->partsC; r[2].tiles = m->ychunkC / 64;
+    e = autotune_split_a(m, s);
+    if (e != cudaSuccess) return fin(e);
   }
   fin(cudaSuccess);
   *out = m;
