@@ -224,7 +224,7 @@ __device__ __forceinline__ float row_grid(float mx) {
 template <class T>
 __global__ void __launch_bounds__(128) split_mh_rows_kernel(
     const T* __restrict__ src, long cols, long ld_src, const float* __restrict__ sc, int gidx,
-    __half* __restrict__ mo, __half* __restrict__ ho, long ld_dst) {
+    __half* __restrict__ mo, __half* __restrict__ ho, __half* __restrict__ lo, long ld_dst) {
   __shared__ float red[4];
   const long r = blockIdx.x;
   const T G = (T)sc[gidx];
@@ -240,15 +240,17 @@ __global__ void __launch_bounds__(128) split_mh_rows_kernel(
   __half* mrow = mo + r * ld_dst;
   __half* hrow = ho + r * ld_dst;
   for (long c = threadIdx.x; c < ld_dst; c += blockDim.x) {
-    __half mh = __float2half(0.0f), hh = __float2half(0.0f);
+    __half mh = __float2half(0.0f), hh = __float2half(0.0f), lh = __float2half(0.0f);
     if (c < cols) {
       const float x = (float)(row[c] * G);
       const float m = q * rintf(x * qi);
       mh = __float2half_rn(m);
       hh = __float2half_rn(x - m);
+      lh = __float2half_rn((x - m) - __half2float(hh));
     }
     mrow[c] = mh;
     hrow[c] = hh;
+    if (lo) lo[r * ld_dst + c] = lh;
   }
 }
 
@@ -341,7 +343,8 @@ __global__ void transpose_f64_f32_kernel(const double* __restrict__ src, long ro
 __global__ void split_rows_f32_kernel(const float* __restrict__ src, long rows, int cols,
                                       long ld_src, const float* __restrict__ sc, int gidx,
                                       __half* __restrict__ mo, __half* __restrict__ ho,
-                                      long ld_dst, unsigned* __restrict__ rn2) {
+                                      __half* __restrict__ lo, long ld_dst,
+                                      unsigned* __restrict__ rn2) {
   __shared__ float red[32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const float G = sc[gidx];
@@ -361,7 +364,7 @@ __global__ void split_rows_f32_kernel(const float* __restrict__ src, long rows, 
     wn = fmaxf(wn, nrm);
     const float q = row_grid(mx), qi = 1.0f / q;
     for (long c = (long)lane * 8; c < ld_dst; c += 256) {
-      uint32_t mw[4], hw[4];
+      uint32_t mw[4], hw[4], lw[4];
 #pragma unroll
       for (int j = 0; j < 8; j += 2) {
         const float x0 = c + j < cols ? row[c + j] * G : 0.0f;
@@ -369,11 +372,15 @@ __global__ void split_rows_f32_kernel(const float* __restrict__ src, long rows, 
         const float m0 = q * rintf(x0 * qi), m1 = q * rintf(x1 * qi);
         const __half2 hm = __floats2half2_rn(m0, m1);
         const __half2 hh = __floats2half2_rn(x0 - m0, x1 - m1);
+        const float2 fh = __half22float2(hh);
+        const __half2 hl = __floats2half2_rn((x0 - m0) - fh.x, (x1 - m1) - fh.y);
         mw[j / 2] = *reinterpret_cast<const uint32_t*>(&hm);
         hw[j / 2] = *reinterpret_cast<const uint32_t*>(&hh);
+        lw[j / 2] = *reinterpret_cast<const uint32_t*>(&hl);
       }
       *reinterpret_cast<uint4*>(mo + r * ld_dst + c) = make_uint4(mw[0], mw[1], mw[2], mw[3]);
       *reinterpret_cast<uint4*>(ho + r * ld_dst + c) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      if (lo) *reinterpret_cast<uint4*>(lo + r * ld_dst + c) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
     }
   }
   if (lane == 0) red[wib] = wn;
@@ -520,6 +527,10 @@ struct GemmArgs {
   long ld_t;
   double* epart;
   int kdrain;  // k-blocks per accumulator drain (0: kDrain)
+  // Three pieces per operand (K-major only): x = m + h + l, l = fp16(x - m - h);
+  // A1 adds m l' + l m' (products below 2^-30 of the row maxima are dropped).
+  // Two stages of six 16 KB tiles instead of three of four.
+  int pieces3;
 };
 
 constexpr int G_STAGES = 3;
@@ -530,6 +541,7 @@ constexpr int kDrain = 3;
 __global__ void __launch_bounds__(192, 1)
     gemm_kernel(const __grid_constant__ CUtensorMap mAm, const __grid_constant__ CUtensorMap mAh,
                 const __grid_constant__ CUtensorMap mBm, const __grid_constant__ CUtensorMap mBh,
+                const __grid_constant__ CUtensorMap mAl, const __grid_constant__ CUtensorMap mBl,
                 GemmArgs g) {
   extern __shared__ uint8_t g_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(g_raw) + 1023) & ~uintptr_t(1023));
@@ -543,6 +555,9 @@ __global__ void __launch_bounds__(192, 1)
   const int nkb = kend > kbeg ? (kend - kbeg + 63) / 64 : 0;
   const int kd = g.kdrain > 0 ? g.kdrain : kDrain;
   const int ngroups = (nkb + kd - 1) / kd;
+  const bool p3 = g.pieces3 != 0;
+  const int ns = p3 ? 2 : G_STAGES;                       // stages
+  const int sbytes = p3 ? 6 * 16384 : G_STAGE_BYTES;      // bytes per stage
 
   if (tid == 0) {
     for (int s = 0; s < G_STAGES; ++s) {
@@ -570,13 +585,23 @@ __global__ void __launch_bounds__(192, 1)
     prefetch_tmap(&mAm); prefetch_tmap(&mAh); prefetch_tmap(&mBm); prefetch_tmap(&mBh);
     int last_parity[G_STAGES] = {-1, -1, -1};
     for (int kb = 0; kb < nkb && !abort_flag; ++kb) {
-      const int s = kb % G_STAGES, use = kb / G_STAGES;
+      const int s = kb % ns, use = kb / ns;
       if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) {
         atomicExch(g.status, 11); abort_flag = 1; break;
       }
-      uint8_t* st = sm + s * G_STAGE_BYTES;
-      mbar_expect_tx(&full[s], G_STAGE_BYTES);
+      uint8_t* st = sm + s * sbytes;
+      mbar_expect_tx(&full[s], sbytes);
       const int kc = kbeg + kb * 64;
+      if (p3) {  // A m, h, l at 0, 16, 32 KB; B m, h, l at 48, 64, 80 KB
+        tma_load_2d(st, &mAm, &full[s], kc, m0);
+        tma_load_2d(st + 16384, &mAh, &full[s], kc, m0);
+        tma_load_2d(st + 32768, &mAl, &full[s], kc, m0);
+        tma_load_2d(st + 49152, &mBm, &full[s], kc, n0);
+        tma_load_2d(st + 65536, &mBh, &full[s], kc, n0);
+        tma_load_2d(st + 81920, &mBl, &full[s], kc, n0);
+        last_parity[s] = use & 1;
+        continue;
+      }
       if (!g.a_mn) {
         tma_load_2d(st, &mAm, &full[s], kc, m0);
         tma_load_2d(st + 16384, &mAh, &full[s], kc, m0);
@@ -597,7 +622,7 @@ __global__ void __launch_bounds__(192, 1)
       }
       last_parity[s] = use & 1;
     }
-    for (int s = 0; s < G_STAGES; ++s)
+    for (int s = 0; s < ns; ++s)
       if (last_parity[s] >= 0) mbar_wait(&full[s], last_parity[s]);
   } else if (warp == 5) {
     // whole warp runs the loop; one elected lane issues each MMA and commit
@@ -613,14 +638,39 @@ __global__ void __launch_bounds__(192, 1)
       __syncwarp();
     };
     for (int kb = 0; kb < nkb && !__shfl_sync(0xffffffffu, (int)abort_flag, 0); ++kb) {
-      const int s = kb % G_STAGES, grp = kb / kd, set = grp & 1;
+      const int s = kb % ns, grp = kb / kd, set = grp & 1;
       const bool first = (kb % kd) == 0;
       const bool last = (kb % kd) == kd - 1 || kb == nkb - 1;
       if (first && grp >= 2 && !mbar_wait_warp(&set_free[set], ((grp >> 1) - 1) & 1)) {
         fail(14); break;
       }
-      if (!mbar_wait_warp(&full[s], (kb / G_STAGES) & 1)) { fail(12); break; }
+      if (!mbar_wait_warp(&full[s], (kb / ns) & 1)) { fail(12); break; }
       tc_fence_after();
+      if (p3) {
+        const uint64_t dam = dkm + s * (uint64_t)(sbytes >> 4), dah = dam + 1024, dal = dam + 2048;
+        const uint64_t dbm = dam + 3072, dbh = dam + 4096, dbl = dam + 5120;
+        const uint32_t t0 = tbase + set * 256, t1 = t0 + 128;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          if (elect_one()) mma_f16(t0, dam + kk * 2, dbm + kk * 2, idesc, (first && kk == 0) ? 0u : 1u);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          if (elect_one()) mma_f16(t1, dam + kk * 2, dbh + kk * 2, idesc, (first && kk == 0) ? 0u : 1u);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) if (elect_one()) mma_f16(t1, dah + kk * 2, dbm + kk * 2, idesc, 1u);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) if (elect_one()) mma_f16(t1, dah + kk * 2, dbh + kk * 2, idesc, 1u);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) if (elect_one()) mma_f16(t1, dam + kk * 2, dbl + kk * 2, idesc, 1u);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) if (elect_one()) mma_f16(t1, dal + kk * 2, dbm + kk * 2, idesc, 1u);
+        if (elect_one()) {
+          mma_commit(&empty[s]);
+          if (last) mma_commit(&set_ready[set]);
+        }
+        __syncwarp();
+        continue;
+      }
       // stage s: A m-piece at +0, A h at +16 KB, B m at +32 KB, B h at +48 KB; the
       // descriptor address field counts 16-byte units (1024 per 16 KB, 2 per K step)
       const uint64_t dam = da0 + s * (G_STAGE_BYTES >> 4), dah = dam + 1024;
@@ -1260,9 +1310,9 @@ int blocks_for(long total, int tpb = 256) {
 
 template <class T>
 cudaError_t split_rows(const T* src, long rows, long cols, long ld_src, const float* sc, int gidx,
-                       __half* mo, __half* ho, long ld_dst, cudaStream_t s) {
+                       __half* mo, __half* ho, long ld_dst, cudaStream_t s, __half* lo = nullptr) {
   if (rows <= 0) return cudaSuccess;
-  split_mh_rows_kernel<T><<<(unsigned)rows, 128, 0, s>>>(src, cols, ld_src, sc, gidx, mo, ho, ld_dst);
+  split_mh_rows_kernel<T><<<(unsigned)rows, 128, 0, s>>>(src, cols, ld_src, sc, gidx, mo, ho, lo, ld_dst);
   count_launch();
   return cudaGetLastError();
 }
@@ -1297,7 +1347,10 @@ struct MixedState {
   int nt = 1;
   long epA = 1, epC = 1;
   __half *TA_h = nullptr, *TA_l = nullptr, *TC_h = nullptr, *TC_l = nullptr;
-  CUtensorMap m_TA_h, m_TA_l, m_TAmn_h, m_TAmn_l, m_TC_h, m_TC_l;
+  // n > 128: third pieces of Psi (the S product) and of Phi', Q (the orbital product)
+  __half *psi_l = nullptr, *psig_l = nullptr, *phi_l = nullptr, *CT_l = nullptr;
+  CUtensorMap m_TA_h, m_TA_l, m_TAmn_h, m_TAmn_l, m_TC_h, m_TC_l, m_psi128_l, m_psig128_l,
+      m_phi_l, m_CT_l;
   // n <= 128: the three roles of the fused pair launch
   PairRole roles[3];
   float tuned_ms = 0.0f;  // pair launch time of the split the autotuner kept
@@ -1419,7 +1472,8 @@ size_t mixed_footprint(int64_t Ng, int N, int n, int Naux) {
   size_t b = 0;
   b += 2 * ng * p.Np * 2 + 2 * (size_t)N * p.Ng8 * 2 + 2 * (size_t)N * p.Na8 * 2;  // Phi pieces
   b += na * p.Ng4 * 4 + (p.large ? 0 : ng * p.Na4 * 4) + na * p.Na4 * 4 + na * 4;  // V, V^T, W, idx
-  if (p.large) b += 2 * na * p.Ng8 * 2 + 2 * na * p.Na8 * 2;                      // T_A, T_C
+  if (p.large)  // T, third pieces
+    b += 2 * na * p.Ng8 * 2 + 2 * na * p.Na8 * 2 + (ng + na) * p.np * 2 + (ng + n) * p.Np * 2;
   b += 2 * (size_t)n * p.Np * 2 + (size_t)n * p.Np * 8 + 2 * ng * p.np * 2 + 2 * na * p.np * 2;
   b += (size_t)p.partsA_max * na * n * 4 + (size_t)p.partsC * na * n * 4 + (size_t)n * p.Ng4 * 4;
   b += na * n * 8 + (size_t)n * p.Na8 * 8 + 2 * (size_t)n * p.Ng8 * 2 + 2 * (size_t)n * p.Na8 * 2;
@@ -1551,6 +1605,8 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   if (p.large) {
     MX(m->TA_h, na * p.Ng8); MX(m->TA_l, na * p.Ng8);
     MX(m->TC_h, na * p.Na8); MX(m->TC_l, na * p.Na8);
+    MX(m->psi_l, ng * p.np); MX(m->psig_l, na * p.np);
+    MX(m->phi_l, ng * p.Np); MX(m->CT_l, (size_t)n * p.Np);
   }
   MX(m->idx, na);
   MX(m->CT_m, (size_t)n * p.Np); MX(m->CT_h, (size_t)n * p.Np); MX(m->CT64, (size_t)n * p.Np);
@@ -1620,7 +1676,7 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
     absmax_kernel<double><<<blocks_for(ng * N), 256, 0, s>>>(stage, ng, N, N, m->am + AM_PHI);
     set_phi_scale_kernel<<<1, 32, 0, s>>>(m->am, m->sc);
     count_launch(4);
-    e = split_rows<double>(phip, ng, N, N, m->sc, SC_PHIP, m->phi_m, m->phi_h, p.Np, s);
+    e = split_rows<double>(phip, ng, N, N, m->sc, SC_PHIP, m->phi_m, m->phi_h, p.Np, s, m->phi_l);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fin(e);
   }
@@ -1696,6 +1752,10 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
         {&m->m_TAmn_l, m->TA_l, F16, 2, (long)na, p.Ng8, 64, 64},
         {&m->m_TC_h, m->TC_h, F16, 2, (long)na, p.Na8, 128, 64},
         {&m->m_TC_l, m->TC_l, F16, 2, (long)na, p.Na8, 128, 64},
+        {&m->m_psi128_l, m->psi_l, F16, 2, (long)ng, p.np, 128, 64},
+        {&m->m_psig128_l, m->psig_l, F16, 2, (long)na, p.np, 128, 64},
+        {&m->m_phi_l, m->phi_l, F16, 2, (long)ng, p.Np, 128, 64},
+        {&m->m_CT_l, m->CT_l, F16, 2, n, p.Np, 128, 64},
     };
     for (const MapSpec& ms : tspecs) {
       e = make_map(ms.m, ms.p, ms.t, ms.es, ms.rows, ms.ld, ms.br, ms.bc);
@@ -1759,27 +1819,34 @@ cudaError_t mixed_enqueue_pre(MixedState* m, const double* C, cudaStream_t s, co
   scales_kernel<<<1, 32, 0, s>>>(m->am, m->sc, 0);
   count_launch(3);
   e = transpose<double>(m->Q64, N, n, n, m->CT64, m->Np, s);  // Q^T [j][mu], zero for mu >= N
-  if (e == cudaSuccess) e = split_rows<double>(m->CT64, n, m->Np, m->Np, m->sc, SC_C, m->CT_m, m->CT_h, m->Np, s);
+  if (e == cudaSuccess)
+    e = split_rows<double>(m->CT64, n, m->Np, m->Np, m->sc, SC_C, m->CT_m, m->CT_h, m->Np, s, m->CT_l);
   if (e != cudaSuccess) return e;
   if (!m->large) {  // Psi = Phi' Q, written directly as per-row pieces
     GemmArgs g{(int)ng, n, N, (int)m->Np, nullptr, 0, 0, m->sc, SC_OUT_ORB, m->status,
                m->psi_m, m->psi_h, np, SC_PSI, m->am + AM_RN2};
     dim3 grid((unsigned)((ng + 127) / 128), 1, 1);
-    gemm_kernel<<<grid, 192, G_SMEM, s>>>(m->m_phi_m, m->m_phi_h, m->m_CT_m, m->m_CT_h, g);
+    gemm_kernel<<<grid, 192, G_SMEM, s>>>(m->m_phi_m, m->m_phi_h, m->m_CT_m, m->m_CT_h, m->m_phi_m, m->m_CT_m, g);
   } else {  // n > 128: Psi in FP32 (the M1 buffer, free until step 3), then per-row pieces
     GemmArgs g{};
     g.M = (int)ng; g.Ncols = n; g.K = N; g.kchunk = (int)m->Np;
     g.out = m->M1; g.ldo = n; g.sc = m->sc; g.scale_idx = SC_OUT_ORB; g.status = m->status;
+    g.pieces3 = 1;  // three pieces: the orbital split error would dominate E_x at this n
     dim3 grid((unsigned)((ng + 127) / 128), (unsigned)m->nt, 1);
-    gemm_kernel<<<grid, 192, G_SMEM, s>>>(m->m_phi_m, m->m_phi_h, m->m_CT_m, m->m_CT_h, g);
+    gemm_kernel<<<grid, 192, G_SMEM, s>>>(m->m_phi_m, m->m_phi_h, m->m_CT_m, m->m_CT_h, m->m_phi_l,
+                                          m->m_CT_l, g);
     split_rows_f32_kernel<<<152 * 4, 256, 0, s>>>(m->M1, ng, n, n, m->sc, SC_PSI, m->psi_m,
-                                                  m->psi_h, np, m->am + AM_RN2);
+                                                  m->psi_h, m->psi_l, np, m->am + AM_RN2);
     count_launch();
   }
   scales_kernel<<<1, 32, 0, s>>>(m->am, m->sc, 1);
   gather_rows_half_kernel<<<blocks_for(na * np), 256, 0, s>>>(m->psi_m, np, m->idx, (int)na, m->psig_m);
   gather_rows_half_kernel<<<blocks_for(na * np), 256, 0, s>>>(m->psi_h, np, m->idx, (int)na, m->psig_h);
   count_launch(4);
+  if (m->psi_l) {
+    gather_rows_half_kernel<<<blocks_for(na * np), 256, 0, s>>>(m->psi_l, np, m->idx, (int)na, m->psig_l);
+    count_launch();
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   hook(0, 0);
@@ -1799,30 +1866,29 @@ cudaError_t mixed_enqueue_pair(MixedState* m, cudaStream_t s, const StepHook& ho
     GemmArgs t{};
     t.M = (int)na; t.Ncols = (int)ng; t.K = np; t.kchunk = np; t.sc = m->sc; t.status = m->status;
     t.tv = m->V32; t.ldv = m->Ng4; t.f_idx = SC_F_AB; t.th = m->TA_h; t.tl = m->TA_l;
-    t.ld_t = m->Ng8; t.epart = m->EpA;
+    t.ld_t = m->Ng8; t.epart = m->EpA; t.pieces3 = 1;
     gemm_kernel<<<dim3((unsigned)m->xa, (unsigned)((ng + 127) / 128), 1), 192, G_SMEM, s>>>(
-        m->m_psig128_m, m->m_psig128_h, m->m_psi128_m, m->m_psi128_h, t);
+        m->m_psig128_m, m->m_psig128_h, m->m_psi128_m, m->m_psi128_h, m->m_psig128_l,
+        m->m_psi128_l, t);
     GemmArgs tc = t;
     tc.Ncols = (int)na; tc.tv = m->W32; tc.ldv = m->Na4; tc.f_idx = SC_F_C; tc.th = m->TC_h;
     tc.tl = m->TC_l; tc.ld_t = m->Na8; tc.epart = m->EpC;
     gemm_kernel<<<dim3((unsigned)m->xa, (unsigned)((na + 127) / 128), 1), 192, G_SMEM, s>>>(
-        m->m_psig128_m, m->m_psig128_h, m->m_psig128_m, m->m_psig128_h, tc);
+        m->m_psig128_m, m->m_psig128_h, m->m_psig128_m, m->m_psig128_h, m->m_psig128_l,
+        m->m_psig128_l, tc);
     GemmArgs g2{};
     g2.M = (int)na; g2.Ncols = n; g2.K = (int)ng; g2.kchunk = m->ychunkA; g2.out = m->M2p;
     g2.ldo = n; g2.split_stride = na * n; g2.sc = m->sc; g2.scale_idx = SC_OUT_AB;
     g2.status = m->status; g2.b_mn = 1;
-    gemm_kernel<<<dim3((unsigned)m->xa, (unsigned)m->nt, (unsigned)m->partsA), 192, G_SMEM, s>>>(
-        m->m_TA_h, m->m_TA_l, m->m_psi64_m, m->m_psi64_h, g2);
+    gemm_kernel<<<dim3((unsigned)m->xa, (unsigned)m->nt, (unsigned)m->partsA), 192, G_SMEM, s>>>(m->m_TA_h, m->m_TA_l, m->m_psi64_m, m->m_psi64_h, m->m_TA_h, m->m_psi64_m, g2);
     GemmArgs g3 = g2;
     g3.K = (int)na; g3.kchunk = m->ychunkC; g3.out = m->M3p; g3.scale_idx = SC_OUT_C;
-    gemm_kernel<<<dim3((unsigned)m->xa, (unsigned)m->nt, (unsigned)m->partsC), 192, G_SMEM, s>>>(
-        m->m_TC_h, m->m_TC_l, m->m_psig64_m, m->m_psig64_h, g3);
+    gemm_kernel<<<dim3((unsigned)m->xa, (unsigned)m->nt, (unsigned)m->partsC), 192, G_SMEM, s>>>(m->m_TC_h, m->m_TC_l, m->m_psig64_m, m->m_psig64_h, m->m_TC_h, m->m_psig64_m, g3);
     GemmArgs g1{};
     g1.M = (int)ng; g1.Ncols = n; g1.K = (int)na; g1.kchunk = (int)rup(na, 64); g1.out = m->M1;
     g1.ldo = m->Ng4; g1.sc = m->sc; g1.scale_idx = SC_OUT_AB; g1.status = m->status;
     g1.a_mn = 1; g1.b_mn = 1; g1.transposed = 1;
-    gemm_kernel<<<dim3((unsigned)((ng + 127) / 128), (unsigned)m->nt, 1), 192, G_SMEM, s>>>(
-        m->m_TAmn_h, m->m_TAmn_l, m->m_psig64_m, m->m_psig64_h, g1);
+    gemm_kernel<<<dim3((unsigned)((ng + 127) / 128), (unsigned)m->nt, 1), 192, G_SMEM, s>>>(m->m_TAmn_h, m->m_TAmn_l, m->m_psig64_m, m->m_psig64_h, m->m_TAmn_h, m->m_psig64_m, g1);
     count_launch(5);
   } else {
     launch_pair3(m->roles, np, s);
@@ -1860,13 +1926,13 @@ cudaError_t mixed_enqueue_post(MixedState* m, double* K, double* Ex, cudaStream_
     GemmArgs g{N, n, (int)ng, m->kchunkL1, m->L1p, n, (long)N * n, m->sc, SC_OUT_L1, m->status,
                nullptr, nullptr, 0, 0, nullptr};
     dim3 grid((unsigned)((N + 127) / 128), (unsigned)((n + 127) / 128), (unsigned)m->splitsL1);
-    gemm_kernel<<<grid, 192, G_SMEM, s>>>(m->m_phiT_m, m->m_phiT_h, m->m_M1_m, m->m_M1_h, g);
+    gemm_kernel<<<grid, 192, G_SMEM, s>>>(m->m_phiT_m, m->m_phiT_h, m->m_M1_m, m->m_M1_h, m->m_phiT_m, m->m_M1_m, g);
   }
   {
     GemmArgs g{N, n, (int)na, m->kchunkL23, m->L23p, n, (long)N * n, m->sc, SC_OUT_L23, m->status,
                nullptr, nullptr, 0, 0, nullptr};
     dim3 grid((unsigned)((N + 127) / 128), (unsigned)((n + 127) / 128), (unsigned)m->splitsL23);
-    gemm_kernel<<<grid, 192, G_SMEM, s>>>(m->m_phigT_m, m->m_phigT_h, m->m_D23T_m, m->m_D23T_h, g);
+    gemm_kernel<<<grid, 192, G_SMEM, s>>>(m->m_phigT_m, m->m_phigT_h, m->m_D23T_m, m->m_D23T_h, m->m_phigT_m, m->m_D23T_m, g);
   }
   count_launch(2);
   e = cudaGetLastError();
