@@ -64,6 +64,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
     p.add_argument("--no-serve", action="store_true", help="skip the serving-latency loop")
+    p.add_argument("--no-energy", action="store_true", help="skip the energy-only timing")
     p.add_argument("--batch", type=int, default=32,
                    help="cells in the grouped batch / mixed serving run (0 skips both)")
     return p.parse_args()
@@ -209,6 +210,26 @@ def time_device_builds(xk, h, Cd, Kd, Ed, stream, warm, steps, torch):
     st = h.step_times()
     h.timing(False)
     return e0.elapsed_time(e1), xk.kernel_launches() - launches0, st
+
+
+def time_energy(xk, h, Cd, stream, warm, steps, torch):
+    """Warm-up, then `steps` energy-only evaluations (xk_energy_device)
+    between CUDA events on `stream`.  Returns (ms, step times, last E_x)."""
+    Ee = torch.empty(1, dtype=torch.float64, device="cuda")
+    for i in range(warm):
+        h.energy_device(Cd[i].data_ptr(), Ee.data_ptr(), stream.cuda_stream)
+    torch.cuda.synchronize()
+    h.timing(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        h.energy_device(Cd[warm + i].data_ptr(), Ee.data_ptr(), stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st = h.step_times()
+    h.timing(False)
+    return e0.elapsed_time(e1), st, float(Ee.item())
 
 
 def serve_latency(xk, cell, handles, Cs, rate, count, seed):
@@ -408,6 +429,26 @@ def main():
         h.build(Ch[i].numpy())
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
+    energy = None
+    if not args.no_energy and world == 1:
+        ms_e, st_e, E_e = time_energy(xk, h, Cd, stream, warm, steps, torch)
+        pair_ms = st_e["pair"][0] / max(1, st_e["pair"][1])
+        npad = -(-n // 64) * 64
+        # algorithmic DRAM bytes of the energy pair step: V' and W' in FP32 read
+        # once, the orbital pieces (m, h) on the grid and at the points
+        ebytes = 4.0 * Na * Ng + 4.0 * Na * Na + 4.0 * (Ng + Na) * npad
+        pk_e, pk_src_e = peaks()
+        hbm = pk_e.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
+        energy = {"evals_per_s": steps / (ms_e * 1e-3), "ms_per_eval": ms_e / steps,
+                  "step_ms": {k: v[0] / max(1, v[1]) for k, v in st_e.items() if v[1] > 0},
+                  "E_x_last": E_e, "equals_build_E_x": E_e == E_last,
+                  "roofline": {"bound": "hbm", "kernel": "energy-only pair kernel (roles A, C)",
+                               "achieved": ebytes / (pair_ms * 1e-3) / 1e9, "peak": hbm,
+                               "unit": "GB/s", "frac": ebytes / (pair_ms * 1e-3) / 1e9 / hbm,
+                               "peak_source": f"HBM copy bandwidth ({pk_src_e})",
+                               "traffic": None},
+                  "note": "xk_energy_device: E_x alone from the closed form (no K), same "
+                          "coefficient sequence as the builds"}
     h.release()
     e2e_s = max_over_ranks(e2e_s, dist, "cuda")
 
@@ -502,6 +543,8 @@ def main():
             "e2e": {"value": job_throughput(world, steps, e2e_s * 1e3), "unit": "builds/s",
                     "h2d_bytes_per_step": N * n * 8, "d2h_bytes_per_step": N * n * 8 + 8},
         }
+        if energy:
+            line["energy_only"] = energy
         if serving:
             line["serving"] = serving
         if mixed:

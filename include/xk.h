@@ -116,6 +116,31 @@ int xk_build_device(xk_handle* h, const double* C_dev, double* K_dev, double* Ex
                     void* stream);
 
 /*
+ * The exchange energy alone, without K (a cheap convergence monitor between
+ * full builds): Eq. exoccri contracted with C gives the closed form
+ *   E_x = -dV (2 sum_{g,R} V(g,R) P(g,R)^2 - sum_{g,g'} W(g,g') Q(g,g')^2),
+ *   P = Psi_g Psi^T,  Q = Psi_g Psi_g^T,  Psi = Phi C,
+ * (line 1 and line 2 each contribute the V term, line 3 the W term).  Only
+ * the orbitals and the pair products run: no second product and no line
+ * contraction.  XK_FP64: P and Q in FP64 and the two weighted sums of
+ * squares in FP64.  XK_F16X3: the pair kernel's S products and energy sums
+ * with the same splits and summation order as xk_build, so for n <= 128 the
+ * value equals the E_x of xk_build bit for bit (n > 128: the same T-product
+ * energy sums, also bit for bit).  C (host, N x n) is copied; Ex (host)
+ * receives E_x.  Neither K nor the state xk_ace reads is touched.
+ * Errors: XK_EINVAL (null pointers), XK_ETIMEDOUT (a bounded wait inside a
+ * kernel gave up), XK_ECUDA.
+ */
+int xk_energy(xk_handle* h, const double* C, double* Ex);
+
+/*
+ * xk_energy on device memory, enqueued on `stream` (cudaStream_t, NULL =
+ * legacy default) and returning at once: C_dev (N x n) and Ex_dev (1 double)
+ * are caller-owned device pointers.  Errors: XK_EINVAL, XK_ECUDA.
+ */
+int xk_energy_device(xk_handle* h, const double* C_dev, double* Ex_dev, void* stream);
+
+/*
  * occ-RI K_ij of the last completed build on this handle and its ACE
  * factorisation (Sec. III.C), computed on the device in FP64:
  * K_ij = C^T K_{mu i} symmetrised; Cholesky K_ij = L L^T when it is positive

@@ -81,6 +81,7 @@ struct xk_handle {
   // FP64 tables and scratch
   double *phi = nullptr, *phig = nullptr, *V = nullptr, *W = nullptr;
   int32_t* idx = nullptr;
+  double* Ce = nullptr;  // xk_energy: C (N x n) and E_x (one more double), apart from the build's
   double *C = nullptr, *psi = nullptr, *psig = nullptr, *V2 = nullptr, *M1 = nullptr,
          *M2 = nullptr, *Q = nullptr, *M3 = nullptr, *L1 = nullptr, *L2 = nullptr,
          *L3 = nullptr, *K = nullptr, *Ex = nullptr, *work = nullptr, *red = nullptr;
@@ -142,6 +143,7 @@ Plan plan_fp64(int64_t Ng, int N, int n, int Naux) {
           + na * ng + (size_t)n * ng + na * n       // V2, M1, M2
           + na * na + na * n + 3 * (size_t)n * N    // Q, M3, lines
           + (size_t)N * n + 1 + xk::reduce_work_elems()  // K, Ex, reduction
+          + (size_t)N * n + 1                            // C and E_x of xk_energy
           + 3 * (size_t)n * n + 2 * (size_t)N * n + n;   // K_ij, L, U, Y, xi, sign
   p.work = max_work(Ng, N, n, Naux);
   p.f64 += p.work;
@@ -285,6 +287,42 @@ int enqueue_fp64(xk_handle* h) {
   return XK_OK;
 }
 
+// Enqueue E_x alone from h->Ce into h->Ce[N n] (the closed form of E_x:
+// -dV (2 sum V o P o P - sum W o Q o Q), no K).
+int enqueue_energy(xk_handle* h) {
+  double* Ex = h->Ce + (size_t)h->N * h->n;
+  if (h->mode != XK_FP64) {
+    xk::StepHook hook{h->timing ? &step_hook : nullptr, h};
+    cudaError_t e = xk::mixed_enqueue_energy(h->mixed, h->Ce, Ex, h->stream, hook);
+    if (e != cudaSuccess) return cuda_fail(e, "mixed-precision energy");
+    return XK_OK;
+  }
+  using xk::DGemm;
+  cudaStream_t s = h->stream;
+  const int ng = (int)h->Ng, N = h->N, n = h->n, na = h->Naux;
+  auto G = [&](int M, int Nc, int K, const double* A, long lda, bool ta, const double* B, long ldb,
+               bool tb, double* C, long ldc) {
+    DGemm g{M, Nc, K, A, lda, ta, B, ldb, tb, C, ldc, 1.0, nullptr, 0, 0, h->work};
+    return xk::dgemm(g, s);
+  };
+  {
+    StepMark m(h, XK_STEP_ORBITALS);
+    XK_CUDA(G(ng, n, N, h->phi, N, false, h->Ce, n, false, h->psi, n));
+    XK_CUDA(xk::gather_rows_f64(h->psi, n, h->idx, na, n, h->psig, n, s));
+  }
+  {  // P = Psi_g Psi^T and Q = Psi_g Psi_g^T
+    StepMark m(h, XK_STEP_PAIR);
+    XK_CUDA(G(na, ng, n, h->psig, n, false, h->psi, n, true, h->V2, ng));
+    XK_CUDA(G(na, na, n, h->psig, n, false, h->psig, n, true, h->Q, na));
+  }
+  {
+    StepMark m(h, XK_STEP_ASSEMBLE);
+    XK_CUDA(xk::closed_form_ex_f64(h->V, h->V2, (long)na * ng, h->W, h->Q, (long)na * na, h->dV,
+                                   h->red, Ex, s));
+  }
+  return XK_OK;
+}
+
 int enqueue_build(xk_handle* h) {
   if (h->mode == XK_FP64) return enqueue_fp64(h);
   xk::StepHook hook{h->timing ? &step_hook : nullptr, h};
@@ -309,7 +347,7 @@ int xk_footprint(int64_t Ng, int32_t N, int32_t n, int32_t Naux, int mode, size_
     return XK_OK;
   }
   if (mode == XK_F16X3) {
-    *bytes = xk::mixed_footprint(Ng, N, n, Naux) + (size_t)N * n * 8 * 2 +
+    *bytes = xk::mixed_footprint(Ng, N, n, Naux) + (size_t)N * n * 8 * 3 + 8 +
              (size_t)max_work(Ng, N, n, Naux, true) * 8 + 4 * (size_t)n * n * 8 + 2 * (size_t)N * n * 8 +
              65536;
     return XK_OK;
@@ -383,6 +421,7 @@ int xk_setup(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* phi,
     if (e_ != cudaSuccess) return bail(cuda_fail(e_, "cudaMalloc " #ptr)); \
   } while (0)
   XK_ALLOC(h->C, (size_t)N * n);
+  XK_ALLOC(h->Ce, (size_t)N * n + 1);
   XK_ALLOC(h->K, (size_t)N * n);
   XK_ALLOC(h->Ex, 1);
   XK_ALLOC(h->Kij, (size_t)n * n);
@@ -478,6 +517,44 @@ int xk_build(xk_handle* h, const double* C, double* K_out, double* Ex) {
       return fail(XK_ETIMEDOUT, "xk_build: a bounded wait inside a kernel gave up (code " +
                                     std::to_string(st) + ")");
   }
+  return XK_OK;
+}
+
+int xk_energy(xk_handle* h, const double* C, double* Ex) {
+  if (!h || !C || !Ex) return fail(XK_EINVAL, "xk_energy: NULL argument");
+  std::lock_guard<std::mutex> lk(h->mu);
+  DeviceGuard g(h->device);
+  const size_t cb = (size_t)h->N * h->n * 8;
+  XK_CUDA(cudaMemcpyAsync(h->Ce, C, cb, cudaMemcpyHostToDevice, h->stream));
+  int rc = enqueue_energy(h);
+  if (rc != XK_OK) return rc;
+  XK_CUDA(cudaMemcpyAsync(Ex, h->Ce + (size_t)h->N * h->n, 8, cudaMemcpyDeviceToHost, h->stream));
+  XK_CUDA(cudaStreamSynchronize(h->stream));
+  if (h->mixed) {
+    const int st = xk::mixed_take_status(h->mixed);
+    if (st != 0)
+      return fail(XK_ETIMEDOUT, "xk_energy: a bounded wait inside a kernel gave up (code " +
+                                    std::to_string(st) + ")");
+  }
+  return XK_OK;
+}
+
+int xk_energy_device(xk_handle* h, const double* C_dev, double* Ex_dev, void* stream) {
+  if (!h || !C_dev || !Ex_dev) return fail(XK_EINVAL, "xk_energy_device: NULL argument");
+  std::lock_guard<std::mutex> lk(h->mu);
+  DeviceGuard g(h->device);
+  cudaStream_t us = static_cast<cudaStream_t>(stream);
+  cudaEvent_t ev;
+  XK_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  XK_CUDA(cudaEventRecord(ev, us));
+  XK_CUDA(cudaStreamWaitEvent(h->stream, ev, 0));
+  XK_CUDA(cudaMemcpyAsync(h->Ce, C_dev, (size_t)h->N * h->n * 8, cudaMemcpyDeviceToDevice, h->stream));
+  int rc = enqueue_energy(h);
+  if (rc != XK_OK) { cudaEventDestroy(ev); return rc; }
+  XK_CUDA(cudaMemcpyAsync(Ex_dev, h->Ce + (size_t)h->N * h->n, 8, cudaMemcpyDeviceToDevice, h->stream));
+  XK_CUDA(cudaEventRecord(ev, h->stream));
+  XK_CUDA(cudaStreamWaitEvent(us, ev, 0));
+  cudaEventDestroy(ev);
   return XK_OK;
 }
 

@@ -243,6 +243,57 @@ cudaError_t neg_dot_f64(const double* a, const double* b, long len, double* work
   return cudaGetLastError();
 }
 
+// E_x from its closed form, -dV (2 sum w_A p_A^2 - sum w_C p_C^2) (Eq. exoccri
+// contracted with C: line 1 and line 2 each give sum V o P o P, line 3 gives
+// sum W o Q o Q).  Stage 1: half of the blocks sum the V term, the other
+// half the W term; stage 2 adds the per-block sums in a fixed order.
+__global__ void wsq_stage1(const double* __restrict__ wa, const double* __restrict__ pa, long la,
+                           const double* __restrict__ wc, const double* __restrict__ pc, long lc,
+                           double* __restrict__ part) {
+  __shared__ double sh[RED_TPB];
+  const int half = gridDim.x / 2;
+  const bool c = (int)blockIdx.x >= half;
+  const double* w = c ? wc : wa;
+  const double* p = c ? pc : pa;
+  const long len = c ? lc : la;
+  const long blk = c ? blockIdx.x - half : blockIdx.x;
+  const long chunk = (len + half - 1) / half;
+  const long beg = blk * chunk, end = min(len, beg + chunk);
+  double s = 0.0;
+  for (long t = beg + threadIdx.x; t < end; t += blockDim.x) s = fma(w[t] * p[t], p[t], s);
+  const double tot = block_sum(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void closed_ex_stage2(const double* __restrict__ part, int half, double dV, double* out) {
+  __shared__ double sa[RED_TPB], sc[RED_TPB];
+  double a = 0.0, c = 0.0;
+  for (int t = threadIdx.x; t < half; t += blockDim.x) {
+    a += part[t];
+    c += part[half + t];
+  }
+  sa[threadIdx.x] = a;
+  sc[threadIdx.x] = c;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sa[threadIdx.x] += sa[threadIdx.x + w];
+      sc[threadIdx.x] += sc[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = -dV * (2.0 * sa[0] - sc[0]);
+}
+
+cudaError_t closed_form_ex_f64(const double* V, const double* P, long lenA, const double* W,
+                               const double* Q, long lenC, double dV, double* work, double* out,
+                               cudaStream_t s) {
+  wsq_stage1<<<RED_BLOCKS, RED_TPB, 0, s>>>(V, P, lenA, W, Q, lenC, work);
+  closed_ex_stage2<<<1, RED_TPB, 0, s>>>(work, RED_BLOCKS / 2, dV, out);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Small dense FP64 factorisations (n <= a few hundred; one block each).
 

@@ -53,6 +53,12 @@ cudaError_t neg_dot_f64(const double* a, const double* b, long len, double* work
                         cudaStream_t s);
 size_t reduce_work_elems();
 
+// *out = -dV (2 sum_t V[t] P[t]^2 - sum_t W[t] Q[t]^2) over lenA and lenC
+// elements, in a fixed order; `work` holds reduce_work_elems() doubles.
+cudaError_t closed_form_ex_f64(const double* V, const double* P, long lenA, const double* W,
+                               const double* Q, long lenC, double dV, double* work, double* out,
+                               cudaStream_t s);
+
 // A <- (A + A^T) / 2 for an n x n matrix.
 cudaError_t symmetrize_f64(double* A, int n, cudaStream_t s);
 

@@ -801,7 +801,7 @@ __global__ void __launch_bounds__(192, 1)
           lw[j / 2] = *reinterpret_cast<const uint32_t*>(&l01);
         }
         esum += (double)e;
-        if (xok) {
+        if (xok && g.th) {
           *reinterpret_cast<uint4*>(g.th + x * g.ld_t + col) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
           *reinterpret_cast<uint4*>(g.tl + x * g.ld_t + col) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
@@ -900,6 +900,64 @@ struct PairCfg {
   static constexpr int AC = NP / 4;            // accumulator columns per epilogue warp
 };
 
+// X tile -> tensor memory, by the epilogue warps (lane = row; warp w / 4
+// picks the piece (m, h) and the half of its NP / 2 columns; fp16 pairs as in
+// memory).  Rows past the end of X are zero.
+template <int NP>
+__device__ __forceinline__ void load_x_tile(const PairArgs& a, int x0, uint32_t tbase, int warp,
+                                            int lane) {
+  using C = PairCfg<NP>;
+  const int quad = warp & 3, c = warp >> 2;
+  const int piece = c >> 1, part = c & 1;
+  const int r = quad * 32 + lane;
+  const long x = (long)x0 + r;
+  const uint32_t lane_off = static_cast<uint32_t>(quad * 32) << 16;
+  const uint4* src = reinterpret_cast<const uint4*>((piece ? a.xh : a.xm) + x * a.ldx + part * (NP / 2));
+  uint32_t w[C::AC];
+#pragma unroll
+  for (int v = 0; v < C::AC / 4; ++v) {
+    const uint4 q = (x < a.X) ? src[v] : make_uint4(0u, 0u, 0u, 0u);
+    w[4 * v] = q.x; w[4 * v + 1] = q.y; w[4 * v + 2] = q.z; w[4 * v + 3] = q.w;
+  }
+  const uint32_t col = (piece ? C::T_XH : C::T_XM) + part * C::AC;
+  if constexpr (C::AC == 32) tmem_st32(tbase + lane_off + col, w);
+  else tmem_st16(tbase + lane_off + col, w);
+  tmem_wait_st();
+}
+
+// TMA producer (one thread): T stages of (Y pieces m, h; the [128][64] V'
+// tile) through the kStages ring; gives up (status 21) when a stage is not
+// released within the bounded wait, then waits for its own copies in flight.
+template <int NP>
+__device__ __forceinline__ void produce_tiles(const CUtensorMap* mYm, const CUtensorMap* mYh,
+                                              const CUtensorMap* mV, uint8_t* sm, uint64_t* full,
+                                              uint64_t* empty, int T, int y0, int x0,
+                                              volatile int& abort_flag, int* status) {
+  using C = PairCfg<NP>;
+  constexpr int NKB = NP / 64;
+  prefetch_tmap(mYm); prefetch_tmap(mYh); prefetch_tmap(mV);
+  int last_parity[kStages];
+  for (int s = 0; s < kStages; ++s) last_parity[s] = -1;
+  for (int t = 0; t < T && !abort_flag; ++t) {
+    const int s = t % kStages, use = t / kStages;
+    if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) {
+      atomicExch(status, 21); abort_flag = 1; break;
+    }
+    uint8_t* st = sm + s * C::STAGE;
+    mbar_expect_tx(&full[s], C::STAGE);
+    const int yr = y0 + t * 64;
+    for (int kb = 0; kb < NKB; ++kb) {
+      tma_load_2d(st + kb * 8192, mYm, &full[s], kb * 64, yr);
+      tma_load_2d(st + C::Y_BYTES + kb * 8192, mYh, &full[s], kb * 64, yr);
+    }
+    tma_load_2d(st + 2 * C::Y_BYTES, mV, &full[s], yr, x0);
+    tma_load_2d(st + 2 * C::Y_BYTES + 16384, mV, &full[s], yr + 32, x0);
+    last_parity[s] = use & 1;
+  }
+  for (int s = 0; s < kStages; ++s)
+    if (last_parity[s] >= 0) mbar_wait(&full[s], last_parity[s]);
+}
+
 // The kernel body: one X tile against a range of Y tiles for one role.
 template <int NP>
 __device__ __forceinline__ void pair_body(const CUtensorMap* mYm, const CUtensorMap* mYh,
@@ -919,7 +977,6 @@ __device__ __forceinline__ void pair_body(const CUtensorMap* mYm, const CUtensor
   const int y0 = by * a.ychunk;
   const int y1 = min(a.Y, y0 + a.ychunk);
   const int T = y1 > y0 ? (y1 - y0 + 63) / 64 : 0;
-  constexpr int NKB = NP / 64;
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -947,53 +1004,13 @@ __device__ __forceinline__ void pair_body(const CUtensorMap* mYm, const CUtensor
   tc_fence_after();
   const uint32_t tbase = tslot;
 
-  // ---------------- X tile -> tensor memory (lane = row; warp w / 4 picks the
-  // piece (m, h) and the half of its NP / 2 columns; fp16 pairs as in memory)
-  if (warp < kEpiWarps) {
-    const int quad = warp & 3, c = warp >> 2;
-    const int piece = c >> 1, part = c & 1;
-    const int r = quad * 32 + lane;
-    const long x = (long)x0 + r;
-    const uint32_t lane_off = static_cast<uint32_t>(quad * 32) << 16;
-    const uint4* src = reinterpret_cast<const uint4*>((piece ? a.xh : a.xm) + x * a.ldx + part * (NP / 2));
-    uint32_t w[C::AC];
-#pragma unroll
-    for (int v = 0; v < C::AC / 4; ++v) {
-      const uint4 q = (x < a.X) ? src[v] : make_uint4(0u, 0u, 0u, 0u);
-      w[4 * v] = q.x; w[4 * v + 1] = q.y; w[4 * v + 2] = q.z; w[4 * v + 3] = q.w;
-    }
-    const uint32_t col = (piece ? C::T_XH : C::T_XM) + part * C::AC;
-    if constexpr (C::AC == 32) tmem_st32(tbase + lane_off + col, w);
-    else tmem_st16(tbase + lane_off + col, w);
-    tmem_wait_st();
-  }
+  if (warp < kEpiWarps) load_x_tile<NP>(a, x0, tbase, warp, lane);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
 
   if (warp == prod_warp && lane == 0) {
-    // ---------------- TMA producer
-    prefetch_tmap(mYm); prefetch_tmap(mYh); prefetch_tmap(mV);
-    int last_parity[kStages];
-    for (int s = 0; s < kStages; ++s) last_parity[s] = -1;
-    for (int t = 0; t < T && !abort_flag; ++t) {
-      const int s = t % kStages, use = t / kStages;
-      if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) {
-        atomicExch(a.status, 21); abort_flag = 1; break;
-      }
-      uint8_t* st = sm + s * C::STAGE;
-      mbar_expect_tx(&full[s], C::STAGE);
-      const int yr = y0 + t * 64;
-      for (int kb = 0; kb < NKB; ++kb) {
-        tma_load_2d(st + kb * 8192, mYm, &full[s], kb * 64, yr);
-        tma_load_2d(st + C::Y_BYTES + kb * 8192, mYh, &full[s], kb * 64, yr);
-      }
-      tma_load_2d(st + 2 * C::Y_BYTES, mV, &full[s], yr, x0);
-      tma_load_2d(st + 2 * C::Y_BYTES + 16384, mV, &full[s], yr + 32, x0);
-      last_parity[s] = use & 1;
-    }
-    for (int s = 0; s < kStages; ++s)
-      if (last_parity[s] >= 0) mbar_wait(&full[s], last_parity[s]);
+    produce_tiles<NP>(mYm, mYh, mV, sm, full, empty, T, y0, x0, abort_flag, a.status);
   } else if (warp == mma_warp) {
     // ---------------- MMA issuer: the whole warp runs the loop (warp-uniform
     // descriptors and waits); one elected lane issues each MMA and commit.
@@ -1240,6 +1257,182 @@ __global__ void __launch_bounds__(kPairThreads, 1)
   pair_body<NP>(&job.ym[ri], &job.yh[ri], &job.v[ri], job.a[ri], blk % gx, blk / gx, gx);
 }
 
+// ============================================================ energy-only pair kernel
+// E_x without K (the closed form of E_x contracted from Eq. exoccri):
+// for one X tile of 128 rows and a range of Y tiles,
+//   S = X Y^T   (the four split passes of the pair kernel, same order)
+//   e += sum_y V' o S o S
+// and no second product.  S is double-buffered in tensor memory (buffer b:
+// A0 at 128 + 128 b, A1 at 192 + 128 b), so the S product of the next tile
+// runs while the epilogue reads V'.  A stage of (Y pieces, V') is released
+// by one MMA commit (the S product has read Y) plus one arrival per epilogue
+// warp (V' has been read).  The per-tile and per-CTA sums are formed exactly
+// as in the pair kernel: with the same split of the Y range the energy
+// equals that of the full build bit for bit.
+
+struct EnergyJob {
+  CUtensorMap ym[2], yh[2], v[2];
+  PairArgs a[2];
+  int gx[2], nblk[2];
+};
+
+template <int NP>
+__device__ __forceinline__ void energy_body(const CUtensorMap* mYm, const CUtensorMap* mYh,
+                                            const CUtensorMap* mV, const PairArgs& a, int bx,
+                                            int by, int gx) {
+  using C = PairCfg<NP>;
+  extern __shared__ uint8_t p_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ uint64_t full[kStages], empty[kStages], s_full[2], s_free[2], drain;
+  __shared__ uint32_t tslot;
+  __shared__ volatile int abort_flag;
+  __shared__ double ered[kEpiWarps];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int prod_warp = kEpiWarps, mma_warp = kEpiWarps + 1;
+  const int x0 = bx * 128;
+  const int y0 = by * a.ychunk;
+  const int y1 = min(a.Y, y0 + a.ychunk);
+  const int T = y1 > y0 ? (y1 - y0 + 63) / 64 : 0;
+  constexpr uint32_t T_SB = 128;  // first S buffer; the second follows 128 columns on
+
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1 + kEpiWarps);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&s_full[b], 1);
+      mbar_init(&s_free[b], kEpiWarps);
+    }
+    mbar_init(&drain, 1);
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == mma_warp) {
+    tmem_alloc(&tslot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tslot;
+
+  if (warp < kEpiWarps) load_x_tile<NP>(a, x0, tbase, warp, lane);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  if (warp == prod_warp && lane == 0) {
+    produce_tiles<NP>(mYm, mYh, mV, sm, full, empty, T, y0, x0, abort_flag, a.status);
+  } else if (warp == mma_warp) {
+    const uint32_t id_s = idesc_f16(128, 64, false, false, false);
+    const uint64_t dy0 = sdesc_sw128(smem_u32(sm), 16, 1024);
+    constexpr uint64_t kStage16 = C::STAGE >> 4, kYh16 = C::Y_BYTES >> 4;
+    const uint32_t txm = tbase + C::T_XM, txh = tbase + C::T_XH;
+    auto aborted = [&]() { return __shfl_sync(0xffffffffu, (int)abort_flag, 0) != 0; };
+    auto fail = [&](int code) {
+      if (lane == 0) { atomicExch(a.status, code); abort_flag = 1; }
+      __syncwarp();
+    };
+    for (int t = 0; t < T && !aborted(); ++t) {
+      const int s = t % kStages, use = t / kStages, b = t & 1;
+      if (!mbar_wait_warp(&full[s], use & 1)) { fail(31); break; }
+      if (t >= 2 && !mbar_wait_warp(&s_free[b], ((t - 2) >> 1) & 1)) { fail(32); break; }
+      tc_fence_after();
+      const uint64_t dym = dy0 + s * kStage16, dyh = dym + kYh16;
+      const uint32_t ts0 = tbase + T_SB + 128 * b, ts1 = ts0 + 64;
+      // passes m.m' -> A0, then m.h', h.m', h.h' -> A1 (a runtime loop over
+      // the passes keeps the descriptors of one pass live at a time)
+#pragma unroll 1
+      for (int pass = 0; pass < 4; ++pass) {
+        const uint32_t td = pass == 0 ? ts0 : ts1;
+        const uint32_t ta = pass < 2 ? txm : txh;
+        const uint64_t db = (pass & 1) ? dyh : dym;
+        const uint32_t acc0 = pass >= 2 ? 1u : 0u;
+#pragma unroll
+        for (int kk = 0; kk < NP / 16; ++kk)
+          if (elect_one()) mma_f16_ts(td, ta + kk * 8, db + (kk >> 2) * 512 + (kk & 3) * 2, id_s, kk > 0 ? 1u : acc0);
+      }
+      if (elect_one()) {
+        mma_commit(&s_full[b]);
+        mma_commit(&empty[s]);
+      }
+      __syncwarp();
+    }
+    if (elect_one()) mma_commit(&drain);
+    __syncwarp();
+    mbar_wait_warp(&drain, 0);
+  } else if (warp < kEpiWarps) {
+    const int quad = warp & 3, c = warp >> 2;
+    const int r = quad * 32 + lane;
+    const uint32_t lane_off = static_cast<uint32_t>(quad * 32) << 16;
+    const long x = (long)x0 + r;
+    const bool xok = x < a.X;
+    const int vbox_off = 2 * C::Y_BYTES + (c >> 1) * 16384 + r * 128;
+    const int sw = r & 7, q0 = (c & 1) * 4;
+    double esum = 0.0;
+    bool ok = T > 0;
+    auto aborted = [&]() { return __shfl_sync(0xffffffffu, (int)abort_flag, 0) != 0; };
+    auto fail = [&](int code) {
+      if (lane == 0) { atomicExch(a.status, code); abort_flag = 1; }
+      __syncwarp();
+    };
+    for (int t = 0; t < T && !aborted(); ++t) {
+      const int b = t & 1;
+      if (!mbar_wait_warp(&s_full[b], (t >> 1) & 1)) { fail(33); ok = false; break; }
+      tc_fence_after();
+      float sv[16];
+      {
+        const uint32_t t_s0 = tbase + lane_off + T_SB + 128 * b + 16 * c;
+        uint32_t u0[16], u1[16];
+        tmem_ld16(t_s0, u0);
+        tmem_ld16(t_s0 + 64, u1);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) sv[j] = __uint_as_float(u0[j]) + __uint_as_float(u1[j]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&s_free[b]);
+      float etile = 0.0f;
+      const uint8_t* vrow = sm + (t % kStages) * C::STAGE + vbox_off;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 v4 = *reinterpret_cast<const float4*>(vrow + (((q0 + (q >> 1)) ^ sw) << 4));
+        const float v0 = (q & 1) ? v4.z : v4.x, v1 = (q & 1) ? v4.w : v4.y;
+        const float p0 = v0 * sv[2 * q], p1 = v1 * sv[2 * q + 1];
+        etile = fmaf(p0, sv[2 * q], etile);
+        etile = fmaf(p1, sv[2 * q + 1], etile);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[t % kStages]);
+      esum += (double)etile;
+    }
+    ok = ok && !aborted();
+    double e = (ok && xok) ? esum : 0.0;
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if (lane == 0) ered[warp] = e;
+    asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory");
+    if (tid == 0) {
+      double sum = 0.0;
+      for (int i = 0; i < kEpiWarps; ++i) sum += ered[i];
+      a.epart[(long)by * gx + bx] = sum;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == mma_warp) tmem_dealloc(tbase, 512);
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kPairThreads, 1) energy_kernel(const __grid_constant__ EnergyJob job) {
+  const int ri = (int)blockIdx.x >= job.nblk[0] ? 1 : 0;
+  const int blk = (int)blockIdx.x - (ri ? job.nblk[0] : 0);
+  const int gx = ri ? job.gx[1] : job.gx[0];
+  energy_body<NP>(ri ? &job.ym[1] : &job.ym[0], ri ? &job.yh[1] : &job.yh[0],
+                  ri ? &job.v[1] : &job.v[0], ri ? job.a[1] : job.a[0], blk % gx, blk / gx, gx);
+}
+
 // ------------------------------------------------------------- host side
 
 // Launches the roles (sorted, longest first) in chunks of at most kGroupRoles.
@@ -1272,6 +1465,22 @@ void launch_pair3(const PairRole* r, int np, cudaStream_t s) {
     pair_kernel<64><<<blocks, kPairThreads, PairCfg<64>::SMEM, s>>>(job);
   else
     pair_kernel<128><<<blocks, kPairThreads, PairCfg<128>::SMEM, s>>>(job);
+  count_launch();
+}
+
+// Energy-only launch of two roles (the V role and the W role of a build).
+void launch_energy2(const PairRole& ra, const PairRole& rc, int np, cudaStream_t s) {
+  EnergyJob job;
+  const PairRole* r[2] = {&ra, &rc};
+  for (int k = 0; k < 2; ++k) {
+    job.ym[k] = r[k]->ym; job.yh[k] = r[k]->yh; job.v[k] = r[k]->v;
+    job.a[k] = r[k]->a; job.gx[k] = r[k]->gx; job.nblk[k] = r[k]->nblk;
+  }
+  const unsigned blocks = (unsigned)(ra.nblk + rc.nblk);
+  if (np == 64)
+    energy_kernel<64><<<blocks, kPairThreads, PairCfg<64>::SMEM, s>>>(job);
+  else
+    energy_kernel<128><<<blocks, kPairThreads, PairCfg<128>::SMEM, s>>>(job);
   count_launch();
 }
 
@@ -1579,6 +1788,10 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(pair_kernel_group<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairCfg<128>::SMEM);
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(energy_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairCfg<64>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(energy_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairCfg<128>::SMEM);
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G_SMEM);
   if (e != cudaSuccess) return e;
 
@@ -1853,6 +2066,49 @@ cudaError_t mixed_enqueue_pre(MixedState* m, const double* C, cudaStream_t s, co
   return cudaSuccess;
 }
 
+// n > 128: the two T products (S = Psi_g Psi^T and Psi_g Psi_g^T, three
+// pieces each) with their energy sums sum V' o S^2 and sum W' o S^2; with
+// store = false only the energy sums are formed (T is not written).
+void enqueue_t_products(MixedState* m, cudaStream_t s, bool store) {
+  const long ng = m->Ng, na = m->Naux;
+  GemmArgs t{};
+  t.M = (int)na; t.Ncols = (int)ng; t.K = m->np; t.kchunk = m->np; t.sc = m->sc;
+  t.status = m->status; t.tv = m->V32; t.ldv = m->Ng4; t.f_idx = SC_F_AB;
+  t.th = store ? m->TA_h : nullptr; t.tl = store ? m->TA_l : nullptr;
+  t.ld_t = m->Ng8; t.epart = m->EpA; t.pieces3 = 1;
+  gemm_kernel<<<dim3((unsigned)m->xa, (unsigned)((ng + 127) / 128), 1), 192, G_SMEM, s>>>(
+      m->m_psig128_m, m->m_psig128_h, m->m_psi128_m, m->m_psi128_h, m->m_psig128_l,
+      m->m_psi128_l, t);
+  GemmArgs tc = t;
+  tc.Ncols = (int)na; tc.tv = m->W32; tc.ldv = m->Na4; tc.f_idx = SC_F_C;
+  tc.th = store ? m->TC_h : nullptr; tc.tl = store ? m->TC_l : nullptr;
+  tc.ld_t = m->Na8; tc.epart = m->EpC;
+  gemm_kernel<<<dim3((unsigned)m->xa, (unsigned)((na + 127) / 128), 1), 192, G_SMEM, s>>>(
+      m->m_psig128_m, m->m_psig128_h, m->m_psig128_m, m->m_psig128_h, m->m_psig128_l,
+      m->m_psig128_l, tc);
+  count_launch(2);
+}
+
+cudaError_t mixed_enqueue_energy(MixedState* m, const double* C, double* Ex, cudaStream_t s,
+                                 const StepHook& hook) {
+  cudaError_t e = mixed_enqueue_pre(m, C, s, hook);
+  if (e != cudaSuccess) return e;
+  hook(1, 1);
+  if (m->large)
+    enqueue_t_products(m, s, false);
+  else
+    launch_energy2(m->roles[0], m->roles[2], m->np, s);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  hook(1, 0);
+  hook(7, 1);
+  final_ex_kernel<<<1, 256, 0, s>>>(m->EpA, (int)m->epA, m->EpC, (int)m->epC, m->sc, m->dV, Ex);
+  count_launch();
+  e = cudaGetLastError();
+  hook(7, 0);
+  return e;
+}
+
 cudaError_t mixed_enqueue_pair(MixedState* m, cudaStream_t s, const StepHook& hook) {
   const long ng = m->Ng, na = m->Naux;
   const int n = m->n, np = m->np;
@@ -1863,19 +2119,7 @@ cudaError_t mixed_enqueue_pair(MixedState* m, cudaStream_t s, const StepHook& ho
     // n > 128: T_A = f_AB V o (Psi_g Psi^T) and T_C = f_C W o (Psi_g Psi_g^T)
     // as hi/lo FP16 with their energy sums, then M2 = T_A Psi, M3 = T_C Psi_g
     // and M1^T = T_A^T Psi_g (written transposed) on the tensor cores.
-    GemmArgs t{};
-    t.M = (int)na; t.Ncols = (int)ng; t.K = np; t.kchunk = np; t.sc = m->sc; t.status = m->status;
-    t.tv = m->V32; t.ldv = m->Ng4; t.f_idx = SC_F_AB; t.th = m->TA_h; t.tl = m->TA_l;
-    t.ld_t = m->Ng8; t.epart = m->EpA; t.pieces3 = 1;
-    gemm_kernel<<<dim3((unsigned)m->xa, (unsigned)((ng + 127) / 128), 1), 192, G_SMEM, s>>>(
-        m->m_psig128_m, m->m_psig128_h, m->m_psi128_m, m->m_psi128_h, m->m_psig128_l,
-        m->m_psi128_l, t);
-    GemmArgs tc = t;
-    tc.Ncols = (int)na; tc.tv = m->W32; tc.ldv = m->Na4; tc.f_idx = SC_F_C; tc.th = m->TC_h;
-    tc.tl = m->TC_l; tc.ld_t = m->Na8; tc.epart = m->EpC;
-    gemm_kernel<<<dim3((unsigned)m->xa, (unsigned)((na + 127) / 128), 1), 192, G_SMEM, s>>>(
-        m->m_psig128_m, m->m_psig128_h, m->m_psig128_m, m->m_psig128_h, m->m_psig128_l,
-        m->m_psig128_l, tc);
+    enqueue_t_products(m, s, true);
     GemmArgs g2{};
     g2.M = (int)na; g2.Ncols = n; g2.K = (int)ng; g2.kchunk = m->ychunkA; g2.out = m->M2p;
     g2.ldo = n; g2.split_stride = na * n; g2.sc = m->sc; g2.scale_idx = SC_OUT_AB;
@@ -1889,7 +2133,7 @@ cudaError_t mixed_enqueue_pair(MixedState* m, cudaStream_t s, const StepHook& ho
     g1.ldo = m->Ng4; g1.sc = m->sc; g1.scale_idx = SC_OUT_AB; g1.status = m->status;
     g1.a_mn = 1; g1.b_mn = 1; g1.transposed = 1;
     gemm_kernel<<<dim3((unsigned)((ng + 127) / 128), (unsigned)m->nt, 1), 192, G_SMEM, s>>>(m->m_TAmn_h, m->m_TAmn_l, m->m_psig64_m, m->m_psig64_h, m->m_TAmn_h, m->m_psig64_m, g1);
-    count_launch(5);
+    count_launch(3);
   } else {
     launch_pair3(m->roles, np, s);
   }

@@ -42,6 +42,13 @@ cudaError_t mixed_enqueue_pair(MixedState* m, cudaStream_t s, const StepHook& ho
 cudaError_t mixed_enqueue_post(MixedState* m, double* K_dev, double* Ex_dev, cudaStream_t s,
                                const StepHook& hook);
 
+// E_x alone (no K): the orbitals, then the pair products S with the sums
+// sum V' o S^2 and sum W' o S^2 only (no second product, no line
+// contractions), then E_x from the closed form.  Uses the same split and
+// summation order as mixed_enqueue, so for n <= 128 the two give the same E_x.
+cudaError_t mixed_enqueue_energy(MixedState* m, const double* C_dev, double* Ex_dev,
+                                 cudaStream_t s, const StepHook& hook);
+
 // Pair contractions of several handles as one grouped launch per piece width
 // (64 or 128 columns): the roles of every n <= 128 member, longest first, in
 // launches of up to 16 roles; members with n > 128 run their own pair step.

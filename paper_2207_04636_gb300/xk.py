@@ -45,6 +45,8 @@ def lib():
                                c_int, ctypes.POINTER(ctypes.c_void_p)]
         L.xk_build.argtypes = [c_d, c_d, c_d, c_d]
         L.xk_build_device.argtypes = [c_d, c_d, c_d, c_d, c_d]
+        L.xk_energy.argtypes = [c_d, c_d, c_d]
+        L.xk_energy_device.argtypes = [c_d, c_d, c_d, c_d]
         L.xk_ace.argtypes = [c_d, c_d, c_d, c_d, ctypes.POINTER(c_int)]
         L.xk_submit.argtypes = [c_d, c_d, ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)]
         L.xk_poll.argtypes = [ctypes.c_uint64, c_d, c_d, c_d]
@@ -58,7 +60,8 @@ def lib():
         L.xk_batch_release.argtypes = [c_d]
         L.xk_last_error.restype = ctypes.c_char_p
         L.xk_kernel_launches.restype = ctypes.c_uint64
-        for f in ("xk_footprint", "xk_setup", "xk_build", "xk_build_device", "xk_ace",
+        for f in ("xk_footprint", "xk_setup", "xk_build", "xk_build_device", "xk_energy",
+                  "xk_energy_device", "xk_ace",
                   "xk_submit", "xk_poll", "xk_release", "xk_timing_enable", "xk_timing_read",
                   "xk_exchange_energy_noalloc", "xk_batch_create", "xk_batch_build",
                   "xk_batch_release"):
@@ -128,6 +131,18 @@ class Handle:
         e.g. torch tensor .data_ptr()) on the given cudaStream_t handle."""
         _check(lib().xk_build_device(self._h, ctypes.c_void_p(C_dev), ctypes.c_void_p(K_dev),
                                      ctypes.c_void_p(Ex_dev), ctypes.c_void_p(stream)))
+
+    def energy(self, C):
+        """E_x alone from host C (N x n), without K (xk_energy)."""
+        C = _f64(C, (self.N, self.n), "C")
+        Ex = np.empty(1)
+        _check(lib().xk_energy(self._h, _ptr(C), _ptr(Ex)))
+        return float(Ex[0])
+
+    def energy_device(self, C_dev, Ex_dev, stream=0):
+        """Enqueue xk_energy on device buffers (integers: device addresses)."""
+        _check(lib().xk_energy_device(self._h, ctypes.c_void_p(C_dev), ctypes.c_void_p(Ex_dev),
+                                      ctypes.c_void_p(stream)))
 
     def ace(self):
         """(K_ij, xi, sign, branch) of the last build: branch 'cholesky' or 'eigen'."""

@@ -29,12 +29,15 @@ def _check(xk, c):
     h = xk.Handle(c.phi, c.idx, c.V, c.W, c.dV, c.n, mode="f16x3")
     try:
         K, E = h.build(c.C)
+        Ee = h.energy(c.C)
         K2, E2 = h.build(c.C)
     finally:
         h.release()
     assert abs(E - E0) <= TOL_E, (E, E0)
     assert np.max(np.abs(K - K0)) <= TOL_K, np.max(np.abs(K - K0))
     assert np.array_equal(K, K2) and E == E2  # fixed reduction order
+    # E_x alone (xk_energy): the same S products, splits and summation order
+    assert Ee == E, (Ee, E)
     return K, E
 
 

@@ -27,10 +27,13 @@ def _check(xk, c, mode="fp64"):
     h = xk.Handle(c.phi, c.idx, c.V, c.W, c.dV, c.n, mode=mode)
     try:
         K, E = h.build(c.C)
+        Ee = h.energy(c.C)
     finally:
         h.release()
     assert abs(E - E0) <= TOL_E, (E, E0)
     assert np.max(np.abs(K - K0)) <= TOL_K
+    # E_x alone from the closed form -dV (2 sum V o P^2 - sum W o Q^2)
+    assert abs(Ee - E0) <= TOL_E, (Ee, E0)
     return K, E
 
 
@@ -107,6 +110,28 @@ def test_ace_matches_oracle(xk, cell1):
     assert br == br0 == "cholesky"
     assert np.max(np.abs(Kij - Kij0)) <= 1e-9 * np.max(np.abs(Kij0))
     assert np.max(np.abs(xi - xi0)) <= 1e-7 * np.max(np.abs(xi0))
+
+
+@pytest.mark.parametrize("mode", ["fp64", "f16x3"])
+def test_energy_leaves_build_state(xk, cell1, mode):
+    """xk_energy with other coefficients neither changes the last build's
+    K_ij / ACE factor nor its own result when repeated."""
+    c = cell1
+    h = xk.Handle(c.phi, c.idx, c.V, c.W, c.dV, c.n, mode=mode)
+    h.build(c.C)
+    ref = h.ace()
+    rng = np.random.default_rng(5)
+    C2 = c.C + 0.05 * rng.standard_normal(c.C.shape)
+    e1 = h.energy(C2)
+    e2 = h.energy(C2)
+    after = h.ace()
+    _, E2 = h.build(C2)
+    h.release()
+    assert e1 == e2
+    assert abs(e1 - E2) <= (TOL_E if mode == "fp64" else 0.0)
+    for a, b in zip(ref[:3], after[:3]):
+        assert np.array_equal(a, b)
+    assert ref[3] == after[3]
 
 
 def test_ace_eigen_branch(xk):
