@@ -518,7 +518,7 @@ struct GemmArgs {
   // T mode (tv set, one split): the tile is S = A B^T (both in piece units);
   // write the hi/lo FP16 split of f V'[row][col] S into th / tl [M][ld_t]
   // (zero for Ncols <= col < ld_t) and the tile's sum V' S^2 into
-  // epart[blockIdx.y * gridDim.x + blockIdx.x].
+  // epart[by * tiles_x + bx] for the tile (bx, by).
   const float* tv;
   long ldv;
   int f_idx;
@@ -531,6 +531,10 @@ struct GemmArgs {
   // A1 adds m l' + l m' (products below 2^-30 of the row maxima are dropped).
   // Two stages of six 16 KB tiles instead of three of four.
   int pieces3;
+  // Logical grid of tiles (x: 128-row M tiles, y: 128-column N tiles, z: K
+  // splits); the launch has at most one CTA per SM and each CTA walks the
+  // tiles blockIdx.x, blockIdx.x + gridDim.x, ... (x fastest).
+  int tiles_x, tiles_y, tiles_z;
 };
 
 constexpr int G_STAGES = 3;
@@ -549,12 +553,18 @@ __global__ void __launch_bounds__(192, 1)
   __shared__ uint32_t tslot;
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.x * 128, n0 = blockIdx.y * 128;
-  const int kbeg = blockIdx.z * g.kchunk;
-  const int kend = min(g.K, kbeg + g.kchunk);
-  const int nkb = kend > kbeg ? (kend - kbeg + 63) / 64 : 0;
+  const int ntiles = g.tiles_x * g.tiles_y * g.tiles_z;
   const int kd = g.kdrain > 0 ? g.kdrain : kDrain;
-  const int ngroups = (nkb + kd - 1) / kd;
+  // tile t -> (M tile, N tile, K split) and its number of 64-wide k-blocks
+  auto tile_at = [&](int t, int& bx, int& by, int& bz) {
+    bx = t % g.tiles_x;
+    by = (t / g.tiles_x) % g.tiles_y;
+    bz = t / (g.tiles_x * g.tiles_y);
+  };
+  auto kblocks = [&](int bz) {
+    const int kb0 = bz * g.kchunk, ke = min(g.K, kb0 + g.kchunk);
+    return ke > kb0 ? (ke - kb0 + 63) / 64 : 0;
+  };
   const bool p3 = g.pieces3 != 0;
   const int ns = p3 ? 2 : G_STAGES;                       // stages
   const int sbytes = p3 ? 6 * 16384 : G_STAGE_BYTES;      // bytes per stage
@@ -584,8 +594,13 @@ __global__ void __launch_bounds__(192, 1)
   if (warp == 4 && lane == 0) {
     prefetch_tmap(&mAm); prefetch_tmap(&mAh); prefetch_tmap(&mBm); prefetch_tmap(&mBh);
     int last_parity[G_STAGES] = {-1, -1, -1};
-    for (int kb = 0; kb < nkb && !abort_flag; ++kb) {
-      const int s = kb % ns, use = kb / ns;
+    int it = 0;  // k-blocks issued by this CTA over all its tiles
+    for (int tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x) {
+    int bx, by, bz;
+    tile_at(tile, bx, by, bz);
+    const int m0 = bx * 128, n0 = by * 128, kbeg = bz * g.kchunk, nkb = kblocks(bz);
+    for (int kb = 0; kb < nkb && !abort_flag; ++kb, ++it) {
+      const int s = it % ns, use = it / ns;
       if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) {
         atomicExch(g.status, 11); abort_flag = 1; break;
       }
@@ -622,6 +637,7 @@ __global__ void __launch_bounds__(192, 1)
       }
       last_parity[s] = use & 1;
     }
+    }
     for (int s = 0; s < ns; ++s)
       if (last_parity[s] >= 0) mbar_wait(&full[s], last_parity[s]);
   } else if (warp == 5) {
@@ -637,14 +653,23 @@ __global__ void __launch_bounds__(192, 1)
       if (lane == 0) { atomicExch(g.status, code); abort_flag = 1; }
       __syncwarp();
     };
-    for (int kb = 0; kb < nkb && !__shfl_sync(0xffffffffu, (int)abort_flag, 0); ++kb) {
-      const int s = kb % ns, grp = kb / kd, set = grp & 1;
+    // it: k-blocks over all tiles (stage ring); G0: the tile's first drain group
+    // over all tiles (accumulator sets alternate across tile boundaries too)
+    int it = 0, G0 = 0;
+    bool good = true;
+    for (int tile = blockIdx.x; good && tile < ntiles; tile += gridDim.x) {
+    int bx, by, bz;
+    tile_at(tile, bx, by, bz);
+    const int nkb = kblocks(bz);
+    for (int kb = 0; kb < nkb; ++kb, ++it) {
+      if (__shfl_sync(0xffffffffu, (int)abort_flag, 0)) { good = false; break; }
+      const int s = it % ns, grp = G0 + kb / kd, set = grp & 1;
       const bool first = (kb % kd) == 0;
       const bool last = (kb % kd) == kd - 1 || kb == nkb - 1;
       if (first && grp >= 2 && !mbar_wait_warp(&set_free[set], ((grp >> 1) - 1) & 1)) {
-        fail(14); break;
+        fail(14); good = false; break;
       }
-      if (!mbar_wait_warp(&full[s], (kb / ns) & 1)) { fail(12); break; }
+      if (!mbar_wait_warp(&full[s], (it / ns) & 1)) { fail(12); good = false; break; }
       tc_fence_after();
       if (p3) {
         const uint64_t dam = dkm + s * (uint64_t)(sbytes >> 4), dah = dam + 1024, dal = dam + 2048;
@@ -694,21 +719,32 @@ __global__ void __launch_bounds__(192, 1)
       }
       __syncwarp();
     }
+    G0 += (nkb + kd - 1) / kd;
+    }
     if (elect_one()) mma_commit(&drain);
     __syncwarp();
     mbar_wait_warp(&drain, 0);
   } else if (warp < 4) {
     const int r = warp * 32 + lane;
     const uint32_t lane_off = static_cast<uint32_t>(warp * 32) << 16;
+    // Every epilogue warp walks all of the CTA's tiles (after a failed wait
+    // without waiting further), so the named barriers below match up.
+    int G0 = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int bx, by, bz;
+    tile_at(tile, bx, by, bz);
+    const int m0 = bx * 128, n0 = by * 128;
+    const int ngroups = (kblocks(bz) + kd - 1) / kd;
     float run[128];
 #pragma unroll
     for (int c = 0; c < 128; ++c) run[c] = 0.0f;
     bool ok = true;
     for (int gi = 0; gi < ngroups; ++gi) {
-      const int set = gi & 1;
-      if (!mbar_wait_warp(&set_ready[set], (gi >> 1) & 1)) {
+      const int grp = G0 + gi, set = grp & 1;
+      if (__shfl_sync(0xffffffffu, (int)abort_flag, 0) || !mbar_wait_warp(&set_ready[set], (grp >> 1) & 1)) {
         ok = false;
-        if (lane == 0) atomicExch(g.status, 13);
+        if (lane == 0 && !abort_flag) { atomicExch(g.status, 13); abort_flag = 1; }
+        __syncwarp();
         break;
       }
       tc_fence_after();
@@ -725,6 +761,7 @@ __global__ void __launch_bounds__(192, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&set_free[set]);
     }
+    G0 += ngroups;
     ok = ok && !abort_flag;
     const float scale = g.sc[g.scale_idx];
     if (g.pm) {
@@ -812,7 +849,8 @@ __global__ void __launch_bounds__(192, 1)
         if (lane == 0) ered[warp] = esum;
         asm volatile("bar.sync 1, 128;" ::: "memory");
         if (r == 0)
-          g.epart[(long)blockIdx.y * gridDim.x + blockIdx.x] = ered[0] + ered[1] + ered[2] + ered[3];
+          g.epart[(long)by * g.tiles_x + bx] = ered[0] + ered[1] + ered[2] + ered[3];
+        asm volatile("bar.sync 1, 128;" ::: "memory");  // ered is rewritten by the next tile
       }
     } else if (g.transposed) {
       const long row = (long)m0 + r;
@@ -824,17 +862,44 @@ __global__ void __launch_bounds__(192, 1)
         }
       }
     } else if (m0 + r < g.M) {
-      float* orow = g.out + (long)blockIdx.z * g.split_stride + (long)(m0 + r) * g.ldo;
+      float* orow = g.out + (long)bz * g.split_stride + (long)(m0 + r) * g.ldo;
 #pragma unroll
       for (int c = 0; c < 128; ++c) {
         const int col = n0 + c;
         if (col < g.Ncols) orow[col] = ok ? run[c] * scale : 0.0f;
       }
     }
+    }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 5) tmem_dealloc(tbase, 512);
+}
+
+// SMs of the current device (cached per device).
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 152;
+  if (cached[dev] == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = v > 0 ? v : 152;
+  }
+  return cached[dev];
+}
+
+// gemm_kernel over the logical grid `tiles` with at most one CTA per SM.
+void launch_gemm(const CUtensorMap& mAm, const CUtensorMap& mAh, const CUtensorMap& mBm,
+                 const CUtensorMap& mBh, const CUtensorMap& mAl, const CUtensorMap& mBl, GemmArgs g,
+                 dim3 tiles, cudaStream_t s) {
+  g.tiles_x = (int)tiles.x;
+  g.tiles_y = (int)tiles.y;
+  g.tiles_z = (int)tiles.z;
+  const long total = (long)tiles.x * tiles.y * tiles.z;
+  const unsigned ctas = (unsigned)std::max<long>(1, std::min<long>(total, sm_count()));
+  gemm_kernel<<<ctas, 192, G_SMEM, s>>>(mAm, mAh, mBm, mBh, mAl, mBl, g);
 }
 
 // ============================================================ pair kernel
@@ -2038,16 +2103,15 @@ cudaError_t mixed_enqueue_pre(MixedState* m, const double* C, cudaStream_t s, co
   if (!m->large) {  // Psi = Phi' Q, written directly as per-row pieces
     GemmArgs g{(int)ng, n, N, (int)m->Np, nullptr, 0, 0, m->sc, SC_OUT_ORB, m->status,
                m->psi_m, m->psi_h, np, SC_PSI, m->am + AM_RN2};
-    dim3 grid((unsigned)((ng + 127) / 128), 1, 1);
-    gemm_kernel<<<grid, 192, G_SMEM, s>>>(m->m_phi_m, m->m_phi_h, m->m_CT_m, m->m_CT_h, m->m_phi_m, m->m_CT_m, g);
+    launch_gemm(m->m_phi_m, m->m_phi_h, m->m_CT_m, m->m_CT_h, m->m_phi_m, m->m_CT_m, g,
+                dim3((unsigned)((ng + 127) / 128), 1, 1), s);
   } else {  // n > 128: Psi in FP32 (the M1 buffer, free until step 3), then per-row pieces
     GemmArgs g{};
     g.M = (int)ng; g.Ncols = n; g.K = N; g.kchunk = (int)m->Np;
     g.out = m->M1; g.ldo = n; g.sc = m->sc; g.scale_idx = SC_OUT_ORB; g.status = m->status;
     g.pieces3 = 1;  // three pieces: the orbital split error would dominate E_x at this n
-    dim3 grid((unsigned)((ng + 127) / 128), (unsigned)m->nt, 1);
-    gemm_kernel<<<grid, 192, G_SMEM, s>>>(m->m_phi_m, m->m_phi_h, m->m_CT_m, m->m_CT_h, m->m_phi_l,
-                                          m->m_CT_l, g);
+    launch_gemm(m->m_phi_m, m->m_phi_h, m->m_CT_m, m->m_CT_h, m->m_phi_l, m->m_CT_l, g,
+                dim3((unsigned)((ng + 127) / 128), (unsigned)m->nt, 1), s);
     split_rows_f32_kernel<<<152 * 4, 256, 0, s>>>(m->M1, ng, n, n, m->sc, SC_PSI, m->psi_m,
                                                   m->psi_h, m->psi_l, np, m->am + AM_RN2);
     count_launch();
@@ -2076,16 +2140,14 @@ void enqueue_t_products(MixedState* m, cudaStream_t s, bool store) {
   t.status = m->status; t.tv = m->V32; t.ldv = m->Ng4; t.f_idx = SC_F_AB;
   t.th = store ? m->TA_h : nullptr; t.tl = store ? m->TA_l : nullptr;
   t.ld_t = m->Ng8; t.epart = m->EpA; t.pieces3 = 1;
-  gemm_kernel<<<dim3((unsigned)m->xa, (unsigned)((ng + 127) / 128), 1), 192, G_SMEM, s>>>(
-      m->m_psig128_m, m->m_psig128_h, m->m_psi128_m, m->m_psi128_h, m->m_psig128_l,
-      m->m_psi128_l, t);
+  launch_gemm(m->m_psig128_m, m->m_psig128_h, m->m_psi128_m, m->m_psi128_h, m->m_psig128_l,
+              m->m_psi128_l, t, dim3((unsigned)m->xa, (unsigned)((ng + 127) / 128), 1), s);
   GemmArgs tc = t;
   tc.Ncols = (int)na; tc.tv = m->W32; tc.ldv = m->Na4; tc.f_idx = SC_F_C;
   tc.th = store ? m->TC_h : nullptr; tc.tl = store ? m->TC_l : nullptr;
   tc.ld_t = m->Na8; tc.epart = m->EpC;
-  gemm_kernel<<<dim3((unsigned)m->xa, (unsigned)((na + 127) / 128), 1), 192, G_SMEM, s>>>(
-      m->m_psig128_m, m->m_psig128_h, m->m_psig128_m, m->m_psig128_h, m->m_psig128_l,
-      m->m_psig128_l, tc);
+  launch_gemm(m->m_psig128_m, m->m_psig128_h, m->m_psig128_m, m->m_psig128_h, m->m_psig128_l,
+              m->m_psig128_l, tc, dim3((unsigned)m->xa, (unsigned)((na + 127) / 128), 1), s);
   count_launch(2);
 }
 
@@ -2124,15 +2186,18 @@ cudaError_t mixed_enqueue_pair(MixedState* m, cudaStream_t s, const StepHook& ho
     g2.M = (int)na; g2.Ncols = n; g2.K = (int)ng; g2.kchunk = m->ychunkA; g2.out = m->M2p;
     g2.ldo = n; g2.split_stride = na * n; g2.sc = m->sc; g2.scale_idx = SC_OUT_AB;
     g2.status = m->status; g2.b_mn = 1;
-    gemm_kernel<<<dim3((unsigned)m->xa, (unsigned)m->nt, (unsigned)m->partsA), 192, G_SMEM, s>>>(m->m_TA_h, m->m_TA_l, m->m_psi64_m, m->m_psi64_h, m->m_TA_h, m->m_psi64_m, g2);
+    launch_gemm(m->m_TA_h, m->m_TA_l, m->m_psi64_m, m->m_psi64_h, m->m_TA_h, m->m_psi64_m, g2,
+                dim3((unsigned)m->xa, (unsigned)m->nt, (unsigned)m->partsA), s);
     GemmArgs g3 = g2;
     g3.K = (int)na; g3.kchunk = m->ychunkC; g3.out = m->M3p; g3.scale_idx = SC_OUT_C;
-    gemm_kernel<<<dim3((unsigned)m->xa, (unsigned)m->nt, (unsigned)m->partsC), 192, G_SMEM, s>>>(m->m_TC_h, m->m_TC_l, m->m_psig64_m, m->m_psig64_h, m->m_TC_h, m->m_psig64_m, g3);
+    launch_gemm(m->m_TC_h, m->m_TC_l, m->m_psig64_m, m->m_psig64_h, m->m_TC_h, m->m_psig64_m, g3,
+                dim3((unsigned)m->xa, (unsigned)m->nt, (unsigned)m->partsC), s);
     GemmArgs g1{};
     g1.M = (int)ng; g1.Ncols = n; g1.K = (int)na; g1.kchunk = (int)rup(na, 64); g1.out = m->M1;
     g1.ldo = m->Ng4; g1.sc = m->sc; g1.scale_idx = SC_OUT_AB; g1.status = m->status;
     g1.a_mn = 1; g1.b_mn = 1; g1.transposed = 1;
-    gemm_kernel<<<dim3((unsigned)((ng + 127) / 128), (unsigned)m->nt, 1), 192, G_SMEM, s>>>(m->m_TAmn_h, m->m_TAmn_l, m->m_psig64_m, m->m_psig64_h, m->m_TAmn_h, m->m_psig64_m, g1);
+    launch_gemm(m->m_TAmn_h, m->m_TAmn_l, m->m_psig64_m, m->m_psig64_h, m->m_TAmn_h, m->m_psig64_m,
+                g1, dim3((unsigned)((ng + 127) / 128), (unsigned)m->nt, 1), s);
     count_launch(3);
   } else {
     launch_pair3(m->roles, np, s);
@@ -2169,14 +2234,14 @@ cudaError_t mixed_enqueue_post(MixedState* m, double* K, double* Ex, cudaStream_
   {
     GemmArgs g{N, n, (int)ng, m->kchunkL1, m->L1p, n, (long)N * n, m->sc, SC_OUT_L1, m->status,
                nullptr, nullptr, 0, 0, nullptr};
-    dim3 grid((unsigned)((N + 127) / 128), (unsigned)((n + 127) / 128), (unsigned)m->splitsL1);
-    gemm_kernel<<<grid, 192, G_SMEM, s>>>(m->m_phiT_m, m->m_phiT_h, m->m_M1_m, m->m_M1_h, m->m_phiT_m, m->m_M1_m, g);
+    launch_gemm(m->m_phiT_m, m->m_phiT_h, m->m_M1_m, m->m_M1_h, m->m_phiT_m, m->m_M1_m, g,
+                dim3((unsigned)((N + 127) / 128), (unsigned)((n + 127) / 128), (unsigned)m->splitsL1), s);
   }
   {
     GemmArgs g{N, n, (int)na, m->kchunkL23, m->L23p, n, (long)N * n, m->sc, SC_OUT_L23, m->status,
                nullptr, nullptr, 0, 0, nullptr};
-    dim3 grid((unsigned)((N + 127) / 128), (unsigned)((n + 127) / 128), (unsigned)m->splitsL23);
-    gemm_kernel<<<grid, 192, G_SMEM, s>>>(m->m_phigT_m, m->m_phigT_h, m->m_D23T_m, m->m_D23T_h, m->m_phigT_m, m->m_D23T_m, g);
+    launch_gemm(m->m_phigT_m, m->m_phigT_h, m->m_D23T_m, m->m_D23T_h, m->m_phigT_m, m->m_D23T_m, g,
+                dim3((unsigned)((N + 127) / 128), (unsigned)((n + 127) / 128), (unsigned)m->splitsL23), s);
   }
   count_launch(2);
   e = cudaGetLastError();
