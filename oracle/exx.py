@@ -24,6 +24,8 @@ Functions and their pins (tests/test_oracle_pins.py):
                       P6 (symmetry), P7 (E_x < 0), P8 (closed form), P9
                       (invariances)
   exx_rps_4index    : P3, P6 (full K_{mu nu} symmetric)
+  exx_rps_full      : == exx_rps_4index's K_{mu nu}; symmetric; K C equals
+                      the occ-RI rectangle
   exx_exact_fft     : P1, P2, P7 (K PSD); Poisson pinned by P10
   exx_energy_direct : P8
   ace_factor        : reconstruction and definiteness checks
@@ -109,6 +111,38 @@ def exx_energy_direct(phi, idx, V, W, C, dV, gblock: int = 512) -> float:
         acc.append(float(np.sum(V[s:s + gblock] * P * P)))
     Q = psig @ psig.T
     return -dV * (2.0 * math.fsum(acc) - float(np.sum(W * Q * Q)))
+
+
+# --------------------------------------------------------------------------
+# Full exchange matrix K_{mu nu} with the robust-PS integrals (Eq. rpsEx)
+# --------------------------------------------------------------------------
+
+def exx_rps_full(phi, idx, V, W, C, dV, gblock: int = 512):
+    """K_{mu nu} (N x N) of Eq. rpsEx with all three terms of Eq. rps, in the
+    order of the steps listed after Eq. rpsEx for the first term:
+      rho(g,R') = sum_i psi_i(R_g) psi_i(R')  (= P),   V2 = V o rho,
+      M_mu(R') = sum_g V2(g,R') phi_mu(R_g),   term1 = sum_R' M_mu(R') phi_nu(R');
+    the second term of Eq. rps (rho_{mu lam} at R, rho_{sig nu} at R_g) the
+    same way with the roles of R_g and R exchanged, and the third with W and
+    Q(g,g') = sum_i psi_i(R_g) psi_i(R_g') between interpolation points:
+      K = dV (term1 + term2 - term3)."""
+    psi, psig = orbitals(phi, C, idx)
+    phig = phi[idx]
+    naux, ng = V.shape
+    N = phi.shape[1]
+    M = np.zeros((N, ng))             # M[mu,R'] = sum_g phi_mu(R_g) V2(g,R')
+    M2 = np.zeros((naux, N))          # M2[g,mu] = sum_R V2(g,R) phi_mu(R)
+    for s in range(0, naux, gblock):
+        e = min(s + gblock, naux)
+        rho = psig[s:e] @ psi.T       # step 2
+        V2 = V[s:e] * rho             # step 3
+        M += phig[s:e].T @ V2         # step 4 (first term)
+        M2[s:e] = V2 @ phi            # second term: sum over R first
+    term1 = M @ phi                   # step 5: contraction over R'
+    term2 = M2.T @ phig               # second term: contraction over R_g
+    Q = psig @ psig.T
+    term3 = phig.T @ ((W * Q) @ phig)
+    return dV * (term1 + term2 - term3)
 
 
 # --------------------------------------------------------------------------

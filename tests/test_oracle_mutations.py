@@ -100,3 +100,63 @@ def test_unmutated_pins_hold(settings):
 def test_mutant_is_caught(settings, mutant, monkeypatch):
     monkeypatch.setattr(ox, "rps_lines", mutant)
     assert not _pins_hold(*settings)
+
+
+# ------------------------------------------------ full K_{mu nu} (Eq. rpsEx)
+
+_ORIG_FULL = ox.exx_rps_full
+
+
+def _full_terms(phi, idx, V, W, C):
+    psi = phi @ C
+    psig = psi[idx]
+    phig = phi[idx]
+    V2 = V * (psig @ psi.T)
+    t1 = (phig.T @ V2) @ phi
+    t2 = (V2 @ phi).T @ phig
+    t3 = phig.T @ ((W * (psig @ psig.T)) @ phig)
+    return t1, t2, t3
+
+
+def f_drop_term2(phi, idx, V, W, C, dV, gblock=512):
+    t1, t2, t3 = _full_terms(phi, idx, V, W, C)
+    return dV * (2.0 * t1 - t3)
+
+
+def f_sign_term3(phi, idx, V, W, C, dV, gblock=512):
+    t1, t2, t3 = _full_terms(phi, idx, V, W, C)
+    return dV * (t1 + t2 + t3)
+
+
+def f_term1_ket_at_points(phi, idx, V, W, C, dV, gblock=512):
+    # term 1 with phi_nu taken at R_g instead of R'
+    t1, t2, t3 = _full_terms(phi, idx, V, W, C)
+    psi = phi @ C
+    V2 = V * (psi[idx] @ psi.T)
+    bad = (phi[idx].T @ V2[:, idx]) @ phi[idx]
+    return dV * (bad + t2 - t3)
+
+
+def f_W_unsquared(phi, idx, V, W, C, dV, gblock=512):
+    t1, t2, _ = _full_terms(phi, idx, V, W, C)
+    return dV * (t1 + t2 - phi[idx].T @ W @ phi[idx])
+
+
+FULL_MUTANTS = [f_drop_term2, f_sign_term3, f_term1_ket_at_points, f_W_unsquared]
+
+
+def _full_pin_holds(tiny):
+    c = tiny
+    Kf = ox.exx_rps_full(c.phi, c.idx, c.V, c.W, c.C, c.dV)
+    K4, _, _ = oracle.exx_rps_4index(c.phi, c.idx, c.V, c.W, c.C, c.dV)
+    return np.max(np.abs(Kf - K4)) < 1e-12 * np.max(np.abs(K4))
+
+
+def test_unmutated_full_pin_holds(settings):
+    assert _full_pin_holds(settings[1])
+
+
+@pytest.mark.parametrize("mutant", FULL_MUTANTS, ids=[m.__name__ for m in FULL_MUTANTS])
+def test_full_mutant_is_caught(settings, mutant, monkeypatch):
+    monkeypatch.setattr(ox, "exx_rps_full", mutant)
+    assert not _full_pin_holds(settings[1])

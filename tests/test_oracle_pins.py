@@ -144,6 +144,21 @@ def test_occri_equals_4index_definition(tiny):
     assert np.max(np.abs(K - Kmui4)) < 1e-12 * np.max(np.abs(K))
 
 
+def test_full_k_equals_4index_definition(tiny, cell1):
+    """Eq. rpsEx in its step order, with the three terms of Eq. rps, equals
+    the literal 4-index integrals contracted with D = C C^T; the result is
+    symmetric, and K C is the occ-RI rectangle of Eq. exoccri."""
+    c = tiny
+    Kf = oracle.exx_rps_full(c.phi, c.idx, c.V, c.W, c.C, c.dV)
+    K4, _, _ = oracle.exx_rps_4index(c.phi, c.idx, c.V, c.W, c.C, c.dV)
+    assert np.max(np.abs(Kf - K4)) < 1e-12 * np.max(np.abs(K4))
+    c = cell1
+    Kf = oracle.exx_rps_full(c.phi, c.idx, c.V, c.W, c.C, c.dV, gblock=100)
+    assert np.max(np.abs(Kf - Kf.T)) < 1e-12 * np.max(np.abs(Kf))
+    Kmui, _ = oracle.exx_rps_occri(c.phi, c.idx, c.V, c.W, c.C, c.dV)
+    assert np.max(np.abs(Kf @ c.C - Kmui)) < 1e-12 * np.max(np.abs(Kmui))
+
+
 # ---------------------------------------------------------------- P6 ------
 
 def test_symmetry(tiny, cell1):
