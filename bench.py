@@ -65,6 +65,7 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
     p.add_argument("--no-serve", action="store_true", help="skip the serving-latency loop")
     p.add_argument("--no-energy", action="store_true", help="skip the energy-only timing")
+    p.add_argument("--no-full", action="store_true", help="skip the full K_mu_nu timing")
     p.add_argument("--batch", type=int, default=32,
                    help="cells in the grouped batch / mixed serving run (0 skips both)")
     return p.parse_args()
@@ -449,6 +450,19 @@ def main():
                                "traffic": None},
                   "note": "xk_energy_device: E_x alone from the closed form (no K), same "
                           "coefficient sequence as the builds"}
+    full = None
+    if not args.no_full and world == 1:
+        Kf = h.build_full(C_last)  # the first call allocates the full-K scratch
+        reps = 5 if mode != "fp64" else 1
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            Kf = h.build_full(C_last)
+        full = {"ms_per_build": (time.perf_counter() - t0) * 1e3 / reps,
+                "note": "xk_build_full: K_mu_nu (N x N) of Eq. rpsEx with the three robust-PS "
+                        "terms, host buffers in and out, same C as the last build",
+                "symmetry_rel": float(np.max(np.abs(Kf - Kf.T)) / np.max(np.abs(Kf))),
+                "max_dKC_vs_build": float(np.max(np.abs(Kf @ C_last - K_last)))}
     h.release()
     e2e_s = max_over_ranks(e2e_s, dist, "cuda")
 
@@ -478,6 +492,12 @@ def main():
                         stream.cuda_stream)
         torch.cuda.synchronize()
         K64, E64 = Kd.cpu().numpy(), float(Ed.item())
+        if full is not None:
+            t0 = time.perf_counter()
+            Kf64 = hf.build_full(C_last)
+            full["fp64_path_ms"] = (time.perf_counter() - t0) * 1e3
+            full["max_dK_vs_fp64"] = float(np.max(np.abs(Kf - Kf64)))
+            full["max_abs_K"] = float(np.max(np.abs(Kf64)))
         hf.release()
         fp64 = {"builds_per_s": 2.0 / (ms64 * 1e-3), "ms_per_build": ms64 / 2.0,
                 "dE_x_vs_fp64": abs(E_last - E64),
@@ -545,6 +565,8 @@ def main():
         }
         if energy:
             line["energy_only"] = energy
+        if full:
+            line["full_k"] = full
         if serving:
             line["serving"] = serving
         if mixed:

@@ -116,6 +116,25 @@ int xk_build_device(xk_handle* h, const double* C_dev, double* K_dev, double* Ex
                     void* stream);
 
 /*
+ * The full exchange matrix K_{mu nu} (N x N) with the robust-PS integrals,
+ * for the one non-occ-RI build at the end of an SCF run (Eq. rpsEx with all
+ * three terms of Eq. rps, Sec. III.B-C):
+ *   K = dV (Phi_g^T (V o P) Phi + Phi^T (V o P)^T Phi_g - Phi_g^T (W o Q) Phi_g),
+ *   P = Psi_g Psi^T,  Q = Psi_g Psi_g^T,  Psi = Phi C.
+ * It is symmetric (to rounding) and K C equals the K_{mu i} of xk_build.
+ * The contractions run over the grid first (M = (V o P) Phi, N_aux x N),
+ * O(N N_aux N_g) work against the occ-RI build's O(n N_aux N_g).
+ * XK_FP64: every product in FP64.  XK_F16X3: V o P and W o Q stored as hi/lo
+ * FP16 and contracted on the tensor cores; the first call on a handle
+ * allocates about 4 N_aux (N_g + N_aux) bytes of extra device memory (on top
+ * of xk_footprint; admitted like xk_setup: XK_ENOMEM when it does not fit).
+ * C (host, N x n) is copied; K_out (host, N x N, row-major) receives K.
+ * Neither the last build's K_{mu i} nor the state xk_ace reads is touched.
+ * Errors: XK_EINVAL (null pointers), XK_ENOMEM, XK_ETIMEDOUT, XK_ECUDA.
+ */
+int xk_build_full(xk_handle* h, const double* C, double* K_out);
+
+/*
  * The exchange energy alone, without K (a cheap convergence monitor between
  * full builds): Eq. exoccri contracted with C gives the closed form
  *   E_x = -dV (2 sum_{g,R} V(g,R) P(g,R)^2 - sum_{g,g'} W(g,g') Q(g,g')^2),

@@ -82,6 +82,9 @@ struct xk_handle {
   double *phi = nullptr, *phig = nullptr, *V = nullptr, *W = nullptr;
   int32_t* idx = nullptr;
   double* Ce = nullptr;  // xk_energy: C (N x n) and E_x (one more double), apart from the build's
+  // xk_build_full: K_{mu nu} (N x N); FP64 path also M_A, M_C (N_aux x N), Y, Z (N x N)
+  double *Kf = nullptr, *MA = nullptr, *MC = nullptr, *Yf = nullptr, *Zf = nullptr;
+  size_t full_extra = 0;  // bytes of the tensor path's full-K scratch, admitted on first use
   double *C = nullptr, *psi = nullptr, *psig = nullptr, *V2 = nullptr, *M1 = nullptr,
          *M2 = nullptr, *Q = nullptr, *M3 = nullptr, *L1 = nullptr, *L2 = nullptr,
          *L3 = nullptr, *K = nullptr, *Ex = nullptr, *work = nullptr, *red = nullptr;
@@ -132,6 +135,9 @@ size_t max_work(int64_t Ng, int N, int n, int Naux, bool ace_only = false) {
   acc(n, N, Naux);      // line2, line3
   acc(Naux, Naux, n);   // W o Q
   acc(Naux, n, Naux);   // M3
+  acc(Naux, N, ng);     // full K: M_A = V2 Phi
+  acc(Naux, N, Naux);   // full K: M_C = (W o Q) Phi_g
+  acc(N, N, Naux);      // full K: Phi_g^T M
   return w;
 }
 
@@ -144,6 +150,7 @@ Plan plan_fp64(int64_t Ng, int N, int n, int Naux) {
           + na * na + na * n + 3 * (size_t)n * N    // Q, M3, lines
           + (size_t)N * n + 1 + xk::reduce_work_elems()  // K, Ex, reduction
           + (size_t)N * n + 1                            // C and E_x of xk_energy
+          + 2 * na * N + 3 * (size_t)N * N                // full K: M_A, M_C, Y, Z, K
           + 3 * (size_t)n * n + 2 * (size_t)N * n + n;   // K_ij, L, U, Y, xi, sign
   p.work = max_work(Ng, N, n, Naux);
   p.f64 += p.work;
@@ -323,6 +330,46 @@ int enqueue_energy(xk_handle* h) {
   return XK_OK;
 }
 
+// Enqueue K_{mu nu} (Eq. rpsEx, all three terms of Eq. rps) from h->Ce into h->Kf.
+int enqueue_full(xk_handle* h) {
+  if (h->mode != XK_FP64) {
+    xk::StepHook hook{h->timing ? &step_hook : nullptr, h};
+    cudaError_t e = xk::mixed_enqueue_full(h->mixed, h->Ce, h->Kf, h->stream, hook);
+    if (e != cudaSuccess) return cuda_fail(e, "mixed-precision full K");
+    return XK_OK;
+  }
+  using xk::DGemm;
+  cudaStream_t s = h->stream;
+  const int ng = (int)h->Ng, N = h->N, n = h->n, na = h->Naux;
+  auto G = [&](int M, int Nc, int K, const double* A, long lda, bool ta, const double* B, long ldb,
+               bool tb, double* C, long ldc, const double* H, long ldh) {
+    DGemm g{M, Nc, K, A, lda, ta, B, ldb, tb, C, ldc, 1.0, H, ldh, 0, h->work};
+    return xk::dgemm(g, s);
+  };
+  {
+    StepMark m(h, XK_STEP_ORBITALS);
+    XK_CUDA(G(ng, n, N, h->phi, N, false, h->Ce, n, false, h->psi, n, nullptr, 0));
+    XK_CUDA(xk::gather_rows_f64(h->psi, n, h->idx, na, n, h->psig, n, s));
+  }
+  {  // V2 = V o (Psi_g Psi^T), M_A = V2 Phi
+    StepMark m(h, XK_STEP_PAIR);
+    XK_CUDA(G(na, ng, n, h->psig, n, false, h->psi, n, true, h->V2, ng, h->V, ng));
+    XK_CUDA(G(na, N, ng, h->V2, ng, false, h->phi, N, false, h->MA, N, nullptr, 0));
+  }
+  {  // W o (Psi_g Psi_g^T), M_C = (W o Q) Phi_g
+    StepMark m(h, XK_STEP_LINE3);
+    XK_CUDA(G(na, na, n, h->psig, n, false, h->psig, n, true, h->Q, na, h->W, na));
+    XK_CUDA(G(na, N, na, h->Q, na, false, h->phig, N, false, h->MC, N, nullptr, 0));
+  }
+  {  // Y = Phi_g^T M_A, Z = Phi_g^T M_C, K = dV (Y + Y^T - Z)
+    StepMark m(h, XK_STEP_ASSEMBLE);
+    XK_CUDA(G(N, N, na, h->phig, N, true, h->MA, N, false, h->Yf, N, nullptr, 0));
+    XK_CUDA(G(N, N, na, h->phig, N, true, h->MC, N, false, h->Zf, N, nullptr, 0));
+    XK_CUDA(xk::assemble_full_f64(h->Yf, h->Zf, N, h->dV, h->Kf, s));
+  }
+  return XK_OK;
+}
+
 int enqueue_build(xk_handle* h) {
   if (h->mode == XK_FP64) return enqueue_fp64(h);
   xk::StepHook hook{h->timing ? &step_hook : nullptr, h};
@@ -347,7 +394,7 @@ int xk_footprint(int64_t Ng, int32_t N, int32_t n, int32_t Naux, int mode, size_
     return XK_OK;
   }
   if (mode == XK_F16X3) {
-    *bytes = xk::mixed_footprint(Ng, N, n, Naux) + (size_t)N * n * 8 * 3 + 8 +
+    *bytes = xk::mixed_footprint(Ng, N, n, Naux) + (size_t)N * n * 8 * 3 + 8 + (size_t)N * N * 8 +
              (size_t)max_work(Ng, N, n, Naux, true) * 8 + 4 * (size_t)n * n * 8 + 2 * (size_t)N * n * 8 +
              65536;
     return XK_OK;
@@ -422,6 +469,7 @@ int xk_setup(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* phi,
   } while (0)
   XK_ALLOC(h->C, (size_t)N * n);
   XK_ALLOC(h->Ce, (size_t)N * n + 1);
+  XK_ALLOC(h->Kf, (size_t)N * N);
   XK_ALLOC(h->K, (size_t)N * n);
   XK_ALLOC(h->Ex, 1);
   XK_ALLOC(h->Kij, (size_t)n * n);
@@ -450,6 +498,10 @@ int xk_setup(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* phi,
     XK_ALLOC(h->L1, (size_t)n * N);
     XK_ALLOC(h->L2, (size_t)n * N);
     XK_ALLOC(h->L3, (size_t)n * N);
+    XK_ALLOC(h->MA, na * N);
+    XK_ALLOC(h->MC, na * N);
+    XK_ALLOC(h->Yf, (size_t)N * N);
+    XK_ALLOC(h->Zf, (size_t)N * N);
     e = cudaMemcpyAsync(h->phi, phi, ng * N * 8, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->V, V, na * ng * 8, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->W, W, na * na * 8, cudaMemcpyHostToDevice, h->stream);
@@ -515,6 +567,47 @@ int xk_build(xk_handle* h, const double* C, double* K_out, double* Ex) {
     const int st = xk::mixed_take_status(h->mixed);
     if (st != 0)
       return fail(XK_ETIMEDOUT, "xk_build: a bounded wait inside a kernel gave up (code " +
+                                    std::to_string(st) + ")");
+  }
+  return XK_OK;
+}
+
+int xk_build_full(xk_handle* h, const double* C, double* K_out) {
+  if (!h || !C || !K_out) return fail(XK_EINVAL, "xk_build_full: NULL argument");
+  std::lock_guard<std::mutex> lk(h->mu);
+  DeviceGuard g(h->device);
+  if (h->mode != XK_FP64 && h->full_extra == 0) {
+    // first use on the tensor path: admit and allocate the full-K scratch
+    const size_t extra = xk::mixed_full_footprint(h->Ng, h->N, h->n, h->Naux);
+    size_t freeb = 0, totalb = 0;
+    XK_CUDA(cudaMemGetInfo(&freeb, &totalb));
+    {
+      std::lock_guard<std::mutex> al(g_admit_mu);
+      const size_t reserve = (size_t)1 << 30;
+      size_t budget = freeb > reserve ? freeb - reserve : 0;
+      if (const char* env = std::getenv("XK_HBM_BUDGET_BYTES")) {
+        const size_t cap = (size_t)std::strtoull(env, nullptr, 10);
+        budget = std::min(budget, cap > g_admitted ? cap - g_admitted : 0);
+      }
+      if (extra > budget)
+        return fail(XK_ENOMEM, "xk_build_full: full-K scratch of " + std::to_string(extra) +
+                                   " bytes exceeds the admission budget " + std::to_string(budget));
+      g_admitted += extra;
+    }
+    h->full_extra = extra;
+    h->footprint += extra;
+    cudaError_t e = xk::mixed_full_prepare(h->mixed);
+    if (e != cudaSuccess) return cuda_fail(e, "xk_build_full scratch");
+  }
+  XK_CUDA(cudaMemcpyAsync(h->Ce, C, (size_t)h->N * h->n * 8, cudaMemcpyHostToDevice, h->stream));
+  int rc = enqueue_full(h);
+  if (rc != XK_OK) return rc;
+  XK_CUDA(cudaMemcpyAsync(K_out, h->Kf, (size_t)h->N * h->N * 8, cudaMemcpyDeviceToHost, h->stream));
+  XK_CUDA(cudaStreamSynchronize(h->stream));
+  if (h->mixed) {
+    const int st = xk::mixed_take_status(h->mixed);
+    if (st != 0)
+      return fail(XK_ETIMEDOUT, "xk_build_full: a bounded wait inside a kernel gave up (code " +
                                     std::to_string(st) + ")");
   }
   return XK_OK;

@@ -243,6 +243,26 @@ cudaError_t neg_dot_f64(const double* a, const double* b, long len, double* work
   return cudaGetLastError();
 }
 
+// Full K: K[mu][nu] = dV (Y[mu][nu] + Y[nu][mu] - Z[mu][nu]) (N x N).
+__global__ void assemble_full_kernel(const double* __restrict__ Y, const double* __restrict__ Z,
+                                     int N, double dV, double* __restrict__ K) {
+  const long count = (long)N * N;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count;
+       t += (long)gridDim.x * blockDim.x) {
+    const long mu = t / N, nu = t % N;
+    K[t] = dV * ((Y[t] + Y[nu * N + mu]) - Z[t]);
+  }
+}
+
+cudaError_t assemble_full_f64(const double* Y, const double* Z, int N, double dV, double* K,
+                              cudaStream_t s) {
+  const long count = (long)N * N;
+  const int blocks = (int)std::min<long>((count + 255) / 256, 152L * 16);
+  assemble_full_kernel<<<std::max(blocks, 1), 256, 0, s>>>(Y, Z, N, dV, K);
+  count_launch();
+  return cudaGetLastError();
+}
+
 // E_x from its closed form, -dV (2 sum w_A p_A^2 - sum w_C p_C^2) (Eq. exoccri
 // contracted with C: line 1 and line 2 each give sum V o P o P, line 3 gives
 // sum W o Q o Q).  Stage 1: half of the blocks sum the V term, the other

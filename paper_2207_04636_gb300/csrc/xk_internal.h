@@ -53,6 +53,10 @@ cudaError_t neg_dot_f64(const double* a, const double* b, long len, double* work
                         cudaStream_t s);
 size_t reduce_work_elems();
 
+// K[mu][nu] = dV (Y[mu][nu] + Y[nu][mu] - Z[mu][nu]) for N x N matrices.
+cudaError_t assemble_full_f64(const double* Y, const double* Z, int N, double dV, double* K,
+                              cudaStream_t s);
+
 // *out = -dV (2 sum_t V[t] P[t]^2 - sum_t W[t] Q[t]^2) over lenA and lenC
 // elements, in a fixed order; `work` holds reduce_work_elems() doubles.
 cudaError_t closed_form_ex_f64(const double* V, const double* P, long lenA, const double* W,

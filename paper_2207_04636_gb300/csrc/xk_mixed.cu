@@ -63,10 +63,16 @@ enum {
   SC_OUT_L1,    // line1 = acc * this
   SC_OUT_L23,   // line2 - line3 = acc * this
   SC_PHIP,      // Phi' = Phi L^{-T} (the orbital contraction)
+  SC_FA,        // full K: M_A^T = ((V o P) Phi)^T before its split
+  SC_FD,        // full K: (M_A - M_C)^T before its split
+  SC_OUT_FA,    // full K: M_A = acc * this
+  SC_OUT_FC,    // full K: M_C = ((W o Q) Phi_g) = acc * this
+  SC_OUT_FY,    // full K: Phi_g^T M_A = acc * this
+  SC_OUT_FZ,    // full K: Phi_g^T (M_A - M_C) = acc * this
   NSC
 };
 enum { AM_PHI = 0, AM_V, AM_W, AM_PHIP, AM_PHIP_RN, AM_C, AM_QCN, AM_PSI, AM_RN2, AM_M1, AM_D23,
-       NAM };
+       AM_FA, AM_FD, NAM };
 
 constexpr float kHalfTarget = 16384.0f;  // 2^14: split inputs are scaled to |x| <= 2^14
 constexpr float kProdTarget = 32768.0f;  // 2^15: V o P is scaled to |x| <= 2^15
@@ -82,7 +88,7 @@ __device__ float pow2_scale(float maxabs, float target) {
 
 __device__ __forceinline__ float am_get(const unsigned* am, int i) { return __uint_as_float(am[i]); }
 
-// stage 0: C scale; 1: Psi / pair scales; 2: M1, (M2 - M3) scales.
+// stage 0: C scale; 1: Psi / pair scales; 2: M1, (M2 - M3) scales; 3: full-K scales.
 __global__ void scales_kernel(const unsigned* __restrict__ am, float* __restrict__ sc, int stage) {
   if (threadIdx.x != 0) return;
   if (stage == 0) {
@@ -101,6 +107,13 @@ __global__ void scales_kernel(const unsigned* __restrict__ am, float* __restrict
     sc[SC_F_C] = fc;
     sc[SC_OUT_AB] = 1.0f / (fab * sp * sp * sp);
     sc[SC_OUT_C] = 1.0f / (fc * sp * sp * sp);
+    sc[SC_OUT_FA] = 1.0f / (fab * sp * sp * sc[SC_PHI]);
+    sc[SC_OUT_FC] = 1.0f / (fc * sp * sp * sc[SC_PHI]);
+  } else if (stage == 3) {
+    sc[SC_FA] = pow2_scale(am_get(am, AM_FA), kHalfTarget);
+    sc[SC_FD] = pow2_scale(am_get(am, AM_FD), kHalfTarget);
+    sc[SC_OUT_FY] = 1.0f / (sc[SC_PHI] * sc[SC_FA]);
+    sc[SC_OUT_FZ] = 1.0f / (sc[SC_PHI] * sc[SC_FD]);
   } else {
     sc[SC_M1] = pow2_scale(am_get(am, AM_M1), kHalfTarget);
     sc[SC_D23] = pow2_scale(am_get(am, AM_D23), kHalfTarget);
@@ -483,6 +496,21 @@ __global__ void final_ex_kernel(const double* __restrict__ ea, int na_, const do
     const double g = (double)sc[SC_PSI];
     const double g4 = (g * g) * (g * g);
     *Ex = -dV * (2.0 * sa[0] - sb[0]) / g4;
+  }
+}
+
+// Full K: K[mu][nu] = dV (sum_s Z[s][mu][nu] + sum_s Y[s][nu][mu]), FP64, with
+// Z = Phi_g^T (M_A - M_C) and Y = Phi_g^T M_A (two-sum FP32 over the splits).
+__global__ void final_kfull_kernel(const float* __restrict__ Z, int nz, const float* __restrict__ Y,
+                                   int ny, int N, double dV, double* __restrict__ K) {
+  const long count = (long)N * N;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count;
+       t += (long)gridDim.x * blockDim.x) {
+    const long mu = t / N, nu = t % N;
+    float h1 = 0.0f, l1 = 0.0f, h2 = 0.0f, l2 = 0.0f;
+    for (int p = 0; p < nz; ++p) ff_add(h1, l1, Z[(long)p * count + t]);
+    for (int p = 0; p < ny; ++p) ff_add(h2, l2, Y[(long)p * count + nu * N + mu]);
+    K[t] = dV * (((double)h1 + (double)l1) + ((double)h2 + (double)l2));
   }
 }
 
@@ -1625,6 +1653,13 @@ struct MixedState {
   __half *psi_l = nullptr, *psig_l = nullptr, *phi_l = nullptr, *CT_l = nullptr;
   CUtensorMap m_TA_h, m_TA_l, m_TAmn_h, m_TAmn_l, m_TC_h, m_TC_l, m_psi128_l, m_psig128_l,
       m_phi_l, m_CT_l;
+  // Full K_{mu nu} (mixed_enqueue_full): scratch allocated on first use
+  bool full_ready = false;
+  int splitsF = 1, splitsFC = 1, splitsY = 1, kchunkF = 64, kchunkFC = 64, kchunkY = 64;
+  float *MpA = nullptr, *MpC = nullptr, *Yp = nullptr, *Zp = nullptr;
+  double *DA = nullptr, *DD = nullptr, *DAT64 = nullptr, *DDT64 = nullptr;
+  __half *DAT_m = nullptr, *DAT_h = nullptr, *DDT_m = nullptr, *DDT_h = nullptr;
+  CUtensorMap m_DAT_m, m_DAT_h, m_DDT_m, m_DDT_h;
   // n <= 128: the three roles of the fused pair launch
   PairRole roles[3];
   float tuned_ms = 0.0f;  // pair launch time of the split the autotuner kept
@@ -1721,6 +1756,27 @@ Plan make_plan(int64_t Ng, int N, int n, int Naux) {
 // work evenly over the SMs.
 int q_ksplit(int N) { return std::max(1, std::min(64, (N + 15) / 16)); }
 
+// K splits of the full-K contractions: M_A = T_A Phi (K = N_g), M_C = T_C
+// Phi_g (K = N_aux) over (N_aux / 128) x (N / 128) tiles, and Phi_g^T M
+// (K = N_aux) over (N / 128)^2 tiles: about four waves, K chunks >= 1024.
+struct FullPlan {
+  int splitsF, kchunkF, splitsFC, kchunkFC, splitsY, kchunkY;
+};
+
+FullPlan make_full_plan(int64_t Ng, int N, int Naux) {
+  const int xa = (Naux + 127) / 128, tn = (N + 127) / 128;
+  auto split = [](long K, int tiles, int& kchunk) {
+    int sp = (int)std::max<long>(1, std::min<long>((K + 1023) / 1024, (608 + tiles - 1) / tiles));
+    kchunk = (int)rup((K + sp - 1) / sp, 64);
+    return (int)((K + kchunk - 1) / kchunk);
+  };
+  FullPlan f;
+  f.splitsF = split(Ng, xa * tn, f.kchunkF);
+  f.splitsFC = split(Naux, xa * tn, f.kchunkFC);
+  f.splitsY = split(Naux, tn * tn, f.kchunkY);
+  return f;
+}
+
 // Split-K work of the FP64 contractions of the set-up and of Q = L^T C.
 // Device staging for the set-up (two buffers): Phi and its layouts, W, and V
 // in row chunks of at most N rows.
@@ -1755,6 +1811,18 @@ size_t mixed_footprint(int64_t Ng, int N, int n, int Naux) {
   b += (size_t)(p.epA + p.epC) * 8;
   b += (size_t)N * N * 8 + (size_t)N * n * 8 + dwork_elems(Ng, N, n) * 8;
   b += 2 * stage_elems(Ng, N, Naux, p.Ng8) * 8;
+  return b + 64 * 1024;
+}
+
+size_t mixed_full_footprint(int64_t Ng, int N, int n, int Naux) {
+  const Plan p = make_plan(Ng, N, n, Naux);
+  const FullPlan f = make_full_plan(Ng, N, Naux);
+  const size_t na = Naux, nN = N;
+  size_t b = p.large ? 0 : 2 * na * p.Ng8 * 2 + 2 * na * p.Na8 * 2;  // T_A, T_C (hi, lo)
+  b += (size_t)(f.splitsF + f.splitsFC) * na * nN * 4;                // M_A, M_C partial sums
+  b += 2 * na * nN * 8 + 2 * nN * p.Na8 * 8;                         // M_A, M_A - M_C, transposed
+  b += 4 * nN * p.Na8 * 2;                                           // their pieces
+  b += 2 * (size_t)f.splitsY * nN * nN * 4;                          // Phi_g^T M partial sums
   return b + 64 * 1024;
 }
 
@@ -2130,25 +2198,131 @@ cudaError_t mixed_enqueue_pre(MixedState* m, const double* C, cudaStream_t s, co
   return cudaSuccess;
 }
 
-// n > 128: the two T products (S = Psi_g Psi^T and Psi_g Psi_g^T, three
-// pieces each) with their energy sums sum V' o S^2 and sum W' o S^2; with
-// store = false only the energy sums are formed (T is not written).
-void enqueue_t_products(MixedState* m, cudaStream_t s, bool store) {
+// The two T products (S = Psi_g Psi^T and Psi_g Psi_g^T; three pieces each
+// for n > 128, two for n <= 128): T = f V' o S and f W' o S as hi/lo FP16
+// when `store`, and the energy sums sum V' o S^2, sum W' o S^2 when `energy`
+// (n > 128 only: the per-tile sums fill EpA / EpC).
+void enqueue_t_products(MixedState* m, cudaStream_t s, bool store, bool energy) {
   const long ng = m->Ng, na = m->Naux;
+  const bool p3 = m->large;
   GemmArgs t{};
   t.M = (int)na; t.Ncols = (int)ng; t.K = m->np; t.kchunk = m->np; t.sc = m->sc;
   t.status = m->status; t.tv = m->V32; t.ldv = m->Ng4; t.f_idx = SC_F_AB;
   t.th = store ? m->TA_h : nullptr; t.tl = store ? m->TA_l : nullptr;
-  t.ld_t = m->Ng8; t.epart = m->EpA; t.pieces3 = 1;
-  launch_gemm(m->m_psig128_m, m->m_psig128_h, m->m_psi128_m, m->m_psi128_h, m->m_psig128_l,
-              m->m_psi128_l, t, dim3((unsigned)m->xa, (unsigned)((ng + 127) / 128), 1), s);
+  t.ld_t = m->Ng8; t.epart = energy ? m->EpA : nullptr; t.pieces3 = p3 ? 1 : 0;
+  launch_gemm(m->m_psig128_m, m->m_psig128_h, m->m_psi128_m, m->m_psi128_h,
+              p3 ? m->m_psig128_l : m->m_psig128_m, p3 ? m->m_psi128_l : m->m_psi128_m, t,
+              dim3((unsigned)m->xa, (unsigned)((ng + 127) / 128), 1), s);
   GemmArgs tc = t;
   tc.Ncols = (int)na; tc.tv = m->W32; tc.ldv = m->Na4; tc.f_idx = SC_F_C;
   tc.th = store ? m->TC_h : nullptr; tc.tl = store ? m->TC_l : nullptr;
-  tc.ld_t = m->Na8; tc.epart = m->EpC;
-  launch_gemm(m->m_psig128_m, m->m_psig128_h, m->m_psig128_m, m->m_psig128_h, m->m_psig128_l,
-              m->m_psig128_l, tc, dim3((unsigned)m->xa, (unsigned)((na + 127) / 128), 1), s);
+  tc.ld_t = m->Na8; tc.epart = energy ? m->EpC : nullptr;
+  launch_gemm(m->m_psig128_m, m->m_psig128_h, m->m_psig128_m, m->m_psig128_h,
+              p3 ? m->m_psig128_l : m->m_psig128_m, p3 ? m->m_psig128_l : m->m_psig128_m, tc,
+              dim3((unsigned)m->xa, (unsigned)((na + 127) / 128), 1), s);
   count_launch(2);
+}
+
+cudaError_t mixed_full_prepare(MixedState* m) {
+  if (m->full_ready) return cudaSuccess;
+  const long ng = m->Ng, na = m->Naux;
+  const int N = m->N;
+  const FullPlan f = make_full_plan(ng, N, (int)na);
+  m->splitsF = f.splitsF; m->kchunkF = f.kchunkF;
+  m->splitsFC = f.splitsFC; m->kchunkFC = f.kchunkFC;
+  m->splitsY = f.splitsY; m->kchunkY = f.kchunkY;
+  cudaError_t e = cudaSuccess;
+#define FX(ptr, elems)                      \
+  do {                                      \
+    e = alloc(m, &(ptr), (elems));          \
+    if (e != cudaSuccess) return e;         \
+  } while (0)
+  if (!m->large) {
+    FX(m->TA_h, na * m->Ng8); FX(m->TA_l, na * m->Ng8);
+    FX(m->TC_h, na * m->Na8); FX(m->TC_l, na * m->Na8);
+  }
+  FX(m->MpA, (size_t)f.splitsF * na * N); FX(m->MpC, (size_t)f.splitsFC * na * N);
+  FX(m->DA, na * N); FX(m->DD, na * N);
+  FX(m->DAT64, (size_t)N * m->Na8); FX(m->DDT64, (size_t)N * m->Na8);
+  FX(m->DAT_m, (size_t)N * m->Na8); FX(m->DAT_h, (size_t)N * m->Na8);
+  FX(m->DDT_m, (size_t)N * m->Na8); FX(m->DDT_h, (size_t)N * m->Na8);
+  FX(m->Yp, (size_t)f.splitsY * N * N); FX(m->Zp, (size_t)f.splitsY * N * N);
+#undef FX
+  const auto F16 = CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  if (!m->large) {
+    e = make_map(&m->m_TA_h, m->TA_h, F16, 2, na, m->Ng8, 128, 64);
+    if (e == cudaSuccess) e = make_map(&m->m_TA_l, m->TA_l, F16, 2, na, m->Ng8, 128, 64);
+    if (e == cudaSuccess) e = make_map(&m->m_TC_h, m->TC_h, F16, 2, na, m->Na8, 128, 64);
+    if (e == cudaSuccess) e = make_map(&m->m_TC_l, m->TC_l, F16, 2, na, m->Na8, 128, 64);
+    if (e != cudaSuccess) return e;
+  }
+  e = make_map(&m->m_DAT_m, m->DAT_m, F16, 2, N, m->Na8, 128, 64);
+  if (e == cudaSuccess) e = make_map(&m->m_DAT_h, m->DAT_h, F16, 2, N, m->Na8, 128, 64);
+  if (e == cudaSuccess) e = make_map(&m->m_DDT_m, m->DDT_m, F16, 2, N, m->Na8, 128, 64);
+  if (e == cudaSuccess) e = make_map(&m->m_DDT_h, m->DDT_h, F16, 2, N, m->Na8, 128, 64);
+  if (e != cudaSuccess) return e;
+  m->full_ready = true;
+  return cudaSuccess;
+}
+
+// Full K_{mu nu} = dV (Phi_g^T M_A + M_A^T Phi_g - Phi_g^T M_C) with
+// M_A = (V o P) Phi and M_C = (W o Q) Phi_g: the three terms of Eq. rps in
+// Eq. rpsEx, contracted over the grid first (N_aux N_g N + N_aux N^2 flops
+// instead of the listed N N_g N_aux + N_g N^2).
+cudaError_t mixed_enqueue_full(MixedState* m, const double* C, double* Kf, cudaStream_t s,
+                               const StepHook& hook) {
+  if (!m->full_ready) return cudaErrorNotReady;
+  const long ng = m->Ng, na = m->Naux;
+  const int N = m->N;
+  cudaError_t e = mixed_enqueue_pre(m, C, s, hook);
+  if (e != cudaSuccess) return e;
+  hook(1, 1);
+  enqueue_t_products(m, s, true, false);
+  const unsigned tn = (unsigned)((N + 127) / 128);
+  {  // M_A = T_A Phi (A = T_A [g][R] hi/lo, B = Phi^T pieces [nu][R])
+    GemmArgs g{};
+    g.M = (int)na; g.Ncols = N; g.K = (int)ng; g.kchunk = m->kchunkF; g.out = m->MpA; g.ldo = N;
+    g.split_stride = na * N; g.sc = m->sc; g.scale_idx = SC_OUT_FA; g.status = m->status;
+    launch_gemm(m->m_TA_h, m->m_TA_l, m->m_phiT_m, m->m_phiT_h, m->m_TA_h, m->m_phiT_m, g,
+                dim3((unsigned)m->xa, tn, (unsigned)m->splitsF), s);
+    // M_C = T_C Phi_g (A = T_C [g][g'], B = Phi_g^T pieces [nu][g'])
+    GemmArgs gc = g;
+    gc.K = (int)na; gc.kchunk = m->kchunkFC; gc.out = m->MpC; gc.scale_idx = SC_OUT_FC;
+    launch_gemm(m->m_TC_h, m->m_TC_l, m->m_phigT_m, m->m_phigT_h, m->m_TC_h, m->m_phigT_m, gc,
+                dim3((unsigned)m->xa, tn, (unsigned)m->splitsFC), s);
+  }
+  const long cnt = na * N;
+  reduce_parts_kernel<<<blocks_for(cnt), 256, 0, s>>>(m->MpA, m->splitsF, nullptr, 0, cnt, m->DA,
+                                                      m->am + AM_FA);
+  reduce_parts_kernel<<<blocks_for(cnt), 256, 0, s>>>(m->MpA, m->splitsF, m->MpC, m->splitsFC, cnt,
+                                                      m->DD, m->am + AM_FD);
+  scales_kernel<<<1, 32, 0, s>>>(m->am, m->sc, 3);
+  count_launch(3);
+  e = transpose<double>(m->DA, na, N, N, m->DAT64, m->Na8, s);
+  if (e == cudaSuccess) e = transpose<double>(m->DD, na, N, N, m->DDT64, m->Na8, s);
+  if (e == cudaSuccess)
+    e = split_rows<double>(m->DAT64, N, m->Na8, m->Na8, m->sc, SC_FA, m->DAT_m, m->DAT_h, m->Na8, s);
+  if (e == cudaSuccess)
+    e = split_rows<double>(m->DDT64, N, m->Na8, m->Na8, m->sc, SC_FD, m->DDT_m, m->DDT_h, m->Na8, s);
+  if (e != cudaSuccess) return e;
+  {  // Y = Phi_g^T M_A and Z = Phi_g^T (M_A - M_C): A = Phi_g^T pieces, B = M^T pieces
+    GemmArgs g{};
+    g.M = N; g.Ncols = N; g.K = (int)na; g.kchunk = m->kchunkY; g.out = m->Yp; g.ldo = N;
+    g.split_stride = (long)N * N; g.sc = m->sc; g.scale_idx = SC_OUT_FY; g.status = m->status;
+    launch_gemm(m->m_phigT_m, m->m_phigT_h, m->m_DAT_m, m->m_DAT_h, m->m_phigT_m, m->m_DAT_m, g,
+                dim3(tn, tn, (unsigned)m->splitsY), s);
+    GemmArgs gz = g;
+    gz.out = m->Zp; gz.scale_idx = SC_OUT_FZ;
+    launch_gemm(m->m_phigT_m, m->m_phigT_h, m->m_DDT_m, m->m_DDT_h, m->m_phigT_m, m->m_DDT_m, gz,
+                dim3(tn, tn, (unsigned)m->splitsY), s);
+    count_launch(4);
+  }
+  final_kfull_kernel<<<blocks_for((long)N * N), 256, 0, s>>>(m->Zp, m->splitsY, m->Yp, m->splitsY,
+                                                             N, m->dV, Kf);
+  count_launch();
+  e = cudaGetLastError();
+  hook(1, 0);
+  return e;
 }
 
 cudaError_t mixed_enqueue_energy(MixedState* m, const double* C, double* Ex, cudaStream_t s,
@@ -2157,7 +2331,7 @@ cudaError_t mixed_enqueue_energy(MixedState* m, const double* C, double* Ex, cud
   if (e != cudaSuccess) return e;
   hook(1, 1);
   if (m->large)
-    enqueue_t_products(m, s, false);
+    enqueue_t_products(m, s, false, true);
   else
     launch_energy2(m->roles[0], m->roles[2], m->np, s);
   e = cudaGetLastError();
@@ -2181,7 +2355,7 @@ cudaError_t mixed_enqueue_pair(MixedState* m, cudaStream_t s, const StepHook& ho
     // n > 128: T_A = f_AB V o (Psi_g Psi^T) and T_C = f_C W o (Psi_g Psi_g^T)
     // as hi/lo FP16 with their energy sums, then M2 = T_A Psi, M3 = T_C Psi_g
     // and M1^T = T_A^T Psi_g (written transposed) on the tensor cores.
-    enqueue_t_products(m, s, true);
+    enqueue_t_products(m, s, true, true);
     GemmArgs g2{};
     g2.M = (int)na; g2.Ncols = n; g2.K = (int)ng; g2.kchunk = m->ychunkA; g2.out = m->M2p;
     g2.ldo = n; g2.split_stride = na * n; g2.sc = m->sc; g2.scale_idx = SC_OUT_AB;

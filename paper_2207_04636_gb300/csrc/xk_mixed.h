@@ -49,6 +49,16 @@ cudaError_t mixed_enqueue_post(MixedState* m, double* K_dev, double* Ex_dev, cud
 cudaError_t mixed_enqueue_energy(MixedState* m, const double* C_dev, double* Ex_dev,
                                  cudaStream_t s, const StepHook& hook);
 
+// Full exchange matrix K_{mu nu} (N x N, FP64) of Eq. rpsEx with the three
+// terms of Eq. rps: T = V o P and W o Q stored as hi/lo FP16, then
+// M_A = T_A Phi, M_C = T_C Phi_g, Y = Phi_g^T M_A, Z = Phi_g^T (M_A - M_C) on
+// the tensor cores and K = dV (Z + Y^T) in FP64.  mixed_full_prepare
+// allocates the extra scratch (mixed_full_footprint bytes) once per state.
+size_t mixed_full_footprint(int64_t Ng, int N, int n, int Naux);
+cudaError_t mixed_full_prepare(MixedState* m);
+cudaError_t mixed_enqueue_full(MixedState* m, const double* C_dev, double* Kfull_dev,
+                               cudaStream_t s, const StepHook& hook);
+
 // Pair contractions of several handles as one grouped launch per piece width
 // (64 or 128 columns): the roles of every n <= 128 member, longest first, in
 // launches of up to 16 roles; members with n > 128 run their own pair step.

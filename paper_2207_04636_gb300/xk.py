@@ -46,6 +46,7 @@ def lib():
         L.xk_build.argtypes = [c_d, c_d, c_d, c_d]
         L.xk_build_device.argtypes = [c_d, c_d, c_d, c_d, c_d]
         L.xk_energy.argtypes = [c_d, c_d, c_d]
+        L.xk_build_full.argtypes = [c_d, c_d, c_d]
         L.xk_energy_device.argtypes = [c_d, c_d, c_d, c_d]
         L.xk_ace.argtypes = [c_d, c_d, c_d, c_d, ctypes.POINTER(c_int)]
         L.xk_submit.argtypes = [c_d, c_d, ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)]
@@ -60,7 +61,8 @@ def lib():
         L.xk_batch_release.argtypes = [c_d]
         L.xk_last_error.restype = ctypes.c_char_p
         L.xk_kernel_launches.restype = ctypes.c_uint64
-        for f in ("xk_footprint", "xk_setup", "xk_build", "xk_build_device", "xk_energy",
+        for f in ("xk_footprint", "xk_setup", "xk_build", "xk_build_device", "xk_build_full",
+                  "xk_energy",
                   "xk_energy_device", "xk_ace",
                   "xk_submit", "xk_poll", "xk_release", "xk_timing_enable", "xk_timing_read",
                   "xk_exchange_energy_noalloc", "xk_batch_create", "xk_batch_build",
@@ -131,6 +133,13 @@ class Handle:
         e.g. torch tensor .data_ptr()) on the given cudaStream_t handle."""
         _check(lib().xk_build_device(self._h, ctypes.c_void_p(C_dev), ctypes.c_void_p(K_dev),
                                      ctypes.c_void_p(Ex_dev), ctypes.c_void_p(stream)))
+
+    def build_full(self, C):
+        """Full K_{mu nu} (N x N) from host C (xk_build_full)."""
+        C = _f64(C, (self.N, self.n), "C")
+        K = np.empty((self.N, self.N))
+        _check(lib().xk_build_full(self._h, _ptr(C), _ptr(K)))
+        return K
 
     def energy(self, C):
         """E_x alone from host C (N x n), without K (xk_energy)."""

@@ -72,6 +72,35 @@ def test_large_n(xk, n_occ):
     _check(xk, load_cell(spec))
 
 
+def _full_cells(cell1):
+    sh = [Shell(0, (0.35,), (1.0,)), Shell(1, (0.8,), (1.0,)), Shell(2, (1.1,), (1.0,))]
+    rag = build_cell(CellSpec("ragged", np.array([[0.1, 0.2, 0.3], [0.6, 0.5, 0.45],
+                                                   [0.3, 0.75, 0.8]]), 6.5, 13, sh, 7, 97, 9001))
+    big = config_spec(4, k=3)
+    big.n_occ = 150
+    return [cell1, rag, load_cell(config_spec(4, k=3)), load_cell(big)]
+
+
+def test_full_k(xk, cell1):
+    """xk_build_full on the tensor cores against the oracle's K_{mu nu} (Eq.
+    rpsEx, three terms of Eq. rps): the 8-centre cell, a ragged cell, the
+    27-centre cell with n = 54 and with n = 150 (the n > 128 pieces)."""
+    for c in _full_cells(cell1):
+        Kf0 = oracle.exx_rps_full(c.phi, c.idx, c.V, c.W, c.C, c.dV)
+        h = xk.Handle(c.phi, c.idx, c.V, c.W, c.dV, c.n, mode="f16x3")
+        try:
+            K, E = h.build(c.C)
+            Kf = h.build_full(c.C)
+            Kf2 = h.build_full(c.C)
+            K2, E2 = h.build(c.C)
+        finally:
+            h.release()
+        err = np.max(np.abs(Kf - Kf0))
+        assert err <= TOL_K, (c.spec.name, err)
+        assert np.array_equal(Kf, Kf2)
+        assert np.array_equal(K, K2) and E == E2  # the occ-RI build is unaffected
+
+
 def test_ace_on_tensor_path(xk, cell1):
     """K_ij of the tensor-core build is positive definite and factors; the
     reconstruction (xi diag(s) xi^T) C = K_{mu i} holds up to the asymmetry

@@ -134,6 +134,23 @@ def test_energy_leaves_build_state(xk, cell1, mode):
     assert ref[3] == after[3]
 
 
+def test_full_k(xk, cell1):
+    """xk_build_full (Eq. rpsEx, all three terms of Eq. rps) against the
+    oracle's K_{mu nu}; symmetric, and K C is the occ-RI rectangle."""
+    sh = [Shell(0, (0.35,), (1.0,)), Shell(1, (0.8,), (1.0,)), Shell(2, (1.1,), (1.0,))]
+    rag = build_cell(_spec("ragged", [[0.1, 0.2, 0.3], [0.6, 0.5, 0.45], [0.3, 0.75, 0.8]], 6.5,
+                           13, sh, 7, 97, 9001))
+    for c in (cell1, rag):
+        Kf0 = oracle.exx_rps_full(c.phi, c.idx, c.V, c.W, c.C, c.dV)
+        h = xk.Handle(c.phi, c.idx, c.V, c.W, c.dV, c.n)
+        K, _ = h.build(c.C)
+        Kf = h.build_full(c.C)
+        h.release()
+        assert np.max(np.abs(Kf - Kf0)) <= TOL_K
+        assert np.max(np.abs(Kf - Kf.T)) <= 1e-12 * np.max(np.abs(Kf))
+        assert np.max(np.abs(Kf @ c.C - K)) <= 1e-10 * np.max(np.abs(K))
+
+
 def test_ace_eigen_branch(xk):
     """A C whose K_ij is indefinite takes the eigen branch; the factor still
     reproduces K_{mu i} on the occupied space: (xi diag(s) xi^T) C = K_{mu i}."""
