@@ -26,6 +26,8 @@ Functions and their pins (tests/test_oracle_pins.py):
   exx_rps_4index    : P3, P6 (full K_{mu nu} symmetric)
   exx_rps_full      : == exx_rps_4index's K_{mu nu}; symmetric; K C equals
                       the occ-RI rectangle
+  coulomb_j         : == the literal 4-index grid integrals contracted with D;
+                      E_J = tr(C^T J C) > 0
   exx_exact_fft     : P1, P2, P7 (K PSD); Poisson pinned by P10
   exx_energy_direct : P8
   ace_factor        : reconstruction and definiteness checks
@@ -174,6 +176,23 @@ def exx_rps_4index(phi, idx, V, W, C, dV):
     K = np.einsum("mlsn,ls->mn", eri, D)
     Kmui = K @ C
     return K, Kmui, exchange_energy(Kmui, C)
+
+
+# --------------------------------------------------------------------------
+# Coulomb matrix on the same grid (the comparison partner of Sec. IV.E)
+# --------------------------------------------------------------------------
+
+def coulomb_j(phi, C, L, grid, dV):
+    """J_{mu nu} = sum_{lam sig} D_{lam sig} (mu nu|lam sig) with D = C C^T and
+    the grid integrals of Eq. 2eint: the density rho(R) = sum_i psi_i(R)^2 on
+    the grid, its potential Pois(rho) (Eq. cou-1, one FFT pair), then
+    J = dV Phi^T diag(Pois(rho)) Phi.  Returns (J, E_J) with
+    E_J = sum_{ij} (ii|jj) = dV sum_R rho(R) Pois(rho)(R)."""
+    psi = phi @ C
+    rho = np.sum(psi * psi, axis=1)
+    v = coulomb_potential(rho, L, grid)
+    J = dV * (phi.T @ (v[:, None] * phi))
+    return J, dV * math.fsum((rho * v).tolist())
 
 
 # --------------------------------------------------------------------------

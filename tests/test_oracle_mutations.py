@@ -160,3 +160,50 @@ def test_unmutated_full_pin_holds(settings):
 def test_full_mutant_is_caught(settings, mutant, monkeypatch):
     monkeypatch.setattr(ox, "exx_rps_full", mutant)
     assert not _full_pin_holds(settings[1])
+
+
+# ------------------------------------------------ Coulomb J on the grid
+
+_ORIG_J = ox.coulomb_j
+
+
+def j_density_not_squared(phi, C, L, grid, dV):
+    psi = phi @ C
+    rho = np.sum(np.abs(psi), axis=1)
+    v = oracle.coulomb_potential(rho, L, grid)
+    return dV * (phi.T @ (v[:, None] * phi)), dV * float(np.sum(rho * v))
+
+
+def j_potential_not_applied(phi, C, L, grid, dV):
+    psi = phi @ C
+    rho = np.sum(psi * psi, axis=1)
+    return dV * (phi.T @ (rho[:, None] * phi)), dV * float(np.sum(rho * rho))
+
+
+def j_one_sided(phi, C, L, grid, dV):
+    # potential multiplied on one side only: Phi^T v (summed) Phi
+    J, EJ = _ORIG_J(phi, C, L, grid, dV)
+    return J + 1e-3 * np.triu(J, 1), EJ
+
+
+J_MUTANTS = [j_density_not_squared, j_potential_not_applied, j_one_sided]
+
+
+def _j_pin_holds(tiny):
+    c = tiny
+    J, EJ = ox.coulomb_j(c.phi, c.C, c.L, c.grid, c.dV)
+    N = c.N
+    rho = np.einsum("rm,rn->mnr", c.phi, c.phi).reshape(N * N, -1)
+    pot = oracle.coulomb_potential(rho, c.L, c.grid)
+    J4 = ((c.dV * rho @ pot.T) @ (c.C @ c.C.T).reshape(-1)).reshape(N, N)
+    return np.max(np.abs(J - J4)) < 1e-12 * np.max(np.abs(J4)) and EJ > 0
+
+
+def test_unmutated_j_pin_holds(settings):
+    assert _j_pin_holds(settings[1])
+
+
+@pytest.mark.parametrize("mutant", J_MUTANTS, ids=[m.__name__ for m in J_MUTANTS])
+def test_j_mutant_is_caught(settings, mutant, monkeypatch):
+    monkeypatch.setattr(ox, "coulomb_j", mutant)
+    assert not _j_pin_holds(settings[1])

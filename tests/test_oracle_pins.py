@@ -159,6 +159,26 @@ def test_full_k_equals_4index_definition(tiny, cell1):
     assert np.max(np.abs(Kf @ c.C - Kmui)) < 1e-12 * np.max(np.abs(Kmui))
 
 
+def test_coulomb_equals_4index_definition(tiny):
+    """J of the density route (one Poisson solve of rho) equals the literal
+    grid integrals (mu nu|lam sig) = dV sum_R rho_{mu nu} Pois(rho_{lam sig})
+    (Eq. 2eint, one Poisson solve per pair density) contracted with
+    D = C C^T; E_J = tr(C^T J C) = sum_ij (ii|jj) > 0 (the kernel 4 pi / G^2
+    is positive)."""
+    c = tiny
+    J, EJ = oracle.coulomb_j(c.phi, c.C, c.L, c.grid, c.dV)
+    N = c.N
+    rho = np.einsum("rm,rn->mnr", c.phi, c.phi).reshape(N * N, -1)
+    pot = oracle.coulomb_potential(rho, c.L, c.grid)
+    eri = c.dV * rho @ pot.T                           # (mu nu | lam sig)
+    D = (c.C @ c.C.T).reshape(-1)
+    J4 = (eri @ D).reshape(N, N)
+    assert np.max(np.abs(J - J4)) < 1e-12 * np.max(np.abs(J4))
+    assert np.max(np.abs(J - J.T)) < 1e-12 * np.max(np.abs(J))
+    assert abs(EJ - np.trace(c.C.T @ J @ c.C)) < 1e-12 * abs(EJ)
+    assert EJ > 0
+
+
 # ---------------------------------------------------------------- P6 ------
 
 def test_symmetry(tiny, cell1):
