@@ -135,6 +135,25 @@ int xk_build_device(xk_handle* h, const double* C_dev, double* K_dev, double* Ex
 int xk_build_full(xk_handle* h, const double* C, double* K_out);
 
 /*
+ * Coulomb matrix on the same grid tables (the comparison partner of the
+ * exchange build, Sec. IV.E), for a cubic cell of side L with grid^3 = N_g
+ * points in the flat order of xk_setup:
+ *   rho(R) = sum_i psi_i(R)^2,  v = Pois(rho) (Eq. cou-1: 4 pi / G^2 on the
+ *   grid's reciprocal vectors G = 2 pi m / L, G = 0 removed),
+ *   J = dV Phi^T diag(v) Phi,   E_J = sum_ij (ii|jj) = dV sum_R rho(R) v(R),
+ * with D = C C^T as for E_x (closed shell: E_2e = 2 E_J + E_x).  The Poisson
+ * solve is a 3-D DFT done as three passes of 1-D DFTs in FP64 (O(g) per
+ * output, no FFT library); everything runs in FP64.  XK_FP64 handles only
+ * (the tensor-path handle keeps no FP64 basis table).  The first call
+ * allocates about 8 N_g (N + 6) bytes of scratch, admitted like xk_setup.
+ * C (host, N x n) is copied; J_out (host, N x N) and E_J (host) receive the
+ * results.  Errors: XK_EINVAL (null pointers, XK_F16X3 handle,
+ * grid^3 != N_g, L <= 0), XK_ENOMEM, XK_ECUDA.
+ */
+int xk_coulomb(xk_handle* h, int32_t grid, double L, const double* C, double* J_out,
+               double* E_J);
+
+/*
  * The exchange energy alone, without K (a cheap convergence monitor between
  * full builds): Eq. exoccri contracted with C gives the closed form
  *   E_x = -dV (2 sum_{g,R} V(g,R) P(g,R)^2 - sum_{g,g'} W(g,g') Q(g,g')^2),

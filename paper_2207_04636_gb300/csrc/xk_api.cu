@@ -85,6 +85,10 @@ struct xk_handle {
   // xk_build_full: K_{mu nu} (N x N); FP64 path also M_A, M_C (N_aux x N), Y, Z (N x N)
   double *Kf = nullptr, *MA = nullptr, *MC = nullptr, *Yf = nullptr, *Zf = nullptr;
   size_t full_extra = 0;  // bytes of the tensor path's full-K scratch, admitted on first use
+  // xk_coulomb (FP64 handles): allocated and admitted on first use
+  double *Jrho = nullptr, *Jv = nullptr, *Jphiv = nullptr, *Jd = nullptr, *Jout = nullptr;
+  double2 *Jc0 = nullptr, *Jc1 = nullptr, *Jtw = nullptr;
+  int Jg = 0;
   double *C = nullptr, *psi = nullptr, *psig = nullptr, *V2 = nullptr, *M1 = nullptr,
          *M2 = nullptr, *Q = nullptr, *M3 = nullptr, *L1 = nullptr, *L2 = nullptr,
          *L3 = nullptr, *K = nullptr, *Ex = nullptr, *work = nullptr, *red = nullptr;
@@ -138,6 +142,7 @@ size_t max_work(int64_t Ng, int N, int n, int Naux, bool ace_only = false) {
   acc(Naux, N, ng);     // full K: M_A = V2 Phi
   acc(Naux, N, Naux);   // full K: M_C = (W o Q) Phi_g
   acc(N, N, Naux);      // full K: Phi_g^T M
+  acc(N, N, ng);        // Coulomb J = Phi^T (v o Phi)
   return w;
 }
 
@@ -610,6 +615,79 @@ int xk_build_full(xk_handle* h, const double* C, double* K_out) {
       return fail(XK_ETIMEDOUT, "xk_build_full: a bounded wait inside a kernel gave up (code " +
                                     std::to_string(st) + ")");
   }
+  return XK_OK;
+}
+
+int xk_coulomb(xk_handle* h, int32_t grid, double L, const double* C, double* J_out,
+               double* E_J) {
+  if (!h || !C || !J_out || !E_J) return fail(XK_EINVAL, "xk_coulomb: NULL argument");
+  if (h->mode != XK_FP64)
+    return fail(XK_EINVAL, "xk_coulomb: needs an XK_FP64 handle (the FP64 basis table)");
+  if (grid <= 0 || (int64_t)grid * grid * grid != h->Ng)
+    return fail(XK_EINVAL, "xk_coulomb: grid^3 must equal N_g");
+  if (!(L > 0.0) || !std::isfinite(L)) return fail(XK_EINVAL, "xk_coulomb: L must be > 0");
+  std::lock_guard<std::mutex> lk(h->mu);
+  DeviceGuard g(h->device);
+  cudaStream_t s = h->stream;
+  const int N = h->N, n = h->n;
+  const size_t ng = (size_t)h->Ng;
+  if (h->Jg == 0) {  // first use: admit and allocate the scratch
+    const size_t extra = (ng * (size_t)N + 2 * ng + 4 * ng + (size_t)N * N + 1 + 2 * (size_t)grid) * 8;
+    size_t freeb = 0, totalb = 0;
+    XK_CUDA(cudaMemGetInfo(&freeb, &totalb));
+    {
+      std::lock_guard<std::mutex> al(g_admit_mu);
+      const size_t reserve = (size_t)1 << 30;
+      size_t budget = freeb > reserve ? freeb - reserve : 0;
+      if (const char* env = std::getenv("XK_HBM_BUDGET_BYTES")) {
+        const size_t cap = (size_t)std::strtoull(env, nullptr, 10);
+        budget = std::min(budget, cap > g_admitted ? cap - g_admitted : 0);
+      }
+      if (extra > budget)
+        return fail(XK_ENOMEM, "xk_coulomb: scratch of " + std::to_string(extra) +
+                                   " bytes exceeds the admission budget " + std::to_string(budget));
+      g_admitted += extra;
+    }
+    h->footprint += extra;
+    auto A = [&](double** p, size_t elems) { return dalloc(h, p, elems); };
+    XK_CUDA(A(&h->Jphiv, ng * N));
+    XK_CUDA(A(&h->Jrho, ng));
+    XK_CUDA(A(&h->Jv, ng));
+    double* cbuf = nullptr;
+    XK_CUDA(A(&cbuf, 4 * ng));
+    h->Jc0 = reinterpret_cast<double2*>(cbuf);
+    h->Jc1 = h->Jc0 + ng;
+    XK_CUDA(A(&h->Jout, (size_t)N * N + 1));
+    double* tw = nullptr;
+    XK_CUDA(A(&tw, 2 * (size_t)grid));
+    h->Jtw = reinterpret_cast<double2*>(tw);
+    std::vector<double> t(2 * (size_t)grid);
+    for (int m = 0; m < grid; ++m) {
+      const double a = 2.0 * M_PI * (double)m / (double)grid;
+      t[2 * m] = std::cos(a);
+      t[2 * m + 1] = std::sin(a);
+    }
+    XK_CUDA(cudaMemcpyAsync(tw, t.data(), t.size() * 8, cudaMemcpyHostToDevice, s));
+    XK_CUDA(cudaStreamSynchronize(s));
+    h->Jg = grid;
+  }
+  XK_CUDA(cudaMemcpyAsync(h->Ce, C, (size_t)N * n * 8, cudaMemcpyHostToDevice, s));
+  {
+    StepMark m(h, XK_STEP_ORBITALS);
+    xk::DGemm g1{(int)ng, n, N, h->phi, N, false, h->Ce, n, false, h->psi, n, 1.0, nullptr, 0, 0, h->work};
+    XK_CUDA(xk::dgemm(g1, s));
+  }
+  {  // density, Poisson solve, J = dV Phi^T (v o Phi), E_J = dV sum rho v
+    StepMark m(h, XK_STEP_PAIR);
+    XK_CUDA(xk::coulomb_potential_f64(h->psi, (long)ng, n, grid, L, h->Jtw, h->Jrho, h->Jc0, h->Jc1, s));
+    XK_CUDA(xk::potential_rows_f64(h->Jc0, h->phi, (long)ng, N, h->Jv, h->Jphiv, s));
+    xk::DGemm gj{N, N, (int)ng, h->phi, N, true, h->Jphiv, N, false, h->Jout, N, h->dV, nullptr, 0, 0, h->work};
+    XK_CUDA(xk::dgemm(gj, s));
+    XK_CUDA(xk::dot_f64(h->Jrho, h->Jv, (long)ng, h->dV, h->red, h->Jout + (size_t)N * N, s));
+  }
+  XK_CUDA(cudaMemcpyAsync(J_out, h->Jout, (size_t)N * N * 8, cudaMemcpyDeviceToHost, s));
+  XK_CUDA(cudaMemcpyAsync(E_J, h->Jout + (size_t)N * N, 8, cudaMemcpyDeviceToHost, s));
+  XK_CUDA(cudaStreamSynchronize(s));
   return XK_OK;
 }
 

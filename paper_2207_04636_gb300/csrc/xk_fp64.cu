@@ -243,6 +243,123 @@ cudaError_t neg_dot_f64(const double* a, const double* b, long len, double* work
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Coulomb J on the grid: density, Poisson solve by a 3-D DFT written as three
+// passes of 1-D DFTs (each output an O(g) sum in FP64; the grids here are
+// g <= ~100 per axis, so the O(g^4) total is a few hundred MFLOP), and
+// J = dV Phi^T diag(v) Phi.
+
+namespace {
+int blocks_of(long total) { return (int)std::max<long>(1, std::min<long>((total + 255) / 256, 152L * 16)); }
+}  // namespace
+
+// rho[R] = sum_i psi[R][i]^2, also as a complex grid function (imaginary 0).
+__global__ void density_kernel(const double* __restrict__ psi, long ng, int n,
+                               double* __restrict__ rho, double2* __restrict__ c) {
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < ng;
+       r += (long)gridDim.x * blockDim.x) {
+    const double* row = psi + r * n;
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s = fma(row[i], row[i], s);
+    rho[r] = s;
+    c[r] = make_double2(s, 0.0);
+  }
+}
+
+// One pass of a length-g DFT along `axis` (0 = slowest index) of a g^3 grid:
+// out[k] = sum_j in[j] exp(sign 2 pi i j k / g), tw[m] = (cos, sin)(2 pi m / g).
+__global__ void dft_axis_kernel(const double2* __restrict__ in, double2* __restrict__ out, int g,
+                                int axis, const double2* __restrict__ tw, double sign) {
+  const long count = (long)g * g * g;
+  const long stride = axis == 0 ? (long)g * g : axis == 1 ? g : 1;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count;
+       t += (long)gridDim.x * blockDim.x) {
+    const int k = (int)((t / stride) % g);
+    const long base = t - (long)k * stride;
+    double re = 0.0, im = 0.0;
+    int m = 0;  // j k mod g
+    for (int j = 0; j < g; ++j) {
+      const double2 x = in[base + (long)j * stride];
+      const double2 w = tw[m];
+      const double ws = sign * w.y;
+      re = fma(x.x, w.x, fma(-x.y, ws, re));
+      im = fma(x.x, ws, fma(x.y, w.x, im));
+      m += k;
+      if (m >= g) m -= g;
+    }
+    out[t] = make_double2(re, im);
+  }
+}
+
+// f(G) *= scale * 4 pi / |G|^2 with G = 2 pi m / L, m the signed frequency
+// index of each axis; the G = 0 term is set to zero.
+__global__ void coulomb_multiply_kernel(double2* __restrict__ f, int g, double L, double scale) {
+  const long count = (long)g * g * g;
+  const double two_pi_over_L = 6.283185307179586 / L;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count;
+       t += (long)gridDim.x * blockDim.x) {
+    const int i0 = (int)(t / ((long)g * g)), i1 = (int)((t / g) % g), i2 = (int)(t % g);
+    const int m0 = i0 <= (g - 1) / 2 ? i0 : i0 - g;
+    const int m1 = i1 <= (g - 1) / 2 ? i1 : i1 - g;
+    const int m2 = i2 <= (g - 1) / 2 ? i2 : i2 - g;
+    const double g2 = two_pi_over_L * two_pi_over_L * ((double)m0 * m0 + (double)m1 * m1 + (double)m2 * m2);
+    const double k = g2 > 0.0 ? scale * 12.566370614359172 / g2 : 0.0;
+    f[t] = make_double2(f[t].x * k, f[t].y * k);
+  }
+}
+
+// v[R] = Re(c[R]); out[R][nu] = v[R] phi[R][nu].
+__global__ void potential_rows_kernel(const double2* __restrict__ c, const double* __restrict__ phi,
+                                      long ng, int N, double* __restrict__ v, double* __restrict__ out) {
+  const long count = ng * N;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count;
+       t += (long)gridDim.x * blockDim.x) {
+    const long r = t / N;
+    const double vr = c[r].x;
+    out[t] = vr * phi[t];
+    if (t % N == 0) v[r] = vr;
+  }
+}
+
+__global__ void dot_scaled_stage2(const double* __restrict__ part, int np, double scale, double* out) {
+  __shared__ double sh[RED_TPB];
+  double s = 0.0;
+  for (int t = threadIdx.x; t < np; t += blockDim.x) s += part[t];
+  const double tot = block_sum(s, sh);
+  if (threadIdx.x == 0) *out = scale * tot;
+}
+
+cudaError_t coulomb_potential_f64(const double* psi, long ng, int n, int g, double L,
+                                  const double2* tw, double* rho, double2* c0, double2* c1,
+                                  cudaStream_t s) {
+  const int b = blocks_of(ng);
+  density_kernel<<<b, 256, 0, s>>>(psi, ng, n, rho, c0);
+  dft_axis_kernel<<<b, 256, 0, s>>>(c0, c1, g, 2, tw, -1.0);
+  dft_axis_kernel<<<b, 256, 0, s>>>(c1, c0, g, 1, tw, -1.0);
+  dft_axis_kernel<<<b, 256, 0, s>>>(c0, c1, g, 0, tw, -1.0);
+  coulomb_multiply_kernel<<<b, 256, 0, s>>>(c1, g, L, 1.0 / (double)ng);  // 1/N_g: inverse DFT
+  dft_axis_kernel<<<b, 256, 0, s>>>(c1, c0, g, 2, tw, 1.0);
+  dft_axis_kernel<<<b, 256, 0, s>>>(c0, c1, g, 1, tw, 1.0);
+  dft_axis_kernel<<<b, 256, 0, s>>>(c1, c0, g, 0, tw, 1.0);
+  count_launch(8);
+  return cudaGetLastError();
+}
+
+cudaError_t potential_rows_f64(const double2* c, const double* phi, long ng, int N, double* v,
+                               double* out, cudaStream_t s) {
+  potential_rows_kernel<<<blocks_of(ng * N), 256, 0, s>>>(c, phi, ng, N, v, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t dot_f64(const double* a, const double* b, long len, double scale, double* work,
+                    double* out, cudaStream_t s) {
+  dot_stage1<<<RED_BLOCKS, RED_TPB, 0, s>>>(a, b, len, work);
+  dot_scaled_stage2<<<1, RED_TPB, 0, s>>>(work, RED_BLOCKS, scale, out);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
 // Full K: K[mu][nu] = dV (Y[mu][nu] + Y[nu][mu] - Z[mu][nu]) (N x N).
 __global__ void assemble_full_kernel(const double* __restrict__ Y, const double* __restrict__ Z,
                                      int N, double dV, double* __restrict__ K) {

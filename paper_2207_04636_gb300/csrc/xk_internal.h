@@ -53,6 +53,20 @@ cudaError_t neg_dot_f64(const double* a, const double* b, long len, double* work
                         cudaStream_t s);
 size_t reduce_work_elems();
 
+// Coulomb potential of the density of psi (ng x n) on a cubic g^3 grid of
+// side L: rho[R] = sum_i psi[R][i]^2, then c0 = IDFT[(4 pi / G^2) DFT[rho]]
+// (G = 0 removed; the real part of c0 is the potential).  tw holds
+// (cos, sin)(2 pi m / g) for m < g; c1 is scratch of ng complex values.
+cudaError_t coulomb_potential_f64(const double* psi, long ng, int n, int g, double L,
+                                  const double2* tw, double* rho, double2* c0, double2* c1,
+                                  cudaStream_t s);
+// v[R] = Re(c[R]) and out[R][nu] = v[R] phi[R][nu].
+cudaError_t potential_rows_f64(const double2* c, const double* phi, long ng, int N, double* v,
+                               double* out, cudaStream_t s);
+// *out = scale * sum_j a[j] b[j] (fixed order); `work` holds reduce_work_elems() doubles.
+cudaError_t dot_f64(const double* a, const double* b, long len, double scale, double* work,
+                    double* out, cudaStream_t s);
+
 // K[mu][nu] = dV (Y[mu][nu] + Y[nu][mu] - Z[mu][nu]) for N x N matrices.
 cudaError_t assemble_full_f64(const double* Y, const double* Z, int N, double dV, double* K,
                               cudaStream_t s);

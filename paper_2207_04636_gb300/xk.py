@@ -47,6 +47,7 @@ def lib():
         L.xk_build_device.argtypes = [c_d, c_d, c_d, c_d, c_d]
         L.xk_energy.argtypes = [c_d, c_d, c_d]
         L.xk_build_full.argtypes = [c_d, c_d, c_d]
+        L.xk_coulomb.argtypes = [c_d, c_i32, ctypes.c_double, c_d, c_d, c_d]
         L.xk_energy_device.argtypes = [c_d, c_d, c_d, c_d]
         L.xk_ace.argtypes = [c_d, c_d, c_d, c_d, ctypes.POINTER(c_int)]
         L.xk_submit.argtypes = [c_d, c_d, ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)]
@@ -62,6 +63,7 @@ def lib():
         L.xk_last_error.restype = ctypes.c_char_p
         L.xk_kernel_launches.restype = ctypes.c_uint64
         for f in ("xk_footprint", "xk_setup", "xk_build", "xk_build_device", "xk_build_full",
+                  "xk_coulomb",
                   "xk_energy",
                   "xk_energy_device", "xk_ace",
                   "xk_submit", "xk_poll", "xk_release", "xk_timing_enable", "xk_timing_read",
@@ -140,6 +142,14 @@ class Handle:
         K = np.empty((self.N, self.N))
         _check(lib().xk_build_full(self._h, _ptr(C), _ptr(K)))
         return K
+
+    def coulomb(self, C, grid, L):
+        """(J (N x N), E_J) on a cubic grid of side L with grid^3 = N_g (xk_coulomb)."""
+        C = _f64(C, (self.N, self.n), "C")
+        J = np.empty((self.N, self.N))
+        EJ = np.empty(1)
+        _check(lib().xk_coulomb(self._h, int(grid), float(L), _ptr(C), _ptr(J), _ptr(EJ)))
+        return J, float(EJ[0])
 
     def energy(self, C):
         """E_x alone from host C (N x n), without K (xk_energy)."""

@@ -151,6 +151,25 @@ def test_full_k(xk, cell1):
         assert np.max(np.abs(Kf @ c.C - K)) <= 1e-10 * np.max(np.abs(K))
 
 
+def test_coulomb_j(xk, cell1):
+    """xk_coulomb (density, DFT-based Poisson solve, J = dV Phi^T diag(v) Phi,
+    all FP64) against the oracle's J and E_J; a ragged 13^3 grid too."""
+    sh = [Shell(0, (0.35,), (1.0,)), Shell(1, (0.8,), (1.0,)), Shell(2, (1.1,), (1.0,))]
+    rag = build_cell(_spec("ragged", [[0.1, 0.2, 0.3], [0.6, 0.5, 0.45], [0.3, 0.75, 0.8]], 6.5,
+                           13, sh, 7, 97, 9001))
+    for c in (cell1, rag):
+        J0, EJ0 = oracle.coulomb_j(c.phi, c.C, c.L, c.grid, c.dV)
+        h = xk.Handle(c.phi, c.idx, c.V, c.W, c.dV, c.n)
+        J, EJ = h.coulomb(c.C, c.grid, c.L)
+        J2, EJ2 = h.coulomb(c.C, c.grid, c.L)
+        with pytest.raises(xk.XKError):
+            h.coulomb(c.C, c.grid + 1, c.L)
+        h.release()
+        assert np.max(np.abs(J - J0)) <= 1e-10 * np.max(np.abs(J0))
+        assert abs(EJ - EJ0) <= 1e-10 * abs(EJ0)
+        assert np.array_equal(J, J2) and EJ == EJ2
+
+
 def test_ace_eigen_branch(xk):
     """A C whose K_ij is indefinite takes the eigen branch; the factor still
     reproduces K_{mu i} on the occupied space: (xi diag(s) xi^T) C = K_{mu i}."""
