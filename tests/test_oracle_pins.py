@@ -369,3 +369,35 @@ def test_ace_factor(cell1):
     Kij, xi, s, branch = oracle.ace_factor(K, c.C)
     assert branch == "cholesky"
     assert np.max(np.abs((xi * s) @ xi.T @ c.C - K)) < 1e-10 * np.max(np.abs(K))
+
+
+# ------------------------------------------------------- ISDF set-up -------
+
+def test_isdf_oracle_interpolates_and_fits(cell1):
+    """The least-squares fit of Eq. lsqfit interpolates: chi_g(R_g') = delta
+    at the interpolation points (the fit's columns at R_g are X_gg^{-1} X_gg);
+    with all points of a full-rank selection the fitted pair products are
+    exact everywhere; W is symmetric and equals V chi^T; V is the potential
+    of chi (the Poisson solver is pinned by P10)."""
+    c = cell1
+    chi, V, W, ridge = oracle.isdf_tables(c.phi, c.idx, c.L, c.grid)
+    assert ridge == 0.0
+    assert np.max(np.abs(chi[:, c.idx] - np.eye(c.Naux))) < 1e-8
+    assert np.max(np.abs(W - W.T)) == 0.0
+    Wr = V @ chi.T
+    assert np.max(np.abs(W - Wr)) < 1e-10 * np.max(np.abs(W))
+    # full-rank selection: the fit reproduces every pair product rho_mn(R)
+    idx = np.sort(select_points_exact(c.phi, 10 ** 6))
+    chi2, _, _, _ = oracle.isdf_tables(c.phi, idx, c.L, c.grid)
+    rho = np.einsum("rm,rn->rmn", c.phi, c.phi).reshape(c.Ng, -1)
+    fit = chi2.T @ rho[idx]
+    assert np.max(np.abs(fit - rho)) < 1e-7 * np.max(np.abs(rho))
+
+
+def test_isdf_oracle_matches_cell_tables(cell1):
+    """The generator's tables of the 8-centre cell (its own fit, Poisson and
+    W) agree with the oracle's for the same points."""
+    c = cell1
+    chi, V, W, _ = oracle.isdf_tables(c.phi, c.idx, c.L, c.grid)
+    assert np.max(np.abs(V - c.V)) < 1e-9 * np.max(np.abs(c.V))
+    assert np.max(np.abs(W - c.W)) < 1e-9 * np.max(np.abs(c.W))
