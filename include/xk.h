@@ -98,6 +98,36 @@ int xk_setup(int64_t Ng, int32_t N, int32_t n, int32_t Naux,
              double dV, int mode, xk_handle** out);
 
 /*
+ * The same set-up with the ISDF tables formed on the device in FP64 from the
+ * basis and the interpolation points (Sec. III.A, IV.C): on a cubic cell of
+ * side L with grid^3 = N_g points (flat order as above, dV = L^3 / N_g),
+ *   X_gg = (Phi_g Phi_g^T) o (Phi_g Phi_g^T),  X_gR = (Phi_g Phi^T) o (Phi_g Phi^T),
+ *   chi  = X_gg^{-1} X_gR  (Eq. lsqfit: blocked Cholesky and two blocked solves;
+ *          a ridge of 1e-14 tr(X_gg) / N_aux when the plain factorisation fails),
+ *   V    = Pois(chi_g) with the grid kernel 4 pi / G^2, G = 0 removed (Eq. rpsPot),
+ *   W    = V chi^T, symmetrised (Eq. thcpot),
+ * and then the handle as xk_setup would build it from those V and W.  The
+ * point selection stays with the caller (interp_idx).  XK_FP64 forms the
+ * tables in the handle's own buffers; XK_F16X3 holds FP64 temporaries of
+ * about 8 (N_g N + 2 N_aux N_g + 2 N_aux^2) bytes during the call, admitted
+ * with the handle.  Errors: as xk_setup, plus XK_EINVAL when grid^3 != N_g,
+ * L <= 0 or X_gg is not positive definite even with the ridge.
+ */
+int xk_setup_isdf(int64_t Ng, int32_t N, int32_t n, int32_t Naux,
+                  const double* basis_on_points, const int32_t* interp_idx,
+                  int32_t grid, double L, int mode, xk_handle** out);
+
+/*
+ * Read back tables of an XK_FP64 handle (e.g. those xk_setup_isdf formed):
+ * W_out (host, N_aux x N_aux, nullable), the rows rows[0..nrows) of V into
+ * V_rows_out (host, nrows x N_g; nrows may be 0), and the ridge added to
+ * X_gg (nullable; 0 for xk_setup handles).  Errors: XK_EINVAL (null handle,
+ * XK_F16X3 handle, bad rows), XK_ECUDA.
+ */
+int xk_tables(xk_handle* h, double* W_out, const int32_t* rows, int32_t nrows,
+              double* V_rows_out, double* ridge);
+
+/*
  * One exchange build, blocking.  C (host, N x n) are the occupied
  * coefficients; K_out (host, N x n) receives K_{mu i}; Ex (host) receives
  * E_x.  Builds on one handle are serialised.

@@ -96,6 +96,7 @@ struct xk_handle {
   double *Kij = nullptr, *Lf = nullptr, *U = nullptr, *Y = nullptr, *xi = nullptr,
          *sgn = nullptr;
   int* status = nullptr;
+  double ridge = 0.0;  // xk_setup_isdf: ridge added to X_gg (0 when none was needed)
 
   xk::MixedState* mixed = nullptr;
   Slot slots[kSlots];
@@ -143,7 +144,10 @@ size_t max_work(int64_t Ng, int N, int n, int Naux, bool ace_only = false) {
   acc(Naux, N, Naux);   // full K: M_C = (W o Q) Phi_g
   acc(N, N, Naux);      // full K: Phi_g^T M
   acc(N, N, ng);        // Coulomb J = Phi^T (v o Phi)
-  return w;
+  acc(Naux, Naux, N);   // ISDF set-up: Phi_g Phi_g^T
+  acc(Naux, ng, N);     // ISDF set-up: Phi_g Phi^T
+  acc(Naux, Naux, ng);  // ISDF set-up: W = V chi^T
+  return std::max(w, (size_t)Naux);  // the set-up also keeps the diagonal of X_gg here
 }
 
 Plan plan_fp64(int64_t Ng, int N, int n, int Naux) {
@@ -407,12 +411,15 @@ int xk_footprint(int64_t Ng, int32_t N, int32_t n, int32_t Naux, int mode, size_
   return fail(XK_EINVAL, "xk_footprint: unknown mode");
 }
 
-int xk_setup(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* phi,
-             const int32_t* idx, const double* V, const double* W, double dV, int mode,
-             xk_handle** out) {
+// xk_setup (V, W given) and xk_setup_isdf (V == W == nullptr: chi, V and W
+// formed on the device from phi and idx on a cubic grid^3 grid of side L).
+static int setup_impl(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* phi,
+               const int32_t* idx, const double* V, const double* W, double dV, int mode,
+               int32_t grid, double L, xk_handle** out) {
   if (!out) return fail(XK_EINVAL, "xk_setup: out is NULL");
   *out = nullptr;
-  if (!phi || !idx || !V || !W) return fail(XK_EINVAL, "xk_setup: NULL table pointer");
+  const bool isdf = V == nullptr && W == nullptr && grid > 0;
+  if (!phi || !idx || (!isdf && (!V || !W))) return fail(XK_EINVAL, "xk_setup: NULL table pointer");
   if (!valid_sizes(Ng, N, n, Naux)) return fail(XK_EINVAL, "xk_setup: invalid sizes");
   if (!(dV > 0.0) || !std::isfinite(dV)) return fail(XK_EINVAL, "xk_setup: dV must be > 0");
   if (mode != XK_FP64 && mode != XK_F16X3) return fail(XK_EINVAL, "xk_setup: unsupported mode");
@@ -424,7 +431,7 @@ int xk_setup(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* phi,
     if (std::adjacent_find(s.begin(), s.end()) != s.end())
       return fail(XK_EINVAL, "xk_setup: interp_idx has duplicates");
   }
-  {
+  if (!isdf) {
     double wmax = 0.0, asym = 0.0;
     const size_t na = (size_t)Naux;
     for (size_t i = 0; i < na; ++i)
@@ -439,6 +446,12 @@ int xk_setup(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* phi,
   size_t need = 0;
   int rc = xk_footprint(Ng, N, n, Naux, mode, &need);
   if (rc != XK_OK) return rc;
+  // the tensor path's ISDF set-up holds FP64 temporaries next to its tables:
+  // Phi, Phi_g, X_gg, chi, V, W and the product work (freed before return)
+  const size_t isdf_tmp = (isdf && mode != XK_FP64)
+      ? ((size_t)Ng * N + (size_t)Naux * N + 2 * (size_t)Naux * Naux + 2 * (size_t)Naux * Ng +
+         max_work(Ng, N, n, Naux) + (size_t)Naux) * 8 + (size_t)Naux * 4
+      : 0;
 
   int dev = 0;
   XK_CUDA(cudaGetDevice(&dev));
@@ -453,8 +466,8 @@ int xk_setup(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* phi,
       const size_t left = cap > g_admitted ? cap - g_admitted : 0;
       budget = std::min(budget, left);
     }
-    if (need > budget)
-      return fail(XK_ENOMEM, "xk_setup: footprint " + std::to_string(need) +
+    if (need + isdf_tmp > budget)
+      return fail(XK_ENOMEM, "xk_setup: footprint " + std::to_string(need + isdf_tmp) +
                                  " bytes exceeds the admission budget " + std::to_string(budget));
     g_admitted += need;
   }
@@ -508,14 +521,63 @@ int xk_setup(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* phi,
     XK_ALLOC(h->Yf, (size_t)N * N);
     XK_ALLOC(h->Zf, (size_t)N * N);
     e = cudaMemcpyAsync(h->phi, phi, ng * N * 8, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->V, V, na * ng * 8, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->W, W, na * na * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && !isdf)
+      e = cudaMemcpyAsync(h->V, V, na * ng * 8, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && !isdf)
+      e = cudaMemcpyAsync(h->W, W, na * na * 8, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->idx, idx, na * 4, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = xk::gather_rows_f64(h->phi, N, h->idx, Naux, N, h->phig, N, h->stream);
+    if (e == cudaSuccess && isdf)  // X_gg in Q, chi in V2 (both scratch of the build)
+      e = xk::isdf_tables_f64(h->phi, (long)ng, N, h->phig, Naux, grid, L, h->Q, h->V2, h->V, h->W,
+                              h->work, h->status, &h->ridge, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaErrorInvalidValue && isdf)
+      return bail(fail(XK_EINVAL, "xk_setup_isdf: X_gg is not positive definite even with the ridge"));
     if (e != cudaSuccess) return bail(cuda_fail(e, "xk_setup upload"));
   } else {
-    e = xk::mixed_create(Ng, N, n, Naux, phi, idx, V, W, dV, h->stream, &h->mixed);
+    if (isdf) {  // FP64 tables on the device first, then the tensor path's own tables
+      std::vector<void*> tmp;
+      auto talloc = [&](double** p, size_t elems) {
+        void* q = nullptr;
+        cudaError_t r = cudaMalloc(&q, std::max<size_t>(elems, 1) * 8);
+        if (r == cudaSuccess) tmp.push_back(q);
+        *p = static_cast<double*>(q);
+        return r;
+      };
+      auto release = [&]() {
+        for (void* q : tmp) cudaFree(q);
+        tmp.clear();
+      };
+      double *dphi = nullptr, *dphig = nullptr, *Xgg = nullptr, *chi = nullptr, *dV_ = nullptr,
+             *dW = nullptr, *wk = nullptr, *didx = nullptr;
+      e = talloc(&dphi, ng * N);
+      if (e == cudaSuccess) e = talloc(&dphig, na * N);
+      if (e == cudaSuccess) e = talloc(&Xgg, na * na);
+      if (e == cudaSuccess) e = talloc(&chi, na * ng);
+      if (e == cudaSuccess) e = talloc(&dV_, na * ng);
+      if (e == cudaSuccess) e = talloc(&dW, na * na);
+      if (e == cudaSuccess) e = talloc(&wk, std::max(max_work(Ng, N, n, Naux), na));
+      if (e == cudaSuccess) e = talloc(&didx, (na + 1) / 2);
+      int32_t* di = reinterpret_cast<int32_t*>(didx);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(dphi, phi, ng * N * 8, cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(di, idx, na * 4, cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess) e = xk::gather_rows_f64(dphi, N, di, Naux, N, dphig, N, h->stream);
+      if (e == cudaSuccess)
+        e = xk::isdf_tables_f64(dphi, (long)ng, N, dphig, Naux, grid, L, Xgg, chi, dV_, dW, wk,
+                                h->status, &h->ridge, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      if (e == cudaSuccess) {  // chi and X_gg are no longer needed
+        cudaFree(chi); cudaFree(Xgg);
+        tmp.erase(std::remove_if(tmp.begin(), tmp.end(),
+                                 [&](void* q) { return q == chi || q == Xgg; }), tmp.end());
+        e = xk::mixed_create(Ng, N, n, Naux, dphi, idx, dV_, dW, dV, h->stream, &h->mixed);
+      }
+      if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, 8, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      release();
+    } else {
+      e = xk::mixed_create(Ng, N, n, Naux, phi, idx, V, W, dV, h->stream, &h->mixed);
+    }
     if (e == cudaErrorInvalidValue)
       return bail(fail(XK_EINVAL, "xk_setup: basis columns are linearly dependent on the grid"));
     if (e != cudaSuccess) return bail(cuda_fail(e, "xk_setup mixed tables"));
@@ -529,6 +591,46 @@ int xk_setup(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* phi,
     if (e != cudaSuccess) return bail(cuda_fail(e, "xk_setup slots"));
   }
   *out = h;
+  return XK_OK;
+}
+
+int xk_setup(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* phi,
+             const int32_t* idx, const double* V, const double* W, double dV, int mode,
+             xk_handle** out) {
+  if (!V || !W) {
+    if (out) *out = nullptr;
+    return fail(XK_EINVAL, "xk_setup: NULL table pointer");
+  }
+  return setup_impl(Ng, N, n, Naux, phi, idx, V, W, dV, mode, 0, 0.0, out);
+}
+
+int xk_setup_isdf(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* phi,
+                  const int32_t* idx, int32_t grid, double L, int mode, xk_handle** out) {
+  if (out) *out = nullptr;
+  if (grid <= 0 || (int64_t)grid * grid * grid != Ng)
+    return fail(XK_EINVAL, "xk_setup_isdf: grid^3 must equal N_g");
+  if (!(L > 0.0) || !std::isfinite(L)) return fail(XK_EINVAL, "xk_setup_isdf: L must be > 0");
+  return setup_impl(Ng, N, n, Naux, phi, idx, nullptr, nullptr, L * L * L / (double)Ng, mode, grid,
+                    L, out);
+}
+
+int xk_tables(xk_handle* h, double* W_out, const int32_t* rows, int32_t nrows, double* V_rows_out,
+              double* ridge) {
+  if (!h) return fail(XK_EINVAL, "xk_tables: NULL handle");
+  if (h->mode != XK_FP64) return fail(XK_EINVAL, "xk_tables: needs an XK_FP64 handle");
+  if (nrows < 0 || (nrows > 0 && (!rows || !V_rows_out)))
+    return fail(XK_EINVAL, "xk_tables: bad row list");
+  for (int32_t i = 0; i < nrows; ++i)
+    if (rows[i] < 0 || rows[i] >= h->Naux) return fail(XK_EINVAL, "xk_tables: row out of range");
+  std::lock_guard<std::mutex> lk(h->mu);
+  DeviceGuard g(h->device);
+  const size_t na = (size_t)h->Naux, ng = (size_t)h->Ng;
+  if (W_out) XK_CUDA(cudaMemcpyAsync(W_out, h->W, na * na * 8, cudaMemcpyDeviceToHost, h->stream));
+  for (int32_t i = 0; i < nrows; ++i)
+    XK_CUDA(cudaMemcpyAsync(V_rows_out + (size_t)i * ng, h->V + (size_t)rows[i] * ng, ng * 8,
+                            cudaMemcpyDeviceToHost, h->stream));
+  XK_CUDA(cudaStreamSynchronize(h->stream));
+  if (ridge) *ridge = h->ridge;
   return XK_OK;
 }
 

@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(TPB) dgemm_kernel(DGemm g, int kchunk) {
       } else {
         double v = g.alpha * acc[i][j];
         if (HAD) v *= g.H[m * g.ldh + n];
+        if (g.beta != 0.0) v += g.beta * g.C[m * g.ldc + n];
         g.C[m * g.ldc + n] = v;
       }
     }
@@ -98,6 +99,7 @@ __global__ void splitk_reduce_kernel(DGemm g) {
     const long m = t / g.N, n = t % g.N;
     double v = g.alpha * s;
     if (g.H) v *= g.H[m * g.ldh + n];
+    if (g.beta != 0.0) v += g.beta * g.C[m * g.ldc + n];
     g.C[m * g.ldc + n] = v;
   }
 }
@@ -266,11 +268,11 @@ __global__ void density_kernel(const double* __restrict__ psi, long ng, int n,
   }
 }
 
-// One pass of a length-g DFT along `axis` (0 = slowest index) of a g^3 grid:
+// One pass of a length-g DFT along `axis` (0 = slowest index) of `count`
+// values (whole g^3 grids one after another):
 // out[k] = sum_j in[j] exp(sign 2 pi i j k / g), tw[m] = (cos, sin)(2 pi m / g).
 __global__ void dft_axis_kernel(const double2* __restrict__ in, double2* __restrict__ out, int g,
-                                int axis, const double2* __restrict__ tw, double sign) {
-  const long count = (long)g * g * g;
+                                int axis, const double2* __restrict__ tw, double sign, long count) {
   const long stride = axis == 0 ? (long)g * g : axis == 1 ? g : 1;
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count;
        t += (long)gridDim.x * blockDim.x) {
@@ -293,12 +295,14 @@ __global__ void dft_axis_kernel(const double2* __restrict__ in, double2* __restr
 
 // f(G) *= scale * 4 pi / |G|^2 with G = 2 pi m / L, m the signed frequency
 // index of each axis; the G = 0 term is set to zero.
-__global__ void coulomb_multiply_kernel(double2* __restrict__ f, int g, double L, double scale) {
-  const long count = (long)g * g * g;
+__global__ void coulomb_multiply_kernel(double2* __restrict__ f, int g, double L, double scale,
+                                        long count) {
+  const long g3 = (long)g * g * g;
   const double two_pi_over_L = 6.283185307179586 / L;
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count;
        t += (long)gridDim.x * blockDim.x) {
-    const int i0 = (int)(t / ((long)g * g)), i1 = (int)((t / g) % g), i2 = (int)(t % g);
+    const long u = t % g3;
+    const int i0 = (int)(u / ((long)g * g)), i1 = (int)((u / g) % g), i2 = (int)(u % g);
     const int m0 = i0 <= (g - 1) / 2 ? i0 : i0 - g;
     const int m1 = i1 <= (g - 1) / 2 ? i1 : i1 - g;
     const int m2 = i2 <= (g - 1) / 2 ? i2 : i2 - g;
@@ -329,20 +333,27 @@ __global__ void dot_scaled_stage2(const double* __restrict__ part, int np, doubl
   if (threadIdx.x == 0) *out = scale * tot;
 }
 
+cudaError_t poisson_c2c_f64(double2* c0, double2* c1, long nb, int g, double L,
+                            const double2* tw, cudaStream_t s) {
+  const long g3 = (long)g * g * g, count = nb * g3;
+  const int b = blocks_of(count);
+  dft_axis_kernel<<<b, 256, 0, s>>>(c0, c1, g, 2, tw, -1.0, count);
+  dft_axis_kernel<<<b, 256, 0, s>>>(c1, c0, g, 1, tw, -1.0, count);
+  dft_axis_kernel<<<b, 256, 0, s>>>(c0, c1, g, 0, tw, -1.0, count);
+  coulomb_multiply_kernel<<<b, 256, 0, s>>>(c1, g, L, 1.0 / (double)g3, count);  // 1/N_g: inverse
+  dft_axis_kernel<<<b, 256, 0, s>>>(c1, c0, g, 2, tw, 1.0, count);
+  dft_axis_kernel<<<b, 256, 0, s>>>(c0, c1, g, 1, tw, 1.0, count);
+  dft_axis_kernel<<<b, 256, 0, s>>>(c1, c0, g, 0, tw, 1.0, count);
+  count_launch(7);
+  return cudaGetLastError();
+}
+
 cudaError_t coulomb_potential_f64(const double* psi, long ng, int n, int g, double L,
                                   const double2* tw, double* rho, double2* c0, double2* c1,
                                   cudaStream_t s) {
-  const int b = blocks_of(ng);
-  density_kernel<<<b, 256, 0, s>>>(psi, ng, n, rho, c0);
-  dft_axis_kernel<<<b, 256, 0, s>>>(c0, c1, g, 2, tw, -1.0);
-  dft_axis_kernel<<<b, 256, 0, s>>>(c1, c0, g, 1, tw, -1.0);
-  dft_axis_kernel<<<b, 256, 0, s>>>(c0, c1, g, 0, tw, -1.0);
-  coulomb_multiply_kernel<<<b, 256, 0, s>>>(c1, g, L, 1.0 / (double)ng);  // 1/N_g: inverse DFT
-  dft_axis_kernel<<<b, 256, 0, s>>>(c1, c0, g, 2, tw, 1.0);
-  dft_axis_kernel<<<b, 256, 0, s>>>(c0, c1, g, 1, tw, 1.0);
-  dft_axis_kernel<<<b, 256, 0, s>>>(c1, c0, g, 0, tw, 1.0);
-  count_launch(8);
-  return cudaGetLastError();
+  density_kernel<<<blocks_of(ng), 256, 0, s>>>(psi, ng, n, rho, c0);
+  count_launch();
+  return poisson_c2c_f64(c0, c1, 1, g, L, tw, s);
 }
 
 cudaError_t potential_rows_f64(const double2* c, const double* phi, long ng, int N, double* v,

@@ -18,7 +18,7 @@ inline void count_launch(uint64_t k = 1) { g_launches.fetch_add(k, std::memory_o
 // FP64 SIMT path (xk_fp64.cu)
 // ---------------------------------------------------------------------------
 
-// C[M x N] = alpha * op(A) op(B) (o H), row-major.  op(A)[m,k] is
+// C[M x N] = alpha * op(A) op(B) (o H) + beta * C, row-major.  op(A)[m,k] is
 // A[k*lda + m] when transA else A[m*lda + k]; op(B)[k,n] is B[n*ldb + k] when
 // transB else B[k*ldb + n].  H (nullable, ldh) multiplies the result
 // element-wise (the Hadamard epilogue).  ksplit > 1 splits K: partial sums
@@ -34,6 +34,7 @@ struct DGemm {
   int ksplit;
   double* work;
   bool upperA;  // op(A) is upper triangular: K steps below a row tile are skipped
+  double beta;  // C = alpha op(A) op(B) (o H) + beta C (0: C is not read)
 };
 cudaError_t dgemm(const DGemm& g, cudaStream_t s);
 // Split count dgemm picks when DGemm::ksplit == 0 (work needs ksplit*M*N).
@@ -60,6 +61,12 @@ size_t reduce_work_elems();
 cudaError_t coulomb_potential_f64(const double* psi, long ng, int n, int g, double L,
                                   const double2* tw, double* rho, double2* c0, double2* c1,
                                   cudaStream_t s);
+// Pois applied to nb complex g^3 grids in c0 (result in c0; c1 scratch of the
+// same size): 3-D DFT, times 4 pi / G^2 (G = 0 removed), inverse 3-D DFT.
+// The kernel is real and even in G, so real and imaginary parts transform
+// independently (two real functions per complex grid).
+cudaError_t poisson_c2c_f64(double2* c0, double2* c1, long nb, int g, double L,
+                            const double2* tw, cudaStream_t s);
 // v[R] = Re(c[R]) and out[R][nu] = v[R] phi[R][nu].
 cudaError_t potential_rows_f64(const double2* c, const double* phi, long ng, int N, double* v,
                                double* out, cudaStream_t s);
@@ -70,6 +77,23 @@ cudaError_t dot_f64(const double* a, const double* b, long len, double scale, do
 // K[mu][nu] = dV (Y[mu][nu] + Y[nu][mu] - Z[mu][nu]) for N x N matrices.
 cudaError_t assemble_full_f64(const double* Y, const double* Z, int N, double dV, double* K,
                               cudaStream_t s);
+
+// GPU ISDF set-up (xk_isdf.cu), all FP64: from Phi (ng x N) and Phi_g
+// (na x N), X_gg into Xgg (na x na, overwritten by its Cholesky factor),
+// chi = X_gg^{-1} X_gR (na x ng), V = Pois(chi) on the cubic grid^3 grid of
+// side L (na x ng) and W = V chi^T symmetrised (na x na).  `work` holds the
+// split-K work of the products (dgemm_ksplit sizes) and at least na doubles.
+// A ridge of 1e-14 tr(X_gg)/na is added when the plain factorisation fails
+// (*ridge_out); cudaErrorInvalidValue if it still fails.
+cudaError_t isdf_tables_f64(const double* phi, long ng, int N, const double* phig, int na,
+                            int grid, double L, double* Xgg, double* chi, double* V, double* W,
+                            double* work, int* status, double* ridge_out, cudaStream_t s);
+// In-place blocked Cholesky (lower) of the n x n matrix A (lda); *status = 1
+// on a non-positive pivot.
+cudaError_t cholesky_blocked_f64(double* A, int n, long lda, int* status, cudaStream_t s);
+// B (n x ncols, ldb) := (L L^T)^{-1} B with the lower factor L (ldl).
+cudaError_t cholesky_solve_f64(const double* L, int n, long ldl, double* B, long ldb, long ncols,
+                               cudaStream_t s);
 
 // *out = -dV (2 sum_t V[t] P[t]^2 - sum_t W[t] Q[t]^2) over lenA and lenC
 // elements, in a fixed order; `work` holds reduce_work_elems() doubles.

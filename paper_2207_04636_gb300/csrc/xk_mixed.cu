@@ -1991,7 +1991,7 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   if (e == cudaSuccess) e = cudaMemsetAsync(m->status, 0, 16, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(m->idx, idx, na * 4, cudaMemcpyHostToDevice, s);
   // Phi pieces in three layouts: Phi [R][mu], Phi^T [mu][R], Phi_g^T [mu][g]
-  if (e == cudaSuccess) e = cudaMemcpyAsync(stage, phi, ng * N * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(stage, phi, ng * N * 8, cudaMemcpyDefault, s);
   if (e != cudaSuccess) return fin(e);
   // Orthonormalised basis on the grid: Phi^T Phi = L L^T (Cholesky, FP64) and
   // Phi' = Phi L^{-T}.  Each build forms Psi = Phi' (L^T C), which equals
@@ -2040,7 +2040,7 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
     const long chunk = std::max<long>(1, std::min<long>((long)na, N));
     for (long r0 = 0; r0 < (long)na && e == cudaSuccess; r0 += chunk) {
       const long rows = std::min<long>(chunk, (long)na - r0);
-      e = cudaMemcpyAsync(stage, V + (size_t)r0 * ng, rows * ng * 8, cudaMemcpyHostToDevice, s);
+      e = cudaMemcpyAsync(stage, V + (size_t)r0 * ng, rows * ng * 8, cudaMemcpyDefault, s);
       if (e != cudaSuccess) break;
       absmax_kernel<double><<<blocks_for(rows * ng), 256, 0, s>>>(stage, rows, ng, ng, m->am + AM_V);
       f64_to_f32_kernel<<<blocks_for(rows * p.Ng4), 256, 0, s>>>(stage, rows, ng, m->V32 + r0 * p.Ng4, p.Ng4);
@@ -2053,7 +2053,7 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
       e = cudaStreamSynchronize(s);  // the next chunk reuses the staging buffer
     }
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(stage, W, na * na * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(stage, W, na * na * 8, cudaMemcpyDefault, s);
   if (e != cudaSuccess) return fin(e);
   absmax_kernel<double><<<blocks_for(na * na), 256, 0, s>>>(stage, na, na, na, m->am + AM_W);
   f64_to_f32_kernel<<<blocks_for(na * p.Na4), 256, 0, s>>>(stage, na, na, m->W32, p.Na4);

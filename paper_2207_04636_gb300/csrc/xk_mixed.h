@@ -24,7 +24,8 @@ struct StepHook {
 // Device bytes of the mixed-precision tables and scratch.
 size_t mixed_footprint(int64_t Ng, int N, int n, int Naux);
 
-// Convert and upload the per-geometry tables (host FP64 inputs).
+// Convert and upload the per-geometry tables: FP64 phi, V, W in host or
+// device memory (copies use cudaMemcpyDefault), idx in host memory.
 cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
                          const int32_t* idx, const double* V, const double* W, double dV,
                          cudaStream_t s, MixedState** out);

@@ -43,6 +43,9 @@ def lib():
         L.xk_footprint.argtypes = [c_i64, c_i32, c_i32, c_i32, c_int, ctypes.POINTER(ctypes.c_size_t)]
         L.xk_setup.argtypes = [c_i64, c_i32, c_i32, c_i32, c_d, c_d, c_d, c_d, ctypes.c_double,
                                c_int, ctypes.POINTER(ctypes.c_void_p)]
+        L.xk_setup_isdf.argtypes = [c_i64, c_i32, c_i32, c_i32, c_d, c_d, c_i32, ctypes.c_double,
+                                    c_int, ctypes.POINTER(ctypes.c_void_p)]
+        L.xk_tables.argtypes = [c_d, c_d, c_d, c_i32, c_d, c_d]
         L.xk_build.argtypes = [c_d, c_d, c_d, c_d]
         L.xk_build_device.argtypes = [c_d, c_d, c_d, c_d, c_d]
         L.xk_energy.argtypes = [c_d, c_d, c_d]
@@ -62,7 +65,8 @@ def lib():
         L.xk_batch_release.argtypes = [c_d]
         L.xk_last_error.restype = ctypes.c_char_p
         L.xk_kernel_launches.restype = ctypes.c_uint64
-        for f in ("xk_footprint", "xk_setup", "xk_build", "xk_build_device", "xk_build_full",
+        for f in ("xk_footprint", "xk_setup", "xk_setup_isdf", "xk_tables", "xk_build",
+                  "xk_build_device", "xk_build_full",
                   "xk_coulomb",
                   "xk_energy",
                   "xk_energy_device", "xk_ace",
@@ -121,6 +125,32 @@ class Handle:
         _check(lib().xk_setup(Ng, N, self.n, Naux, _ptr(phi), _ptr(idx), _ptr(V), _ptr(W),
                               float(dV), MODES[mode], ctypes.byref(h)))
         self._h = h
+
+    @classmethod
+    def isdf(cls, phi, idx, grid, L, n, mode="fp64"):
+        """Handle whose chi, V and W are formed on the device from the basis and
+        the interpolation points of a cubic grid^3 cell of side L (xk_setup_isdf)."""
+        self = cls.__new__(cls)
+        phi = np.asarray(phi)
+        Ng, N = phi.shape
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        self.Ng, self.N, self.n, self.Naux, self.mode = Ng, N, int(n), idx.shape[0], mode
+        phi = _f64(phi, (Ng, N), "phi")
+        h = ctypes.c_void_p()
+        _check(lib().xk_setup_isdf(Ng, N, self.n, self.Naux, _ptr(phi), _ptr(idx), int(grid),
+                                   float(L), MODES[mode], ctypes.byref(h)))
+        self._h = h
+        return self
+
+    def tables(self, rows=()):
+        """(W, V[rows], ridge) of an XK_FP64 handle (xk_tables)."""
+        rows = np.ascontiguousarray(rows, dtype=np.int32)
+        W = np.empty((self.Naux, self.Naux))
+        Vr = np.empty((max(rows.size, 1), self.Ng))
+        rg = np.empty(1)
+        _check(lib().xk_tables(self._h, _ptr(W), _ptr(rows) if rows.size else None, rows.size,
+                               _ptr(Vr) if rows.size else None, _ptr(rg)))
+        return W, Vr[:rows.size], float(rg[0])
 
     def build(self, C):
         """Blocking build from host C (N x n): returns (K_{mu i}, E_x)."""

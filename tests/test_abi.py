@@ -29,7 +29,7 @@ def _declared():
 def test_exports_every_declared_symbol(L):
     names = _declared()
     assert {"xk_setup", "xk_build", "xk_submit", "xk_poll", "xk_release", "xk_footprint",
-            "xk_last_error", "xk_build_device", "xk_ace", "xk_energy", "xk_build_full", "xk_coulomb"} <= set(names)
+            "xk_last_error", "xk_build_device", "xk_ace", "xk_energy", "xk_build_full", "xk_coulomb", "xk_setup_isdf", "xk_tables"} <= set(names)
     for n in names:
         assert hasattr(L, n), n
 
@@ -87,6 +87,20 @@ def test_setup_rejects_invalid_inputs(L):
     assert L.xk_setup(64, 6, 3, 10, None, None, None, None, 0.1, 0, None) == xk.XK_EINVAL
 
 
+def test_setup_isdf_rejects_invalid_inputs(L):
+    phi, idx, V, W = _tables()
+    h = ctypes.c_void_p()
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    # N_g = 64 = 4^3: grid 5 does not match, L must be positive, idx checked as in xk_setup
+    assert L.xk_setup_isdf(64, 6, 3, 10, p(phi), p(idx), 5, 1.0, 0, ctypes.byref(h)) == xk.XK_EINVAL
+    assert "grid" in xk.last_error()
+    assert L.xk_setup_isdf(64, 6, 3, 10, p(phi), p(idx), 4, 0.0, 0, ctypes.byref(h)) == xk.XK_EINVAL
+    bad = idx.copy()
+    bad[1] = bad[0]
+    assert L.xk_setup_isdf(64, 6, 3, 10, p(phi), p(bad), 4, 1.0, 0, ctypes.byref(h)) == xk.XK_EINVAL
+    assert L.xk_setup_isdf(64, 6, 3, 10, None, p(idx), 4, 1.0, 0, ctypes.byref(h)) == xk.XK_EINVAL
+
+
 def test_null_handles_and_tickets(L):
     buf = np.zeros(4)
     p = buf.ctypes.data_as(ctypes.c_void_p)
@@ -101,6 +115,7 @@ def test_null_handles_and_tickets(L):
     assert L.xk_energy(None, p, p) == xk.XK_EINVAL
     assert L.xk_build_full(None, p, p) == xk.XK_EINVAL
     assert L.xk_coulomb(None, 4, 1.0, p, p, p) == xk.XK_EINVAL
+    assert L.xk_tables(None, p, None, 0, None, None) == xk.XK_EINVAL
     assert L.xk_energy_device(None, p, p, None) == xk.XK_EINVAL
     b = ctypes.c_void_p()
     assert L.xk_batch_create(None, 0, ctypes.byref(b)) == xk.XK_EINVAL
