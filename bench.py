@@ -57,7 +57,8 @@ def parse():
     p.add_argument("--mode", default="f16x3", choices=["f16x3", "fp64"])
     p.add_argument("--impl", default="xk", choices=["xk", "reference"])
     p.add_argument("--config", type=int, default=2,
-                   help="2: the 64-centre cell (the metric's workload); 1 or 4 for smaller cases")
+                   help="2: the 64-centre cell (the metric's workload); 1 or 4 for smaller cases; "
+                        "3: the 216-centre cell (tables formed on the GPU, one JSON line)")
     p.add_argument("--k", type=int, default=None, help="lattice size of config 4 (k^3 centres)")
     p.add_argument("--n-occ", type=int, default=None,
                    help="override the number of occupied orbitals (profiling cases only)")
@@ -366,10 +367,81 @@ def batch_and_mixed_serving(xk, cell64, count, seed=4000):
     return out
 
 
+def run_config3(args):
+    """The 216-centre cell (N = 2808, n = 432, 90^3 grid, N_aux = 13500): its
+    ISDF tables are formed on the GPU (xk_setup_isdf, FP64) because the host
+    fit takes hours.  Sequence: the FP64 handle's set-up and one FP64 build;
+    its V and W read back to the host (79 GB); the handle released; the
+    tensor-path handle set up from those tables; timed builds; the closed-form
+    E_x of the oracle on the host from the same tables (parity at full size)."""
+    import torch
+    import oracle
+    import paper_2207_04636_gb300 as xk
+    from paper_2207_04636_gb300 import build as xkbuild
+    from cellgen import build_cell
+    xkbuild.build_library()
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    cell = build_cell(config_spec(3), fit=False)
+    t_inputs = time.perf_counter() - t0
+    N, n, Ng, Na = cell.N, cell.n, cell.Ng, cell.Naux
+    steps = args.steps or 10
+    warm = max(3, args.warmup)
+    Cs = pseudo_scf_sequence(cell.S, cell.C, steps + warm, 3000)
+    C_last = Cs[-1]
+    t0 = time.perf_counter()
+    hf = xk.Handle.isdf(cell.phi, cell.idx, cell.grid, cell.L, n, mode="fp64")
+    t_isdf = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    K64, E64 = hf.build(C_last)
+    t_fp64 = time.perf_counter() - t0
+    W, V, ridge = hf.tables(np.arange(Na))
+    hf.release()
+    t0 = time.perf_counter()
+    h = xk.Handle(cell.phi, cell.idx, V, W, cell.dV, n, mode="f16x3")
+    t_mixed_setup = time.perf_counter() - t0
+    Cd = [torch.from_numpy(C).cuda() for C in Cs]
+    Kd = torch.empty((N, n), dtype=torch.float64, device="cuda")
+    Ed = torch.empty(1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(None)
+    ms, launches, st = time_device_builds(xk, h, Cd, Kd, Ed, stream, warm, steps, torch)
+    clocks = sampler.stop()
+    K, E = Kd.cpu().numpy(), float(Ed.item())
+    h.release()
+    line = {"metric": "K builds/s (216-centre cell)", "value": steps / (ms * 1e-3),
+            "unit": "builds/s", "n_gpus": 1, "steps": steps, "warmup": warm,
+            "ms_per_step": ms / steps, "higher_is_better": True, "dtype": "f16x3",
+            "data": "synthetic (seeded cell generator; ISDF tables formed on the GPU)",
+            "config": {"workload": "216-centre 3x3x3 diamond supercell, L=20.22 bohr, N=2808, "
+                                   "n_occ=432, 90^3 grid, N_aux=13500", "N": N, "n": n,
+                       "N_g": Ng, "N_aux": Na},
+            "step_ms": {k: v[0] / max(1, v[1]) for k, v in st.items() if v[1]},
+            "gpu_launches": int(launches), "clocks": clocks,
+            "setup_s": {"host_inputs": t_inputs, "isdf_fp64_on_gpu": t_isdf,
+                        "tensor_handle_from_tables": t_mixed_setup},
+            "isdf_ridge": ridge,
+            "fp64_path": {"s_per_build": t_fp64, "dE_x_vs_fp64": abs(E - E64),
+                          "max_dK_vs_fp64": float(np.max(np.abs(K - K64))), "E_x_fp64": E64},
+            "E_x": E}
+    if not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        E0 = oracle.exx_energy_direct(cell.phi, cell.idx, V, W, C_last, cell.dV)
+        line["parity_oracle_closed_form"] = {
+            "E_x_oracle": E0, "dE_x_fp64_path": abs(E64 - E0), "dE_x_tensor_path": abs(E - E0),
+            "oracle_s": time.perf_counter() - t0,
+            "note": "oracle E_x from the closed form -dV(2 sum V P^2 - sum W Q^2) on the host, "
+                    "same tables and C as the last build"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.config == 3:
+        run_config3(args)
         return
     import torch
     import paper_2207_04636_gb300 as xk

@@ -78,8 +78,8 @@ class Cell:
     S    : (N, N) grid overlap dV * phi^T phi
     C    : (N, n) occupied coefficients with C^T S C = I
     idx  : (N_aux,) interpolation points as flat grid indices, ascending
-    V    : (N_aux, N_g) potentials of the ISDF functions
-    W    : (N_aux, N_aux) symmetric THC potential
+    V    : (N_aux, N_g) potentials of the ISDF functions (None when not fitted)
+    W    : (N_aux, N_aux) symmetric THC potential (None when not fitted)
     chi  : (N_aux, N_g) ISDF functions, or None when not kept
     """
     spec: CellSpec
@@ -418,8 +418,12 @@ def pseudo_scf_sequence(S: np.ndarray, C0: np.ndarray, count: int, seed: int,
 # Cell assembly
 # --------------------------------------------------------------------------
 
-def build_cell(spec: CellSpec, keep_chi: bool = False, idx: Optional[np.ndarray] = None) -> Cell:
-    """Generate every input of one cell from its spec (deterministic in the seed)."""
+def build_cell(spec: CellSpec, keep_chi: bool = False, idx: Optional[np.ndarray] = None,
+               fit: bool = True) -> Cell:
+    """Generate every input of one cell from its spec (deterministic in the seed).
+    With fit=False the ISDF fit, V and W are left out (V = W = None): the basis,
+    the coefficients and the interpolation points only, for a set-up that forms
+    the tables elsewhere."""
     rng = np.random.default_rng(spec.seed)
     jit = rng.uniform(-spec.jitter, spec.jitter, size=spec.frac.shape)
     centres = spec.frac * spec.L + jit
@@ -446,6 +450,9 @@ def build_cell(spec: CellSpec, keep_chi: bool = False, idx: Optional[np.ndarray]
     idx = np.sort(np.asarray(idx, dtype=np.int64))
     if idx.size < spec.n_aux:
         raise RuntimeError(f"only {idx.size} independent interpolation points (< {spec.n_aux})")
+    if not fit:
+        return Cell(spec, centres, dV, np.ascontiguousarray(phi), S, C, idx.astype(np.int32),
+                    None, None, None, 0.0, cond_S)
     chi, ridge = fit_isdf(phi, idx)
     V = potentials(chi, spec.L, spec.grid)
     W = thc_potential(V, chi)
