@@ -521,7 +521,8 @@ __global__ void final_kfull_kernel(const float* __restrict__ Z, int nz, const fl
 // sets; every kDrain k-blocks (192 terms) the epilogue adds A0 + A1 of the
 // finished set into FP32 registers (round to nearest) while the MMA warp
 // moves on to the other set.
-// Warps 0-3: epilogue (thread = row); warp 4: TMA producer; warp 5: MMA.
+// Warps 0-7: epilogue (warp w: rows of lane quadrant w % 4, columns
+// 64 (w / 4) .. +63; thread = row); warp 8: TMA producer; warp 9: MMA.
 
 struct GemmArgs {
   int M, Ncols, K, kchunk;
@@ -569,8 +570,11 @@ constexpr int G_STAGES = 3;
 constexpr int G_STAGE_BYTES = 4 * 16384;
 constexpr int G_SMEM = G_STAGES * G_STAGE_BYTES + 1024;
 constexpr int kDrain = 3;
+constexpr int kGemmEpi = 8;                      // epilogue warps (4 lane quadrants x 2 column halves)
+constexpr int kGemmTma = kGemmEpi, kGemmMma = kGemmEpi + 1;
+constexpr int kGemmThreads = 32 * (kGemmEpi + 2);
 
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kGemmThreads, 1)
     gemm_kernel(const __grid_constant__ CUtensorMap mAm, const __grid_constant__ CUtensorMap mAh,
                 const __grid_constant__ CUtensorMap mBm, const __grid_constant__ CUtensorMap mBh,
                 const __grid_constant__ CUtensorMap mAl, const __grid_constant__ CUtensorMap mBl,
@@ -604,13 +608,13 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(&set_ready[s], 1);
-      mbar_init(&set_free[s], 4);  // one arrival per epilogue warp
+      mbar_init(&set_free[s], kGemmEpi);  // one arrival per epilogue warp
     }
     mbar_init(&drain, 1);
     abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == 5) {
+  if (warp == kGemmMma) {
     tmem_alloc(&tslot, 512);
     tmem_relinquish();
   }
@@ -619,7 +623,7 @@ __global__ void __launch_bounds__(192, 1)
   tc_fence_after();
   const uint32_t tbase = tslot;
 
-  if (warp == 4 && lane == 0) {
+  if (warp == kGemmTma && lane == 0) {
     prefetch_tmap(&mAm); prefetch_tmap(&mAh); prefetch_tmap(&mBm); prefetch_tmap(&mBh);
     int last_parity[G_STAGES] = {-1, -1, -1};
     int it = 0;  // k-blocks issued by this CTA over all its tiles
@@ -668,7 +672,7 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int s = 0; s < ns; ++s)
       if (last_parity[s] >= 0) mbar_wait(&full[s], last_parity[s]);
-  } else if (warp == 5) {
+  } else if (warp == kGemmMma) {
     // whole warp runs the loop; one elected lane issues each MMA and commit
     const uint32_t idesc = idesc_f16(128, 128, false, g.a_mn != 0, g.b_mn != 0);
     // K-major tiles step 32 B per K = 16; MN-major tiles step 16 rows (2 KB)
@@ -752,9 +756,14 @@ __global__ void __launch_bounds__(192, 1)
     if (elect_one()) mma_commit(&drain);
     __syncwarp();
     mbar_wait_warp(&drain, 0);
-  } else if (warp < 4) {
-    const int r = warp * 32 + lane;
-    const uint32_t lane_off = static_cast<uint32_t>(warp * 32) << 16;
+  } else if (warp < kGemmEpi) {
+    // warp w: TMEM lane quadrant w % 4 (rows), column half w / 4 (64 columns)
+    const int quad = warp & 3, half = warp >> 2;
+    const int r = quad * 32 + lane;
+    const int cb = 64 * half;
+    const uint32_t lane_off = static_cast<uint32_t>(quad * 32) << 16;
+    __shared__ float prow_mx[2][128], prow_nrm[2][128];
+    __shared__ double ered[kGemmEpi];
     // Every epilogue warp walks all of the CTA's tiles (after a failed wait
     // without waiting further), so the named barriers below match up.
     int G0 = 0;
@@ -763,9 +772,9 @@ __global__ void __launch_bounds__(192, 1)
     tile_at(tile, bx, by, bz);
     const int m0 = bx * 128, n0 = by * 128;
     const int ngroups = (kblocks(bz) + kd - 1) / kd;
-    float run[128];
+    float run[64];
 #pragma unroll
-    for (int c = 0; c < 128; ++c) run[c] = 0.0f;
+    for (int c = 0; c < 64; ++c) run[c] = 0.0f;
     bool ok = true;
     for (int gi = 0; gi < ngroups; ++gi) {
       const int grp = G0 + gi, set = grp & 1;
@@ -777,10 +786,10 @@ __global__ void __launch_bounds__(192, 1)
       }
       tc_fence_after();
 #pragma unroll
-      for (int c = 0; c < 128; c += 16) {
+      for (int c = 0; c < 64; c += 16) {
         uint32_t a0[16], a1[16];
-        tmem_ld16(tbase + lane_off + set * 256 + c, a0);
-        tmem_ld16(tbase + lane_off + set * 256 + 128 + c, a1);
+        tmem_ld16(tbase + lane_off + set * 256 + cb + c, a0);
+        tmem_ld16(tbase + lane_off + set * 256 + 128 + cb + c, a1);
         tmem_wait_ld();
 #pragma unroll
         for (int j = 0; j < 16; ++j) run[c + j] += __uint_as_float(a0[j]) + __uint_as_float(a1[j]);
@@ -793,28 +802,34 @@ __global__ void __launch_bounds__(192, 1)
     ok = ok && !abort_flag;
     const float scale = g.sc[g.scale_idx];
     if (g.pm) {
-      // orbital rows: values, row norm, per-row grid, pieces
+      // orbital rows: values, row norm, per-row grid (over both column halves), pieces
       float mx = 0.0f, nrm = 0.0f;
       const float G = g.sc[g.piece_idx];
 #pragma unroll
-      for (int c = 0; c < 128; ++c) {
-        const float v = (ok && c < g.Ncols) ? run[c] * scale : 0.0f;
+      for (int c = 0; c < 64; ++c) {
+        const float v = (ok && cb + c < g.Ncols) ? run[c] * scale : 0.0f;
         run[c] = v;
         nrm = fmaf(v, v, nrm);
         mx = fmaxf(mx, fabsf(v * G));
       }
-      {
+      prow_mx[half][r] = mx;
+      prow_nrm[half][r] = nrm;
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * kGemmEpi) : "memory");
+      mx = fmaxf(prow_mx[0][r], prow_mx[1][r]);
+      nrm = prow_nrm[0][r] + prow_nrm[1][r];
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * kGemmEpi) : "memory");  // rewritten by the next tile
+      if (half == 0) {
         float wn = (m0 + r < g.M) ? nrm : 0.0f;
         for (int o = 16; o > 0; o >>= 1) wn = fmaxf(wn, __shfl_xor_sync(0xffffffffu, wn, o));
         if (lane == 0) atomicMax(g.rn2, __float_as_uint(wn * 1.0001f));
       }
       if (m0 + r < g.M) {
         const float q = row_grid(mx);
-        __half* mrow = g.pm + (long)(m0 + r) * g.ld_p;
-        __half* hrow = g.ph + (long)(m0 + r) * g.ld_p;
+        __half* mrow = g.pm + (long)(m0 + r) * g.ld_p + cb;
+        __half* hrow = g.ph + (long)(m0 + r) * g.ld_p + cb;
 #pragma unroll
-        for (int c0 = 0; c0 < 128; c0 += 8) {
-          if (c0 >= g.ld_p) break;
+        for (int c0 = 0; c0 < 64; c0 += 8) {
+          if (cb + c0 >= g.ld_p) break;
           uint32_t mw[4], hw[4];
 #pragma unroll
           for (int j = 0; j < 8; j += 2) {
@@ -837,8 +852,8 @@ __global__ void __launch_bounds__(192, 1)
       const float* vrow = g.tv + x * g.ldv;
       double esum = 0.0;
 #pragma unroll
-      for (int c0 = 0; c0 < 128; c0 += 8) {
-        const long col = (long)n0 + c0;
+      for (int c0 = 0; c0 < 64; c0 += 8) {
+        const long col = (long)n0 + cb + c0;
         if (col >= g.ld_t) break;
         float v[8];
         if (xok && col + 8 <= g.Ncols) {
@@ -872,28 +887,30 @@ __global__ void __launch_bounds__(192, 1)
         }
       }
       if (g.epart) {
-        __shared__ double ered[4];
         for (int o = 16; o > 0; o >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, o);
         if (lane == 0) ered[warp] = esum;
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        if (r == 0)
-          g.epart[(long)by * g.tiles_x + bx] = ered[0] + ered[1] + ered[2] + ered[3];
-        asm volatile("bar.sync 1, 128;" ::: "memory");  // ered is rewritten by the next tile
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * kGemmEpi) : "memory");
+        if (warp == 0 && lane == 0) {
+          double t = 0.0;
+          for (int w = 0; w < kGemmEpi; ++w) t += ered[w];
+          g.epart[(long)by * g.tiles_x + bx] = t;
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * kGemmEpi) : "memory");  // rewritten by the next tile
       }
     } else if (g.transposed) {
       const long row = (long)m0 + r;
       if (row < g.M) {
 #pragma unroll
-        for (int c = 0; c < 128; ++c) {
-          const int col = n0 + c;
+        for (int c = 0; c < 64; ++c) {
+          const int col = n0 + cb + c;
           if (col < g.Ncols) g.out[(long)col * g.ldo + row] = ok ? run[c] * scale : 0.0f;
         }
       }
     } else if (m0 + r < g.M) {
       float* orow = g.out + (long)bz * g.split_stride + (long)(m0 + r) * g.ldo;
 #pragma unroll
-      for (int c = 0; c < 128; ++c) {
-        const int col = n0 + c;
+      for (int c = 0; c < 64; ++c) {
+        const int col = n0 + cb + c;
         if (col < g.Ncols) orow[col] = ok ? run[c] * scale : 0.0f;
       }
     }
@@ -901,7 +918,7 @@ __global__ void __launch_bounds__(192, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 5) tmem_dealloc(tbase, 512);
+  if (warp == kGemmMma) tmem_dealloc(tbase, 512);
 }
 
 // SMs of the current device (cached per device).
@@ -927,7 +944,7 @@ void launch_gemm(const CUtensorMap& mAm, const CUtensorMap& mAh, const CUtensorM
   g.tiles_z = (int)tiles.z;
   const long total = (long)tiles.x * tiles.y * tiles.z;
   const unsigned ctas = (unsigned)std::max<long>(1, std::min<long>(total, sm_count()));
-  gemm_kernel<<<ctas, 192, G_SMEM, s>>>(mAm, mAh, mBm, mBh, mAl, mBl, g);
+  gemm_kernel<<<ctas, kGemmThreads, G_SMEM, s>>>(mAm, mAh, mBm, mBh, mAl, mBl, g);
 }
 
 // ============================================================ pair kernel
@@ -1803,7 +1820,8 @@ size_t mixed_footprint(int64_t Ng, int N, int n, int Naux) {
   b += 2 * ng * p.Np * 2 + 2 * (size_t)N * p.Ng8 * 2 + 2 * (size_t)N * p.Na8 * 2;  // Phi pieces
   b += na * p.Ng4 * 4 + (p.large ? 0 : ng * p.Na4 * 4) + na * p.Na4 * 4 + na * 4;  // V, V^T, W, idx
   if (p.large)  // T, third pieces
-    b += 2 * na * p.Ng8 * 2 + 2 * na * p.Na8 * 2 + (ng + na) * p.np * 2 + (ng + n) * p.Np * 2;
+    b += 2 * na * p.Ng8 * 2 + 2 * na * p.Na8 * 2 + (ng + na) * p.np * 2;
+  b += (ng + n) * p.Np * 2;  // third pieces of Phi' and Q
   b += 2 * (size_t)n * p.Np * 2 + (size_t)n * p.Np * 8 + 2 * ng * p.np * 2 + 2 * na * p.np * 2;
   b += (size_t)p.partsA_max * na * n * 4 + (size_t)p.partsC * na * n * 4 + (size_t)n * p.Ng4 * 4;
   b += na * n * 8 + (size_t)n * p.Na8 * 8 + 2 * (size_t)n * p.Ng8 * 2 + 2 * (size_t)n * p.Na8 * 2;
@@ -1952,8 +1970,10 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
     MX(m->TA_h, na * p.Ng8); MX(m->TA_l, na * p.Ng8);
     MX(m->TC_h, na * p.Na8); MX(m->TC_l, na * p.Na8);
     MX(m->psi_l, ng * p.np); MX(m->psig_l, na * p.np);
-    MX(m->phi_l, ng * p.Np); MX(m->CT_l, (size_t)n * p.Np);
   }
+  // third pieces of Phi' and Q for every n: with two pieces the orbital split
+  // alone moves E_x by up to ~1e-6 Ha on the 64-centre cell
+  MX(m->phi_l, ng * p.Np); MX(m->CT_l, (size_t)n * p.Np);
   MX(m->idx, na);
   MX(m->CT_m, (size_t)n * p.Np); MX(m->CT_h, (size_t)n * p.Np); MX(m->CT64, (size_t)n * p.Np);
   MX(m->psi_m, ng * p.np); MX(m->psi_h, ng * p.np);
@@ -2069,6 +2089,8 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
       {&m->m_phi_h, m->phi_h, F16, 2, (long)ng, p.Np, 128, 64},
       {&m->m_CT_m, m->CT_m, F16, 2, n, p.Np, 128, 64},
       {&m->m_CT_h, m->CT_h, F16, 2, n, p.Np, 128, 64},
+      {&m->m_phi_l, m->phi_l, F16, 2, (long)ng, p.Np, 128, 64},
+      {&m->m_CT_l, m->CT_l, F16, 2, n, p.Np, 128, 64},
       {&m->m_psi128_m, m->psi_m, F16, 2, (long)ng, np_, 128, 64},
       {&m->m_psi128_h, m->psi_h, F16, 2, (long)ng, np_, 128, 64},
       {&m->m_psi64_m, m->psi_m, F16, 2, (long)ng, np_, 64, 64},
@@ -2100,8 +2122,6 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
         {&m->m_TC_l, m->TC_l, F16, 2, (long)na, p.Na8, 128, 64},
         {&m->m_psi128_l, m->psi_l, F16, 2, (long)ng, p.np, 128, 64},
         {&m->m_psig128_l, m->psig_l, F16, 2, (long)na, p.np, 128, 64},
-        {&m->m_phi_l, m->phi_l, F16, 2, (long)ng, p.Np, 128, 64},
-        {&m->m_CT_l, m->CT_l, F16, 2, n, p.Np, 128, 64},
     };
     for (const MapSpec& ms : tspecs) {
       e = make_map(ms.m, ms.p, ms.t, ms.es, ms.rows, ms.ld, ms.br, ms.bc);
@@ -2168,10 +2188,11 @@ cudaError_t mixed_enqueue_pre(MixedState* m, const double* C, cudaStream_t s, co
   if (e == cudaSuccess)
     e = split_rows<double>(m->CT64, n, m->Np, m->Np, m->sc, SC_C, m->CT_m, m->CT_h, m->Np, s, m->CT_l);
   if (e != cudaSuccess) return e;
-  if (!m->large) {  // Psi = Phi' Q, written directly as per-row pieces
+  if (!m->large) {  // Psi = Phi' Q (three pieces each), written directly as per-row pieces
     GemmArgs g{(int)ng, n, N, (int)m->Np, nullptr, 0, 0, m->sc, SC_OUT_ORB, m->status,
                m->psi_m, m->psi_h, np, SC_PSI, m->am + AM_RN2};
-    launch_gemm(m->m_phi_m, m->m_phi_h, m->m_CT_m, m->m_CT_h, m->m_phi_m, m->m_CT_m, g,
+    g.pieces3 = 1;
+    launch_gemm(m->m_phi_m, m->m_phi_h, m->m_CT_m, m->m_CT_h, m->m_phi_l, m->m_CT_l, g,
                 dim3((unsigned)((ng + 127) / 128), 1, 1), s);
   } else {  // n > 128: Psi in FP32 (the M1 buffer, free until step 3), then per-row pieces
     GemmArgs g{};

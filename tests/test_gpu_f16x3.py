@@ -120,3 +120,25 @@ def test_ace_on_tensor_path(xk, cell1):
 def test_config2(xk):
     """64-centre supercell (the benchmark workload): E_x within 1e-6 Ha."""
     _check(xk, load_cell(config_spec(2)))
+
+
+@pytest.mark.slow
+def test_config2_scf_steps(xk):
+    """The benchmark's pseudo-SCF coefficients (seed 1000, steps 0 to 202):
+    |dE_x| <= 1e-6 Ha and max|dK| <= 1e-6 against the FP64 path at every
+    sampled step (with two-piece orbital products one of these steps missed
+    by 1.4e-6 Ha)."""
+    from cellgen import pseudo_scf_sequence
+    c = load_cell(config_spec(2))
+    Cs = pseudo_scf_sequence(c.S, c.C, 203, 1000)
+    hf = xk.Handle(c.phi, c.idx, c.V, c.W, c.dV, c.n, mode="fp64")
+    h = xk.Handle(c.phi, c.idx, c.V, c.W, c.dV, c.n, mode="f16x3")
+    try:
+        for t in (0, 52, 102, 152, 202):
+            K0, E0 = hf.build(Cs[t])
+            K, E = h.build(Cs[t])
+            assert abs(E - E0) <= TOL_E, (t, E - E0)
+            assert np.max(np.abs(K - K0)) <= TOL_K, (t, np.max(np.abs(K - K0)))
+    finally:
+        hf.release()
+        h.release()
