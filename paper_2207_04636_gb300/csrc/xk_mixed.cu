@@ -908,10 +908,27 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       }
     } else if (m0 + r < g.M) {
       float* orow = g.out + (long)bz * g.split_stride + (long)(m0 + r) * g.ldo;
+      if (((g.ldo | g.split_stride) & 3) == 0) {  // 16-byte row segments
 #pragma unroll
-      for (int c = 0; c < 64; ++c) {
-        const int col = n0 + cb + c;
-        if (col < g.Ncols) orow[col] = ok ? run[c] * scale : 0.0f;
+        for (int c = 0; c < 64; c += 4) {
+          const int col = n0 + cb + c;
+          if (col + 4 <= g.Ncols) {
+            *reinterpret_cast<float4*>(orow + col) =
+                ok ? make_float4(run[c] * scale, run[c + 1] * scale, run[c + 2] * scale,
+                                 run[c + 3] * scale)
+                   : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              if (col + j < g.Ncols) orow[col + j] = ok ? run[c + j] * scale : 0.0f;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 64; ++c) {
+          const int col = n0 + cb + c;
+          if (col < g.Ncols) orow[col] = ok ? run[c] * scale : 0.0f;
+        }
       }
     }
     }
