@@ -401,3 +401,16 @@ def test_isdf_oracle_matches_cell_tables(cell1):
     chi, V, W, _ = oracle.isdf_tables(c.phi, c.idx, c.L, c.grid)
     assert np.max(np.abs(V - c.V)) < 1e-9 * np.max(np.abs(c.V))
     assert np.max(np.abs(W - c.W)) < 1e-9 * np.max(np.abs(c.W))
+
+
+def test_point_selection_oracle(cell1, tiny):
+    """The greedy pivoted Cholesky of the pair Gram picks the same points as
+    LAPACK's complete-pivoting Cholesky (dpstrf, the generator's route) on
+    the 8-centre cell (256 of 13824 points) and on the tiny cell, where the
+    rank of the pair products stops it early."""
+    from cellgen.cells import _pair_gram, _pivoted_cholesky
+    for c, want in ((cell1, 256), (tiny, 30)):
+        piv = oracle.select_points(c.phi, want)
+        ref = _pivoted_cholesky(_pair_gram(c.phi, c.phi), want)
+        assert np.array_equal(piv, ref[:piv.size])
+        assert piv.size == min(want, ref.size)
