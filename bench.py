@@ -67,6 +67,9 @@ def parse():
     p.add_argument("--no-serve", action="store_true", help="skip the serving-latency loop")
     p.add_argument("--no-energy", action="store_true", help="skip the energy-only timing")
     p.add_argument("--no-full", action="store_true", help="skip the full K_mu_nu timing")
+    p.add_argument("--isdf", action="store_true",
+                   help="form the handle's ISDF tables on the GPU (xk_setup_isdf) instead of "
+                        "taking the generator's, and report the set-up time")
     p.add_argument("--batch", type=int, default=32,
                    help="cells in the grouped batch / mixed serving run (0 skips both)")
     return p.parse_args()
@@ -367,6 +370,32 @@ def batch_and_mixed_serving(xk, cell64, count, seed=4000):
     return out
 
 
+def gpu_points(xk, cell):
+    """The two-stage point selection of Sec. IV.C with the pivoting on the GPU
+    (xk_isdf_points): per-atom candidates from each Voronoi cell of the grid,
+    then a global pivoting over their union.  Returns (sorted idx, seconds)."""
+    t0 = time.perf_counter()
+    x = np.arange(cell.grid) * (cell.L / cell.grid)
+    pts = np.stack(np.meshgrid(x, x, x, indexing="ij"), axis=-1).reshape(-1, 3)
+    owner = np.zeros(pts.shape[0], dtype=np.int64)
+    best = np.full(pts.shape[0], np.inf)
+    for i, a in enumerate(cell.centres):
+        d = pts - a
+        d -= cell.L * np.round(d / cell.L)
+        r2 = np.einsum("ij,ij->i", d, d)
+        m = r2 < best
+        best[m] = r2[m]
+        owner[m] = i
+    per_atom = int(np.ceil(cell.Naux / cell.N * (cell.N // len(cell.centres)))) + 10
+    cand = []
+    for i in range(len(cell.centres)):
+        loc = np.nonzero(owner == i)[0]
+        cand.append(loc[xk.isdf_points(cell.phi[loc], per_atom)])
+    cand = np.unique(np.concatenate(cand))
+    idx = np.sort(cand[xk.isdf_points(cell.phi[cand], cell.Naux)])
+    return idx, time.perf_counter() - t0
+
+
 def run_config3(args):
     """The 216-centre cell (N = 2808, n = 432, 90^3 grid, N_aux = 13500): its
     ISDF tables are formed on the GPU (xk_setup_isdf, FP64) because the host
@@ -472,7 +501,18 @@ def main():
     Ed = torch.empty(1, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
 
-    h = xk.Handle(cell.phi, cell.idx, cell.V, cell.W, cell.dV, n, mode=mode)
+    t_setup = time.perf_counter()
+    points = None
+    if args.isdf:
+        idx_gpu, t_pts = gpu_points(xk, cell)
+        points = {"s": t_pts, "count": int(idx_gpu.size),
+                  "same_as_generator": bool(np.array_equal(idx_gpu, np.sort(cell.idx))),
+                  "common_with_generator": int(np.intersect1d(idx_gpu, cell.idx).size)}
+        t_setup = time.perf_counter()
+        h = xk.Handle.isdf(cell.phi, cell.idx, cell.grid, cell.L, n, mode=mode)
+    else:
+        h = xk.Handle(cell.phi, cell.idx, cell.V, cell.W, cell.dV, n, mode=mode)
+    t_setup = time.perf_counter() - t_setup
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -530,7 +570,17 @@ def main():
         t0 = time.perf_counter()
         for _ in range(reps):
             Kf = h.build_full(C_last)
-        full = {"ms_per_build": (time.perf_counter() - t0) * 1e3 / reps,
+        ms_full = (time.perf_counter() - t0) * 1e3 / reps
+        npad = -(-n // 64) * 64
+        # algorithmic flops: S and W o Q products, M_A = T_A Phi, M_C = T_C Phi_g, Phi_g^T M (x2)
+        fl_full = (2.0 * Na * Ng * n + 2.0 * Na * Na * n + 2.0 * Na * Ng * N + 2.0 * Na * Na * N
+                   + 4.0 * N * N * Na)
+        # split MMA work issued on the tensor path (4 passes each; S with 6 for n > 128)
+        fl_issued = ((6 if n > 128 else 4) * 2.0 * Na * (Ng + Na) * npad
+                     + 4 * (2.0 * Na * Ng * N + 2.0 * Na * Na * N + 4.0 * N * N * Na))
+        full = {"ms_per_build": ms_full,
+                "algorithmic_tflops_per_s": fl_full / (ms_full * 1e-3) / 1e12,
+                "issued_tensor_tflops_per_s": fl_issued / (ms_full * 1e-3) / 1e12,
                 "note": "xk_build_full: K_mu_nu (N x N) of Eq. rpsEx with the three robust-PS "
                         "terms, host buffers in and out, same C as the last build",
                 "symmetry_rel": float(np.max(np.abs(Kf - Kf.T)) / np.max(np.abs(Kf))),
@@ -569,7 +619,11 @@ def main():
             hf.coulomb(C_last, cell.grid, cell.L)  # the first call allocates its scratch
             t0 = time.perf_counter()
             J, EJ = hf.coulomb(C_last, cell.grid, cell.L)
-            coul = {"ms_per_build": (time.perf_counter() - t0) * 1e3, "E_J": EJ,
+            ms_j = (time.perf_counter() - t0) * 1e3
+            fl_j = 2.0 * N * N * Ng + 2.0 * Ng * N * n
+            coul = {"ms_per_build": ms_j, "E_J": EJ,
+                    "fp64_tflops_per_s": fl_j / (ms_j * 1e-3) / 1e12,
+                    "fp64_peak_tflops": FP64_FLOPS_PER_CLK_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12,
                     "note": "xk_coulomb on the FP64 handle: density, DFT Poisson solve, "
                             "J = dV Phi^T diag(v) Phi, host buffers in and out"}
         if full is not None:
@@ -630,7 +684,8 @@ def main():
             "steps": steps, "warmup": warm, "ms_per_step": ms / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if mode == "fp64" else "f16x3",
-            "data": "synthetic (seeded cell generator; inputs resident in HBM)",
+            "data": "synthetic (seeded cell generator; inputs resident in HBM)"
+                    + ("; ISDF tables formed on the GPU" if args.isdf else ""),
             "config": {"workload": workload, "mode": mode, "N": N, "n": n, "N_g": Ng,
                        "N_aux": Na, "l2": "inputs larger than L2 (V is N_aux x N_g)",
                        "parallelism": f"replicas x{world}"},
@@ -643,6 +698,15 @@ def main():
             "e2e": {"value": job_throughput(world, steps, e2e_s * 1e3), "unit": "builds/s",
                     "h2d_bytes_per_step": N * n * 8, "d2h_bytes_per_step": N * n * 8 + 8},
         }
+        if args.isdf:
+            fl_isdf = (2.0 * Na * Ng * N + 2.0 * Na * Na * N + 2.0 * Na ** 3 / 3.0
+                       + 2.0 * Na * Na * Ng + 2.0 * Na * Na * Ng)
+            line["isdf_points_gpu"] = points
+            line["isdf_setup"] = {"s": t_setup, "fp64_tflops_per_s_lower_bound":
+                                  fl_isdf / t_setup / 1e12,
+                                  "note": "xk_setup_isdf: X_gR, X_gg, Cholesky, chi, V, W in FP64 "
+                                          "plus the handle's own set-up (the rate counts the "
+                                          "ISDF products only, so it is a lower bound)"}
         if energy:
             line["energy_only"] = energy
         if full:

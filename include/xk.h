@@ -107,7 +107,7 @@ int xk_setup(int64_t Ng, int32_t N, int32_t n, int32_t Naux,
  *   V    = Pois(chi_g) with the grid kernel 4 pi / G^2, G = 0 removed (Eq. rpsPot),
  *   W    = V chi^T, symmetrised (Eq. thcpot),
  * and then the handle as xk_setup would build it from those V and W.  The
- * point selection stays with the caller (interp_idx).  XK_FP64 forms the
+ * points interp_idx come from the caller (e.g. xk_isdf_points).  XK_FP64 forms the
  * tables in the handle's own buffers; XK_F16X3 holds FP64 temporaries of
  * about 8 (N_g N + 2 N_aux N_g + 2 N_aux^2) bytes during the call, admitted
  * with the handle.  Errors: as xk_setup, plus XK_EINVAL when grid^3 != N_g,
@@ -116,6 +116,25 @@ int xk_setup(int64_t Ng, int32_t N, int32_t n, int32_t Naux,
 int xk_setup_isdf(int64_t Ng, int32_t N, int32_t n, int32_t Naux,
                   const double* basis_on_points, const int32_t* interp_idx,
                   int32_t grid, double L, int mode, xk_handle** out);
+
+/*
+ * Interpolation points on the GPU (Sec. III.A): the greedy complete-pivoting
+ * Cholesky of the pair Gram X(a, b) = (rows_a . rows_b)^2 over m candidate
+ * grid points (rows: host, m x N, the basis at the candidates), in FP64.
+ * At each step the pivot is the largest remaining diagonal (the first on
+ * ties); it stops after `want` pivots or when the largest remaining diagonal
+ * is at most tol_rel times the largest initial one (1e-14 is the usual
+ * choice).  In exact arithmetic these are the column pivots of QRCP on the
+ * pair matrix.  piv_out (host, want) receives the pivots as indices into
+ * rows, in selection order; *count the number taken.  A two-stage selection
+ * (Sec. IV.C: per-atom candidates, then a global pivoting over their union)
+ * is two levels of calls.  Scratch: about 8 (m^2 + m want + m N) bytes of
+ * device memory during the call (admission as xk_setup).
+ * Errors: XK_EINVAL (null pointers, sizes <= 0, bad tol_rel), XK_ENOMEM,
+ * XK_ECUDA.
+ */
+int xk_isdf_points(int32_t m, int32_t N, const double* rows, int32_t want, double tol_rel,
+                   int32_t* piv_out, int32_t* count);
 
 /*
  * Read back tables of an XK_FP64 handle (e.g. those xk_setup_isdf formed):

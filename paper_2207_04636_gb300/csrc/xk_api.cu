@@ -614,6 +614,43 @@ int xk_setup_isdf(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* 
                     L, out);
 }
 
+int xk_isdf_points(int32_t m, int32_t N, const double* rows, int32_t want, double tol_rel,
+                   int32_t* piv_out, int32_t* count) {
+  if (!rows || !piv_out || !count) return fail(XK_EINVAL, "xk_isdf_points: NULL argument");
+  if (m <= 0 || N <= 0 || want <= 0) return fail(XK_EINVAL, "xk_isdf_points: invalid sizes");
+  if (!(tol_rel >= 0.0) || !std::isfinite(tol_rel))
+    return fail(XK_EINVAL, "xk_isdf_points: tol_rel must be finite and >= 0");
+  const size_t need = ((size_t)m * m + (size_t)m * std::min(want, m) + (size_t)m * N + 2 * (size_t)m) * 8;
+  size_t freeb = 0, totalb = 0;
+  XK_CUDA(cudaMemGetInfo(&freeb, &totalb));
+  {
+    std::lock_guard<std::mutex> al(g_admit_mu);
+    const size_t reserve = (size_t)1 << 30;
+    size_t budget = freeb > reserve ? freeb - reserve : 0;
+    if (const char* env = std::getenv("XK_HBM_BUDGET_BYTES")) {
+      const size_t cap = (size_t)std::strtoull(env, nullptr, 10);
+      budget = std::min(budget, cap > g_admitted ? cap - g_admitted : 0);
+    }
+    if (need > budget)
+      return fail(XK_ENOMEM, "xk_isdf_points: scratch of " + std::to_string(need) +
+                                 " bytes exceeds the admission budget " + std::to_string(budget));
+  }
+  cudaStream_t s = nullptr;
+  XK_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  double* F = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&F), (size_t)m * N * 8, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(F, rows, (size_t)m * N * 8, cudaMemcpyHostToDevice, s);
+  int got = 0;
+  if (e == cudaSuccess) e = xk::select_points_f64(F, m, N, want, tol_rel, piv_out, &got, s);
+  if (F) cudaFreeAsync(F, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return cuda_fail(e, "xk_isdf_points");
+  *count = got;
+  return XK_OK;
+}
+
 int xk_tables(xk_handle* h, double* W_out, const int32_t* rows, int32_t nrows, double* V_rows_out,
               double* ridge) {
   if (!h) return fail(XK_EINVAL, "xk_tables: NULL handle");

@@ -88,6 +88,14 @@ cudaError_t assemble_full_f64(const double* Y, const double* Z, int N, double dV
 cudaError_t isdf_tables_f64(const double* phi, long ng, int N, const double* phig, int na,
                             int grid, double L, double* Xgg, double* chi, double* V, double* W,
                             double* work, int* status, double* ridge_out, cudaStream_t s);
+// Interpolation points (Sec. III.A) by a greedy complete-pivoting Cholesky of
+// X = (F F^T) o (F F^T) for the m candidate rows F (m x N, device): up to
+// `want` pivots (indices into F, selection order) into piv (host), stopping
+// when the largest remaining diagonal is at most tol_rel times the largest
+// initial one; *count = pivots taken.  Holds m^2 + m want doubles of
+// stream-ordered scratch during the call.
+cudaError_t select_points_f64(const double* F, int m, int N, int want, double tol_rel,
+                              int32_t* piv, int* count, cudaStream_t s);
 // In-place blocked Cholesky (lower) of the n x n matrix A (lda); *status = 1
 // on a non-positive pivot.
 cudaError_t cholesky_blocked_f64(double* A, int n, long lda, int* status, cudaStream_t s);

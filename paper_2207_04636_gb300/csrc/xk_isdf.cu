@@ -175,7 +175,141 @@ __global__ void unpack_pairs_kernel(const double2* __restrict__ c, long r0, int 
   }
 }
 
+// ---------------------------------------------------------------- point selection
+// Greedy complete-pivoting Cholesky of X = (F F^T) o (F F^T), left-looking:
+// only the diagonal d is kept up to date; each step forms one column.
+// State on the device: d[m] (selected rows set to -1), L[m][want],
+// sel[0] = steps taken, sel[1] = stopped flag, val[t] = pivot value, tol.
+
+__global__ void diag_init_kernel(const double* __restrict__ X, int m, double* __restrict__ d) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    d[i] = X[(long)i * m + i];
+}
+
+// Pivot of step t: the largest d (the lowest index on ties); stops when it is
+// not above tol (tol = tol_rel * the largest initial diagonal, set at t = 0).
+__global__ void __launch_bounds__(1024) pivot_kernel(double* __restrict__ d, int m, int t,
+                                                     double tol_rel, int* __restrict__ sel,
+                                                     int32_t* __restrict__ piv,
+                                                     double* __restrict__ val,
+                                                     double* __restrict__ tol) {
+  __shared__ double bv[32];
+  __shared__ int bi[32];
+  if (sel[1]) return;
+  double best = -1.0;
+  int bidx = 0x7fffffff;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double v = d[i];
+    if (v > best) { best = v; bidx = i; }  // increasing i: the first maximum is kept
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+    if (ov > best || (ov == best && oi < bidx)) { best = ov; bidx = oi; }
+  }
+  if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = best; bi[threadIdx.x >> 5] = bidx; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // fold the warps' results in warp order (ties keep the lower index)
+    double b0 = bv[0];
+    int i0 = bi[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (bv[w] > b0 || (bv[w] == b0 && bi[w] < i0)) { b0 = bv[w]; i0 = bi[w]; }
+    if (t == 0) *tol = tol_rel * b0;
+    if (!(b0 > *tol) || i0 >= m) {
+      sel[1] = 1;
+    } else {
+      piv[t] = i0;
+      val[t] = b0;
+      d[i0] = -1.0;
+      sel[0] = t + 1;
+    }
+  }
+}
+
+// Column t: for every unselected row i (one warp per row),
+// L[i][t] = (X[i][p] - sum_{s<t} L[i][s] L[p][s]) / sqrt(val[t]) and
+// d[i] -= L[i][t]^2; the pivot row gets L[p][t] = sqrt(val[t]).
+__global__ void column_kernel(const double* __restrict__ X, int m, int want, int t,
+                              const int* __restrict__ sel, const int32_t* __restrict__ piv,
+                              const double* __restrict__ val, double* __restrict__ L,
+                              double* __restrict__ d) {
+  if (sel[1] || sel[0] <= t) return;
+  const int p = piv[t];
+  const double sp = sqrt(val[t]);
+  const int lane = threadIdx.x & 31;
+  const long warps = ((long)gridDim.x * blockDim.x) >> 5;
+  const double* lp = L + (long)p * want;
+  for (long i = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < m; i += warps) {
+    if (i == p) {
+      if (lane == 0) L[(long)p * want + t] = sp;
+      continue;
+    }
+    if (d[i] < 0.0) continue;  // selected earlier
+    const double* li = L + i * want;
+    double acc = 0.0;
+    for (int q = lane; q < t; q += 32) acc = fma(li[q], lp[q], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      const double l = (X[i * m + p] - acc) / sp;
+      L[i * want + t] = l;
+      d[i] -= l * l;
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t select_points_f64(const double* F, int m, int N, int want, double tol_rel,
+                              int32_t* piv, int* count, cudaStream_t s) {
+  if (m <= 0 || want <= 0) {
+    *count = 0;
+    return cudaSuccess;
+  }
+  want = std::min(want, m);
+  void* buf = nullptr;
+  const size_t xb = (size_t)m * m * 8, lb = (size_t)m * want * 8;
+  const size_t bytes = xb + lb + (size_t)m * 8 + (size_t)want * 8 + 64 + (size_t)want * 4 + 64;
+  cudaError_t e = cudaMallocAsync(&buf, bytes, s);
+  if (e != cudaSuccess) return e;
+  char* b = static_cast<char*>(buf);
+  double* X = reinterpret_cast<double*>(b);
+  double* L = reinterpret_cast<double*>(b + xb);
+  double* d = reinterpret_cast<double*>(b + xb + lb);
+  double* val = d + m;
+  double* tol = val + want;
+  int* sel = reinterpret_cast<int*>(tol + 2);
+  int32_t* dpiv = reinterpret_cast<int32_t*>(sel + 4);
+  {
+    DGemm g{m, m, N, F, N, false, F, N, true, X, m, 1.0, nullptr, 0, 1, nullptr};
+    e = dgemm(g, s);
+  }
+  if (e == cudaSuccess) {
+    square_kernel<<<nblocks((long)m * m), 256, 0, s>>>(X, m, m, m);
+    diag_init_kernel<<<nblocks(m), 256, 0, s>>>(X, m, d);
+    count_launch(2);
+    e = cudaMemsetAsync(sel, 0, 16, s);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(L, 0, lb, s);
+  const int cb = std::max(1, std::min(152 * 8, (m + 7) / 8));  // 8 warps (rows) per block
+  for (int t = 0; e == cudaSuccess && t < want; ++t) {
+    pivot_kernel<<<1, 1024, 0, s>>>(d, m, t, tol_rel, sel, dpiv, val, tol);
+    column_kernel<<<cb, 256, 0, s>>>(X, m, want, t, sel, dpiv, val, L, d);
+    count_launch(2);
+    if ((t & 255) == 255) e = cudaGetLastError();
+  }
+  int got = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&got, sel, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && got > 0)
+    e = cudaMemcpyAsync(piv, dpiv, (size_t)got * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaError_t e2 = cudaFreeAsync(buf, s);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  *count = got;
+  return e;
+}
 
 cudaError_t cholesky_blocked_f64(double* A, int n, long lda, int* status, cudaStream_t s) {
   for (int k = 0; k < n; k += NB) {

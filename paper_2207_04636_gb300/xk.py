@@ -46,6 +46,7 @@ def lib():
         L.xk_setup_isdf.argtypes = [c_i64, c_i32, c_i32, c_i32, c_d, c_d, c_i32, ctypes.c_double,
                                     c_int, ctypes.POINTER(ctypes.c_void_p)]
         L.xk_tables.argtypes = [c_d, c_d, c_d, c_i32, c_d, c_d]
+        L.xk_isdf_points.argtypes = [c_i32, c_i32, c_d, c_i32, ctypes.c_double, c_d, c_d]
         L.xk_build.argtypes = [c_d, c_d, c_d, c_d]
         L.xk_build_device.argtypes = [c_d, c_d, c_d, c_d, c_d]
         L.xk_energy.argtypes = [c_d, c_d, c_d]
@@ -65,7 +66,8 @@ def lib():
         L.xk_batch_release.argtypes = [c_d]
         L.xk_last_error.restype = ctypes.c_char_p
         L.xk_kernel_launches.restype = ctypes.c_uint64
-        for f in ("xk_footprint", "xk_setup", "xk_setup_isdf", "xk_tables", "xk_build",
+        for f in ("xk_footprint", "xk_setup", "xk_setup_isdf", "xk_tables", "xk_isdf_points",
+                  "xk_build",
                   "xk_build_device", "xk_build_full",
                   "xk_coulomb",
                   "xk_energy",
@@ -266,6 +268,17 @@ class Batch:
             self.release()
         except Exception:
             pass
+
+
+def isdf_points(rows, want, tol_rel=1e-14):
+    """Pivots (indices into rows, selection order) of the greedy pivoted
+    Cholesky of the pair Gram of the candidate rows (xk_isdf_points)."""
+    rows = np.ascontiguousarray(rows, dtype=np.float64)
+    m, N = rows.shape
+    piv = np.empty(max(int(want), 1), dtype=np.int32)
+    cnt = np.empty(1, dtype=np.int32)
+    _check(lib().xk_isdf_points(m, N, _ptr(rows), int(want), float(tol_rel), _ptr(piv), _ptr(cnt)))
+    return piv[:int(cnt[0])].astype(np.int64)
 
 
 def exchange_energy_noalloc(K_dev, C_dev, count, Ex_dev, stream=0):

@@ -29,7 +29,7 @@ def _declared():
 def test_exports_every_declared_symbol(L):
     names = _declared()
     assert {"xk_setup", "xk_build", "xk_submit", "xk_poll", "xk_release", "xk_footprint",
-            "xk_last_error", "xk_build_device", "xk_ace", "xk_energy", "xk_build_full", "xk_coulomb", "xk_setup_isdf", "xk_tables"} <= set(names)
+            "xk_last_error", "xk_build_device", "xk_ace", "xk_energy", "xk_build_full", "xk_coulomb", "xk_setup_isdf", "xk_tables", "xk_isdf_points"} <= set(names)
     for n in names:
         assert hasattr(L, n), n
 
@@ -116,6 +116,10 @@ def test_null_handles_and_tickets(L):
     assert L.xk_build_full(None, p, p) == xk.XK_EINVAL
     assert L.xk_coulomb(None, 4, 1.0, p, p, p) == xk.XK_EINVAL
     assert L.xk_tables(None, p, None, 0, None, None) == xk.XK_EINVAL
+    cnt = ctypes.c_int32()
+    assert L.xk_isdf_points(4, 2, None, 2, 1e-14, p, ctypes.byref(cnt)) == xk.XK_EINVAL
+    assert L.xk_isdf_points(0, 2, p, 2, 1e-14, p, ctypes.byref(cnt)) == xk.XK_EINVAL
+    assert L.xk_isdf_points(2, 2, p, 2, -1.0, p, ctypes.byref(cnt)) == xk.XK_EINVAL
     assert L.xk_energy_device(None, p, p, None) == xk.XK_EINVAL
     b = ctypes.c_void_p()
     assert L.xk_batch_create(None, 0, ctypes.byref(b)) == xk.XK_EINVAL

@@ -23,6 +23,12 @@ def xk():
     return m
 
 
+@pytest.fixture(scope="module")
+def tiny_cell():
+    return build_cell(CellSpec("tiny", np.array([[0.1, 0.2, 0.15], [0.55, 0.6, 0.45]]), 5.0, 10,
+                               [Shell(0, (0.6,), (1.0,)), Shell(1, (0.9,), (1.0,))], 3, 30, 77))
+
+
 def _ragged():
     sh = [Shell(0, (0.35,), (1.0,)), Shell(1, (0.8,), (1.0,)), Shell(2, (1.1,), (1.0,))]
     return build_cell(CellSpec("ragged", np.array([[0.1, 0.2, 0.3], [0.6, 0.5, 0.45],
@@ -62,3 +68,54 @@ def test_isdf_build_f16x3(xk, cell1, which):
     K0, E0 = oracle.exx_rps_occri(c.phi, c.idx, V0, W0, c.C, c.dV)
     assert abs(E - E0) <= 1e-6, (E, E0)
     assert np.max(np.abs(K - K0)) <= 1e-6
+
+
+def test_isdf_points_match_oracle(xk, cell1, tiny_cell):
+    """xk_isdf_points (greedy pivoted Cholesky of the pair Gram on the GPU)
+    picks the oracle's pivots, in the oracle's order: all 13824 points of the
+    8-centre cell for its 256, and the tiny cell where the rank of the pair
+    products stops the pivoting early."""
+    for c, want in ((cell1, 256), (tiny_cell, 30)):
+        piv0 = oracle.select_points(c.phi, want)
+        piv = xk.isdf_points(c.phi, want)
+        assert np.array_equal(piv, piv0), (piv[:10], piv0[:10])
+
+
+def test_isdf_points_two_stage_then_tables(xk):
+    """The two-stage selection of Sec. IV.C on the GPU (per-atom candidates
+    from each Voronoi cell, then a global pivoting over their union) for the
+    27-centre cell matches the oracle run on the same candidate sets, and the
+    tables built from those points give the oracle's E_x."""
+    from cellgen.cells import build_cell
+    spec = config_spec(4, k=3)
+    c = build_cell(spec, fit=False)
+    x = np.arange(c.grid) * (c.L / c.grid)
+    pts = np.stack(np.meshgrid(x, x, x, indexing="ij"), axis=-1).reshape(-1, 3)
+    owner = np.zeros(pts.shape[0], dtype=np.int64)
+    best = np.full(pts.shape[0], np.inf)
+    for I, A in enumerate(c.centres):
+        d = pts - A
+        d -= c.L * np.round(d / c.L)
+        r2 = np.einsum("ij,ij->i", d, d)
+        m = r2 < best
+        best[m] = r2[m]
+        owner[m] = I
+    per_atom = int(np.ceil(c.Naux / c.N * 13)) + 10
+    cand, cand0 = [], []
+    for I in range(len(c.centres)):
+        loc = np.nonzero(owner == I)[0]
+        cand.append(loc[xk.isdf_points(c.phi[loc], per_atom)])
+        cand0.append(loc[oracle.select_points(c.phi[loc], per_atom)])
+    cand = np.unique(np.concatenate(cand))
+    assert np.array_equal(cand, np.unique(np.concatenate(cand0)))
+    idx = np.sort(cand[xk.isdf_points(c.phi[cand], c.Naux)])
+    idx0 = np.sort(cand[oracle.select_points(c.phi[cand], c.Naux)])
+    assert np.array_equal(idx, idx0)
+    h = xk.Handle.isdf(c.phi, idx, c.grid, c.L, c.n, mode="fp64")
+    try:
+        K, E = h.build(c.C)
+    finally:
+        h.release()
+    _, V0, W0, _ = oracle.isdf_tables(c.phi, idx, c.L, c.grid)
+    K0, E0 = oracle.exx_rps_occri(c.phi, idx, V0, W0, c.C, c.dV)
+    assert abs(E - E0) <= 1e-8
