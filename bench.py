@@ -158,6 +158,8 @@ def run_reference(args):
         return
     import oracle
     cell = load_cell(config_spec(args.config, k=args.k))
+    workload = WORKLOAD if args.config == 2 else (
+        f"{cell.spec.name}: N={cell.N}, n={cell.n}, N_g={cell.Ng}, N_aux={cell.Naux}")
     steps = args.steps or 5
     Cs = pseudo_scf_sequence(cell.S, cell.C, steps + args.warmup, 77)
     for i in range(args.warmup):
@@ -172,9 +174,9 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded cell generator)",
-        "config": {"workload": WORKLOAD, "impl": "FP64 NumPy oracle of Eq. exoccri"},
+        "config": {"workload": workload, "impl": "FP64 NumPy oracle of Eq. exoccri"},
         "cpu_baseline": {"value": v, "unit": "builds/s", "cores": cpu_cores(), "kind": "oracle",
-                         "sample": f"{steps} full builds of the 64-centre cell"},
+                         "sample": f"{steps} full builds of the {cell.spec.name} cell"},
         "e2e": {"value": v, "unit": "builds/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }

@@ -43,3 +43,24 @@ def test_two_gloo_ranks():
 def test_single_rank_is_identity():
     assert bench.max_over_ranks(12.5, None, "cpu") == 12.5
     assert bench.job_throughput(1, 10, 1000.0) == pytest.approx(10.0)
+
+
+def test_reference_arm_json_line():
+    """`bench.py --impl reference` (the oracle on the host) prints one JSON
+    line with the keys the benchmark contract asks for."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                        "--config", "1", "--steps", "1", "--warmup", "1"],
+                       capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
+    assert line["cpu_baseline"]["kind"] == "oracle"
