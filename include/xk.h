@@ -17,6 +17,14 @@
  * Coulomb integral, Eq. 2eint).  No FFT runs inside a build: V and W are
  * computed once per geometry by the caller (Eq. rpsPot, Eq. thcpot).
  *
+ * Entry points: set-up and release (xk_footprint, xk_setup, xk_setup_isdf,
+ * xk_isdf_points, xk_tables, xk_release); builds (xk_build, xk_build_device,
+ * xk_ace); serving (xk_submit, xk_poll) and batches (xk_batch_create,
+ * xk_batch_build, xk_batch_release); other products on the same tables
+ * (xk_energy, xk_energy_device, xk_build_full, xk_coulomb,
+ * xk_exchange_energy_noalloc); diagnostics (xk_last_error,
+ * xk_kernel_launches, xk_timing_enable, xk_timing_read).
+ *
  * Conventions for every entry point:
  *   - All matrices are row-major, double precision, densely packed.
  *   - Host pointers are owned by the caller; the library copies what it
