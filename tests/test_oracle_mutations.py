@@ -207,3 +207,90 @@ def test_unmutated_j_pin_holds(settings):
 def test_j_mutant_is_caught(settings, mutant, monkeypatch):
     monkeypatch.setattr(ox, "coulomb_j", mutant)
     assert not _j_pin_holds(settings[1])
+
+
+# ------------------------------------------------ ISDF set-up and point selection
+
+import oracle.isdf as oi  # noqa: E402
+
+_ORIG_TABLES = oi.isdf_tables
+_ORIG_SELECT = oi.select_points
+
+
+def t_no_solve(phi, idx, L, grid):
+    # the pair Gram columns taken as the fit (no X_gg^{-1})
+    G = phi[idx] @ phi.T
+    chi = G * G
+    V = oracle.coulomb_potential(chi, L, grid)
+    W = V @ chi.T
+    return chi, V, 0.5 * (W + W.T), 0.0
+
+
+def t_no_poisson(phi, idx, L, grid):
+    chi, _, _, r = _ORIG_TABLES(phi, idx, L, grid)
+    W = chi @ chi.T
+    return chi, chi, 0.5 * (W + W.T), r
+
+
+def t_unsymmetrised(phi, idx, L, grid):
+    chi, V, _, r = _ORIG_TABLES(phi, idx, L, grid)
+    return chi, V, V @ chi.T, r
+
+
+def s_no_update(rows, want, tol_rel=1e-14):
+    # pivots by the initial diagonal only (no Schur-complement update)
+    d = np.einsum("ij,ij->i", rows, rows) ** 2
+    return np.argsort(-d, kind="stable")[:want]
+
+
+def s_wrong_gram(rows, want, tol_rel=1e-14):
+    # Gram of the rows instead of the pair products
+    import scipy.linalg
+    X = rows @ rows.T
+    _, piv, rank, _ = scipy.linalg.lapack.dpstrf(X, tol=tol_rel * float(np.max(np.diag(X))), lower=1)
+    return np.asarray(piv[:min(want, rank)], dtype=np.int64) - 1
+
+
+T_MUTANTS = [t_no_solve, t_no_poisson, t_unsymmetrised]
+S_MUTANTS = [s_no_update, s_wrong_gram]
+
+
+def _tables_pins_hold(c):
+    chi, V, W, _ = oi.isdf_tables(c.phi, c.idx, c.L, c.grid)
+    interp = np.max(np.abs(chi[:, c.idx] - np.eye(c.Naux))) < 1e-8
+    sym = np.max(np.abs(W - W.T)) == 0.0
+    gen = (np.max(np.abs(V - c.V)) < 1e-9 * np.max(np.abs(c.V))
+           and np.max(np.abs(W - c.W)) < 1e-9 * np.max(np.abs(c.W)))
+    return interp and sym and gen
+
+
+def _select_pins_hold(c):
+    from cellgen.cells import _pair_gram, _pivoted_cholesky
+    piv = oi.select_points(c.phi, 40)
+    ref = _pivoted_cholesky(_pair_gram(c.phi, c.phi), 40)
+    return piv.size == ref[:40].size and np.array_equal(piv, ref[:40])
+
+
+@pytest.fixture(scope="module")
+def small_fitted():
+    # a cell with fitted tables small enough for many re-fits
+    spec = CellSpec("mut", np.array([[0.1, 0.2, 0.15], [0.55, 0.6, 0.45]]), 5.0, 10,
+                    [Shell(0, (0.6,), (1.0,)), Shell(1, (0.9,), (1.0,))], 3, 30, 78)
+    return build_cell(spec)
+
+
+def test_unmutated_isdf_pins_hold(small_fitted):
+    assert _tables_pins_hold(small_fitted)
+    assert _select_pins_hold(small_fitted)
+
+
+@pytest.mark.parametrize("mutant", T_MUTANTS, ids=[m.__name__ for m in T_MUTANTS])
+def test_tables_mutant_is_caught(small_fitted, mutant, monkeypatch):
+    monkeypatch.setattr(oi, "isdf_tables", mutant)
+    assert not _tables_pins_hold(small_fitted)
+
+
+@pytest.mark.parametrize("mutant", S_MUTANTS, ids=[m.__name__ for m in S_MUTANTS])
+def test_select_mutant_is_caught(small_fitted, mutant, monkeypatch):
+    monkeypatch.setattr(oi, "select_points", mutant)
+    assert not _select_pins_hold(small_fitted)
