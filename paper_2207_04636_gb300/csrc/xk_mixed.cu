@@ -14,9 +14,11 @@
 //     A1 = sum m_x h_y + h_x m_y + h_x h_y,
 // and A1 is about 2^-9 of A0, so its truncation bias is negligible.  A0 and
 // A1 live in separate TMEM accumulators; longer sums are drained every
-// <= 256 terms into round-to-nearest FP32 running sums.  The pair-kernel
-// second product (V o P times the orbitals) uses a floating hi/lo split of
-// V o P and drains every two tiles.
+// <= 256 terms into round-to-nearest FP32 running sums.  The orbital product
+// Psi = Phi' Q takes a third piece l = fp16(x - m - h) of both operands (six
+// MMA passes): with two, its split error alone moved E_x by up to ~1e-6 Ha.
+// The pair-kernel second product (V o P times the orbitals) uses a floating
+// hi/lo split of V o P and drains every two tiles.
 //
 // Build chain (arXiv 2207.04636, Eq. exoccri with contraction order (a) of
 // Sec. IV.D):
@@ -1683,7 +1685,8 @@ struct MixedState {
   int nt = 1;
   long epA = 1, epC = 1;
   __half *TA_h = nullptr, *TA_l = nullptr, *TC_h = nullptr, *TC_l = nullptr;
-  // n > 128: third pieces of Psi (the S product) and of Phi', Q (the orbital product)
+  // third pieces: of Psi and Psi_g for n > 128 (the S product), of Phi' and Q
+  // for every n (the orbital product)
   __half *psi_l = nullptr, *psig_l = nullptr, *phi_l = nullptr, *CT_l = nullptr;
   CUtensorMap m_TA_h, m_TA_l, m_TAmn_h, m_TAmn_l, m_TC_h, m_TC_l, m_psi128_l, m_psig128_l,
       m_phi_l, m_CT_l;
