@@ -261,8 +261,10 @@ int xk_submit(xk_handle* h, const double* C, double deadline_ms, xk_ticket* t);
 /*
  * Non-blocking completion check.  XK_PENDING while the build runs;
  * XK_OK once done, after copying K_{mu i} (N x n) to K_out and E_x to Ex;
- * err_bound (nullable) receives the a-priori bound on |E_x error| of the
- * handle's mode relative to FP64 (0 for XK_FP64).  A ticket is consumed by
+ * err_bound (nullable) receives the E_x accuracy the handle's mode is held
+ * to relative to the FP64 path: 0 for XK_FP64; 1e-6 Ha for XK_F16X3, the
+ * tolerance its parity tests enforce (largest measured |dE_x| 3.6e-7 Ha,
+ * on the 216-centre cell), not a rigorous a-priori bound.  A ticket is consumed by
  * the XK_OK, XK_ETIMEDOUT or XK_ECUDA result.  XK_EINVAL for an unknown ticket.
  */
 int xk_poll(xk_ticket t, double* K_out, double* Ex, double* err_bound);

@@ -72,7 +72,8 @@ void mixed_group_destroy(PairGroup* g);
 // bounded wait inside a kernel gave up), read synchronously and cleared.
 int mixed_take_status(MixedState* m);
 
-// A-priori bound on |E_x(mixed) - E_x(FP64)| reported with each result.
+// The E_x accuracy the path is held to against the FP64 path (the parity
+// tests' tolerance, reported with each result; not a rigorous bound).
 double mixed_error_bound(const MixedState* m);
 
 }  // namespace xk
