@@ -42,6 +42,9 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # DRAM bytes per (X row, Y row) pair of the pair kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum = 1496 MB over 3.2316e8 pairs)
 PAIR_DRAM_BYTES_PER_PAIR = 1496e6 / (2.0 * 1755 * 91125 + 1755.0 * 1755)
+# The same for the fused role (one pass over V per N_aux x N_g pair): not yet
+# captured for the current kernel.
+FUSED_DRAM_BYTES_PER_PAIR = None
 # FP64 on the CUDA cores of GB300: 2 DFMA (4 flops) per clock per SM, measured
 # 3.81 flops/clock/SM with an FMA-chain probe; x 152 SMs x 2070 MHz.
 FP64_FLOPS_PER_CLK_SM = 4.0
@@ -655,27 +658,38 @@ def main():
             dom = "pair"
             dom_ms = st[dom][0] / max(1, st[dom][1])
             algo = fl["pair"] + fl["m2"] + fl["m1"] + 4.0 * Na * Na * n
-            # tensor products issued: S = 4 MMA passes, second product = 3 passes,
-            # roles A and B each form S over the N_aux x N_g pairs, role C over N_aux^2
             npad = -(-n // 64) * 64
-            issued = 7 * 2.0 * 2 * Na * Ng * npad + 7 * 2.0 * Na * Na * npad
+            if npad == 128:
+                # fused role: S once (4 split MMA passes) and both back-contractions
+                # (3 passes each) per N_aux x N_g pair; role C: S + one product
+                issued = 10 * 2.0 * Na * Ng * npad + 7 * 2.0 * Na * Na * npad
+                kname = ("pair kernel (fused role: S = Psi Psi_g^T once, V^T o S, M1 and M2 "
+                         "from one pass over V; role C in the same launch)")
+            else:
+                # roles A and B each form S (4 passes) and one product (3 passes)
+                issued = 7 * 2.0 * 2 * Na * Ng * npad + 7 * 2.0 * Na * Na * npad
+                kname = ("pair kernel (fused P, V o P, back-contraction; roles A, B, C "
+                         "in one launch per build)")
             peak = pk.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"])
+            pair_bytes = (FUSED_DRAM_BYTES_PER_PAIR if npad == 128 else PAIR_DRAM_BYTES_PER_PAIR)
             roof = {"bound": "tensor",
-                    "kernel": "pair kernel (fused P, V o P, back-contraction; roles A, B, C "
-                              "in one launch per build)",
+                    "kernel": kname,
                     "achieved": algo / (dom_ms * 1e-3) / 1e12, "peak": peak,
                     "unit": "TFLOP/s",
                     "peak_source": f"dense bf16/fp16 tensor rate ({pk_src})",
                     "issued_tensor_tflops": issued / (dom_ms * 1e-3) / 1e12,
-                    # tensor-pipe fraction: MMA FLOPs issued (7 split passes) over the
-                    # same peak; the algorithmic 'frac' counts each product once
+                    # tensor-pipe fraction: split MMA FLOPs issued over the same peak;
+                    # the algorithmic 'frac' counts each product once
                     "issued_frac": issued / (dom_ms * 1e-3) / 1e12 / peak,
                     "issued_frac_of_sustained": issued / (dom_ms * 1e-3) / 1e12 / pk.get(
                         "bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"]),
                     # DRAM bytes of the pair launch: dram__bytes_read + write of one ncu
-                    # capture (27-centre cell, n = 128: 1496 MB for 3.23e8 pairs), scaled
-                    # to this cell by its pair count (the traffic is per pair)
-                    "traffic": PAIR_DRAM_BYTES_PER_PAIR * (2.0 * Na * Ng + float(Na) * Na),
+                    # capture of the same kernel on the 27-centre cell with n = 128,
+                    # scaled to this cell by its pair count (the traffic is per pair);
+                    # None until a capture of the current kernel exists
+                    "traffic": (None if pair_bytes is None else
+                                pair_bytes * (Na * Ng * (1.0 if npad == 128 else 2.0)
+                                              + float(Na) * Na)),
                     "traffic_source": "ncu capture of the pair kernel on the 27-centre cell "
                                       "(n = 128), scaled by pair count"}
         roof["frac"] = roof["achieved"] / roof["peak"]

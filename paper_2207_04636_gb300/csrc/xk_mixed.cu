@@ -997,11 +997,21 @@ struct PairArgs {
   int transposed;  // 0: out[part][x][j]; 1: out[j][x] (single part)
   double* epart;   // nullable: per-CTA sum_y V' S^2 (scaled by G^4)
   int* status;
+  // Fused role only (fused_body): V'^T [X rows][ldvt] read through L2 by the
+  // epilogue, and the M2 side product reduced into FP32 copies
+  // m2acc[copy][y][j] (copy = X tile % ncopy, copies m2_copy_stride apart).
+  const float* vt;
+  long ldvt;
+  float* m2acc;
+  int ncopy;
+  long m2_copy_stride;
 };
 
 // One role of a pair launch (host record; copied into the launch parameters).
 struct PairRole {
   CUtensorMap ym, yh, v;  // Y pieces (m, h) and the V' tiles
+  CUtensorMap xm, xh;     // fused role: X pieces as [128][64] boxes (the X^T operand)
+  int kind;               // 0: pair_body (one back-contraction); 1: fused_body
   PairArgs a;
   int gx;     // the role's own grid is gx x (nblk / gx)
   int nblk;
@@ -1343,6 +1353,396 @@ __device__ __forceinline__ void pair_body(const CUtensorMap* mYm, const CUtensor
   if (warp == mma_warp) tmem_dealloc(tbase, 512);
 }
 
+// ============================================================ fused pair kernel
+// Both back-contractions of Eq. exoccri from one pass over V (n <= 128, the
+// 128-column piece layout).  One CTA takes 128 grid points R (X = Psi rows)
+// against every interpolation tile g (Y = Psi_g rows, 64 per tile):
+//   S^T = X Y^T                    four split passes (A0 exact, A1 cross terms)
+//   U^T = f V^T' o S^T             floating hi/lo FP16; e += sum V' S^2
+//   M1^T[R][j] += sum_g U^T Y      TS MMAs (U in tensor memory), drained every
+//                                  kAccDrain tiles into FP32 registers: M1
+//                                  is complete in the CTA (written [j][R])
+//   M2[g][j]   += sum_R U^T X      SS MMAs (A = X^T, B = U^T, both MN-major
+//                                  in shared memory), drained every tile and
+//                                  added with red.global.add.f32 into the
+//                                  copy (X tile % ncopy) of M2
+// so S is formed once per pair and V is read once (its transposed FP32 copy).
+// Tensor memory: X pieces [0, 128), S = A0 [128, 192) + A1 [192, 256),
+// U [256, 320) (hi 32 + lo 32), M2 tile [320, 384), M1^T accumulator
+// [384, 512).  Shared memory: Y ring and V'^T ring (2 stages of 32 KB each),
+// X^T pieces (64 KB), U^T pieces (32 KB).  Per tile the epilogue reads S,
+// forms U from the staged V' tile, writes U once the previous tile's products
+// have read it, then drains the M1^T group and the previous M2 tile; the
+// reductions of that M2 tile into L2 come last, off the path to the next U.
+// The M2 copies are FP32 sums whose order depends on the CTA schedule: K_{mu i}
+// is reproducible to rounding, not bit for bit (E_x is: its per-CTA sums are
+// fixed-order).
+constexpr int kFusedStages = 2;
+struct FusedCfg {
+  static constexpr int NP = 128;
+  static constexpr int Y_BYTES = 64 * NP * 2;          // one piece of a 64-row Y tile
+  static constexpr int Y_STAGE = 2 * Y_BYTES;          // (m, h)
+  static constexpr int V_STAGE = 128 * 64 * 4;         // V'^T tile: two [128][32] FP32 boxes
+  static constexpr int OFF_V = kFusedStages * Y_STAGE;
+  static constexpr int OFF_X = OFF_V + kFusedStages * V_STAGE;  // X^T pieces: m [0, 32K), h [32K, 64K)
+  static constexpr int OFF_U = OFF_X + 4 * 16384;      // U^T pieces: hi [0, 16K), lo [16K, 32K)
+  static constexpr int SMEM = OFF_U + 2 * 16384 + 1024;
+  static constexpr uint32_t T_XM = 0, T_XH = 64, T_S0 = 128, T_S1 = 192, T_U = 256, T_M2 = 320,
+                            T_ACC = 384;
+  static constexpr int AC = NP / 4;                    // M1^T columns per epilogue warp
+};
+static_assert(FusedCfg::SMEM >= PairCfg<128>::SMEM, "one launch size covers both bodies");
+
+__device__ __forceinline__ void red_add_f32(float* p, float v) {
+  asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ void fused_body(const CUtensorMap* mYm, const CUtensorMap* mYh,
+                                           const CUtensorMap* mV, const CUtensorMap* mXm,
+                                           const CUtensorMap* mXh, const PairArgs& a, int bx) {
+  using C = FusedCfg;
+  constexpr int NP = C::NP;
+  extern __shared__ uint8_t p_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ uint64_t y_full[kFusedStages], y_empty[kFusedStages], v_full[kFusedStages],
+      v_empty[kFusedStages], xfull, s_full, s_free, u_full, u_free, acc_ready, acc_free, m2_ready,
+      m2_free, drain;
+  __shared__ uint32_t tslot;
+  __shared__ volatile int abort_flag;
+  __shared__ double ered[kEpiWarps];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int prod_warp = kEpiWarps, mma_warp = kEpiWarps + 1;
+  const int x0 = bx * 128;
+  const int T = a.Y > 0 ? (a.Y + 63) / 64 : 0;
+
+  if (tid == 0) {
+    for (int s = 0; s < kFusedStages; ++s) {
+      mbar_init(&y_full[s], 1);
+      mbar_init(&y_empty[s], 1);
+      mbar_init(&v_full[s], 1);
+      mbar_init(&v_empty[s], kEpiWarps);
+    }
+    mbar_init(&xfull, 1);
+    mbar_init(&s_full, 1);
+    mbar_init(&s_free, kEpiWarps);
+    mbar_init(&u_full, kEpiWarps);
+    mbar_init(&u_free, 1);
+    mbar_init(&acc_ready, 1);
+    mbar_init(&acc_free, kEpiWarps);
+    mbar_init(&m2_ready, 1);
+    mbar_init(&m2_free, kEpiWarps);
+    mbar_init(&drain, 1);
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == mma_warp) {
+    tmem_alloc(&tslot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tslot;
+
+  if (warp < kEpiWarps) load_x_tile<NP>(a, x0, tbase, warp, lane);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  if (warp == prod_warp && lane == 0) {
+    // ---------------- TMA producer: X^T pieces once, then per tile the Y
+    // pieces (released by the MMA warp) and the V'^T tile (released by the
+    // epilogue) through their own rings
+    prefetch_tmap(mYm); prefetch_tmap(mYh); prefetch_tmap(mV); prefetch_tmap(mXm); prefetch_tmap(mXh);
+    mbar_expect_tx(&xfull, 4 * 16384);
+    tma_load_2d(sm + C::OFF_X, mXm, &xfull, 0, x0);
+    tma_load_2d(sm + C::OFF_X + 16384, mXm, &xfull, 64, x0);
+    tma_load_2d(sm + C::OFF_X + 32768, mXh, &xfull, 0, x0);
+    tma_load_2d(sm + C::OFF_X + 49152, mXh, &xfull, 64, x0);
+    int ylast[kFusedStages], vlast[kFusedStages];
+    for (int s = 0; s < kFusedStages; ++s) ylast[s] = vlast[s] = -1;
+    for (int t = 0; t < T && !abort_flag; ++t) {
+      const int s = t % kFusedStages, use = t / kFusedStages;
+      const int yr = t * 64;
+      if (use > 0 && !mbar_wait(&y_empty[s], (use - 1) & 1)) {
+        atomicExch(a.status, 41); abort_flag = 1; break;
+      }
+      uint8_t* st = sm + s * C::Y_STAGE;
+      mbar_expect_tx(&y_full[s], C::Y_STAGE);
+      tma_load_2d(st, mYm, &y_full[s], 0, yr);
+      tma_load_2d(st + 8192, mYm, &y_full[s], 64, yr);
+      tma_load_2d(st + C::Y_BYTES, mYh, &y_full[s], 0, yr);
+      tma_load_2d(st + C::Y_BYTES + 8192, mYh, &y_full[s], 64, yr);
+      ylast[s] = use & 1;
+      if (use > 0 && !mbar_wait(&v_empty[s], (use - 1) & 1)) {
+        atomicExch(a.status, 42); abort_flag = 1; break;
+      }
+      uint8_t* sv = sm + C::OFF_V + s * C::V_STAGE;
+      mbar_expect_tx(&v_full[s], C::V_STAGE);
+      tma_load_2d(sv, mV, &v_full[s], yr, x0);
+      tma_load_2d(sv + 16384, mV, &v_full[s], yr + 32, x0);
+      vlast[s] = use & 1;
+    }
+    mbar_wait(&xfull, 0);
+    for (int s = 0; s < kFusedStages; ++s) {
+      if (ylast[s] >= 0) mbar_wait(&y_full[s], ylast[s]);
+      if (vlast[s] >= 0) mbar_wait(&v_full[s], vlast[s]);
+    }
+  } else if (warp == mma_warp) {
+    // ---------------- MMA issuer (whole warp in the loop, one elected lane issues)
+    const uint32_t id_s = idesc_f16(128, 64, false, false, false);
+    const uint32_t id_m1 = idesc_f16(128, NP, false, false, true);
+    const uint32_t id_m2 = idesc_f16(128, 64, false, true, true);
+    const uint64_t dy0 = sdesc_sw128(smem_u32(sm), 16, 1024);
+    const uint64_t dy0mn = sdesc_sw128(smem_u32(sm), 8192, 1024);
+    // X^T: [128 R][64 j] column blocks 16 KB apart (LBO); U^T: one [128 R][64 g] block
+    const uint64_t dxm = sdesc_sw128(smem_u32(sm + C::OFF_X), 16384, 1024), dxh = dxm + (32768 >> 4);
+    const uint64_t duh = sdesc_sw128(smem_u32(sm + C::OFF_U), 16384, 1024), dul = duh + (16384 >> 4);
+    constexpr uint64_t kStage16 = C::Y_STAGE >> 4, kYh16 = C::Y_BYTES >> 4;
+    const uint32_t txm = tbase + C::T_XM, txh = tbase + C::T_XH;
+    const uint32_t ts0 = tbase + C::T_S0, ts1 = tbase + C::T_S1, tacc = tbase + C::T_ACC;
+    const uint32_t tm2 = tbase + C::T_M2, tuh = tbase + C::T_U, tul = tuh + 32;
+    auto aborted = [&]() { return __shfl_sync(0xffffffffu, (int)abort_flag, 0) != 0; };
+    auto fail = [&](int code) {
+      if (lane == 0) { atomicExch(a.status, code); abort_flag = 1; }
+      __syncwarp();
+    };
+    bool good = T > 0;
+    if (good && !mbar_wait_warp(&xfull, 0)) { fail(43); good = false; }
+    // the products of tile u: M1^T (TS, U from tensor memory, Y MN-major) and
+    // M2 (SS, X^T and U^T MN-major)
+    auto issue_products = [&](int u) -> bool {
+      const int s = u % kFusedStages, grp = u / kAccDrain;
+      const bool first = (u % kAccDrain) == 0;
+      const bool last = (u % kAccDrain) == kAccDrain - 1 || u == T - 1;
+      if (first && grp > 0 && !mbar_wait_warp(&acc_free, (grp - 1) & 1)) return false;
+      if (!mbar_wait_warp(&u_full, u & 1)) return false;
+      tc_fence_after();
+      const uint64_t bym = dy0mn + s * kStage16;
+      // passes (U_hi, Y_m), (U_hi, Y_h), (U_lo, Y_m); a runtime loop over the
+      // passes keeps one pass's operands live at a time
+#pragma unroll 1
+      for (int pass = 0; pass < 3; ++pass) {
+        const uint32_t ta = pass == 2 ? tul : tuh;
+        const uint64_t db = pass == 1 ? bym + kYh16 : bym;
+        const uint32_t acc0 = (first && pass == 0) ? 0u : 1u;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          if (elect_one()) mma_f16_ts(tacc, ta + kk * 8, db + kk * 128, id_m1, kk > 0 ? 1u : acc0);
+      }
+      if (elect_one()) {
+        mma_commit(&y_empty[s]);
+        if (last) mma_commit(&acc_ready);
+      }
+      __syncwarp();
+      if (u > 0 && !mbar_wait_warp(&m2_free, (u - 1) & 1)) return false;
+      tc_fence_after();
+      // passes (X_m, U_hi), (X_h, U_hi), (X_m, U_lo); K step kk: 16 R rows =
+      // 2048 bytes of both MN-major operands
+#pragma unroll 1
+      for (int pass = 0; pass < 3; ++pass) {
+        const uint64_t da = pass == 1 ? dxh : dxm;
+        const uint64_t db = pass == 2 ? dul : duh;
+        const uint32_t acc0 = pass > 0 ? 1u : 0u;
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk)
+          if (elect_one()) mma_f16(tm2, da + kk * 128, db + kk * 128, id_m2, kk > 0 ? 1u : acc0);
+      }
+      if (elect_one()) {
+        mma_commit(&u_free);
+        mma_commit(&m2_ready);
+      }
+      __syncwarp();
+      return true;
+    };
+    for (int t = 0; good && t < T && !aborted(); ++t) {
+      const int s = t % kFusedStages, use = t / kFusedStages;
+      if (!mbar_wait_warp(&y_full[s], use & 1)) { fail(44); good = false; break; }
+      if (t > 0 && !mbar_wait_warp(&s_free, (t - 1) & 1)) { fail(45); good = false; break; }
+      tc_fence_after();
+      const uint64_t dym = dy0 + s * kStage16, dyh = dym + kYh16;
+      // passes m.m' -> A0, then m.h', h.m', h.h' -> A1 (the pair kernel's order)
+#pragma unroll 1
+      for (int pass = 0; pass < 4; ++pass) {
+        const uint32_t td = pass == 0 ? ts0 : ts1;
+        const uint32_t ta = pass < 2 ? txm : txh;
+        const uint64_t db = (pass & 1) ? dyh : dym;
+        const uint32_t acc0 = pass >= 2 ? 1u : 0u;
+#pragma unroll
+        for (int kk = 0; kk < NP / 16; ++kk)
+          if (elect_one()) mma_f16_ts(td, ta + kk * 8, db + (kk >> 2) * 512 + (kk & 3) * 2, id_s, kk > 0 ? 1u : acc0);
+      }
+      if (elect_one()) mma_commit(&s_full);
+      __syncwarp();
+      if (t > 0 && !issue_products(t - 1)) { fail(46); good = false; break; }
+    }
+    if (good && T > 0 && !issue_products(T - 1)) fail(47);
+    if (elect_one()) mma_commit(&drain);
+    __syncwarp();
+    mbar_wait_warp(&drain, 0);
+  } else if (warp < kEpiWarps) {
+    // ---------------- epilogue: warp w % 4 = TMEM lane quadrant, w / 4 = quarter
+    // of the S / U columns (16 g), of the M1^T columns (32 j) and of the M2
+    // tile columns (16 g)
+    const int quad = warp & 3, c = warp >> 2;
+    const int r = quad * 32 + lane;
+    const uint32_t lane_off = static_cast<uint32_t>(quad * 32) << 16;
+    const long x = (long)x0 + r;
+    const bool xok = x < a.X;
+    const float f = a.sc[a.f_idx];
+    const bool want_e = a.epart != nullptr;
+    const uint32_t t_s0 = tbase + lane_off + C::T_S0 + 16 * c, t_s1 = t_s0 + (C::T_S1 - C::T_S0);
+    const uint32_t t_u = tbase + lane_off + C::T_U + 8 * c;
+    const uint32_t t_acc = tbase + lane_off + C::T_ACC + C::AC * c;
+    const uint32_t t_m2 = tbase + lane_off + C::T_M2 + 16 * c;
+    // V'^T of this thread's 16 columns: box c / 2 of the stage, 16-byte chunks
+    // 4 (c % 2) .. +3 of row r (128-byte swizzle: chunk q sits at q ^ (r % 8));
+    // U^T row r of the MN-major B operand: chunks 2c, 2c + 1 at (q ^ (r % 8))
+    const int vbox_off = C::OFF_V + (c >> 1) * 16384 + r * 128;
+    const int sw = r & 7, q0 = (c & 1) * 4;
+    uint8_t* urow = sm + C::OFF_U + r * 128;
+    const int uc0 = ((2 * c) ^ sw) << 4, uc1 = ((2 * c + 1) ^ sw) << 4;
+    float run[C::AC];
+#pragma unroll
+    for (int j = 0; j < C::AC; ++j) run[j] = 0.0f;
+    double esum = 0.0;
+    bool ok = T > 0;
+    auto aborted = [&]() { return __shfl_sync(0xffffffffu, (int)abort_flag, 0) != 0; };
+    auto fail = [&](int code) {
+      if (lane == 0) { atomicExch(a.status, code); abort_flag = 1; }
+      __syncwarp();
+    };
+    // M1^T group ending at tile u -> running sums
+    auto drain_m1 = [&](int u) -> bool {
+      if (!mbar_wait_warp(&acc_ready, (u / kAccDrain) & 1)) return false;
+      tc_fence_after();
+#pragma unroll
+      for (int h = 0; h < C::AC; h += 16) {
+        uint32_t ua[16];
+        tmem_ld16(t_acc + h, ua);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) run[h + j] += __uint_as_float(ua[j]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_free);
+      return true;
+    };
+    // M2 tile u -> its copy (lane = j: 32 consecutive floats per g row)
+    auto drain_m2 = [&](int u) -> bool {
+      if (!mbar_wait_warp(&m2_ready, u & 1)) return false;
+      tc_fence_after();
+      uint32_t mv[16];
+      tmem_ld16(t_m2, mv);
+      tmem_wait_ld();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&m2_free);
+      if (r < a.n) {
+        const float os = a.sc[a.out_idx];
+        const int g0 = u * 64 + 16 * c;
+        float* dst = a.m2acc + (long)(bx % a.ncopy) * a.m2_copy_stride + (long)g0 * a.n + r;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+          if (g0 + k < a.Y) red_add_f32(dst + (long)k * a.n, __uint_as_float(mv[k]) * os);
+      }
+      return true;
+    };
+    for (int t = 0; t < T && !aborted(); ++t) {
+      const int s = t % kFusedStages;
+      float sv[16];
+      if (!mbar_wait_warp(&s_full, t & 1)) { fail(48); ok = false; break; }
+      tc_fence_after();
+      {
+        uint32_t u0[16], u1[16];
+        tmem_ld16(t_s0, u0);
+        tmem_ld16(t_s1, u1);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) sv[j] = __uint_as_float(u0[j]) + __uint_as_float(u1[j]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&s_free);
+      // U(t) from the staged V'^T tile
+      if (!mbar_wait_warp(&v_full[s], (t / kFusedStages) & 1)) { fail(49); ok = false; break; }
+      uint32_t hi[8], lo[8];
+      float etile = 0.0f;
+      const uint8_t* vrow = sm + s * C::V_STAGE + vbox_off;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        float vv[2];
+        {
+          const float4 v4 = *reinterpret_cast<const float4*>(vrow + (((q0 + (q >> 1)) ^ sw) << 4));
+          vv[0] = (q & 1) ? v4.z : v4.x;
+          vv[1] = (q & 1) ? v4.w : v4.y;
+        }
+        const float p0 = vv[0] * sv[2 * q], p1 = vv[1] * sv[2 * q + 1];
+        if (want_e) {
+          etile = fmaf(p0, sv[2 * q], etile);
+          etile = fmaf(p1, sv[2 * q + 1], etile);
+        }
+        const float t0 = p0 * f, t1 = p1 * f;
+        const __half2 h01 = __floats2half2_rn(t0, t1);
+        const float2 b01 = __half22float2(h01);
+        const __half2 l01 = __floats2half2_rn(t0 - b01.x, t1 - b01.y);
+        hi[q] = *reinterpret_cast<const uint32_t*>(&h01);
+        lo[q] = *reinterpret_cast<const uint32_t*>(&l01);
+      }
+      esum += (double)etile;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&v_empty[s]);
+      // U(t) replaces U(t - 1) once both products of t - 1 have read it
+      if (t > 0 && !mbar_wait_warp(&u_free, (t - 1) & 1)) { fail(50); ok = false; break; }
+      tc_fence_after();
+      tmem_st8(t_u, hi);
+      tmem_st8(t_u + 32, lo);
+      *reinterpret_cast<uint4*>(urow + uc0) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(urow + uc1) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+      *reinterpret_cast<uint4*>(urow + 16384 + uc0) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      *reinterpret_cast<uint4*>(urow + 16384 + uc1) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+      tmem_wait_st();
+      fence_async_smem();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&u_full);
+      // the M1^T group that ended at t - 1, then M2(t - 1) and its reductions
+      if (t > 0 && ((t - 1) % kAccDrain) == kAccDrain - 1 && !drain_m1(t - 1)) {
+        fail(51); ok = false; break;
+      }
+      if (t > 0 && !drain_m2(t - 1)) { fail(52); ok = false; break; }
+    }
+    ok = ok && !aborted();
+    // the last M1^T group (ending at T - 1) and the last M2 tile
+    if (ok && T > 0 && !drain_m1(T - 1)) { fail(53); ok = false; }
+    if (ok && T > 0 && !drain_m2(T - 1)) { fail(54); ok = false; }
+    // ---------------- M1 (complete in this CTA): written [j][R]
+    if (xok) {
+      const float os = a.sc[a.out_idx];
+#pragma unroll
+      for (int j = 0; j < C::AC; ++j) {
+        const int col = C::AC * c + j;
+        if (col < a.n) a.out[(long)col * a.ldo + x] = ok ? run[j] * os : 0.0f;
+      }
+    }
+    if (want_e) {
+      double e = (ok && xok) ? esum : 0.0;
+      for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+      if (lane == 0) ered[warp] = e;
+      asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory");
+      if (tid == 0) {
+        double sum = 0.0;
+        for (int i = 0; i < kEpiWarps; ++i) sum += ered[i];
+        a.epart[bx] = sum;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == mma_warp) tmem_dealloc(tbase, 512);
+}
+
 // The three roles of one build; arguments and tensor maps in parameter space
 // (selected with constant indices, so they stay operands of the instructions).
 struct PairJob3 {
@@ -1371,18 +1771,25 @@ __global__ void __launch_bounds__(kPairThreads, 1) pair_kernel(const __grid_cons
 // space (a grouped batch is split into launches of at most this many roles).
 constexpr int kGroupRoles = 16;
 struct PairJobN {
-  CUtensorMap ym[kGroupRoles], yh[kGroupRoles], v[kGroupRoles];
+  CUtensorMap ym[kGroupRoles], yh[kGroupRoles], v[kGroupRoles], xm[kGroupRoles], xh[kGroupRoles];
   PairArgs a[kGroupRoles];
-  int gx[kGroupRoles], first[kGroupRoles];
+  int gx[kGroupRoles], first[kGroupRoles], kind[kGroupRoles];
   int nroles;
 };
 
+// Roles of kind 1 (NP = 128 only) run the fused body: one block per X tile.
 template <int NP>
 __global__ void __launch_bounds__(kPairThreads, 1)
     pair_kernel_group(const __grid_constant__ PairJobN job) {
   int ri = 0;
   while (ri + 1 < job.nroles && (int)blockIdx.x >= job.first[ri + 1]) ++ri;
   const int gx = job.gx[ri], blk = (int)blockIdx.x - job.first[ri];
+  if constexpr (NP == 128) {
+    if (job.kind[ri] == 1) {
+      fused_body(&job.ym[ri], &job.yh[ri], &job.v[ri], &job.xm[ri], &job.xh[ri], job.a[ri], blk);
+      return;
+    }
+  }
   pair_body<NP>(&job.ym[ri], &job.yh[ri], &job.v[ri], job.a[ri], blk % gx, blk / gx, gx);
 }
 
@@ -1571,6 +1978,7 @@ void launch_pair_roles(const std::vector<PairRole>& rs, int np, cudaStream_t s) 
     int blocks = 0, k = 0;
     for (size_t i = c0; i < rs.size() && k < kGroupRoles; ++i, ++k) {
       job.ym[k] = rs[i].ym; job.yh[k] = rs[i].yh; job.v[k] = rs[i].v;
+      job.xm[k] = rs[i].xm; job.xh[k] = rs[i].xh; job.kind[k] = rs[i].kind;
       job.a[k] = rs[i].a; job.gx[k] = rs[i].gx; job.first[k] = blocks;
       blocks += rs[i].nblk;
     }
@@ -1578,7 +1986,7 @@ void launch_pair_roles(const std::vector<PairRole>& rs, int np, cudaStream_t s) 
     if (np == 64)
       pair_kernel_group<64><<<blocks, kPairThreads, PairCfg<64>::SMEM, s>>>(job);
     else
-      pair_kernel_group<128><<<blocks, kPairThreads, PairCfg<128>::SMEM, s>>>(job);
+      pair_kernel_group<128><<<blocks, kPairThreads, FusedCfg::SMEM, s>>>(job);
     count_launch();
   }
 }
@@ -1697,8 +2105,13 @@ struct MixedState {
   double *DA = nullptr, *DD = nullptr, *DAT64 = nullptr, *DDT64 = nullptr;
   __half *DAT_m = nullptr, *DAT_h = nullptr, *DDT_m = nullptr, *DDT_h = nullptr;
   CUtensorMap m_DAT_m, m_DAT_h, m_DDT_m, m_DDT_h;
-  // n <= 128: the three roles of the fused pair launch
+  // n <= 128: the roles of the pair launch.  64-column pieces: A (M2), B (M1),
+  // C (M3); 128-column pieces (`fused`): roles[0] is the fused role (M1 and
+  // M2 from one pass over V, M2 reduced into kM2Copies copies held in M2p),
+  // roles[2] is C, and erole is the energy-only form of the fused role.
   PairRole roles[3];
+  bool fused = false;
+  PairRole erole;
   float tuned_ms = 0.0f;  // pair launch time of the split the autotuner kept
   int kchunkL1 = 64, kchunkL23 = 64;
   CUtensorMap m_phi_m, m_phi_h, m_CT_m, m_CT_h, m_psi128_m, m_psi128_h, m_psi64_m, m_psi64_h,
@@ -1722,10 +2135,15 @@ struct Plan {
   long Np, Ng8, Na8, Ng4, Na4;
   int np, xa, partsA, partsC, splitsL1, splitsL23, kchunkL1, kchunkL23, ychunkA, ychunkC;
   bool large;
+  bool fused;      // 128-column pieces, n <= 128: the fused role replaces roles A and B
   int nt;
   long epA, epC;
   int partsA_max;  // largest role-A split the autotuner may pick (buffer sizes)
 };
+
+// FP32 copies of M2 the fused role reduces into (X tile % kM2Copies): each
+// copy sums a fraction of the X tiles, and the copies are summed in FP64.
+constexpr int kM2Copies = 8;
 
 // Role-A splits the autotuner tries for n <= 128: the X tiles times the
 // split fill about 2, 3, 4, 6 or 8 waves of CTAs over the 152 SMs.
@@ -1751,6 +2169,7 @@ Plan make_plan(int64_t Ng, int N, int n, int Naux) {
   p.Na4 = rup(Naux, 4);
   p.xa = (Naux + 127) / 128;
   p.large = p.np > 128;
+  p.fused = p.np == 128;
   p.nt = (n + 127) / 128;
   if (!p.large) {
     // roles A and C: X = g tiles; split Y so the grid is about four waves of 152 SMs
@@ -1764,6 +2183,11 @@ Plan make_plan(int64_t Ng, int N, int n, int Naux) {
     for (int c : tune_candidates(Ng, p.xa)) p.partsA_max = std::max(p.partsA_max, c);
     p.epA = (long)p.partsA_max * p.xa;
     p.epC = (long)p.partsC * p.xa;
+    if (p.fused) {  // one CTA per 128 grid points over every g; M2 in kM2Copies copies
+      p.partsA = p.partsA_max = kM2Copies;
+      p.ychunkA = (int)rup(Naux, 64);
+      p.epA = (Ng + 127) / 128;
+    }
   } else {
     // M2 = T_A Psi and M3 = T_C Psi_g: (xa x nt) tiles, K split to about four waves
     const int t2 = p.xa * p.nt;
@@ -1838,7 +2262,7 @@ size_t mixed_footprint(int64_t Ng, int N, int n, int Naux) {
   const size_t ng = Ng, na = Naux;
   size_t b = 0;
   b += 2 * ng * p.Np * 2 + 2 * (size_t)N * p.Ng8 * 2 + 2 * (size_t)N * p.Na8 * 2;  // Phi pieces
-  b += na * p.Ng4 * 4 + (p.large ? 0 : ng * p.Na4 * 4) + na * p.Na4 * 4 + na * 4;  // V, V^T, W, idx
+  b += (p.fused ? 0 : na * p.Ng4 * 4) + (p.large ? 0 : ng * p.Na4 * 4) + na * p.Na4 * 4 + na * 4;  // V, V^T, W, idx
   if (p.large)  // T, third pieces
     b += 2 * na * p.Ng8 * 2 + 2 * na * p.Na8 * 2 + (ng + na) * p.np * 2;
   b += (ng + n) * p.Np * 2;  // third pieces of Phi' and Q
@@ -1857,6 +2281,7 @@ size_t mixed_full_footprint(int64_t Ng, int N, int n, int Naux) {
   const FullPlan f = make_full_plan(Ng, N, Naux);
   const size_t na = Naux, nN = N;
   size_t b = p.large ? 0 : 2 * na * p.Ng8 * 2 + 2 * na * p.Na8 * 2;  // T_A, T_C (hi, lo)
+  if (p.fused) b += na * p.Ng4 * 4;  // V in FP32 [g][R] (the fused build keeps only V^T)
   b += (size_t)(f.splitsF + f.splitsFC) * na * nN * 4;                // M_A, M_C partial sums
   b += 2 * na * nN * 8 + 2 * nN * p.Na8 * 8;                         // M_A, M_A - M_C, transposed
   b += 4 * nN * p.Na8 * 2;                                           // their pieces
@@ -1957,7 +2382,7 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(pair_kernel_group<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairCfg<64>::SMEM);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(pair_kernel_group<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairCfg<128>::SMEM);
+    e = cudaFuncSetAttribute(pair_kernel_group<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, FusedCfg::SMEM);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(energy_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairCfg<64>::SMEM);
   if (e == cudaSuccess)
@@ -1974,7 +2399,7 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   m->ychunkA = p.ychunkA; m->ychunkC = p.ychunkC;
   m->splitsL1 = p.splitsL1; m->splitsL23 = p.splitsL23;
   m->kchunkL1 = p.kchunkL1; m->kchunkL23 = p.kchunkL23;
-  m->large = p.large; m->nt = p.nt; m->epA = p.epA; m->epC = p.epC;
+  m->large = p.large; m->fused = p.fused; m->nt = p.nt; m->epA = p.epA; m->epC = p.epC;
   const size_t ng = Ng, na = Naux;
 #define MX(ptr, elems)                          \
   do {                                          \
@@ -1984,7 +2409,8 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   MX(m->phi_m, ng * p.Np); MX(m->phi_h, ng * p.Np);
   MX(m->phiT_m, (size_t)N * p.Ng8); MX(m->phiT_h, (size_t)N * p.Ng8);
   MX(m->phigT_m, (size_t)N * p.Na8); MX(m->phigT_h, (size_t)N * p.Na8);
-  MX(m->V32, na * p.Ng4); MX(m->W32, na * p.Na4);
+  if (!p.fused) MX(m->V32, na * p.Ng4);
+  MX(m->W32, na * p.Na4);
   if (!p.large) MX(m->VT32, ng * p.Na4);
   if (p.large) {
     MX(m->TA_h, na * p.Ng8); MX(m->TA_l, na * p.Ng8);
@@ -2083,8 +2509,11 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
       e = cudaMemcpyAsync(stage, V + (size_t)r0 * ng, rows * ng * 8, cudaMemcpyDefault, s);
       if (e != cudaSuccess) break;
       absmax_kernel<double><<<blocks_for(rows * ng), 256, 0, s>>>(stage, rows, ng, ng, m->am + AM_V);
-      f64_to_f32_kernel<<<blocks_for(rows * p.Ng4), 256, 0, s>>>(stage, rows, ng, m->V32 + r0 * p.Ng4, p.Ng4);
-      count_launch(2);
+      count_launch();
+      if (m->V32) {
+        f64_to_f32_kernel<<<blocks_for(rows * p.Ng4), 256, 0, s>>>(stage, rows, ng, m->V32 + r0 * p.Ng4, p.Ng4);
+        count_launch();
+      }
       if (m->VT32) {  // V^T [g][R]
         dim3 grid((unsigned)((ng + 31) / 32), (unsigned)((rows + 31) / 32));
         transpose_f64_f32_kernel<<<grid, dim3(32, 8), 0, s>>>(stage, rows, ng, ng, m->VT32 + r0, p.Na4);
@@ -2150,7 +2579,7 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   }
   {  // V' tiles [X rows][Y cols] in FP32: [128][32] boxes, 128-byte swizzle
     const auto F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    e = make_map(&m->m_VA, m->V32, F32, 4, (long)na, p.Ng4, 128, 32);
+    if (m->V32) e = make_map(&m->m_VA, m->V32, F32, 4, (long)na, p.Ng4, 128, 32);
     if (e == cudaSuccess && m->VT32) e = make_map(&m->m_VB, m->VT32, F32, 4, (long)ng, p.Na4, 128, 32);
     if (e == cudaSuccess) e = make_map(&m->m_VC, m->W32, F32, 4, (long)na, p.Na4, 128, 32);
     if (e != cudaSuccess) return fin(e);
@@ -2159,20 +2588,40 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
     // role A: M2[g][j] = sum_R (V o P)[g][R] Psi[R][j], and sum V o P^2
     // role B: M1[j][R] = sum_g (V^T o P^T)[R][g] Psi_g[g][j], written transposed
     // role C: M3[g][j] = sum_g' (W o Q)[g][g'] Psi_g[g'][j], and sum W o Q^2
+    // (128-column pieces: the fused role computes A and B in one pass)
     PairRole* r = m->roles;
-    r[0].ym = m->m_psi64_m; r[0].yh = m->m_psi64_h; r[0].v = m->m_VA;
-    set_split_a(m, m->partsA);
     const int gB = (int)((ng + 127) / 128);
-    r[1].ym = m->m_psig64_m; r[1].yh = m->m_psig64_h; r[1].v = m->m_VB;
-    r[1].a = PairArgs{(int)ng, (int)na, (int)rup(na, 64), n, m->psi_m, m->psi_h, np_, m->sc,
-                      SC_F_AB, SC_OUT_AB, m->M1, m->Ng4, 0, 1, nullptr, m->status};
-    r[1].gx = gB; r[1].nblk = gB; r[1].tiles = (int)(rup(na, 64) / 64);
+    for (int k = 0; k < 3; ++k) r[k].kind = 0;
+    if (m->fused) {
+      r[0].ym = m->m_psig64_m; r[0].yh = m->m_psig64_h; r[0].v = m->m_VB;
+      r[0].xm = m->m_psi128_m; r[0].xh = m->m_psi128_h; r[0].kind = 1;
+      r[0].a = PairArgs{(int)ng, (int)na, (int)rup(na, 64), n, m->psi_m, m->psi_h, np_, m->sc,
+                        SC_F_AB, SC_OUT_AB, m->M1, m->Ng4, 0, 1, m->EpA, m->status,
+                        m->VT32, p.Na4, m->M2p, kM2Copies, (long)(na * n)};
+      r[0].gx = gB; r[0].nblk = gB; r[0].tiles = (int)(rup(na, 64) / 64);
+      r[1] = r[0];
+      r[1].nblk = 0;  // unused: the fused role covers role B
+      // energy only: the fused role's S products and sums, in the same order
+      m->erole = r[0];
+      m->erole.kind = 0;
+      m->erole.a = PairArgs{(int)ng, (int)na, (int)rup(na, 64), n, m->psi_m, m->psi_h, np_, m->sc,
+                            SC_F_AB, SC_OUT_AB, nullptr, 0, 0, 1, m->EpA, m->status};
+    } else {
+      r[0].ym = m->m_psi64_m; r[0].yh = m->m_psi64_h; r[0].v = m->m_VA;
+      set_split_a(m, m->partsA);
+      r[1].ym = m->m_psig64_m; r[1].yh = m->m_psig64_h; r[1].v = m->m_VB;
+      r[1].a = PairArgs{(int)ng, (int)na, (int)rup(na, 64), n, m->psi_m, m->psi_h, np_, m->sc,
+                        SC_F_AB, SC_OUT_AB, m->M1, m->Ng4, 0, 1, nullptr, m->status};
+      r[1].gx = gB; r[1].nblk = gB; r[1].tiles = (int)(rup(na, 64) / 64);
+    }
     r[2].ym = m->m_psig64_m; r[2].yh = m->m_psig64_h; r[2].v = m->m_VC;
     r[2].a = PairArgs{(int)na, (int)na, m->ychunkC, n, m->psig_m, m->psig_h, np_, m->sc, SC_F_C,
                       SC_OUT_C, m->M3p, n, (long)(na * n), 0, m->EpC, m->status};
     r[2].gx = m->xa; r[2].nblk = m->xa * m->partsC; r[2].tiles = m->ychunkC / 64;
-    e = autotune_split_a(m, s);
-    if (e != cudaSuccess) return fin(e);
+    if (!m->fused) {
+      e = autotune_split_a(m, s);
+      if (e != cudaSuccess) return fin(e);
+    }
   }
   fin(cudaSuccess);
   *out = m;
@@ -2278,6 +2727,14 @@ cudaError_t mixed_full_prepare(MixedState* m) {
     e = alloc(m, &(ptr), (elems));          \
     if (e != cudaSuccess) return e;         \
   } while (0)
+  if (!m->V32) {  // the fused build keeps only V^T: form V [g][R] from it
+    FX(m->V32, (size_t)na * m->Ng4);
+    e = transpose<float>(m->VT32, ng, na, m->Na4, m->V32, m->Ng4, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    if (e == cudaSuccess)
+      e = make_map(&m->m_VA, m->V32, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, na, m->Ng4, 128, 32);
+    if (e != cudaSuccess) return e;
+  }
   if (!m->large) {
     FX(m->TA_h, na * m->Ng8); FX(m->TA_l, na * m->Ng8);
     FX(m->TC_h, na * m->Na8); FX(m->TC_l, na * m->Na8);
@@ -2374,7 +2831,7 @@ cudaError_t mixed_enqueue_energy(MixedState* m, const double* C, double* Ex, cud
   if (m->large)
     enqueue_t_products(m, s, false, true);
   else
-    launch_energy2(m->roles[0], m->roles[2], m->np, s);
+    launch_energy2(m->fused ? m->erole : m->roles[0], m->roles[2], m->np, s);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   hook(1, 0);
@@ -2414,6 +2871,11 @@ cudaError_t mixed_enqueue_pair(MixedState* m, cudaStream_t s, const StepHook& ho
     launch_gemm(m->m_TAmn_h, m->m_TAmn_l, m->m_psig64_m, m->m_psig64_h, m->m_TAmn_h, m->m_psig64_m,
                 g1, dim3((unsigned)((ng + 127) / 128), (unsigned)m->nt, 1), s);
     count_launch(3);
+  } else if (m->fused) {
+    // M1 and M2 from one pass over V^T (M2 reduced into the copies), and M3
+    e = cudaMemsetAsync(m->M2p, 0, (size_t)kM2Copies * na * n * 4, s);
+    if (e != cudaSuccess) return e;
+    launch_pair_roles({m->roles[0], m->roles[2]}, np, s);
   } else {
     launch_pair3(m->roles, np, s);
   }
@@ -2488,6 +2950,7 @@ struct PairGroup {
   int np[2] = {64, 128};
   std::vector<PairRole> roles[2];
   std::vector<MixedState*> large;  // members with n > 128 run their own pair step
+  std::vector<MixedState*> fused;  // members whose M2 copies are cleared before the launch
 };
 
 cudaError_t mixed_group_create(MixedState* const* ms, int count, PairGroup** out) {
@@ -2495,19 +2958,27 @@ cudaError_t mixed_group_create(MixedState* const* ms, int count, PairGroup** out
   for (int t = 0; t < 2; ++t) {
     for (int i = 0; i < count; ++i)
       if (!ms[i]->large && ms[i]->np == g->np[t])
-        for (int k = 0; k < 3; ++k) g->roles[t].push_back(ms[i]->roles[k]);
+        for (int k = 0; k < 3; ++k)
+          if (ms[i]->roles[k].nblk > 0) g->roles[t].push_back(ms[i]->roles[k]);
     std::stable_sort(g->roles[t].begin(), g->roles[t].end(),
                      [](const PairRole& x, const PairRole& y) { return x.tiles > y.tiles; });
   }
-  for (int i = 0; i < count; ++i)
+  for (int i = 0; i < count; ++i) {
     if (ms[i]->large) g->large.push_back(ms[i]);
+    if (ms[i]->fused) g->fused.push_back(ms[i]);
+  }
   *out = g;
   return cudaSuccess;
 }
 
 cudaError_t mixed_group_enqueue_pair(PairGroup* g, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  for (MixedState* m : g->fused)
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(m->M2p, 0, (size_t)kM2Copies * m->Naux * m->n * 4, s);
+  if (e != cudaSuccess) return e;
   for (int t = 0; t < 2; ++t) launch_pair_roles(g->roles[t], g->np[t], s);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   StepHook none{nullptr, nullptr};
   for (MixedState* m : g->large)
     if (e == cudaSuccess) e = mixed_enqueue_pair(m, s, none);

@@ -1,8 +1,10 @@
 """Batches and serving on the tensor-core path (XK_F16X3), through the C ABI.
 
 A batch runs one build of every member (cells of different sizes) as one
-CUDA graph with one grouped pair launch; the tensor-core kernels reduce in a
-fixed order, so every result must equal the member's own xk_build bitwise.
+CUDA graph with one grouped pair launch.  E_x is summed in a fixed order, so
+it equals the member's own xk_build bit for bit; K does too, except for
+members with 65 <= n <= 128, whose fused pair role adds M2 tiles into FP32
+copies in the order the CTAs finish (K then agrees to rounding, 1e-7).
 The same holds for builds of different cells submitted together
 (xk_submit / xk_poll): each result is the same alone and in the mix.
 """
@@ -12,6 +14,15 @@ import pytest
 from cellgen import CellSpec, Shell, build_cell, config_spec, load_cell
 
 pytestmark = pytest.mark.gpu
+
+
+TOL_REPEAT_K = 1e-7
+
+
+def same_build(K, E, Kr, Er, n):
+    if 64 < n <= 128:
+        return E == Er and np.max(np.abs(K - Kr)) <= TOL_REPEAT_K
+    return np.array_equal(K, Kr) and E == Er
 
 
 @pytest.fixture(scope="module")
@@ -48,8 +59,8 @@ def test_batch_equals_single_builds(xk, cells):
             before = xk.kernel_launches()
             for Cs, want in ((C2, ref2), ([c.C for c in cells], ref), (C2, ref2)):
                 Ks, Es = b.build(Cs)
-                for K, E, (Kr, Er) in zip(Ks, Es, want):
-                    assert np.array_equal(K, Kr) and E == Er
+                for K, E, (Kr, Er), c in zip(Ks, Es, want, cells):
+                    assert same_build(K, E, Kr, Er, c.n), c.spec.name
             assert xk.kernel_launches() > before
         finally:
             b.release()
@@ -75,7 +86,7 @@ def test_batch_rejects_bad_members(xk, cell1):
 def test_submit_poll_alone_and_mixed(xk, cells):
     """Serving: builds of three cells of different sizes submitted together
     (overlapping on the GPU) give the same results as each built alone."""
-    use = [cells[0], cells[2], cells[4]]
+    use = [cells[0], cells[2], cells[3], cells[4]]
     hs = [xk.Handle(c.phi, c.idx, c.V, c.W, c.dV, c.n, mode="f16x3") for c in use]
     try:
         ref = [h.build(c.C) for h, c in zip(hs, use)]
@@ -88,7 +99,7 @@ def test_submit_poll_alone_and_mixed(xk, cells):
                 st, K, E, eb = xk.poll(t, c.N, c.n)
                 if st == xk.XK_OK:
                     break
-            assert np.array_equal(K, Kr) and E == Er and eb > 0.0
+            assert same_build(K, E, Kr, Er, c.n) and eb > 0.0
     finally:
         for h in hs:
             h.release()
