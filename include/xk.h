@@ -22,8 +22,8 @@
  * xk_ace); serving (xk_submit, xk_poll) and batches (xk_batch_create,
  * xk_batch_build, xk_batch_release); other products on the same tables
  * (xk_energy, xk_energy_device, xk_build_full, xk_coulomb,
- * xk_exchange_energy_noalloc); diagnostics (xk_last_error,
- * xk_kernel_launches, xk_timing_enable, xk_timing_read).
+ * xk_exchange_energy_noalloc); diagnostics and control (xk_last_error,
+ * xk_kernel_launches, xk_timing_enable, xk_timing_read, xk_set_wait_limit).
  *
  * Conventions for every entry point:
  *   - All matrices are row-major, double precision, densely packed.
@@ -260,17 +260,52 @@ int xk_submit(xk_handle* h, const double* C, double deadline_ms, xk_ticket* t);
 
 /*
  * Non-blocking completion check.  XK_PENDING while the build runs;
- * XK_OK once done, after copying K_{mu i} (N x n) to K_out and E_x to Ex;
- * err_bound (nullable) receives the E_x accuracy the handle's mode is held
- * to relative to the FP64 path: 0 for XK_FP64; 1e-6 Ha for XK_F16X3, the
- * tolerance its parity tests enforce (largest measured |dE_x| 3.6e-7 Ha,
- * on the 216-centre cell), not a rigorous a-priori bound.  A ticket is consumed by
- * the XK_OK, XK_ETIMEDOUT or XK_ECUDA result.  XK_EINVAL for an unknown ticket.
+ * XK_OK once done, after copying K_{mu i} (N x n) to K_out and E_x to Ex.
+ * err_est (nullable) receives this build's a-posteriori error estimate
+ * |E_x - E_K|, where E_K = -sum_{mu,i} K_{mu i} C_{mu i} is the energy of the
+ * returned K (computed on the device in FP64, fixed order) and E_x the
+ * returned energy.  For XK_FP64 the two are the same number (0).  For
+ * XK_F16X3, E_x is the closed form of Eq. exoccri contracted with C,
+ * formed from the exact pair products, while K carries the rounding of the
+ * split FP16 back-contractions: the gap estimates the error of K on the
+ * occupied space (it tracks |E_K - E_x(FP64)| to within the much smaller
+ * error of the closed form).  The parity tests hold E_x to 1e-6 Ha and K to
+ * 1e-6 against the FP64 path.  A ticket is consumed by the XK_OK,
+ * XK_ETIMEDOUT or XK_ECUDA result.  XK_EINVAL for an unknown ticket.
  */
-int xk_poll(xk_ticket t, double* K_out, double* Ex, double* err_bound);
+int xk_poll(xk_ticket t, double* K_out, double* Ex, double* err_est);
 
-/* Free every device and host resource of the handle (waits for its work). */
+/*
+ * The error estimate of xk_poll for the last build enqueued on the handle by
+ * xk_build or xk_build_device (waits for the handle's stream): |E_x - E_K|
+ * with E_K = -sum K o C of the returned K; 0 for XK_FP64.  Errors: XK_EINVAL
+ * (NULL argument, no build yet), XK_ECUDA.
+ */
+int xk_error_estimate(xk_handle* h, double* est);
+
+/*
+ * Free every device and host resource of the handle (waits for its work).
+ * Tickets of the handle still pending become unknown.  It takes the handle's
+ * lock, so it waits for a call already inside the handle, but the caller
+ * must not start xk_submit or xk_poll on the handle (or its tickets) while
+ * xk_release runs: the handle's memory is gone when it returns.
+ */
 int xk_release(xk_handle* h);
+
+/*
+ * Bound, in SM clock cycles, on every pipeline wait inside the handle's
+ * tensor-core kernels (a TMA stage, an MMA result, an epilogue hand-off);
+ * 0 restores the default of 2e9 cycles (about one second).  A wait that runs
+ * out makes its kernel record a code, stop its loops, wait (with the default
+ * bound) for its own TMA copies and MMAs, free its tensor memory and return;
+ * the build then reports XK_ETIMEDOUT and the handle stays usable.  Applies
+ * to builds enqueued afterwards (a batch keeps the limit its members had
+ * when it was created).  No effect on XK_FP64 handles, whose kernels do not
+ * wait on one another.  It exists so that the timeout path can be exercised
+ * (a tiny limit) and so that a caller can bound a build more tightly than
+ * one second per wait.  Errors: XK_EINVAL (NULL handle, negative cycles).
+ */
+int xk_set_wait_limit(xk_handle* h, int64_t cycles);
 
 /*
  * Batches: one exchange build for each of several handles (cells of

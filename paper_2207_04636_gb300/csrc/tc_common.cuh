@@ -63,19 +63,29 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
 }
 
 // Waits for the phase with the given parity to complete; gives up after
-// kWaitCycles and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// `limit` SM clock cycles (default kWaitCycles) and returns false.  Kernels
+// take the limit of their pipeline waits from their launch arguments (a
+// handle can shorten it, e.g. to make a wait run out in a test); the final
+// waits for a kernel's own TMA copies and MMAs always use kWaitCycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          long long limit = kWaitCycles) {
   if (mbar_try(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try(bar, parity)) {
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
 }
 
 // All lanes of a converged warp wait; true only if every lane saw the phase.
-__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity) {
-  return __all_sync(0xffffffffu, mbar_wait(bar, parity));
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity,
+                                               long long limit = kWaitCycles) {
+  return __all_sync(0xffffffffu, mbar_wait(bar, parity, limit));
+}
+
+// The pipeline-wait limit of a launch: `arg` cycles when positive, else the default.
+__device__ __forceinline__ long long wait_limit(long long arg) {
+  return arg > 0 ? arg : kWaitCycles;
 }
 
 // True in exactly one lane (the lowest) of a converged warp.

@@ -56,6 +56,7 @@ struct Slot {
   double* C = nullptr;    // pinned, N x n
   double* K = nullptr;    // pinned, N x n
   double* Ex = nullptr;   // pinned, 1
+  int* st = nullptr;      // pinned, 4: the status word of this slot's build
   cudaEvent_t done = nullptr;
   int state = 0;          // 0 free, 1 in flight, 2 abandoned (timed out)
   xk_ticket ticket = 0;
@@ -195,6 +196,7 @@ void free_handle(xk_handle* h) {
     if (s.C) cudaFreeHost(s.C);
     if (s.K) cudaFreeHost(s.K);
     if (s.Ex) cudaFreeHost(s.Ex);
+    if (s.st) cudaFreeHost(s.st);
   }
   if (h->mixed) xk::mixed_destroy(h->mixed);
   fold_marks(h);
@@ -205,6 +207,21 @@ void free_handle(xk_handle* h) {
     g_admitted -= std::min(g_admitted, h->footprint);
   }
   delete h;
+}
+
+// Status word of the tensor-path kernels of the builds enqueued so far on
+// `s`: read and cleared in stream order (so a later build on the stream
+// starts from zero), then waited for.  0 when none gave up.
+int take_status(xk_handle* h, cudaStream_t s, cudaError_t* err) {
+  *err = cudaSuccess;
+  if (!h->mixed) return 0;
+  int st[4] = {0, 0, 0, 0};
+  int* dev = xk::mixed_status_ptr(h->mixed);
+  cudaError_t e = cudaMemcpyAsync(st, dev, 16, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dev, 0, 16, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  *err = e;
+  return st[0];
 }
 
 // Records the start or the end of `step` when timing is on.
@@ -379,10 +396,20 @@ int enqueue_full(xk_handle* h) {
   return XK_OK;
 }
 
+// Ex[0] = E_x; Ex[1] = -sum K o C of the K the build returns.  On the FP64
+// path the two are the same number; on the tensor path E_x is the closed
+// form (pin P8) and the gap |Ex[0] - Ex[1]| is the build's error estimate.
 int enqueue_build(xk_handle* h) {
-  if (h->mode == XK_FP64) return enqueue_fp64(h);
+  if (h->mode == XK_FP64) {
+    int rc = enqueue_fp64(h);
+    if (rc != XK_OK) return rc;
+    XK_CUDA(cudaMemcpyAsync(h->Ex + 1, h->Ex, 8, cudaMemcpyDeviceToDevice, h->stream));
+    return XK_OK;
+  }
   xk::StepHook hook{h->timing ? &step_hook : nullptr, h};
   cudaError_t e = xk::mixed_enqueue(h->mixed, h->C, h->K, h->Ex, h->stream, hook);
+  if (e == cudaSuccess)
+    e = xk::neg_dot_f64(h->K, h->C, (long)h->N * h->n, h->red, h->Ex + 1, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "mixed-precision build");
   return XK_OK;
 }
@@ -453,6 +480,16 @@ static int setup_impl(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const doub
          max_work(Ng, N, n, Naux) + (size_t)Naux) * 8 + (size_t)Naux * 4
       : 0;
 
+  if (const char* env = std::getenv("XK_HBM_BUDGET_BYTES")) {
+    // a budget set by the caller is checked before any device call
+    std::lock_guard<std::mutex> lk(g_admit_mu);
+    const size_t cap = (size_t)std::strtoull(env, nullptr, 10);
+    const size_t left = cap > g_admitted ? cap - g_admitted : 0;
+    if (need + isdf_tmp > left)
+      return fail(XK_ENOMEM, "xk_setup: footprint " + std::to_string(need + isdf_tmp) +
+                                 " bytes exceeds XK_HBM_BUDGET_BYTES less the live handles (" +
+                                 std::to_string(left) + " bytes)");
+  }
   int dev = 0;
   XK_CUDA(cudaGetDevice(&dev));
   size_t freeb = 0, totalb = 0;
@@ -489,7 +526,7 @@ static int setup_impl(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const doub
   XK_ALLOC(h->Ce, (size_t)N * n + 1);
   XK_ALLOC(h->Kf, (size_t)N * N);
   XK_ALLOC(h->K, (size_t)N * n);
-  XK_ALLOC(h->Ex, 1);
+  XK_ALLOC(h->Ex, 2);  // E_x and the energy of the returned K, -sum K o C
   XK_ALLOC(h->Kij, (size_t)n * n);
   XK_ALLOC(h->Lf, (size_t)n * n);
   XK_ALLOC(h->U, (size_t)n * n);
@@ -586,7 +623,8 @@ static int setup_impl(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const doub
   for (Slot& s : h->slots) {
     e = cudaHostAlloc((void**)&s.C, (size_t)N * n * 8, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&s.K, (size_t)N * n * 8, cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaHostAlloc((void**)&s.Ex, 8, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&s.Ex, 16, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&s.st, 16, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
     if (e != cudaSuccess) return bail(cuda_fail(e, "xk_setup slots"));
   }
@@ -707,8 +745,10 @@ int xk_build(xk_handle* h, const double* C, double* K_out, double* Ex) {
   XK_CUDA(cudaMemcpyAsync(Ex, h->Ex, 8, cudaMemcpyDeviceToHost, h->stream));
   XK_CUDA(cudaStreamSynchronize(h->stream));
   h->has_build = true;
-  if (h->mixed) {
-    const int st = xk::mixed_take_status(h->mixed);
+  {
+    cudaError_t e = cudaSuccess;
+    const int st = take_status(h, h->stream, &e);
+    if (e != cudaSuccess) return cuda_fail(e, "xk_build status");
     if (st != 0)
       return fail(XK_ETIMEDOUT, "xk_build: a bounded wait inside a kernel gave up (code " +
                                     std::to_string(st) + ")");
@@ -748,8 +788,10 @@ int xk_build_full(xk_handle* h, const double* C, double* K_out) {
   if (rc != XK_OK) return rc;
   XK_CUDA(cudaMemcpyAsync(K_out, h->Kf, (size_t)h->N * h->N * 8, cudaMemcpyDeviceToHost, h->stream));
   XK_CUDA(cudaStreamSynchronize(h->stream));
-  if (h->mixed) {
-    const int st = xk::mixed_take_status(h->mixed);
+  {
+    cudaError_t e = cudaSuccess;
+    const int st = take_status(h, h->stream, &e);
+    if (e != cudaSuccess) return cuda_fail(e, "xk_build_full status");
     if (st != 0)
       return fail(XK_ETIMEDOUT, "xk_build_full: a bounded wait inside a kernel gave up (code " +
                                     std::to_string(st) + ")");
@@ -840,8 +882,10 @@ int xk_energy(xk_handle* h, const double* C, double* Ex) {
   if (rc != XK_OK) return rc;
   XK_CUDA(cudaMemcpyAsync(Ex, h->Ce + (size_t)h->N * h->n, 8, cudaMemcpyDeviceToHost, h->stream));
   XK_CUDA(cudaStreamSynchronize(h->stream));
-  if (h->mixed) {
-    const int st = xk::mixed_take_status(h->mixed);
+  {
+    cudaError_t e = cudaSuccess;
+    const int st = take_status(h, h->stream, &e);
+    if (e != cudaSuccess) return cuda_fail(e, "xk_energy status");
     if (st != 0)
       return fail(XK_ETIMEDOUT, "xk_energy: a bounded wait inside a kernel gave up (code " +
                                     std::to_string(st) + ")");
@@ -922,7 +966,15 @@ int xk_submit(xk_handle* h, const double* C, double deadline_ms, xk_ticket* t) {
   int rc = enqueue_build(h);
   if (rc != XK_OK) return rc;
   XK_CUDA(cudaMemcpyAsync(s.K, h->K, kb, cudaMemcpyDeviceToHost, h->stream));
-  XK_CUDA(cudaMemcpyAsync(s.Ex, h->Ex, 8, cudaMemcpyDeviceToHost, h->stream));
+  XK_CUDA(cudaMemcpyAsync(s.Ex, h->Ex, 16, cudaMemcpyDeviceToHost, h->stream));
+  // this build's status word, taken and cleared in stream order: every slot
+  // reports the kernels of its own build
+  s.st[0] = 0;
+  if (h->mixed) {
+    int* dev = xk::mixed_status_ptr(h->mixed);
+    XK_CUDA(cudaMemcpyAsync(s.st, dev, 16, cudaMemcpyDeviceToHost, h->stream));
+    XK_CUDA(cudaMemsetAsync(dev, 0, 16, h->stream));
+  }
   XK_CUDA(cudaEventRecord(s.done, h->stream));
   h->has_build = true;
   s.state = 1;
@@ -937,7 +989,7 @@ int xk_submit(xk_handle* h, const double* C, double deadline_ms, xk_ticket* t) {
   return XK_OK;
 }
 
-int xk_poll(xk_ticket t, double* K_out, double* Ex, double* err_bound) {
+int xk_poll(xk_ticket t, double* K_out, double* Ex, double* err_est) {
   if (!K_out || !Ex) return fail(XK_EINVAL, "xk_poll: NULL argument");
   xk_handle* h = nullptr;
   int k = -1;
@@ -970,18 +1022,16 @@ int xk_poll(xk_ticket t, double* K_out, double* Ex, double* err_bound) {
     return cuda_fail(q, "xk_poll");
   }
   const size_t kb = (size_t)h->N * h->n * 8;
-  if (h->mixed) {
-    const int st = xk::mixed_take_status(h->mixed);
-    if (st != 0) {
-      s.state = 0;
-      consume();
-      return fail(XK_ETIMEDOUT, "xk_poll: a bounded wait inside a kernel gave up (code " +
-                                    std::to_string(st) + ")");
-    }
+  if (s.st[0] != 0) {
+    const int st = s.st[0];
+    s.state = 0;
+    consume();
+    return fail(XK_ETIMEDOUT, "xk_poll: a bounded wait inside a kernel gave up (code " +
+                                  std::to_string(st) + ")");
   }
   std::memcpy(K_out, s.K, kb);
   *Ex = *s.Ex;
-  if (err_bound) *err_bound = h->mode == XK_FP64 ? 0.0 : xk::mixed_error_bound(h->mixed);
+  if (err_est) *err_est = std::fabs(s.Ex[0] - s.Ex[1]);
   s.state = 0;
   consume();
   return XK_OK;
@@ -1029,11 +1079,32 @@ int xk_exchange_energy_noalloc(const double* K_dev, const double* C_dev, int64_t
 int xk_release(xk_handle* h) {
   if (!h) return fail(XK_EINVAL, "xk_release: NULL handle");
   {
+    // after any call that holds the handle (lock order: handle, then tickets)
+    std::lock_guard<std::mutex> lk(h->mu);
     std::lock_guard<std::mutex> tl(g_tickets_mu);
     for (auto it = g_tickets.begin(); it != g_tickets.end();)
       it = (it->second.first == h) ? g_tickets.erase(it) : std::next(it);
   }
   free_handle(h);
+  return XK_OK;
+}
+
+int xk_error_estimate(xk_handle* h, double* est) {
+  if (!h || !est) return fail(XK_EINVAL, "xk_error_estimate: NULL argument");
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (!h->has_build) return fail(XK_EINVAL, "xk_error_estimate: no build on this handle yet");
+  DeviceGuard g(h->device);
+  double e2[2] = {0.0, 0.0};
+  XK_CUDA(cudaMemcpyAsync(e2, h->Ex, 16, cudaMemcpyDeviceToHost, h->stream));
+  XK_CUDA(cudaStreamSynchronize(h->stream));
+  *est = std::fabs(e2[0] - e2[1]);
+  return XK_OK;
+}
+
+int xk_set_wait_limit(xk_handle* h, int64_t cycles) {
+  if (!h || cycles < 0) return fail(XK_EINVAL, "xk_set_wait_limit: NULL handle or negative limit");
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (h->mixed) xk::mixed_set_wait_limit(h->mixed, (long long)cycles);
   return XK_OK;
 }
 
@@ -1140,13 +1211,18 @@ int xk_batch_build(xk_batch* b, const double* const* C, double* const* K_out, do
     XK_CUDA(cudaMemcpyAsync(Ex_out + i, h->Ex, 8, cudaMemcpyDeviceToHost, b->stream));
   }
   XK_CUDA(cudaStreamSynchronize(b->stream));
+  // every member's status word, each read and cleared before returning
+  int first = 0;
   for (xk_handle* h : b->hs) {
     h->has_build = true;
-    const int st = xk::mixed_take_status(h->mixed);
-    if (st != 0)
-      return fail(XK_ETIMEDOUT, "xk_batch_build: a bounded wait inside a kernel gave up (code " +
-                                    std::to_string(st) + ")");
+    cudaError_t e = cudaSuccess;
+    const int st = take_status(h, b->stream, &e);
+    if (e != cudaSuccess) return cuda_fail(e, "xk_batch_build status");
+    if (st != 0 && first == 0) first = st;
   }
+  if (first != 0)
+    return fail(XK_ETIMEDOUT, "xk_batch_build: a bounded wait inside a kernel gave up (code " +
+                                  std::to_string(first) + ")");
   return XK_OK;
 }
 

@@ -566,6 +566,7 @@ struct GemmArgs {
   // splits); the launch has at most one CTA per SM and each CTA walks the
   // tiles blockIdx.x, blockIdx.x + gridDim.x, ... (x fastest).
   int tiles_x, tiles_y, tiles_z;
+  long long wait;  // pipeline-wait limit in SM cycles (0: the default)
 };
 
 constexpr int G_STAGES = 3;
@@ -600,6 +601,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     return ke > kb0 ? (ke - kb0 + 63) / 64 : 0;
   };
   const bool p3 = g.pieces3 != 0;
+  const long long lw = wait_limit(g.wait);
   const int ns = p3 ? 2 : G_STAGES;                       // stages
   const int sbytes = p3 ? 6 * 16384 : G_STAGE_BYTES;      // bytes per stage
 
@@ -635,7 +637,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const int m0 = bx * 128, n0 = by * 128, kbeg = bz * g.kchunk, nkb = kblocks(bz);
     for (int kb = 0; kb < nkb && !abort_flag; ++kb, ++it) {
       const int s = it % ns, use = it / ns;
-      if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) {
+      if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1, lw)) {
         atomicExch(g.status, 11); abort_flag = 1; break;
       }
       uint8_t* st = sm + s * sbytes;
@@ -700,10 +702,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       const int s = it % ns, grp = G0 + kb / kd, set = grp & 1;
       const bool first = (kb % kd) == 0;
       const bool last = (kb % kd) == kd - 1 || kb == nkb - 1;
-      if (first && grp >= 2 && !mbar_wait_warp(&set_free[set], ((grp >> 1) - 1) & 1)) {
+      if (first && grp >= 2 && !mbar_wait_warp(&set_free[set], ((grp >> 1) - 1) & 1, lw)) {
         fail(14); good = false; break;
       }
-      if (!mbar_wait_warp(&full[s], (it / ns) & 1)) { fail(12); good = false; break; }
+      if (!mbar_wait_warp(&full[s], (it / ns) & 1, lw)) { fail(12); good = false; break; }
       tc_fence_after();
       if (p3) {
         const uint64_t dam = dkm + s * (uint64_t)(sbytes >> 4), dah = dam + 1024, dal = dam + 2048;
@@ -780,7 +782,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     bool ok = true;
     for (int gi = 0; gi < ngroups; ++gi) {
       const int grp = G0 + gi, set = grp & 1;
-      if (__shfl_sync(0xffffffffu, (int)abort_flag, 0) || !mbar_wait_warp(&set_ready[set], (grp >> 1) & 1)) {
+      if (__shfl_sync(0xffffffffu, (int)abort_flag, 0) || !mbar_wait_warp(&set_ready[set], (grp >> 1) & 1, lw)) {
         ok = false;
         if (lane == 0 && !abort_flag) { atomicExch(g.status, 13); abort_flag = 1; }
         __syncwarp();
@@ -957,7 +959,8 @@ int sm_count() {
 // gemm_kernel over the logical grid `tiles` with at most one CTA per SM.
 void launch_gemm(const CUtensorMap& mAm, const CUtensorMap& mAh, const CUtensorMap& mBm,
                  const CUtensorMap& mBh, const CUtensorMap& mAl, const CUtensorMap& mBl, GemmArgs g,
-                 dim3 tiles, cudaStream_t s) {
+                 dim3 tiles, cudaStream_t s, long long wait = 0) {
+  g.wait = wait;
   g.tiles_x = (int)tiles.x;
   g.tiles_y = (int)tiles.y;
   g.tiles_z = (int)tiles.z;
@@ -1005,6 +1008,7 @@ struct PairArgs {
   float* m2acc;
   int ncopy;
   long m2_copy_stride;
+  long long wait;  // pipeline-wait limit in SM cycles (0: the default)
 };
 
 // One role of a pair launch (host record; copied into the launch parameters).
@@ -1071,7 +1075,7 @@ template <int NP>
 __device__ __forceinline__ void produce_tiles(const CUtensorMap* mYm, const CUtensorMap* mYh,
                                               const CUtensorMap* mV, uint8_t* sm, uint64_t* full,
                                               uint64_t* empty, int T, int y0, int x0,
-                                              volatile int& abort_flag, int* status) {
+                                              volatile int& abort_flag, int* status, long long lw) {
   using C = PairCfg<NP>;
   constexpr int NKB = NP / 64;
   prefetch_tmap(mYm); prefetch_tmap(mYh); prefetch_tmap(mV);
@@ -1079,7 +1083,7 @@ __device__ __forceinline__ void produce_tiles(const CUtensorMap* mYm, const CUte
   for (int s = 0; s < kStages; ++s) last_parity[s] = -1;
   for (int t = 0; t < T && !abort_flag; ++t) {
     const int s = t % kStages, use = t / kStages;
-    if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) {
+    if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1, lw)) {
       atomicExch(status, 21); abort_flag = 1; break;
     }
     uint8_t* st = sm + s * C::STAGE;
@@ -1116,6 +1120,7 @@ __device__ __forceinline__ void pair_body(const CUtensorMap* mYm, const CUtensor
   const int y0 = by * a.ychunk;
   const int y1 = min(a.Y, y0 + a.ychunk);
   const int T = y1 > y0 ? (y1 - y0 + 63) / 64 : 0;
+  const long long lw = wait_limit(a.wait);
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -1149,7 +1154,7 @@ __device__ __forceinline__ void pair_body(const CUtensorMap* mYm, const CUtensor
   tc_fence_after();
 
   if (warp == prod_warp && lane == 0) {
-    produce_tiles<NP>(mYm, mYh, mV, sm, full, empty, T, y0, x0, abort_flag, a.status);
+    produce_tiles<NP>(mYm, mYh, mV, sm, full, empty, T, y0, x0, abort_flag, a.status, lw);
   } else if (warp == mma_warp) {
     // ---------------- MMA issuer: the whole warp runs the loop (warp-uniform
     // descriptors and waits); one elected lane issues each MMA and commit.
@@ -1172,8 +1177,8 @@ __device__ __forceinline__ void pair_body(const CUtensorMap* mYm, const CUtensor
       const int s = u % kStages, b = u & 1, grp = u / kAccDrain;
       const bool first = (u % kAccDrain) == 0;
       const bool last = (u % kAccDrain) == kAccDrain - 1 || u == T - 1;
-      if (first && grp > 0 && !mbar_wait_warp(&acc_free, (grp - 1) & 1)) return false;
-      if (!mbar_wait_warp(&u_full[b], (u >> 1) & 1)) return false;
+      if (first && grp > 0 && !mbar_wait_warp(&acc_free, (grp - 1) & 1, lw)) return false;
+      if (!mbar_wait_warp(&u_full[b], (u >> 1) & 1, lw)) return false;
       tc_fence_after();
       const uint64_t bym = dy0mn + s * kStage16, byh = bym + kYh16;
       const uint32_t tuh = tbase + C::T_U + b * 64, tul = tuh + 32;
@@ -1197,8 +1202,8 @@ __device__ __forceinline__ void pair_body(const CUtensorMap* mYm, const CUtensor
     };
     for (int t = 0; good && t < T && !aborted(); ++t) {
       const int s = t % kStages, use = t / kStages;
-      if (!mbar_wait_warp(&full[s], use & 1)) { fail(23); good = false; break; }
-      if (t > 0 && !mbar_wait_warp(&s_free, (t - 1) & 1)) { fail(24); good = false; break; }
+      if (!mbar_wait_warp(&full[s], use & 1, lw)) { fail(23); good = false; break; }
+      if (t > 0 && !mbar_wait_warp(&s_free, (t - 1) & 1, lw)) { fail(24); good = false; break; }
       tc_fence_after();
       const uint64_t dym = dy0 + s * kStage16, dyh = dym + kYh16;
       // K step kk: 8 TMEM columns of X; Y tile offset (kk/4)*8192 + (kk%4)*32 bytes
@@ -1258,7 +1263,7 @@ __device__ __forceinline__ void pair_body(const CUtensorMap* mYm, const CUtensor
       const int b = t & 1;
       float sv[16];
       if (t < T) {
-        if (!mbar_wait_warp(&s_full, t & 1)) { fail(27); ok = false; break; }
+        if (!mbar_wait_warp(&s_full, t & 1, lw)) { fail(27); ok = false; break; }
         tc_fence_after();
         uint32_t u0[16], u1[16];
         tmem_ld16(t_s0, u0);
@@ -1273,7 +1278,7 @@ __device__ __forceinline__ void pair_body(const CUtensorMap* mYm, const CUtensor
       // drain the second-product accumulator into the running sums after each group
       if (t > 0 && (((t - 1) % kAccDrain) == kAccDrain - 1 || t == T)) {
         const int grp = (t - 1) / kAccDrain;
-        if (!mbar_wait_warp(&acc_ready, grp & 1)) { fail(29); ok = false; break; }
+        if (!mbar_wait_warp(&acc_ready, grp & 1, lw)) { fail(29); ok = false; break; }
         tc_fence_after();
 #pragma unroll
         for (int h = 0; h < C::AC; h += 16) {  // 16 columns at a time (register budget)
@@ -1312,7 +1317,7 @@ __device__ __forceinline__ void pair_body(const CUtensorMap* mYm, const CUtensor
         lo[q] = *reinterpret_cast<const uint32_t*>(&l01);
       }
       esum += (double)etile;
-      if (t >= 2 && !mbar_wait_warp(&u_free[b], ((t - 2) >> 1) & 1)) { fail(28); ok = false; break; }
+      if (t >= 2 && !mbar_wait_warp(&u_free[b], ((t - 2) >> 1) & 1, lw)) { fail(28); ok = false; break; }
       tc_fence_after();
       tmem_st8(t_u + b * 64, hi);
       tmem_st8(t_u + b * 64 + 32, lo);
@@ -1414,6 +1419,7 @@ __device__ __forceinline__ void fused_body(const CUtensorMap* mYm, const CUtenso
   const int prod_warp = kEpiWarps, mma_warp = kEpiWarps + 1;
   const int x0 = bx * 128;
   const int T = a.Y > 0 ? (a.Y + 63) / 64 : 0;
+  const long long lw = wait_limit(a.wait);
 
   if (tid == 0) {
     for (int s = 0; s < kFusedStages; ++s) {
@@ -1464,7 +1470,7 @@ __device__ __forceinline__ void fused_body(const CUtensorMap* mYm, const CUtenso
     for (int t = 0; t < T && !abort_flag; ++t) {
       const int s = t % kFusedStages, use = t / kFusedStages;
       const int yr = t * 64;
-      if (use > 0 && !mbar_wait(&y_empty[s], (use - 1) & 1)) {
+      if (use > 0 && !mbar_wait(&y_empty[s], (use - 1) & 1, lw)) {
         atomicExch(a.status, 41); abort_flag = 1; break;
       }
       uint8_t* st = sm + s * C::Y_STAGE;
@@ -1474,7 +1480,7 @@ __device__ __forceinline__ void fused_body(const CUtensorMap* mYm, const CUtenso
       tma_load_2d(st + C::Y_BYTES, mYh, &y_full[s], 0, yr);
       tma_load_2d(st + C::Y_BYTES + 8192, mYh, &y_full[s], 64, yr);
       ylast[s] = use & 1;
-      if (use > 0 && !mbar_wait(&v_empty[s], (use - 1) & 1)) {
+      if (use > 0 && !mbar_wait(&v_empty[s], (use - 1) & 1, lw)) {
         atomicExch(a.status, 42); abort_flag = 1; break;
       }
       uint8_t* sv = sm + C::OFF_V + s * C::V_STAGE;
@@ -1508,15 +1514,15 @@ __device__ __forceinline__ void fused_body(const CUtensorMap* mYm, const CUtenso
       __syncwarp();
     };
     bool good = T > 0;
-    if (good && !mbar_wait_warp(&xfull, 0)) { fail(43); good = false; }
+    if (good && !mbar_wait_warp(&xfull, 0, lw)) { fail(43); good = false; }
     // the products of tile u: M1^T (TS, U from tensor memory, Y MN-major) and
     // M2 (SS, X^T and U^T MN-major)
     auto issue_products = [&](int u) -> bool {
       const int s = u % kFusedStages, grp = u / kAccDrain;
       const bool first = (u % kAccDrain) == 0;
       const bool last = (u % kAccDrain) == kAccDrain - 1 || u == T - 1;
-      if (first && grp > 0 && !mbar_wait_warp(&acc_free, (grp - 1) & 1)) return false;
-      if (!mbar_wait_warp(&u_full, u & 1)) return false;
+      if (first && grp > 0 && !mbar_wait_warp(&acc_free, (grp - 1) & 1, lw)) return false;
+      if (!mbar_wait_warp(&u_full, u & 1, lw)) return false;
       tc_fence_after();
       const uint64_t bym = dy0mn + s * kStage16;
       // passes (U_hi, Y_m), (U_hi, Y_h), (U_lo, Y_m); a runtime loop over the
@@ -1535,7 +1541,7 @@ __device__ __forceinline__ void fused_body(const CUtensorMap* mYm, const CUtenso
         if (last) mma_commit(&acc_ready);
       }
       __syncwarp();
-      if (u > 0 && !mbar_wait_warp(&m2_free, (u - 1) & 1)) return false;
+      if (u > 0 && !mbar_wait_warp(&m2_free, (u - 1) & 1, lw)) return false;
       tc_fence_after();
       // passes (X_m, U_hi), (X_h, U_hi), (X_m, U_lo); K step kk: 16 R rows =
       // 2048 bytes of both MN-major operands
@@ -1557,8 +1563,8 @@ __device__ __forceinline__ void fused_body(const CUtensorMap* mYm, const CUtenso
     };
     for (int t = 0; good && t < T && !aborted(); ++t) {
       const int s = t % kFusedStages, use = t / kFusedStages;
-      if (!mbar_wait_warp(&y_full[s], use & 1)) { fail(44); good = false; break; }
-      if (t > 0 && !mbar_wait_warp(&s_free, (t - 1) & 1)) { fail(45); good = false; break; }
+      if (!mbar_wait_warp(&y_full[s], use & 1, lw)) { fail(44); good = false; break; }
+      if (t > 0 && !mbar_wait_warp(&s_free, (t - 1) & 1, lw)) { fail(45); good = false; break; }
       tc_fence_after();
       const uint64_t dym = dy0 + s * kStage16, dyh = dym + kYh16;
       // passes m.m' -> A0, then m.h', h.m', h.h' -> A1 (the pair kernel's order)
@@ -1614,7 +1620,7 @@ __device__ __forceinline__ void fused_body(const CUtensorMap* mYm, const CUtenso
     };
     // M1^T group ending at tile u -> running sums
     auto drain_m1 = [&](int u) -> bool {
-      if (!mbar_wait_warp(&acc_ready, (u / kAccDrain) & 1)) return false;
+      if (!mbar_wait_warp(&acc_ready, (u / kAccDrain) & 1, lw)) return false;
       tc_fence_after();
 #pragma unroll
       for (int h = 0; h < C::AC; h += 16) {
@@ -1631,7 +1637,7 @@ __device__ __forceinline__ void fused_body(const CUtensorMap* mYm, const CUtenso
     };
     // M2 tile u -> its copy (lane = j: 32 consecutive floats per g row)
     auto drain_m2 = [&](int u) -> bool {
-      if (!mbar_wait_warp(&m2_ready, u & 1)) return false;
+      if (!mbar_wait_warp(&m2_ready, u & 1, lw)) return false;
       tc_fence_after();
       uint32_t mv[16];
       tmem_ld16(t_m2, mv);
@@ -1652,7 +1658,7 @@ __device__ __forceinline__ void fused_body(const CUtensorMap* mYm, const CUtenso
     for (int t = 0; t < T && !aborted(); ++t) {
       const int s = t % kFusedStages;
       float sv[16];
-      if (!mbar_wait_warp(&s_full, t & 1)) { fail(48); ok = false; break; }
+      if (!mbar_wait_warp(&s_full, t & 1, lw)) { fail(48); ok = false; break; }
       tc_fence_after();
       {
         uint32_t u0[16], u1[16];
@@ -1666,7 +1672,7 @@ __device__ __forceinline__ void fused_body(const CUtensorMap* mYm, const CUtenso
       __syncwarp();
       if (lane == 0) mbar_arrive(&s_free);
       // U(t) from the staged V'^T tile
-      if (!mbar_wait_warp(&v_full[s], (t / kFusedStages) & 1)) { fail(49); ok = false; break; }
+      if (!mbar_wait_warp(&v_full[s], (t / kFusedStages) & 1, lw)) { fail(49); ok = false; break; }
       uint32_t hi[8], lo[8];
       float etile = 0.0f;
       const uint8_t* vrow = sm + s * C::V_STAGE + vbox_off;
@@ -1694,7 +1700,7 @@ __device__ __forceinline__ void fused_body(const CUtensorMap* mYm, const CUtenso
       __syncwarp();
       if (lane == 0) mbar_arrive(&v_empty[s]);
       // U(t) replaces U(t - 1) once both products of t - 1 have read it
-      if (t > 0 && !mbar_wait_warp(&u_free, (t - 1) & 1)) { fail(50); ok = false; break; }
+      if (t > 0 && !mbar_wait_warp(&u_free, (t - 1) & 1, lw)) { fail(50); ok = false; break; }
       tc_fence_after();
       tmem_st8(t_u, hi);
       tmem_st8(t_u + 32, lo);
@@ -1829,6 +1835,7 @@ __device__ __forceinline__ void energy_body(const CUtensorMap* mYm, const CUtens
   const int y0 = by * a.ychunk;
   const int y1 = min(a.Y, y0 + a.ychunk);
   const int T = y1 > y0 ? (y1 - y0 + 63) / 64 : 0;
+  const long long lw = wait_limit(a.wait);
   constexpr uint32_t T_SB = 128;  // first S buffer; the second follows 128 columns on
 
   if (tid == 0) {
@@ -1859,7 +1866,7 @@ __device__ __forceinline__ void energy_body(const CUtensorMap* mYm, const CUtens
   tc_fence_after();
 
   if (warp == prod_warp && lane == 0) {
-    produce_tiles<NP>(mYm, mYh, mV, sm, full, empty, T, y0, x0, abort_flag, a.status);
+    produce_tiles<NP>(mYm, mYh, mV, sm, full, empty, T, y0, x0, abort_flag, a.status, lw);
   } else if (warp == mma_warp) {
     const uint32_t id_s = idesc_f16(128, 64, false, false, false);
     const uint64_t dy0 = sdesc_sw128(smem_u32(sm), 16, 1024);
@@ -1872,8 +1879,8 @@ __device__ __forceinline__ void energy_body(const CUtensorMap* mYm, const CUtens
     };
     for (int t = 0; t < T && !aborted(); ++t) {
       const int s = t % kStages, use = t / kStages, b = t & 1;
-      if (!mbar_wait_warp(&full[s], use & 1)) { fail(31); break; }
-      if (t >= 2 && !mbar_wait_warp(&s_free[b], ((t - 2) >> 1) & 1)) { fail(32); break; }
+      if (!mbar_wait_warp(&full[s], use & 1, lw)) { fail(31); break; }
+      if (t >= 2 && !mbar_wait_warp(&s_free[b], ((t - 2) >> 1) & 1, lw)) { fail(32); break; }
       tc_fence_after();
       const uint64_t dym = dy0 + s * kStage16, dyh = dym + kYh16;
       const uint32_t ts0 = tbase + T_SB + 128 * b, ts1 = ts0 + 64;
@@ -1915,7 +1922,7 @@ __device__ __forceinline__ void energy_body(const CUtensorMap* mYm, const CUtens
     };
     for (int t = 0; t < T && !aborted(); ++t) {
       const int b = t & 1;
-      if (!mbar_wait_warp(&s_full[b], (t >> 1) & 1)) { fail(33); ok = false; break; }
+      if (!mbar_wait_warp(&s_full[b], (t >> 1) & 1, lw)) { fail(33); ok = false; break; }
       tc_fence_after();
       float sv[16];
       {
@@ -2112,6 +2119,7 @@ struct MixedState {
   PairRole roles[3];
   bool fused = false;
   PairRole erole;
+  long long wait_cycles = 0;  // pipeline-wait limit of the handle's kernels (0: the default)
   float tuned_ms = 0.0f;  // pair launch time of the split the autotuner kept
   int kchunkL1 = 64, kchunkL23 = 64;
   CUtensorMap m_phi_m, m_phi_h, m_CT_m, m_CT_h, m_psi128_m, m_psi128_h, m_psi64_m, m_psi64_h,
@@ -2662,14 +2670,14 @@ cudaError_t mixed_enqueue_pre(MixedState* m, const double* C, cudaStream_t s, co
                m->psi_m, m->psi_h, np, SC_PSI, m->am + AM_RN2};
     g.pieces3 = 1;
     launch_gemm(m->m_phi_m, m->m_phi_h, m->m_CT_m, m->m_CT_h, m->m_phi_l, m->m_CT_l, g,
-                dim3((unsigned)((ng + 127) / 128), 1, 1), s);
+                dim3((unsigned)((ng + 127) / 128), 1, 1), s, m->wait_cycles);
   } else {  // n > 128: Psi in FP32 (the M1 buffer, free until step 3), then per-row pieces
     GemmArgs g{};
     g.M = (int)ng; g.Ncols = n; g.K = N; g.kchunk = (int)m->Np;
     g.out = m->M1; g.ldo = n; g.sc = m->sc; g.scale_idx = SC_OUT_ORB; g.status = m->status;
     g.pieces3 = 1;  // three pieces: the orbital split error would dominate E_x at this n
     launch_gemm(m->m_phi_m, m->m_phi_h, m->m_CT_m, m->m_CT_h, m->m_phi_l, m->m_CT_l, g,
-                dim3((unsigned)((ng + 127) / 128), (unsigned)m->nt, 1), s);
+                dim3((unsigned)((ng + 127) / 128), (unsigned)m->nt, 1), s, m->wait_cycles);
     split_rows_f32_kernel<<<152 * 4, 256, 0, s>>>(m->M1, ng, n, n, m->sc, SC_PSI, m->psi_m,
                                                   m->psi_h, m->psi_l, np, m->am + AM_RN2);
     count_launch();
@@ -2702,14 +2710,14 @@ void enqueue_t_products(MixedState* m, cudaStream_t s, bool store, bool energy) 
   t.ld_t = m->Ng8; t.epart = energy ? m->EpA : nullptr; t.pieces3 = p3 ? 1 : 0;
   launch_gemm(m->m_psig128_m, m->m_psig128_h, m->m_psi128_m, m->m_psi128_h,
               p3 ? m->m_psig128_l : m->m_psig128_m, p3 ? m->m_psi128_l : m->m_psi128_m, t,
-              dim3((unsigned)m->xa, (unsigned)((ng + 127) / 128), 1), s);
+              dim3((unsigned)m->xa, (unsigned)((ng + 127) / 128), 1), s, m->wait_cycles);
   GemmArgs tc = t;
   tc.Ncols = (int)na; tc.tv = m->W32; tc.ldv = m->Na4; tc.f_idx = SC_F_C;
   tc.th = store ? m->TC_h : nullptr; tc.tl = store ? m->TC_l : nullptr;
   tc.ld_t = m->Na8; tc.epart = energy ? m->EpC : nullptr;
   launch_gemm(m->m_psig128_m, m->m_psig128_h, m->m_psig128_m, m->m_psig128_h,
               p3 ? m->m_psig128_l : m->m_psig128_m, p3 ? m->m_psig128_l : m->m_psig128_m, tc,
-              dim3((unsigned)m->xa, (unsigned)((na + 127) / 128), 1), s);
+              dim3((unsigned)m->xa, (unsigned)((na + 127) / 128), 1), s, m->wait_cycles);
   count_launch(2);
 }
 
@@ -2782,12 +2790,12 @@ cudaError_t mixed_enqueue_full(MixedState* m, const double* C, double* Kf, cudaS
     g.M = (int)na; g.Ncols = N; g.K = (int)ng; g.kchunk = m->kchunkF; g.out = m->MpA; g.ldo = N;
     g.split_stride = na * N; g.sc = m->sc; g.scale_idx = SC_OUT_FA; g.status = m->status;
     launch_gemm(m->m_TA_h, m->m_TA_l, m->m_phiT_m, m->m_phiT_h, m->m_TA_h, m->m_phiT_m, g,
-                dim3((unsigned)m->xa, tn, (unsigned)m->splitsF), s);
+                dim3((unsigned)m->xa, tn, (unsigned)m->splitsF), s, m->wait_cycles);
     // M_C = T_C Phi_g (A = T_C [g][g'], B = Phi_g^T pieces [nu][g'])
     GemmArgs gc = g;
     gc.K = (int)na; gc.kchunk = m->kchunkFC; gc.out = m->MpC; gc.scale_idx = SC_OUT_FC;
     launch_gemm(m->m_TC_h, m->m_TC_l, m->m_phigT_m, m->m_phigT_h, m->m_TC_h, m->m_phigT_m, gc,
-                dim3((unsigned)m->xa, tn, (unsigned)m->splitsFC), s);
+                dim3((unsigned)m->xa, tn, (unsigned)m->splitsFC), s, m->wait_cycles);
   }
   const long cnt = na * N;
   reduce_parts_kernel<<<blocks_for(cnt), 256, 0, s>>>(m->MpA, m->splitsF, nullptr, 0, cnt, m->DA,
@@ -2808,11 +2816,11 @@ cudaError_t mixed_enqueue_full(MixedState* m, const double* C, double* Kf, cudaS
     g.M = N; g.Ncols = N; g.K = (int)na; g.kchunk = m->kchunkY; g.out = m->Yp; g.ldo = N;
     g.split_stride = (long)N * N; g.sc = m->sc; g.scale_idx = SC_OUT_FY; g.status = m->status;
     launch_gemm(m->m_phigT_m, m->m_phigT_h, m->m_DAT_m, m->m_DAT_h, m->m_phigT_m, m->m_DAT_m, g,
-                dim3(tn, tn, (unsigned)m->splitsY), s);
+                dim3(tn, tn, (unsigned)m->splitsY), s, m->wait_cycles);
     GemmArgs gz = g;
     gz.out = m->Zp; gz.scale_idx = SC_OUT_FZ;
     launch_gemm(m->m_phigT_m, m->m_phigT_h, m->m_DDT_m, m->m_DDT_h, m->m_phigT_m, m->m_DDT_m, gz,
-                dim3(tn, tn, (unsigned)m->splitsY), s);
+                dim3(tn, tn, (unsigned)m->splitsY), s, m->wait_cycles);
     count_launch(4);
   }
   final_kfull_kernel<<<blocks_for((long)N * N), 256, 0, s>>>(m->Zp, m->splitsY, m->Yp, m->splitsY,
@@ -2859,17 +2867,17 @@ cudaError_t mixed_enqueue_pair(MixedState* m, cudaStream_t s, const StepHook& ho
     g2.ldo = n; g2.split_stride = na * n; g2.sc = m->sc; g2.scale_idx = SC_OUT_AB;
     g2.status = m->status; g2.b_mn = 1;
     launch_gemm(m->m_TA_h, m->m_TA_l, m->m_psi64_m, m->m_psi64_h, m->m_TA_h, m->m_psi64_m, g2,
-                dim3((unsigned)m->xa, (unsigned)m->nt, (unsigned)m->partsA), s);
+                dim3((unsigned)m->xa, (unsigned)m->nt, (unsigned)m->partsA), s, m->wait_cycles);
     GemmArgs g3 = g2;
     g3.K = (int)na; g3.kchunk = m->ychunkC; g3.out = m->M3p; g3.scale_idx = SC_OUT_C;
     launch_gemm(m->m_TC_h, m->m_TC_l, m->m_psig64_m, m->m_psig64_h, m->m_TC_h, m->m_psig64_m, g3,
-                dim3((unsigned)m->xa, (unsigned)m->nt, (unsigned)m->partsC), s);
+                dim3((unsigned)m->xa, (unsigned)m->nt, (unsigned)m->partsC), s, m->wait_cycles);
     GemmArgs g1{};
     g1.M = (int)ng; g1.Ncols = n; g1.K = (int)na; g1.kchunk = (int)rup(na, 64); g1.out = m->M1;
     g1.ldo = m->Ng4; g1.sc = m->sc; g1.scale_idx = SC_OUT_AB; g1.status = m->status;
     g1.a_mn = 1; g1.b_mn = 1; g1.transposed = 1;
     launch_gemm(m->m_TAmn_h, m->m_TAmn_l, m->m_psig64_m, m->m_psig64_h, m->m_TAmn_h, m->m_psig64_m,
-                g1, dim3((unsigned)((ng + 127) / 128), (unsigned)m->nt, 1), s);
+                g1, dim3((unsigned)((ng + 127) / 128), (unsigned)m->nt, 1), s, m->wait_cycles);
     count_launch(3);
   } else if (m->fused) {
     // M1 and M2 from one pass over V^T (M2 reduced into the copies), and M3
@@ -2912,13 +2920,13 @@ cudaError_t mixed_enqueue_post(MixedState* m, double* K, double* Ex, cudaStream_
     GemmArgs g{N, n, (int)ng, m->kchunkL1, m->L1p, n, (long)N * n, m->sc, SC_OUT_L1, m->status,
                nullptr, nullptr, 0, 0, nullptr};
     launch_gemm(m->m_phiT_m, m->m_phiT_h, m->m_M1_m, m->m_M1_h, m->m_phiT_m, m->m_M1_m, g,
-                dim3((unsigned)((N + 127) / 128), (unsigned)((n + 127) / 128), (unsigned)m->splitsL1), s);
+                dim3((unsigned)((N + 127) / 128), (unsigned)((n + 127) / 128), (unsigned)m->splitsL1), s, m->wait_cycles);
   }
   {
     GemmArgs g{N, n, (int)na, m->kchunkL23, m->L23p, n, (long)N * n, m->sc, SC_OUT_L23, m->status,
                nullptr, nullptr, 0, 0, nullptr};
     launch_gemm(m->m_phigT_m, m->m_phigT_h, m->m_D23T_m, m->m_D23T_h, m->m_phigT_m, m->m_D23T_m, g,
-                dim3((unsigned)((N + 127) / 128), (unsigned)((n + 127) / 128), (unsigned)m->splitsL23), s);
+                dim3((unsigned)((N + 127) / 128), (unsigned)((n + 127) / 128), (unsigned)m->splitsL23), s, m->wait_cycles);
   }
   count_launch(2);
   e = cudaGetLastError();
@@ -2987,16 +2995,12 @@ cudaError_t mixed_group_enqueue_pair(PairGroup* g, cudaStream_t s) {
 
 void mixed_group_destroy(PairGroup* g) { delete g; }
 
-int mixed_take_status(MixedState* m) {
-  int st[4] = {0, 0, 0, 0};
-  if (cudaMemcpy(st, m->status, 16, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
-  if (st[0] != 0) cudaMemset(m->status, 0, 16);
-  return st[0];
+void mixed_set_wait_limit(MixedState* m, long long cycles) {
+  m->wait_cycles = cycles > 0 ? cycles : 0;
+  for (PairRole& r : m->roles) r.a.wait = m->wait_cycles;
+  m->erole.a.wait = m->wait_cycles;
 }
 
-double mixed_error_bound(const MixedState* m) {
-  (void)m;
-  return 1e-6;
-}
+int* mixed_status_ptr(MixedState* m) { return m->status; }
 
 }  // namespace xk

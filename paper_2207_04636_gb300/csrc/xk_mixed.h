@@ -68,12 +68,15 @@ cudaError_t mixed_group_create(MixedState* const* ms, int count, PairGroup** out
 cudaError_t mixed_group_enqueue_pair(PairGroup* g, cudaStream_t s);
 void mixed_group_destroy(PairGroup* g);
 
-// Error code a kernel of the last builds recorded (0 = none; nonzero when a
-// bounded wait inside a kernel gave up), read synchronously and cleared.
-int mixed_take_status(MixedState* m);
+// Device word (4 ints) the kernels record their error codes in; the first is
+// the code.  Callers snapshot and clear it on the build's stream.
+int* mixed_status_ptr(MixedState* m);
 
-// The E_x accuracy the path is held to against the FP64 path (the parity
-// tests' tolerance, reported with each result; not a rigorous bound).
-double mixed_error_bound(const MixedState* m);
+// Bound, in SM clock cycles, on every pipeline wait inside the state's kernels
+// (0 restores the default of about one second); waits for a kernel's own
+// copies and MMAs before it exits keep the default.  Applies to launches
+// enqueued afterwards.
+void mixed_set_wait_limit(MixedState* m, long long cycles);
+
 
 }  // namespace xk

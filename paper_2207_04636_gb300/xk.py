@@ -64,6 +64,8 @@ def lib():
         L.xk_batch_create.argtypes = [c_d, c_int, ctypes.POINTER(ctypes.c_void_p)]
         L.xk_batch_build.argtypes = [c_d, c_d, c_d, c_d]
         L.xk_batch_release.argtypes = [c_d]
+        L.xk_set_wait_limit.argtypes = [c_d, c_i64]
+        L.xk_error_estimate.argtypes = [c_d, c_d]
         L.xk_last_error.restype = ctypes.c_char_p
         L.xk_kernel_launches.restype = ctypes.c_uint64
         for f in ("xk_footprint", "xk_setup", "xk_setup_isdf", "xk_tables", "xk_isdf_points",
@@ -74,7 +76,7 @@ def lib():
                   "xk_energy_device", "xk_ace",
                   "xk_submit", "xk_poll", "xk_release", "xk_timing_enable", "xk_timing_read",
                   "xk_exchange_energy_noalloc", "xk_batch_create", "xk_batch_build",
-                  "xk_batch_release"):
+                  "xk_batch_release", "xk_set_wait_limit", "xk_error_estimate"):
             getattr(L, f).restype = c_int
         _lib = L
     return _lib
@@ -210,6 +212,16 @@ class Handle:
         _check(lib().xk_submit(self._h, _ptr(C), float(deadline_ms), ctypes.byref(t)))
         return int(t.value)
 
+    def error_estimate(self) -> float:
+        """|E_x - E_K| of the last build (E_K = -sum K o C of the returned K)."""
+        est = np.empty(1)
+        _check(lib().xk_error_estimate(self._h, _ptr(est)))
+        return float(est[0])
+
+    def set_wait_limit(self, cycles: int):
+        """Bound (SM cycles) on the pipeline waits of this handle's kernels; 0 = default."""
+        _check(lib().xk_set_wait_limit(self._h, int(cycles)))
+
     def timing(self, enable=True):
         """Turn per-step CUDA-event timing on (clearing it) or off."""
         _check(lib().xk_timing_enable(self._h, 1 if enable else 0))
@@ -290,7 +302,7 @@ def exchange_energy_noalloc(K_dev, C_dev, count, Ex_dev, stream=0):
 
 
 def poll(ticket, N, n):
-    """(status, K, E_x, err_bound); status XK_PENDING while running."""
+    """(status, K, E_x, err_est); status XK_PENDING while running."""
     K = np.empty((N, n))
     Ex = np.empty(1)
     eb = np.empty(1)

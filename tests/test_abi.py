@@ -126,3 +126,17 @@ def test_null_handles_and_tickets(L):
     assert L.xk_batch_create(None, 1, None) == xk.XK_EINVAL
     assert L.xk_batch_build(None, p, p, p) == xk.XK_EINVAL
     assert L.xk_batch_release(None) == xk.XK_EINVAL
+    assert L.xk_set_wait_limit(None, 0) == xk.XK_EINVAL
+
+
+def test_setup_refused_beyond_budget(L, monkeypatch):
+    """Admission by footprint: with XK_HBM_BUDGET_BYTES below the handle's
+    footprint, xk_setup returns XK_ENOMEM before any device call (the caller
+    may retry once live handles are released)."""
+    phi, idx, V, W = _tables()
+    need = xk.footprint(phi.shape[0], phi.shape[1], 3, idx.shape[0], "f16x3")
+    monkeypatch.setenv("XK_HBM_BUDGET_BYTES", str(need - 1))
+    assert _setup(L, phi, idx, V, W, mode=2) == xk.XK_ENOMEM
+    assert "XK_HBM_BUDGET_BYTES" in xk.last_error()
+    monkeypatch.setenv("XK_HBM_BUDGET_BYTES", "0")
+    assert _setup(L, phi, idx, V, W, mode=0) == xk.XK_ENOMEM

@@ -99,7 +99,12 @@ def test_submit_poll_alone_and_mixed(xk, cells):
                 st, K, E, eb = xk.poll(t, c.N, c.n)
                 if st == xk.XK_OK:
                     break
-            assert same_build(K, E, Kr, Er, c.n) and eb > 0.0
+            assert same_build(K, E, Kr, Er, c.n)
+            # the ticket's error estimate |E_x - E_K| (E_K = -sum K o C): the
+            # host's value, and within what the K tolerance (1e-6 per element)
+            # allows over the sum of |C|
+            assert abs(eb - abs(E + float(np.sum(K * c.C)))) <= 1e-10
+            assert eb <= 1e-6 * float(np.sum(np.abs(c.C))) + 1e-6
     finally:
         for h in hs:
             h.release()

@@ -44,11 +44,18 @@ def _check(xk, c):
     h = xk.Handle(c.phi, c.idx, c.V, c.W, c.dV, c.n, mode="f16x3")
     try:
         K, E = h.build(c.C)
+        est = h.error_estimate()
         Ee = h.energy(c.C)
         K2, E2 = h.build(c.C)
     finally:
         h.release()
     assert abs(E - E0) <= TOL_E, (E, E0)
+    # the per-build estimate |E_x - E_K| (E_K = -sum K o C, formed on the
+    # device): it matches the host's value and lies within the K tolerance
+    # times sum |C| of the oracle's energy of K
+    EK = -float(np.sum(K * c.C))
+    assert abs(est - abs(E - EK)) <= 1e-10, (est, E - EK)
+    assert abs(EK - E0) <= est + abs(E - E0) + 1e-12
     assert np.max(np.abs(K - K0)) <= TOL_K, np.max(np.abs(K - K0))
     assert same_build(K, E, K2, E2, c.n), (E, E2, np.max(np.abs(K - K2)))
     # E_x alone (xk_energy): the same S products, splits and summation order
@@ -140,6 +147,48 @@ def test_ace_on_tensor_path(xk, cell1):
     asym = np.max(np.abs(Kij - (c.C.T @ K)))
     assert np.max(np.abs((xi * s) @ xi.T @ c.C - K)) <= 1e-5 * np.max(np.abs(K))
     assert asym <= 1e-5 * np.max(np.abs(Kij))
+
+
+@pytest.mark.parametrize("n_occ", [None, 100])
+def test_ace_on_tensor_path_matches_oracle(xk, cell1, n_occ):
+    """Row a11 on the tensor path: xk_ace's K_ij and xi against the oracle's
+    ACE factorisation (i) of the same K (the device's FP64 factorisation,
+    to rounding) and (ii) of the oracle's own K, within the bounds that the
+    measured max|dK| of the build propagates to:
+        |dK_ij| <= max_i sum_mu |C_mu,i| max|dK|,
+        |dxi|   <= |dK| |L^-1| + |K| |L^-1| cond(K_ij) |dK_ij| / |K_ij|
+    (first-order Cholesky perturbation), each with a factor 4 of margin.
+    The 8-centre cell (n = 16) and the 27-centre cell with n = 100 (the
+    fused pair role)."""
+    if n_occ is None:
+        c = cell1
+    else:
+        spec = config_spec(4, k=3)
+        spec.n_occ = n_occ
+        c = load_cell(spec)
+    K0, _ = oracle.exx_rps_occri(c.phi, c.idx, c.V, c.W, c.C, c.dV)
+    h = xk.Handle(c.phi, c.idx, c.V, c.W, c.dV, c.n, mode="f16x3")
+    try:
+        K, _ = h.build(c.C)
+        Kij, xi, sg, br = h.ace()
+    finally:
+        h.release()
+    # (i) the same K through the oracle's factorisation
+    Kij1, xi1, s1, br1 = oracle.ace_factor(K, c.C)
+    assert br == br1 == "cholesky"
+    assert np.max(np.abs(Kij - Kij1)) <= 1e-12 * np.max(np.abs(Kij1))
+    assert np.max(np.abs(xi - xi1)) <= 1e-9 * np.max(np.abs(xi1))
+    # (ii) against the oracle's K, within the propagated K error
+    Kij0, xi0, s0, br0 = oracle.ace_factor(K0, c.C)
+    dK = np.max(np.abs(K - K0))
+    tol_kij = 4.0 * np.max(np.sum(np.abs(c.C), axis=0)) * dK
+    assert np.max(np.abs(Kij - Kij0)) <= tol_kij, (np.max(np.abs(Kij - Kij0)), tol_kij)
+    Linv = np.linalg.inv(np.linalg.cholesky(Kij0))
+    nL = np.linalg.norm(Linv, 2)
+    cond = np.linalg.cond(Kij0)
+    tol_xi = 4.0 * (dK * c.N * nL + np.max(np.abs(K0)) * c.N * nL * cond
+                    * tol_kij / np.linalg.norm(Kij0, 2))
+    assert np.max(np.abs(xi - xi0)) <= tol_xi, (np.max(np.abs(xi - xi0)), tol_xi)
 
 
 @pytest.mark.slow

@@ -34,6 +34,25 @@ def test_noalloc_energy_matches_build(cell1):
         stream.synchronize()
         assert abs(float(Ed.item()) - E) <= 1e-12 * abs(E)
 
+    # counts that exercise the reduction: none (E_x = -0), one chunk, several
+    # chunks with a ragged last one, the 64-centre cell's N n, and the fixed
+    # maximum; each checked against an exactly rounded host sum, twice in a row
+    import math
+    rng = np.random.default_rng(11)
+    for count in (0, 1, 3 * 2048 + 17, 832 * 128, 2048 * 2048):
+        a = rng.standard_normal(max(count, 1))
+        b = rng.standard_normal(max(count, 1))
+        ad, bd = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+        want = -math.fsum((a[:count] * b[:count]).tolist()) if count else 0.0
+        scale = math.fsum(np.abs(a[:count] * b[:count]).tolist()) if count else 0.0
+        for _ in range(2):
+            Ed = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+            xk.exchange_energy_noalloc(ad.data_ptr(), bd.data_ptr(), count, Ed.data_ptr(),
+                                       stream.cuda_stream)
+            stream.synchronize()
+            got = float(Ed.item())
+            assert abs(got - want) <= 1e-13 * scale, (count, got, want)
+
     # a count above the fixed capacity is refused before any device work
     Ed = torch.zeros(1, dtype=torch.float64, device="cuda")
     with pytest.raises(xk.XKError) as err:
