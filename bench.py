@@ -75,6 +75,10 @@ def parse():
                         "taking the generator's, and report the set-up time")
     p.add_argument("--batch", type=int, default=32,
                    help="cells in the grouped batch / mixed serving run (0 skips both)")
+    p.add_argument("--shard", action="store_true",
+                   help="under torchrun: split the interpolation points over the ranks "
+                        "(xk_setup_shard) and sum K and E_x with one allreduce per build "
+                        "(strong scaling) instead of one independent build per rank")
     return p.parse_args()
 
 
@@ -196,17 +200,38 @@ def max_over_ranks(value, dist, device):
     return float(t.item())
 
 
+def shard_slices(naux, world):
+    """Contiguous slices [g0, g1) of the interpolation points, one per rank."""
+    b = [round(r * naux / world) for r in range(world + 1)]
+    return list(zip(b[:-1], b[1:]))
+
+
+def reduce_partials(K, E, dist):
+    """Sum the ranks' shares of K_{mu i} (N x n) and E_x (one element) in
+    place with one allreduce (the only exchange of the g-sharded build)."""
+    if dist is None:
+        return K, E
+    import torch
+    buf = torch.cat([K.reshape(-1), E.reshape(-1)])
+    dist.all_reduce(buf, op=dist.ReduceOp.SUM)
+    K.copy_(buf[:-1].reshape(K.shape))
+    E.copy_(buf[-1:])
+    return K, E
+
+
 def job_throughput(world, steps, ms):
     """Whole-job builds/s: every rank runs `steps` builds; the job takes the
     slowest rank's `ms` (weak scaling, no data-path collective)."""
     return world * steps / (ms * 1e-3)
 
 
-def time_device_builds(xk, h, Cd, Kd, Ed, stream, warm, steps, torch):
-    """Warm-up, then `steps` builds between CUDA events on `stream`.
+def time_device_builds(xk, h, Cd, Kd, Ed, stream, warm, steps, torch, dist=None):
+    """Warm-up, then `steps` builds between CUDA events on `stream` (with
+    `dist`, each build is a shard's and its share is allreduced in the step).
     Returns (ms, launches, step times)."""
     for i in range(warm):
         h.build_device(Cd[i].data_ptr(), Kd.data_ptr(), Ed.data_ptr(), stream.cuda_stream)
+        reduce_partials(Kd, Ed, dist)
     torch.cuda.synchronize()
     h.timing(True)
     launches0 = xk.kernel_launches()
@@ -215,6 +240,7 @@ def time_device_builds(xk, h, Cd, Kd, Ed, stream, warm, steps, torch):
     e0.record(stream)
     for i in range(steps):
         h.build_device(Cd[warm + i].data_ptr(), Kd.data_ptr(), Ed.data_ptr(), stream.cuda_stream)
+        reduce_partials(Kd, Ed, dist)
     e1.record(stream)
     torch.cuda.synchronize()
     st = h.step_times()
@@ -500,7 +526,9 @@ def main():
     cell = load_cell(spec)
     N, n, Ng, Na = cell.N, cell.n, cell.Ng, cell.Naux
     workload = WORKLOAD if args.config == 2 else f"{cell.spec.name}: N={N}, n={n}, N_g={Ng}, N_aux={Na}"
-    Cs = pseudo_scf_sequence(cell.S, cell.C, steps + warm, 1000 + rank)
+    shard = args.shard and world > 1
+    # a sharded run builds one C sequence across all ranks; otherwise each rank its own
+    Cs = pseudo_scf_sequence(cell.S, cell.C, steps + warm, 1000 + (0 if shard else rank))
     Cd = [torch.from_numpy(C).cuda() for C in Cs]
     Kd = torch.empty((N, n), dtype=torch.float64, device="cuda")
     Ed = torch.empty(1, dtype=torch.float64, device="cuda")
@@ -515,6 +543,10 @@ def main():
                   "common_with_generator": int(np.intersect1d(idx_gpu, cell.idx).size)}
         t_setup = time.perf_counter()
         h = xk.Handle.isdf(cell.phi, cell.idx, cell.grid, cell.L, n, mode=mode)
+    elif shard:  # this rank's slice of the interpolation points
+        g0, g1 = shard_slices(Na, world)[rank]
+        h = xk.Handle.shard(cell.phi, cell.idx, cell.V[g0:g1], cell.W[g0:g1], g0, g1, cell.dV, n,
+                            mode=mode)
     else:
         h = xk.Handle(cell.phi, cell.idx, cell.V, cell.W, cell.dV, n, mode=mode)
     t_setup = time.perf_counter() - t_setup
@@ -530,7 +562,8 @@ def main():
         uuid = None
     sampler = ClockSampler(uuid)
     time.sleep(0.3)
-    ms, launches, st = time_device_builds(xk, h, Cd, Kd, Ed, stream, warm, steps, torch)
+    ms, launches, st = time_device_builds(xk, h, Cd, Kd, Ed, stream, warm, steps, torch,
+                                          dist if shard else None)
     clocks = sampler.stop()
     ms = max_over_ranks(ms, dist, "cuda")
     if dist:
@@ -544,7 +577,12 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(steps):
-        h.build(Ch[i].numpy())
+        Kh, Eh = h.build(Ch[i].numpy())
+        if shard:  # the shares, summed over the ranks and read back
+            Kt = torch.from_numpy(Kh).cuda()
+            Et = torch.tensor([Eh], dtype=torch.float64, device="cuda")
+            reduce_partials(Kt, Et, dist)
+            Kh, Eh = Kt.cpu().numpy(), float(Et.item())
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     energy = None
@@ -694,24 +732,29 @@ def main():
                                       "(n = 128), scaled by pair count"}
         roof["frac"] = roof["achieved"] / roof["peak"]
         roof["ms_per_build"] = dom_ms
-        value = job_throughput(world, steps, ms)
+        # a sharded job completes one build per step across all ranks (strong
+        # scaling); replicas complete one build per rank per step (weak scaling)
+        value = job_throughput(1 if shard else world, steps, ms)
         line = {
             "metric": METRIC, "value": value, "unit": "builds/s", "n_gpus": world,
             "steps": steps, "warmup": warm, "ms_per_step": ms / steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "strong" if shard else "weak",
+            "vs_baseline": None,
             "dtype": "f64" if mode == "fp64" else "f16x3",
             "data": "synthetic (seeded cell generator; inputs resident in HBM)"
                     + ("; ISDF tables formed on the GPU" if args.isdf else ""),
             "config": {"workload": workload, "mode": mode, "N": N, "n": n, "N_g": Ng,
                        "N_aux": Na, "l2": "inputs larger than L2 (V is N_aux x N_g)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": (f"g-sharded x{world} (one allreduce of K and E_x "
+                                       "per build)" if shard else f"replicas x{world}")},
             "E_x": E_last,
             "step_ms": {k: v[0] / max(1, v[1]) for k, v in st.items()},
             "algorithmic_tflops_per_s": sum(fl.values()) / (ms * 1e-3 / steps) / 1e12,
             "roofline": roof,
             "gpu_launches": int(launches),
             "clocks": clocks,
-            "e2e": {"value": job_throughput(world, steps, e2e_s * 1e3), "unit": "builds/s",
+            "e2e": {"value": job_throughput(1 if shard else world, steps, e2e_s * 1e3),
+                    "unit": "builds/s",
                     "h2d_bytes_per_step": N * n * 8, "d2h_bytes_per_step": N * n * 8 + 8},
         }
         if args.isdf:

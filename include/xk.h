@@ -17,7 +17,7 @@
  * Coulomb integral, Eq. 2eint).  No FFT runs inside a build: V and W are
  * computed once per geometry by the caller (Eq. rpsPot, Eq. thcpot).
  *
- * Entry points: set-up and release (xk_footprint, xk_setup, xk_setup_isdf,
+ * Entry points: set-up and release (xk_footprint, xk_setup, xk_setup_shard, xk_setup_isdf,
  * xk_isdf_points, xk_tables, xk_release); builds (xk_build, xk_build_device,
  * xk_ace); serving (xk_submit, xk_poll) and batches (xk_batch_create,
  * xk_batch_build, xk_batch_release); other products on the same tables
@@ -104,6 +104,33 @@ int xk_setup(int64_t Ng, int32_t N, int32_t n, int32_t Naux,
              const double* basis_on_points, const int32_t* interp_idx,
              const double* V_aux, const double* W_aux,
              double dV, int mode, xk_handle** out);
+
+/*
+ * A shard of the build for a g-partitioned multi-GPU run (one process per
+ * GPU).  Every term of Eq. exoccri is a sum over the interpolation points g
+ * (lines 1 and 2 over the g of V o P, line 3 over the g of the rows of
+ * W o Q), so the build splits over g-slices with no exchange until the end:
+ * the shard holds the rows [g0, g1) of V and of W, the whole basis table and
+ * all Naux interpolation points (the orbitals at every point are needed for
+ * the g' of W o Q), and each build returns the slice's share of K_{mu i} and
+ * of E_x.  The shares of a partition of [0, Naux) sum to the full build's K
+ * and E_x: one allreduce of the N x n K and one scalar (Sec. IV.B-D: the
+ * paper also keeps the O(n N_chi N) contraction of order (a) local).
+ *   interp_idx  Naux, all interpolation points (as in xk_setup)
+ *   V_rows      (g1 - g0) x Ng: rows g0 .. g1-1 of V_aux
+ *   W_rows      (g1 - g0) x Naux: rows g0 .. g1-1 of W_aux (all columns)
+ * Other arguments and the device tables as in xk_setup; the footprint is
+ * that of the slice.  A shard handle builds (xk_build, xk_build_device,
+ * xk_submit, xk_energy: partial E_x, batches); xk_build_full, xk_ace and
+ * xk_tables return XK_EINVAL for it (they need the summed K or all rows).
+ * xk_poll's and xk_error_estimate's estimate is that of the share.
+ * Errors: as xk_setup, plus XK_EINVAL unless 0 <= g0 < g1 <= Naux; W is
+ * checked for symmetry on its block [g0, g1) x [g0, g1).
+ */
+int xk_setup_shard(int64_t Ng, int32_t N, int32_t n, int32_t Naux, int32_t g0, int32_t g1,
+                   const double* basis_on_points, const int32_t* interp_idx,
+                   const double* V_rows, const double* W_rows, double dV, int mode,
+                   xk_handle** out);
 
 /*
  * The same set-up with the ISDF tables formed on the device in FP64 from the

@@ -62,6 +62,30 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Non-blocking test of the phase (never suspends the thread).
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// A wait with a shortened limit: polls with mbarrier.test_wait, so the limit
+// holds even when it is shorter than the interval try_wait may sleep.  Kept
+// out of line: the default path below stays as short as it was.
+__device__ __noinline__ bool mbar_wait_short(uint64_t* bar, uint32_t parity, long long limit) {
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity)) {
+    if (clock64() - t0 > limit) return false;
+  }
+  return true;
+}
+
 // Waits for the phase with the given parity to complete; gives up after
 // `limit` SM clock cycles (default kWaitCycles) and returns false.  Kernels
 // take the limit of their pipeline waits from their launch arguments (a
@@ -69,6 +93,7 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
 // waits for a kernel's own TMA copies and MMAs always use kWaitCycles.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
                                           long long limit = kWaitCycles) {
+  if (limit < kWaitCycles) return mbar_wait_short(bar, parity, limit);
   if (mbar_try(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try(bar, parity)) {

@@ -72,6 +72,10 @@ std::mutex g_admit_mu;
 struct xk_handle {
   int64_t Ng = 0;
   int N = 0, n = 0, Naux = 0, mode = 0, device = 0;
+  // The handle holds the rows of V and W of the interpolation points
+  // [g0, g0 + ga) (all Naux points unless it is a shard) and returns that
+  // slice's share of K_{mu i} and E_x; the orbitals are gathered at all Naux.
+  int g0 = 0, ga = 0;
   double dV = 0.0;
   size_t footprint = 0;
   cudaStream_t stream = nullptr;
@@ -123,8 +127,9 @@ struct Plan {
 
 // Doubles of split-K work the FP64 contractions need (a contraction that
 // runs unsplit needs none); with ace_only, only the occ-RI K_ij products.
-size_t max_work(int64_t Ng, int N, int n, int Naux, bool ace_only = false) {
+size_t max_work(int64_t Ng, int N, int n, int Naux, bool ace_only = false, int ga = -1) {
   const int ng = (int)Ng;
+  if (ga < 0) ga = Naux;  // rows of V and W held (a shard's slice)
   size_t w = 1;
   auto acc = [&](int M, int Nc, int K) {
     const size_t ks = (size_t)xk::dgemm_ksplit(M, Nc, K);
@@ -134,16 +139,16 @@ size_t max_work(int64_t Ng, int N, int n, int Naux, bool ace_only = false) {
   acc(N, n, n);         // K U
   if (ace_only) return w;
   acc(ng, n, N);        // Psi = Phi C
-  acc(Naux, ng, n);     // V2 = V o (Psi_g Psi^T)
-  acc(Naux, n, ng);     // M2 = V2 Psi
-  acc(n, ng, Naux);     // M1 = Psi_g^T V2
+  acc(ga, ng, n);       // V2 = V o (Psi_g Psi^T)
+  acc(ga, n, ng);       // M2 = V2 Psi
+  acc(n, ng, ga);       // M1 = Psi_g^T V2
   acc(n, N, ng);        // line1
-  acc(n, N, Naux);      // line2, line3
-  acc(Naux, Naux, n);   // W o Q
-  acc(Naux, n, Naux);   // M3
-  acc(Naux, N, ng);     // full K: M_A = V2 Phi
-  acc(Naux, N, Naux);   // full K: M_C = (W o Q) Phi_g
-  acc(N, N, Naux);      // full K: Phi_g^T M
+  acc(n, N, ga);        // line2, line3
+  acc(ga, Naux, n);     // W o Q
+  acc(ga, n, Naux);     // M3
+  acc(ga, N, ng);       // full K: M_A = V2 Phi
+  acc(ga, N, Naux);     // full K: M_C = (W o Q) Phi_g
+  acc(N, N, ga);        // full K: Phi_g^T M
   acc(N, N, ng);        // Coulomb J = Phi^T (v o Phi)
   acc(Naux, Naux, N);   // ISDF set-up: Phi_g Phi_g^T
   acc(Naux, ng, N);     // ISDF set-up: Phi_g Phi^T
@@ -151,18 +156,20 @@ size_t max_work(int64_t Ng, int N, int n, int Naux, bool ace_only = false) {
   return std::max(w, (size_t)Naux);  // the set-up also keeps the diagonal of X_gg here
 }
 
-Plan plan_fp64(int64_t Ng, int N, int n, int Naux) {
+// Rows ga of V and W held (ga = Naux unless a shard); Psi_g at all Naux points.
+Plan plan_fp64(int64_t Ng, int N, int n, int Naux, int ga = -1) {
   Plan p;
-  const size_t ng = (size_t)Ng, na = (size_t)Naux;
-  p.f64 = ng * N + na * N + na * ng + na * na       // Phi, Phi_g, V, W
+  if (ga < 0) ga = Naux;
+  const size_t ng = (size_t)Ng, na = (size_t)Naux, gs = (size_t)ga;
+  p.f64 = ng * N + gs * N + gs * ng + gs * na       // Phi, Phi_g (slice), V, W rows
           + (size_t)N * n + ng * n + na * n         // C, Psi, Psi_g
-          + na * ng + (size_t)n * ng + na * n       // V2, M1, M2
-          + na * na + na * n + 3 * (size_t)n * N    // Q, M3, lines
-          + (size_t)N * n + 1 + xk::reduce_work_elems()  // K, Ex, reduction
+          + gs * ng + (size_t)n * ng + gs * n       // V2, M1, M2
+          + gs * na + gs * n + 3 * (size_t)n * N    // Q, M3, lines
+          + (size_t)N * n + 2 + xk::reduce_work_elems()  // K, E_x and E_K, reduction
           + (size_t)N * n + 1                            // C and E_x of xk_energy
-          + 2 * na * N + 3 * (size_t)N * N                // full K: M_A, M_C, Y, Z, K
+          + 2 * gs * N + 3 * (size_t)N * N                // full K: M_A, M_C, Y, Z, K
           + 3 * (size_t)n * n + 2 * (size_t)N * n + n;   // K_ij, L, U, Y, xi, sign
-  p.work = max_work(Ng, N, n, Naux);
+  p.work = max_work(Ng, N, n, Naux, false, ga);
   p.f64 += p.work;
   p.i32 = na + 2;
   return p;
@@ -275,7 +282,8 @@ void fold_marks(xk_handle* h) {
 int enqueue_fp64(xk_handle* h) {
   using xk::DGemm;
   cudaStream_t s = h->stream;
-  const int ng = (int)h->Ng, N = h->N, n = h->n, na = h->Naux;
+  const int ng = (int)h->Ng, N = h->N, n = h->n, na = h->Naux, ga = h->ga;
+  const double* psl = h->psig + (size_t)h->g0 * n;  // Psi_g of the held slice
   auto G = [&](int M, int Nc, int K, const double* A, long lda, bool ta, const double* B, long ldb,
                bool tb, double* C, long ldc, const double* H, long ldh) {
     DGemm g{M, Nc, K, A, lda, ta, B, ldb, tb, C, ldc, 1.0, H, ldh, 0, h->work};
@@ -288,15 +296,15 @@ int enqueue_fp64(xk_handle* h) {
   }
   {  // Steps 2-3: pair kernel at (R_g, R) and the Hadamard with V, fused.
     StepMark m(h, XK_STEP_PAIR);
-    XK_CUDA(G(na, ng, n, h->psig, n, false, h->psi, n, true, h->V2, ng, h->V, ng));
+    XK_CUDA(G(ga, ng, n, psl, n, false, h->psi, n, true, h->V2, ng, h->V, ng));
   }
   {  // Line 2, first contraction (order (a)): M2 = V2 Psi.
     StepMark m(h, XK_STEP_M2);
-    XK_CUDA(G(na, n, ng, h->V2, ng, false, h->psi, n, false, h->M2, n, nullptr, 0));
+    XK_CUDA(G(ga, n, ng, h->V2, ng, false, h->psi, n, false, h->M2, n, nullptr, 0));
   }
   {  // Line 1, first contraction: M1 = Psi_g^T V2.
     StepMark m(h, XK_STEP_M1);
-    XK_CUDA(G(n, ng, na, h->psig, n, true, h->V2, ng, false, h->M1, ng, nullptr, 0));
+    XK_CUDA(G(n, ng, ga, psl, n, true, h->V2, ng, false, h->M1, ng, nullptr, 0));
   }
   {  // Line 1, contraction with the basis on the grid.
     StepMark m(h, XK_STEP_LINE1);
@@ -304,13 +312,13 @@ int enqueue_fp64(xk_handle* h) {
   }
   {  // Line 2, contraction with the basis at R_g.
     StepMark m(h, XK_STEP_LINE2);
-    XK_CUDA(G(n, N, na, h->M2, n, true, h->phig, N, false, h->L2, N, nullptr, 0));
+    XK_CUDA(G(n, N, ga, h->M2, n, true, h->phig, N, false, h->L2, N, nullptr, 0));
   }
-  {  // Line 3: W o (Psi_g Psi_g^T), then two contractions.
+  {  // Line 3: W o (Psi_g Psi_g^T) over the slice's rows and every g', then two contractions.
     StepMark m(h, XK_STEP_LINE3);
-    XK_CUDA(G(na, na, n, h->psig, n, false, h->psig, n, true, h->Q, na, h->W, na));
-    XK_CUDA(G(na, n, na, h->Q, na, false, h->psig, n, false, h->M3, n, nullptr, 0));
-    XK_CUDA(G(n, N, na, h->M3, n, true, h->phig, N, false, h->L3, N, nullptr, 0));
+    XK_CUDA(G(ga, na, n, psl, n, false, h->psig, n, true, h->Q, na, h->W, na));
+    XK_CUDA(G(ga, n, na, h->Q, na, false, h->psig, n, false, h->M3, n, nullptr, 0));
+    XK_CUDA(G(n, N, ga, h->M3, n, true, h->phig, N, false, h->L3, N, nullptr, 0));
   }
   {  // K_{mu i} = dV (line1 + line2 - line3)^T and E_x = -sum K o C.
     StepMark m(h, XK_STEP_ASSEMBLE);
@@ -332,7 +340,8 @@ int enqueue_energy(xk_handle* h) {
   }
   using xk::DGemm;
   cudaStream_t s = h->stream;
-  const int ng = (int)h->Ng, N = h->N, n = h->n, na = h->Naux;
+  const int ng = (int)h->Ng, N = h->N, n = h->n, na = h->Naux, ga = h->ga;
+  const double* psl = h->psig + (size_t)h->g0 * n;  // Psi_g of the held slice
   auto G = [&](int M, int Nc, int K, const double* A, long lda, bool ta, const double* B, long ldb,
                bool tb, double* C, long ldc) {
     DGemm g{M, Nc, K, A, lda, ta, B, ldb, tb, C, ldc, 1.0, nullptr, 0, 0, h->work};
@@ -345,12 +354,12 @@ int enqueue_energy(xk_handle* h) {
   }
   {  // P = Psi_g Psi^T and Q = Psi_g Psi_g^T
     StepMark m(h, XK_STEP_PAIR);
-    XK_CUDA(G(na, ng, n, h->psig, n, false, h->psi, n, true, h->V2, ng));
-    XK_CUDA(G(na, na, n, h->psig, n, false, h->psig, n, true, h->Q, na));
+    XK_CUDA(G(ga, ng, n, psl, n, false, h->psi, n, true, h->V2, ng));
+    XK_CUDA(G(ga, na, n, psl, n, false, h->psig, n, true, h->Q, na));
   }
   {
     StepMark m(h, XK_STEP_ASSEMBLE);
-    XK_CUDA(xk::closed_form_ex_f64(h->V, h->V2, (long)na * ng, h->W, h->Q, (long)na * na, h->dV,
+    XK_CUDA(xk::closed_form_ex_f64(h->V, h->V2, (long)ga * ng, h->W, h->Q, (long)ga * na, h->dV,
                                    h->red, Ex, s));
   }
   return XK_OK;
@@ -430,7 +439,7 @@ int xk_footprint(int64_t Ng, int32_t N, int32_t n, int32_t Naux, int mode, size_
     return XK_OK;
   }
   if (mode == XK_F16X3) {
-    *bytes = xk::mixed_footprint(Ng, N, n, Naux) + (size_t)N * n * 8 * 3 + 8 + (size_t)N * N * 8 +
+    *bytes = xk::mixed_footprint(Ng, N, n, Naux, Naux) + (size_t)N * n * 8 * 3 + 16 + (size_t)N * N * 8 +
              (size_t)max_work(Ng, N, n, Naux, true) * 8 + 4 * (size_t)n * n * 8 + 2 * (size_t)N * n * 8 +
              65536;
     return XK_OK;
@@ -440,14 +449,20 @@ int xk_footprint(int64_t Ng, int32_t N, int32_t n, int32_t Naux, int mode, size_
 
 // xk_setup (V, W given) and xk_setup_isdf (V == W == nullptr: chi, V and W
 // formed on the device from phi and idx on a cubic grid^3 grid of side L).
+// A shard (xk_setup_shard) holds the rows [g0, g1) of V and W; V and W then
+// point at those g1 - g0 rows (V: N_g columns, W: all Naux columns).
 static int setup_impl(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* phi,
                const int32_t* idx, const double* V, const double* W, double dV, int mode,
-               int32_t grid, double L, xk_handle** out) {
+               int32_t grid, double L, xk_handle** out, int32_t g0 = 0, int32_t g1 = -1) {
   if (!out) return fail(XK_EINVAL, "xk_setup: out is NULL");
   *out = nullptr;
+  if (g1 < 0) g1 = Naux;
   const bool isdf = V == nullptr && W == nullptr && grid > 0;
   if (!phi || !idx || (!isdf && (!V || !W))) return fail(XK_EINVAL, "xk_setup: NULL table pointer");
   if (!valid_sizes(Ng, N, n, Naux)) return fail(XK_EINVAL, "xk_setup: invalid sizes");
+  if (g0 < 0 || g1 > Naux || g0 >= g1)
+    return fail(XK_EINVAL, "xk_setup_shard: the slice [g0, g1) must be non-empty within [0, Naux)");
+  const int32_t ga = g1 - g0;
   if (!(dV > 0.0) || !std::isfinite(dV)) return fail(XK_EINVAL, "xk_setup: dV must be > 0");
   if (mode != XK_FP64 && mode != XK_F16X3) return fail(XK_EINVAL, "xk_setup: unsupported mode");
   {
@@ -459,20 +474,27 @@ static int setup_impl(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const doub
       return fail(XK_EINVAL, "xk_setup: interp_idx has duplicates");
   }
   if (!isdf) {
+    // W is symmetric: checked on the block of the held rows [g0, g1) x [g0, g1)
     double wmax = 0.0, asym = 0.0;
-    const size_t na = (size_t)Naux;
-    for (size_t i = 0; i < na; ++i)
+    const size_t na = (size_t)Naux, gs = (size_t)ga;
+    for (size_t i = 0; i < gs; ++i)
       for (size_t j = 0; j < na; ++j) {
         const double a = W[i * na + j];
         if (!std::isfinite(a)) return fail(XK_EINVAL, "xk_setup: W has non-finite entries");
         wmax = std::max(wmax, std::fabs(a));
-        if (j > i) asym = std::max(asym, std::fabs(a - W[j * na + i]));
+        if (j >= (size_t)g0 && j - g0 > i && j - g0 < gs)
+          asym = std::max(asym, std::fabs(a - W[(j - g0) * na + g0 + i]));
       }
     if (asym > 1e-12 * wmax) return fail(XK_EINVAL, "xk_setup: W_aux is not symmetric");
   }
   size_t need = 0;
   int rc = xk_footprint(Ng, N, n, Naux, mode, &need);
   if (rc != XK_OK) return rc;
+  if (ga != Naux)  // a shard holds the slice's rows only
+    need = mode == XK_FP64 ? plan_bytes(plan_fp64(Ng, N, n, Naux, ga))
+                           : xk::mixed_footprint(Ng, N, n, ga, Naux) + (size_t)N * n * 8 * 3 + 16 +
+                                 (size_t)N * N * 8 + (size_t)max_work(Ng, N, n, Naux, true) * 8 +
+                                 4 * (size_t)n * n * 8 + 2 * (size_t)N * n * 8 + 65536;
   // the tensor path's ISDF set-up holds FP64 temporaries next to its tables:
   // Phi, Phi_g, X_gg, chi, V, W and the product work (freed before return)
   const size_t isdf_tmp = (isdf && mode != XK_FP64)
@@ -511,6 +533,7 @@ static int setup_impl(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const doub
 
   xk_handle* h = new xk_handle();
   h->Ng = Ng; h->N = N; h->n = n; h->Naux = Naux; h->dV = dV; h->mode = mode; h->device = dev;
+  h->g0 = g0; h->ga = ga;
   h->footprint = need;
   auto bail = [&](int code) { free_handle(h); return code; };
   cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
@@ -535,35 +558,37 @@ static int setup_impl(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const doub
   XK_ALLOC(h->sgn, (size_t)n);
   XK_ALLOC(h->status, 2);
   XK_ALLOC(h->red, xk::reduce_work_elems());
-  const size_t work = max_work(Ng, N, n, Naux, mode != XK_FP64);
+  const size_t work = max_work(Ng, N, n, Naux, mode != XK_FP64, ga);
   XK_ALLOC(h->work, work);
   if (mode == XK_FP64) {
+    const size_t gs = (size_t)ga;  // rows of V, W, P and Q held
     XK_ALLOC(h->phi, ng * N);
-    XK_ALLOC(h->phig, na * N);
-    XK_ALLOC(h->V, na * ng);
-    XK_ALLOC(h->W, na * na);
+    XK_ALLOC(h->phig, gs * N);
+    XK_ALLOC(h->V, gs * ng);
+    XK_ALLOC(h->W, gs * na);
     XK_ALLOC(h->idx, na);
     XK_ALLOC(h->psi, ng * n);
     XK_ALLOC(h->psig, na * n);
-    XK_ALLOC(h->V2, na * ng);
+    XK_ALLOC(h->V2, gs * ng);
     XK_ALLOC(h->M1, (size_t)n * ng);
-    XK_ALLOC(h->M2, na * n);
-    XK_ALLOC(h->Q, na * na);
-    XK_ALLOC(h->M3, na * n);
+    XK_ALLOC(h->M2, gs * n);
+    XK_ALLOC(h->Q, gs * na);
+    XK_ALLOC(h->M3, gs * n);
     XK_ALLOC(h->L1, (size_t)n * N);
     XK_ALLOC(h->L2, (size_t)n * N);
     XK_ALLOC(h->L3, (size_t)n * N);
-    XK_ALLOC(h->MA, na * N);
-    XK_ALLOC(h->MC, na * N);
+    XK_ALLOC(h->MA, gs * N);
+    XK_ALLOC(h->MC, gs * N);
     XK_ALLOC(h->Yf, (size_t)N * N);
     XK_ALLOC(h->Zf, (size_t)N * N);
     e = cudaMemcpyAsync(h->phi, phi, ng * N * 8, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess && !isdf)
-      e = cudaMemcpyAsync(h->V, V, na * ng * 8, cudaMemcpyHostToDevice, h->stream);
+      e = cudaMemcpyAsync(h->V, V, gs * ng * 8, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess && !isdf)
-      e = cudaMemcpyAsync(h->W, W, na * na * 8, cudaMemcpyHostToDevice, h->stream);
+      e = cudaMemcpyAsync(h->W, W, gs * na * 8, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->idx, idx, na * 4, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = xk::gather_rows_f64(h->phi, N, h->idx, Naux, N, h->phig, N, h->stream);
+    if (e == cudaSuccess)  // the basis at the slice's points
+      e = xk::gather_rows_f64(h->phi, N, h->idx + g0, ga, N, h->phig, N, h->stream);
     if (e == cudaSuccess && isdf)  // X_gg in Q, chi in V2 (both scratch of the build)
       e = xk::isdf_tables_f64(h->phi, (long)ng, N, h->phig, Naux, grid, L, h->Q, h->V2, h->V, h->W,
                               h->work, h->status, &h->ridge, h->stream);
@@ -607,13 +632,13 @@ static int setup_impl(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const doub
         cudaFree(chi); cudaFree(Xgg);
         tmp.erase(std::remove_if(tmp.begin(), tmp.end(),
                                  [&](void* q) { return q == chi || q == Xgg; }), tmp.end());
-        e = xk::mixed_create(Ng, N, n, Naux, dphi, idx, dV_, dW, dV, h->stream, &h->mixed);
+        e = xk::mixed_create(Ng, N, n, Naux, 0, Naux, dphi, idx, dV_, dW, dV, h->stream, &h->mixed);
       }
       if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, 8, h->stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
       release();
     } else {
-      e = xk::mixed_create(Ng, N, n, Naux, phi, idx, V, W, dV, h->stream, &h->mixed);
+      e = xk::mixed_create(Ng, N, n, Naux, g0, g1, phi, idx, V, W, dV, h->stream, &h->mixed);
     }
     if (e == cudaErrorInvalidValue)
       return bail(fail(XK_EINVAL, "xk_setup: basis columns are linearly dependent on the grid"));
@@ -640,6 +665,18 @@ int xk_setup(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* phi,
     return fail(XK_EINVAL, "xk_setup: NULL table pointer");
   }
   return setup_impl(Ng, N, n, Naux, phi, idx, V, W, dV, mode, 0, 0.0, out);
+}
+
+int xk_setup_shard(int64_t Ng, int32_t N, int32_t n, int32_t Naux, int32_t g0, int32_t g1,
+                   const double* basis_on_points, const int32_t* interp_idx,
+                   const double* V_rows, const double* W_rows, double dV, int mode,
+                   xk_handle** out) {
+  if (!V_rows || !W_rows) {
+    if (out) *out = nullptr;
+    return fail(XK_EINVAL, "xk_setup_shard: NULL table pointer");
+  }
+  return setup_impl(Ng, N, n, Naux, basis_on_points, interp_idx, V_rows, W_rows, dV, mode, 0, 0.0,
+                    out, g0, g1);
 }
 
 int xk_setup_isdf(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* phi,
@@ -693,6 +730,7 @@ int xk_tables(xk_handle* h, double* W_out, const int32_t* rows, int32_t nrows, d
               double* ridge) {
   if (!h) return fail(XK_EINVAL, "xk_tables: NULL handle");
   if (h->mode != XK_FP64) return fail(XK_EINVAL, "xk_tables: needs an XK_FP64 handle");
+  if (h->ga != h->Naux) return fail(XK_EINVAL, "xk_tables: not for a shard handle");
   if (nrows < 0 || (nrows > 0 && (!rows || !V_rows_out)))
     return fail(XK_EINVAL, "xk_tables: bad row list");
   for (int32_t i = 0; i < nrows; ++i)
@@ -758,6 +796,7 @@ int xk_build(xk_handle* h, const double* C, double* K_out, double* Ex) {
 
 int xk_build_full(xk_handle* h, const double* C, double* K_out) {
   if (!h || !C || !K_out) return fail(XK_EINVAL, "xk_build_full: NULL argument");
+  if (h->ga != h->Naux) return fail(XK_EINVAL, "xk_build_full: not for a shard handle");
   std::lock_guard<std::mutex> lk(h->mu);
   DeviceGuard g(h->device);
   if (h->mode != XK_FP64 && h->full_extra == 0) {
@@ -914,6 +953,8 @@ int xk_energy_device(xk_handle* h, const double* C_dev, double* Ex_dev, void* st
 
 int xk_ace(xk_handle* h, double* Kij_out, double* xi_out, double* sign_out, int* branch) {
   if (!h || !Kij_out || !xi_out) return fail(XK_EINVAL, "xk_ace: NULL argument");
+  if (h->ga != h->Naux)
+    return fail(XK_EINVAL, "xk_ace: a shard's K is a partial sum; factor the summed K");
   std::lock_guard<std::mutex> lk(h->mu);
   if (!h->has_build) return fail(XK_EINVAL, "xk_ace: no completed build on this handle");
   DeviceGuard g(h->device);

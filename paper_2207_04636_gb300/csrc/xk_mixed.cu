@@ -2074,8 +2074,12 @@ cudaError_t split_rows(const T* src, long rows, long cols, long ld_src, const fl
 
 struct MixedState {
   int64_t Ng = 0;
-  int N = 0, n = 0, Naux = 0, np = 0;
-  long Np = 0, Ng8 = 0, Na8 = 0, Ng4 = 0, Na4 = 0;
+  // Naux: the interpolation points whose rows of V and W this state holds
+  // (a slice [g0, g0 + Naux) of NaT points; the whole set unless sharded).
+  // The orbitals are gathered at all NaT points (psigA); psig is the view of
+  // the slice's rows.
+  int N = 0, n = 0, Naux = 0, np = 0, NaT = 0, g0 = 0;
+  long Np = 0, Ng8 = 0, Na8 = 0, Ng4 = 0, Na4 = 0, NaT4 = 0, NaT8 = 0;
   double dV = 0.0;
   std::vector<void*> allocs;
   __half *phi_m = nullptr, *phi_h = nullptr, *phiT_m = nullptr, *phiT_h = nullptr,
@@ -2103,6 +2107,8 @@ struct MixedState {
   // third pieces: of Psi and Psi_g for n > 128 (the S product), of Phi' and Q
   // for every n (the orbital product)
   __half *psi_l = nullptr, *psig_l = nullptr, *phi_l = nullptr, *CT_l = nullptr;
+  __half *psigA_m = nullptr, *psigA_h = nullptr, *psigA_l = nullptr;  // all NaT points
+  CUtensorMap m_psigA64_m, m_psigA64_h, m_psigA128_m, m_psigA128_h, m_psigA128_l;
   CUtensorMap m_TA_h, m_TA_l, m_TAmn_h, m_TAmn_l, m_TC_h, m_TC_l, m_psi128_l, m_psig128_l,
       m_phi_l, m_CT_l;
   // Full K_{mu nu} (mixed_enqueue_full): scratch allocated on first use
@@ -2140,7 +2146,7 @@ cudaError_t alloc(MixedState* m, T** p, size_t elems) {
 }
 
 struct Plan {
-  long Np, Ng8, Na8, Ng4, Na4;
+  long Np, Ng8, Na8, Ng4, Na4, NaT4, NaT8;
   int np, xa, partsA, partsC, splitsL1, splitsL23, kchunkL1, kchunkL23, ychunkA, ychunkC;
   bool large;
   bool fused;      // 128-column pieces, n <= 128: the fused role replaces roles A and B
@@ -2167,8 +2173,12 @@ std::vector<int> tune_candidates(int64_t Ng, int xa) {
   return c;
 }
 
-Plan make_plan(int64_t Ng, int N, int n, int Naux) {
+// Naux: the held slice of interpolation points; NaT: all of them (the g'
+// range of the W term).
+Plan make_plan(int64_t Ng, int N, int n, int Naux, int NaT) {
   Plan p;
+  p.NaT4 = rup(NaT, 4);
+  p.NaT8 = rup(NaT, 8);
   p.np = (int)rup(n, 64);
   p.Np = rup(N, 64);
   p.Ng8 = rup(Ng, 8);
@@ -2184,9 +2194,9 @@ Plan make_plan(int64_t Ng, int N, int n, int Naux) {
     p.partsA = std::max(1, std::min<int>((608 + p.xa - 1) / p.xa, (int)((Ng + 63) / 64)));
     p.ychunkA = (int)rup((Ng + p.partsA - 1) / p.partsA, 64);
     p.partsA = (int)((Ng + p.ychunkA - 1) / p.ychunkA);
-    p.partsC = std::max(1, std::min<int>((608 + p.xa - 1) / p.xa, (Naux + 63) / 64));
-    p.ychunkC = (int)rup((Naux + p.partsC - 1) / p.partsC, 64);
-    p.partsC = (Naux + p.ychunkC - 1) / p.ychunkC;
+    p.partsC = std::max(1, std::min<int>((608 + p.xa - 1) / p.xa, (NaT + 63) / 64));
+    p.ychunkC = (int)rup((NaT + p.partsC - 1) / p.partsC, 64);
+    p.partsC = (NaT + p.ychunkC - 1) / p.ychunkC;
     p.partsA_max = p.partsA;
     for (int c : tune_candidates(Ng, p.xa)) p.partsA_max = std::max(p.partsA_max, c);
     p.epA = (long)p.partsA_max * p.xa;
@@ -2202,11 +2212,11 @@ Plan make_plan(int64_t Ng, int N, int n, int Naux) {
     p.partsA = std::max(1, std::min<int>((608 + t2 - 1) / t2, (int)((Ng + 4095) / 4096)));
     p.ychunkA = (int)rup((Ng + p.partsA - 1) / p.partsA, 64);
     p.partsA = (int)((Ng + p.ychunkA - 1) / p.ychunkA);
-    p.partsC = std::max(1, std::min<int>((304 + t2 - 1) / t2, (Naux + 1023) / 1024));
-    p.ychunkC = (int)rup((Naux + p.partsC - 1) / p.partsC, 64);
-    p.partsC = (Naux + p.ychunkC - 1) / p.ychunkC;
+    p.partsC = std::max(1, std::min<int>((304 + t2 - 1) / t2, (NaT + 1023) / 1024));
+    p.ychunkC = (int)rup((NaT + p.partsC - 1) / p.partsC, 64);
+    p.partsC = (NaT + p.ychunkC - 1) / p.ychunkC;
     p.epA = (long)p.xa * ((Ng + 127) / 128);
-    p.epC = (long)p.xa * ((Naux + 127) / 128);
+    p.epC = (long)p.xa * ((NaT + 127) / 128);
     p.partsA_max = p.partsA;
   }
   // line GEMMs: (N / 128) x (n / 128) tiles x K splits of >= 1024
@@ -2265,27 +2275,27 @@ size_t dwork_elems(int64_t Ng, int N, int n) {
 
 }  // namespace
 
-size_t mixed_footprint(int64_t Ng, int N, int n, int Naux) {
-  const Plan p = make_plan(Ng, N, n, Naux);
-  const size_t ng = Ng, na = Naux;
+size_t mixed_footprint(int64_t Ng, int N, int n, int Naux, int NaT) {
+  const Plan p = make_plan(Ng, N, n, Naux, NaT);
+  const size_t ng = Ng, na = Naux, nat = NaT;
   size_t b = 0;
   b += 2 * ng * p.Np * 2 + 2 * (size_t)N * p.Ng8 * 2 + 2 * (size_t)N * p.Na8 * 2;  // Phi pieces
-  b += (p.fused ? 0 : na * p.Ng4 * 4) + (p.large ? 0 : ng * p.Na4 * 4) + na * p.Na4 * 4 + na * 4;  // V, V^T, W, idx
+  b += (p.fused ? 0 : na * p.Ng4 * 4) + (p.large ? 0 : ng * p.Na4 * 4) + na * p.NaT4 * 4 + nat * 4;  // V, V^T, W, idx
   if (p.large)  // T, third pieces
-    b += 2 * na * p.Ng8 * 2 + 2 * na * p.Na8 * 2 + (ng + na) * p.np * 2;
+    b += 2 * na * p.Ng8 * 2 + 2 * na * p.NaT8 * 2 + (ng + nat) * p.np * 2;
   b += (ng + n) * p.Np * 2;  // third pieces of Phi' and Q
-  b += 2 * (size_t)n * p.Np * 2 + (size_t)n * p.Np * 8 + 2 * ng * p.np * 2 + 2 * na * p.np * 2;
+  b += 2 * (size_t)n * p.Np * 2 + (size_t)n * p.Np * 8 + 2 * ng * p.np * 2 + 2 * nat * p.np * 2;
   b += (size_t)p.partsA_max * na * n * 4 + (size_t)p.partsC * na * n * 4 + (size_t)n * p.Ng4 * 4;
   b += na * n * 8 + (size_t)n * p.Na8 * 8 + 2 * (size_t)n * p.Ng8 * 2 + 2 * (size_t)n * p.Na8 * 2;
   b += (size_t)p.splitsL1 * N * n * 4 + (size_t)p.splitsL23 * N * n * 4;
   b += (size_t)(p.epA + p.epC) * 8;
   b += (size_t)N * N * 8 + (size_t)N * n * 8 + dwork_elems(Ng, N, n) * 8;
-  b += 2 * stage_elems(Ng, N, Naux, p.Ng8) * 8;
+  b += 2 * stage_elems(Ng, N, NaT, p.Ng8) * 8;
   return b + 64 * 1024;
 }
 
 size_t mixed_full_footprint(int64_t Ng, int N, int n, int Naux) {
-  const Plan p = make_plan(Ng, N, n, Naux);
+  const Plan p = make_plan(Ng, N, n, Naux, Naux);
   const FullPlan f = make_full_plan(Ng, N, Naux);
   const size_t na = Naux, nN = N;
   size_t b = p.large ? 0 : 2 * na * p.Ng8 * 2 + 2 * na * p.Na8 * 2;  // T_A, T_C (hi, lo)
@@ -2377,13 +2387,14 @@ cudaError_t autotune_split_a(MixedState* m, cudaStream_t s) {
   return e;
 }
 
-cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
+cudaError_t mixed_create(int64_t Ng, int N, int n, int NaT, int g0, int g1, const double* phi,
                          const int32_t* idx, const double* V, const double* W, double dV,
                          cudaStream_t s, MixedState** out) {
   *out = nullptr;
   cudaError_t e = get_encode();
   if (e != cudaSuccess) return e;
-  const Plan p = make_plan(Ng, N, n, Naux);
+  const int Naux = g1 - g0;
+  const Plan p = make_plan(Ng, N, n, Naux, NaT);
   e = cudaFuncSetAttribute(pair_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairCfg<64>::SMEM);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(pair_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairCfg<128>::SMEM);
@@ -2402,13 +2413,14 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   MixedState* m = new MixedState();
   auto bail = [&](cudaError_t err) { mixed_destroy(m); return err; };
   m->Ng = Ng; m->N = N; m->n = n; m->Naux = Naux; m->dV = dV; m->np = p.np;
+  m->NaT = NaT; m->g0 = g0; m->NaT4 = p.NaT4; m->NaT8 = p.NaT8;
   m->Np = p.Np; m->Ng8 = p.Ng8; m->Na8 = p.Na8; m->Ng4 = p.Ng4; m->Na4 = p.Na4;
   m->xa = p.xa; m->partsA = p.partsA; m->partsC = p.partsC;
   m->ychunkA = p.ychunkA; m->ychunkC = p.ychunkC;
   m->splitsL1 = p.splitsL1; m->splitsL23 = p.splitsL23;
   m->kchunkL1 = p.kchunkL1; m->kchunkL23 = p.kchunkL23;
   m->large = p.large; m->fused = p.fused; m->nt = p.nt; m->epA = p.epA; m->epC = p.epC;
-  const size_t ng = Ng, na = Naux;
+  const size_t ng = Ng, na = Naux, nat = NaT;
 #define MX(ptr, elems)                          \
   do {                                          \
     cudaError_t e_ = alloc(m, &(ptr), (elems)); \
@@ -2418,20 +2430,23 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   MX(m->phiT_m, (size_t)N * p.Ng8); MX(m->phiT_h, (size_t)N * p.Ng8);
   MX(m->phigT_m, (size_t)N * p.Na8); MX(m->phigT_h, (size_t)N * p.Na8);
   if (!p.fused) MX(m->V32, na * p.Ng4);
-  MX(m->W32, na * p.Na4);
+  MX(m->W32, na * p.NaT4);
   if (!p.large) MX(m->VT32, ng * p.Na4);
   if (p.large) {
     MX(m->TA_h, na * p.Ng8); MX(m->TA_l, na * p.Ng8);
-    MX(m->TC_h, na * p.Na8); MX(m->TC_l, na * p.Na8);
-    MX(m->psi_l, ng * p.np); MX(m->psig_l, na * p.np);
+    MX(m->TC_h, na * p.NaT8); MX(m->TC_l, na * p.NaT8);
+    MX(m->psi_l, ng * p.np); MX(m->psigA_l, nat * p.np);
+    m->psig_l = m->psigA_l + (size_t)g0 * p.np;
   }
   // third pieces of Phi' and Q for every n: with two pieces the orbital split
   // alone moves E_x by up to ~1e-6 Ha on the 64-centre cell
   MX(m->phi_l, ng * p.Np); MX(m->CT_l, (size_t)n * p.Np);
-  MX(m->idx, na);
+  MX(m->idx, nat);
   MX(m->CT_m, (size_t)n * p.Np); MX(m->CT_h, (size_t)n * p.Np); MX(m->CT64, (size_t)n * p.Np);
   MX(m->psi_m, ng * p.np); MX(m->psi_h, ng * p.np);
-  MX(m->psig_m, na * p.np); MX(m->psig_h, na * p.np);
+  MX(m->psigA_m, nat * p.np); MX(m->psigA_h, nat * p.np);
+  m->psig_m = m->psigA_m + (size_t)g0 * p.np;  // the slice's rows
+  m->psig_h = m->psigA_h + (size_t)g0 * p.np;
   MX(m->M2p, (size_t)p.partsA_max * na * n); MX(m->M3p, (size_t)p.partsC * na * n);
   MX(m->M1, (size_t)n * p.Ng4);
   MX(m->D23, na * n); MX(m->D23T64, (size_t)n * p.Na8);
@@ -2446,7 +2461,7 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
 #undef MX
   double *stage = nullptr, *stage2 = nullptr;
   {
-    const size_t elems = stage_elems(Ng, N, Naux, p.Ng8);
+    const size_t elems = stage_elems(Ng, N, NaT, p.Ng8);
     void* q = nullptr;
     e = cudaMalloc(&q, elems * 8);
     if (e != cudaSuccess) return bail(e);
@@ -2463,7 +2478,7 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   e = cudaMemsetAsync(m->am, 0, NAM * 4, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->sc, 0, NSC * 4, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->status, 0, 16, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(m->idx, idx, na * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m->idx, idx, nat * 4, cudaMemcpyHostToDevice, s);
   // Phi pieces in three layouts: Phi [R][mu], Phi^T [mu][R], Phi_g^T [mu][g]
   if (e == cudaSuccess) e = cudaMemcpyAsync(stage, phi, ng * N * 8, cudaMemcpyDefault, s);
   if (e != cudaSuccess) return fin(e);
@@ -2502,7 +2517,7 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
   }
   e = transpose<double>(stage, ng, N, N, stage2, p.Ng8, s);
   if (e == cudaSuccess) e = split_rows<double>(stage2, N, p.Ng8, p.Ng8, m->sc, SC_PHI, m->phiT_m, m->phiT_h, p.Ng8, s);
-  if (e == cudaSuccess) e = gather_rows_f64(stage, N, m->idx, Naux, N, stage2, N, s);
+  if (e == cudaSuccess) e = gather_rows_f64(stage, N, m->idx + g0, Naux, N, stage2, N, s);
   if (e == cudaSuccess) e = transpose<double>(stage2, na, N, N, stage, p.Na8, s);
   if (e == cudaSuccess) e = split_rows<double>(stage, N, p.Na8, p.Na8, m->sc, SC_PHI, m->phigT_m, m->phigT_h, p.Na8, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -2530,10 +2545,11 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
       e = cudaStreamSynchronize(s);  // the next chunk reuses the staging buffer
     }
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(stage, W, na * na * 8, cudaMemcpyDefault, s);
+  // W: the slice's rows, all NaT columns
+  if (e == cudaSuccess) e = cudaMemcpyAsync(stage, W, na * nat * 8, cudaMemcpyDefault, s);
   if (e != cudaSuccess) return fin(e);
-  absmax_kernel<double><<<blocks_for(na * na), 256, 0, s>>>(stage, na, na, na, m->am + AM_W);
-  f64_to_f32_kernel<<<blocks_for(na * p.Na4), 256, 0, s>>>(stage, na, na, m->W32, p.Na4);
+  absmax_kernel<double><<<blocks_for(na * nat), 256, 0, s>>>(stage, na, nat, nat, m->am + AM_W);
+  f64_to_f32_kernel<<<blocks_for(na * p.NaT4), 256, 0, s>>>(stage, na, nat, m->W32, p.NaT4);
   count_launch(2);
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fin(e);
@@ -2556,6 +2572,10 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
       {&m->m_psig128_h, m->psig_h, F16, 2, (long)na, np_, 128, 64},
       {&m->m_psig64_m, m->psig_m, F16, 2, (long)na, np_, 64, 64},
       {&m->m_psig64_h, m->psig_h, F16, 2, (long)na, np_, 64, 64},
+      {&m->m_psigA64_m, m->psigA_m, F16, 2, (long)nat, np_, 64, 64},
+      {&m->m_psigA64_h, m->psigA_h, F16, 2, (long)nat, np_, 64, 64},
+      {&m->m_psigA128_m, m->psigA_m, F16, 2, (long)nat, np_, 128, 64},
+      {&m->m_psigA128_h, m->psigA_h, F16, 2, (long)nat, np_, 128, 64},
       {&m->m_phiT_m, m->phiT_m, F16, 2, N, p.Ng8, 128, 64},
       {&m->m_phiT_h, m->phiT_h, F16, 2, N, p.Ng8, 128, 64},
       {&m->m_M1_m, m->M1_m, F16, 2, n, p.Ng8, 128, 64},
@@ -2575,8 +2595,9 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
         {&m->m_TA_l, m->TA_l, F16, 2, (long)na, p.Ng8, 128, 64},
         {&m->m_TAmn_h, m->TA_h, F16, 2, (long)na, p.Ng8, 64, 64},
         {&m->m_TAmn_l, m->TA_l, F16, 2, (long)na, p.Ng8, 64, 64},
-        {&m->m_TC_h, m->TC_h, F16, 2, (long)na, p.Na8, 128, 64},
-        {&m->m_TC_l, m->TC_l, F16, 2, (long)na, p.Na8, 128, 64},
+        {&m->m_TC_h, m->TC_h, F16, 2, (long)na, p.NaT8, 128, 64},
+        {&m->m_TC_l, m->TC_l, F16, 2, (long)na, p.NaT8, 128, 64},
+        {&m->m_psigA128_l, m->psigA_l, F16, 2, (long)nat, p.np, 128, 64},
         {&m->m_psi128_l, m->psi_l, F16, 2, (long)ng, p.np, 128, 64},
         {&m->m_psig128_l, m->psig_l, F16, 2, (long)na, p.np, 128, 64},
     };
@@ -2589,7 +2610,7 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
     const auto F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     if (m->V32) e = make_map(&m->m_VA, m->V32, F32, 4, (long)na, p.Ng4, 128, 32);
     if (e == cudaSuccess && m->VT32) e = make_map(&m->m_VB, m->VT32, F32, 4, (long)ng, p.Na4, 128, 32);
-    if (e == cudaSuccess) e = make_map(&m->m_VC, m->W32, F32, 4, (long)na, p.Na4, 128, 32);
+    if (e == cudaSuccess) e = make_map(&m->m_VC, m->W32, F32, 4, (long)na, p.NaT4, 128, 32);
     if (e != cudaSuccess) return fin(e);
   }
   if (!p.large) {
@@ -2622,8 +2643,9 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
                         SC_F_AB, SC_OUT_AB, m->M1, m->Ng4, 0, 1, nullptr, m->status};
       r[1].gx = gB; r[1].nblk = gB; r[1].tiles = (int)(rup(na, 64) / 64);
     }
-    r[2].ym = m->m_psig64_m; r[2].yh = m->m_psig64_h; r[2].v = m->m_VC;
-    r[2].a = PairArgs{(int)na, (int)na, m->ychunkC, n, m->psig_m, m->psig_h, np_, m->sc, SC_F_C,
+    // role C: X = the slice's points, Y = all NaT points (the g' of W)
+    r[2].ym = m->m_psigA64_m; r[2].yh = m->m_psigA64_h; r[2].v = m->m_VC;
+    r[2].a = PairArgs{(int)na, (int)nat, m->ychunkC, n, m->psig_m, m->psig_h, np_, m->sc, SC_F_C,
                       SC_OUT_C, m->M3p, n, (long)(na * n), 0, m->EpC, m->status};
     r[2].gx = m->xa; r[2].nblk = m->xa * m->partsC; r[2].tiles = m->ychunkC / 64;
     if (!m->fused) {
@@ -2683,11 +2705,12 @@ cudaError_t mixed_enqueue_pre(MixedState* m, const double* C, cudaStream_t s, co
     count_launch();
   }
   scales_kernel<<<1, 32, 0, s>>>(m->am, m->sc, 1);
-  gather_rows_half_kernel<<<blocks_for(na * np), 256, 0, s>>>(m->psi_m, np, m->idx, (int)na, m->psig_m);
-  gather_rows_half_kernel<<<blocks_for(na * np), 256, 0, s>>>(m->psi_h, np, m->idx, (int)na, m->psig_h);
+  const long nat = m->NaT;  // the orbitals at every interpolation point (psig is the slice's view)
+  gather_rows_half_kernel<<<blocks_for(nat * np), 256, 0, s>>>(m->psi_m, np, m->idx, (int)nat, m->psigA_m);
+  gather_rows_half_kernel<<<blocks_for(nat * np), 256, 0, s>>>(m->psi_h, np, m->idx, (int)nat, m->psigA_h);
   count_launch(4);
   if (m->psi_l) {
-    gather_rows_half_kernel<<<blocks_for(na * np), 256, 0, s>>>(m->psi_l, np, m->idx, (int)na, m->psig_l);
+    gather_rows_half_kernel<<<blocks_for(nat * np), 256, 0, s>>>(m->psi_l, np, m->idx, (int)nat, m->psigA_l);
     count_launch();
   }
   e = cudaGetLastError();
@@ -2711,18 +2734,19 @@ void enqueue_t_products(MixedState* m, cudaStream_t s, bool store, bool energy) 
   launch_gemm(m->m_psig128_m, m->m_psig128_h, m->m_psi128_m, m->m_psi128_h,
               p3 ? m->m_psig128_l : m->m_psig128_m, p3 ? m->m_psi128_l : m->m_psi128_m, t,
               dim3((unsigned)m->xa, (unsigned)((ng + 127) / 128), 1), s, m->wait_cycles);
-  GemmArgs tc = t;
-  tc.Ncols = (int)na; tc.tv = m->W32; tc.ldv = m->Na4; tc.f_idx = SC_F_C;
+  GemmArgs tc = t;  // rows: the slice's points; columns: all NaT points
+  tc.Ncols = m->NaT; tc.tv = m->W32; tc.ldv = m->NaT4; tc.f_idx = SC_F_C;
   tc.th = store ? m->TC_h : nullptr; tc.tl = store ? m->TC_l : nullptr;
-  tc.ld_t = m->Na8; tc.epart = energy ? m->EpC : nullptr;
-  launch_gemm(m->m_psig128_m, m->m_psig128_h, m->m_psig128_m, m->m_psig128_h,
-              p3 ? m->m_psig128_l : m->m_psig128_m, p3 ? m->m_psig128_l : m->m_psig128_m, tc,
-              dim3((unsigned)m->xa, (unsigned)((na + 127) / 128), 1), s, m->wait_cycles);
+  tc.ld_t = m->NaT8; tc.epart = energy ? m->EpC : nullptr;
+  launch_gemm(m->m_psig128_m, m->m_psig128_h, m->m_psigA128_m, m->m_psigA128_h,
+              p3 ? m->m_psig128_l : m->m_psig128_m, p3 ? m->m_psigA128_l : m->m_psigA128_m, tc,
+              dim3((unsigned)m->xa, (unsigned)((m->NaT + 127) / 128), 1), s, m->wait_cycles);
   count_launch(2);
 }
 
 cudaError_t mixed_full_prepare(MixedState* m) {
   if (m->full_ready) return cudaSuccess;
+  if (m->NaT != m->Naux) return cudaErrorNotSupported;  // a slice has no full K of its own
   const long ng = m->Ng, na = m->Naux;
   const int N = m->N;
   const FullPlan f = make_full_plan(ng, N, (int)na);
@@ -2869,8 +2893,8 @@ cudaError_t mixed_enqueue_pair(MixedState* m, cudaStream_t s, const StepHook& ho
     launch_gemm(m->m_TA_h, m->m_TA_l, m->m_psi64_m, m->m_psi64_h, m->m_TA_h, m->m_psi64_m, g2,
                 dim3((unsigned)m->xa, (unsigned)m->nt, (unsigned)m->partsA), s, m->wait_cycles);
     GemmArgs g3 = g2;
-    g3.K = (int)na; g3.kchunk = m->ychunkC; g3.out = m->M3p; g3.scale_idx = SC_OUT_C;
-    launch_gemm(m->m_TC_h, m->m_TC_l, m->m_psig64_m, m->m_psig64_h, m->m_TC_h, m->m_psig64_m, g3,
+    g3.K = m->NaT; g3.kchunk = m->ychunkC; g3.out = m->M3p; g3.scale_idx = SC_OUT_C;
+    launch_gemm(m->m_TC_h, m->m_TC_l, m->m_psigA64_m, m->m_psigA64_h, m->m_TC_h, m->m_psigA64_m, g3,
                 dim3((unsigned)m->xa, (unsigned)m->nt, (unsigned)m->partsC), s, m->wait_cycles);
     GemmArgs g1{};
     g1.M = (int)ng; g1.Ncols = n; g1.K = (int)na; g1.kchunk = (int)rup(na, 64); g1.out = m->M1;

@@ -21,12 +21,16 @@ struct StepHook {
   }
 };
 
-// Device bytes of the mixed-precision tables and scratch.
-size_t mixed_footprint(int64_t Ng, int N, int n, int Naux);
+// Device bytes of the mixed-precision tables and scratch for a state that
+// holds the rows of Naux of the NaT interpolation points (Naux = NaT unsharded).
+size_t mixed_footprint(int64_t Ng, int N, int n, int Naux, int NaT);
 
-// Convert and upload the per-geometry tables: FP64 phi, V, W in host or
-// device memory (copies use cudaMemcpyDefault), idx in host memory.
-cudaError_t mixed_create(int64_t Ng, int N, int n, int Naux, const double* phi,
+// Convert and upload the per-geometry tables: FP64 phi (Ng x N), idx (all NaT
+// interpolation points, host memory), and the rows [g0, g1) of V (g1 - g0 rows
+// of Ng) and of W (g1 - g0 rows of NaT), in host or device memory (copies use
+// cudaMemcpyDefault).  g0 = 0, g1 = NaT is the whole cell; a slice makes the
+// builds return that slice's share of K and E_x (the sum over g splits).
+cudaError_t mixed_create(int64_t Ng, int N, int n, int NaT, int g0, int g1, const double* phi,
                          const int32_t* idx, const double* V, const double* W, double dV,
                          cudaStream_t s, MixedState** out);
 void mixed_destroy(MixedState* m);

@@ -45,6 +45,8 @@ def lib():
                                c_int, ctypes.POINTER(ctypes.c_void_p)]
         L.xk_setup_isdf.argtypes = [c_i64, c_i32, c_i32, c_i32, c_d, c_d, c_i32, ctypes.c_double,
                                     c_int, ctypes.POINTER(ctypes.c_void_p)]
+        L.xk_setup_shard.argtypes = [c_i64, c_i32, c_i32, c_i32, c_i32, c_i32, c_d, c_d, c_d, c_d,
+                                     ctypes.c_double, c_int, ctypes.POINTER(ctypes.c_void_p)]
         L.xk_tables.argtypes = [c_d, c_d, c_d, c_i32, c_d, c_d]
         L.xk_isdf_points.argtypes = [c_i32, c_i32, c_d, c_i32, ctypes.c_double, c_d, c_d]
         L.xk_build.argtypes = [c_d, c_d, c_d, c_d]
@@ -68,7 +70,7 @@ def lib():
         L.xk_error_estimate.argtypes = [c_d, c_d]
         L.xk_last_error.restype = ctypes.c_char_p
         L.xk_kernel_launches.restype = ctypes.c_uint64
-        for f in ("xk_footprint", "xk_setup", "xk_setup_isdf", "xk_tables", "xk_isdf_points",
+        for f in ("xk_footprint", "xk_setup", "xk_setup_shard", "xk_setup_isdf", "xk_tables", "xk_isdf_points",
                   "xk_build",
                   "xk_build_device", "xk_build_full",
                   "xk_coulomb",
@@ -129,6 +131,27 @@ class Handle:
         _check(lib().xk_setup(Ng, N, self.n, Naux, _ptr(phi), _ptr(idx), _ptr(V), _ptr(W),
                               float(dV), MODES[mode], ctypes.byref(h)))
         self._h = h
+
+    @classmethod
+    def shard(cls, phi, idx, V_rows, W_rows, g0, g1, dV, n, mode="fp64"):
+        """Handle of the g-slice [g0, g1) (xk_setup_shard): V_rows and W_rows are
+        the slice's rows of V (N_g columns) and W (all N_aux columns); its builds
+        return the slice's share of K and E_x."""
+        self = cls.__new__(cls)
+        phi = np.asarray(phi)
+        Ng, N = phi.shape
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        Naux = idx.shape[0]
+        self.Ng, self.N, self.n, self.Naux, self.mode = Ng, N, int(n), Naux, mode
+        phi = _f64(phi, (Ng, N), "phi")
+        V_rows = _f64(V_rows, (g1 - g0, Ng), "V_rows")
+        W_rows = _f64(W_rows, (g1 - g0, Naux), "W_rows")
+        h = ctypes.c_void_p()
+        _check(lib().xk_setup_shard(Ng, N, self.n, Naux, int(g0), int(g1), _ptr(phi), _ptr(idx),
+                                    _ptr(V_rows), _ptr(W_rows), float(dV), MODES[mode],
+                                    ctypes.byref(h)))
+        self._h = h
+        return self
 
     @classmethod
     def isdf(cls, phi, idx, grid, L, n, mode="fp64"):

@@ -140,3 +140,22 @@ def test_setup_refused_beyond_budget(L, monkeypatch):
     assert "XK_HBM_BUDGET_BYTES" in xk.last_error()
     monkeypatch.setenv("XK_HBM_BUDGET_BYTES", "0")
     assert _setup(L, phi, idx, V, W, mode=0) == xk.XK_ENOMEM
+
+
+def test_setup_shard_rejects_bad_slices(L):
+    """xk_setup_shard checks its slice [g0, g1) (non-empty, inside [0, N_aux))
+    and the symmetry of W on the slice's diagonal block before any device call."""
+    phi, idx, V, W = _tables()
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    h = ctypes.c_void_p()
+    for g0, g1 in ((5, 5), (-1, 4), (6, 11), (7, 3)):
+        rows = max(g1 - max(g0, 0), 1)
+        Vr = np.ascontiguousarray(V[:rows])
+        Wr = np.ascontiguousarray(W[:rows])
+        assert L.xk_setup_shard(64, 6, 3, 10, g0, g1, p(phi), p(idx), p(Vr), p(Wr), 0.1, 0,
+                                ctypes.byref(h)) == xk.XK_EINVAL, (g0, g1)
+    Wr = np.ascontiguousarray(W[2:6])
+    Wr[0, 3] += 1e-6  # W[2, 3] != W[3, 2]: the block [2, 6) x [2, 6) is not symmetric
+    assert L.xk_setup_shard(64, 6, 3, 10, 2, 6, p(phi), p(idx), p(np.ascontiguousarray(V[2:6])),
+                            p(Wr), 0.1, 0, ctypes.byref(h)) == xk.XK_EINVAL
+    assert "symmetric" in xk.last_error()

@@ -40,6 +40,51 @@ def test_two_gloo_ranks():
         assert value == pytest.approx(2 * 20 / 0.150)
 
 
+def _shard_rank(rank, world, port, out):
+    """One rank of a g-sharded build: the oracle's share of its slice (V and W
+    rows outside the slice set to zero: every line of Eq. exoccri is a sum
+    over the rows g), then bench.reduce_partials over gloo."""
+    import numpy as np
+    import torch
+    import oracle
+    from cellgen import build_cell, config_spec
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    c = build_cell(config_spec(1))
+    g0, g1 = bench.shard_slices(c.idx.size, world)[rank]
+    Vs = np.zeros_like(c.V)
+    Ws = np.zeros_like(c.W)
+    Vs[g0:g1] = c.V[g0:g1]
+    Ws[g0:g1] = c.W[g0:g1]
+    Kp, Ep = oracle.exx_rps_occri(c.phi, c.idx, Vs, Ws, c.C, c.dV)
+    K = torch.from_numpy(np.ascontiguousarray(Kp))
+    E = torch.tensor([Ep], dtype=torch.float64)
+    bench.reduce_partials(K, E, dist)
+    out[rank] = (K.numpy().copy(), float(E.item()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_shard_partials_reduce_to_the_full_build():
+    """The g-sharded decomposition on CPU: two gloo ranks each hold one slice
+    of the interpolation points; their shares of K_{mu i} and E_x, summed by
+    the bench's single allreduce, equal the unsharded oracle build."""
+    import numpy as np
+    import oracle
+    from cellgen import build_cell, config_spec
+    world = 2
+    port = _free_port()
+    out = mp.Manager().dict()
+    mp.spawn(_shard_rank, args=(world, port, out), nprocs=world, join=True)
+    c = build_cell(config_spec(1))
+    K0, E0 = oracle.exx_rps_occri(c.phi, c.idx, c.V, c.W, c.C, c.dV)
+    assert bench.shard_slices(256, 2) == [(0, 128), (128, 256)]
+    for r in range(world):
+        K, E = out[r]
+        assert np.max(np.abs(K - K0)) <= 1e-12 * np.max(np.abs(K0))
+        assert abs(E - E0) <= 1e-12 * abs(E0)
+
+
 def test_single_rank_is_identity():
     assert bench.max_over_ranks(12.5, None, "cpu") == 12.5
     assert bench.job_throughput(1, 10, 1000.0) == pytest.approx(10.0)
