@@ -113,6 +113,11 @@ __device__ __forceinline__ long long wait_limit(long long arg) {
   return arg > 0 ? arg : kWaitCycles;
 }
 
+// True when a launch shortened its pipeline-wait limit.  Kernels then run a
+// separate instantiation of their body (template flag kShort), so that the
+// default instantiation compiles the plain bounded wait and nothing else.
+__device__ __forceinline__ bool short_wait(long long arg) { return arg > 0 && arg < kWaitCycles; }
+
 // True in exactly one lane (the lowest) of a converged warp.
 __device__ __forceinline__ bool elect_one() {
   uint32_t p;

@@ -577,11 +577,13 @@ constexpr int kGemmEpi = 8;                      // epilogue warps (4 lane quadr
 constexpr int kGemmTma = kGemmEpi, kGemmMma = kGemmEpi + 1;
 constexpr int kGemmThreads = 32 * (kGemmEpi + 2);
 
-__global__ void __launch_bounds__(kGemmThreads, 1)
-    gemm_kernel(const __grid_constant__ CUtensorMap mAm, const __grid_constant__ CUtensorMap mAh,
-                const __grid_constant__ CUtensorMap mBm, const __grid_constant__ CUtensorMap mBh,
-                const __grid_constant__ CUtensorMap mAl, const __grid_constant__ CUtensorMap mBl,
-                GemmArgs g) {
+// kShort: the launch shortened its pipeline-wait limit (a separate
+// instantiation, so the default one keeps the plain bounded wait).
+template <bool kShort>
+__device__ __forceinline__ void gemm_body(const CUtensorMap* pAm, const CUtensorMap* pAh,
+                                          const CUtensorMap* pBm, const CUtensorMap* pBh,
+                                          const CUtensorMap* pAl, const CUtensorMap* pBl,
+                                          const GemmArgs& g) {
   extern __shared__ uint8_t g_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(g_raw) + 1023) & ~uintptr_t(1023));
   __shared__ uint64_t full[G_STAGES], empty[G_STAGES], set_ready[2], set_free[2], drain;
@@ -601,7 +603,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     return ke > kb0 ? (ke - kb0 + 63) / 64 : 0;
   };
   const bool p3 = g.pieces3 != 0;
-  const long long lw = wait_limit(g.wait);
+  const long long lw = kShort ? wait_limit(g.wait) : kWaitCycles;
   const int ns = p3 ? 2 : G_STAGES;                       // stages
   const int sbytes = p3 ? 6 * 16384 : G_STAGE_BYTES;      // bytes per stage
 
@@ -628,7 +630,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   const uint32_t tbase = tslot;
 
   if (warp == kGemmTma && lane == 0) {
-    prefetch_tmap(&mAm); prefetch_tmap(&mAh); prefetch_tmap(&mBm); prefetch_tmap(&mBh);
+    prefetch_tmap(pAm); prefetch_tmap(pAh); prefetch_tmap(pBm); prefetch_tmap(pBh);
     int last_parity[G_STAGES] = {-1, -1, -1};
     int it = 0;  // k-blocks issued by this CTA over all its tiles
     for (int tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x) {
@@ -644,32 +646,32 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       mbar_expect_tx(&full[s], sbytes);
       const int kc = kbeg + kb * 64;
       if (p3) {  // A m, h, l at 0, 16, 32 KB; B m, h, l at 48, 64, 80 KB
-        tma_load_2d(st, &mAm, &full[s], kc, m0);
-        tma_load_2d(st + 16384, &mAh, &full[s], kc, m0);
-        tma_load_2d(st + 32768, &mAl, &full[s], kc, m0);
-        tma_load_2d(st + 49152, &mBm, &full[s], kc, n0);
-        tma_load_2d(st + 65536, &mBh, &full[s], kc, n0);
-        tma_load_2d(st + 81920, &mBl, &full[s], kc, n0);
+        tma_load_2d(st, pAm, &full[s], kc, m0);
+        tma_load_2d(st + 16384, pAh, &full[s], kc, m0);
+        tma_load_2d(st + 32768, pAl, &full[s], kc, m0);
+        tma_load_2d(st + 49152, pBm, &full[s], kc, n0);
+        tma_load_2d(st + 65536, pBh, &full[s], kc, n0);
+        tma_load_2d(st + 81920, pBl, &full[s], kc, n0);
         last_parity[s] = use & 1;
         continue;
       }
       if (!g.a_mn) {
-        tma_load_2d(st, &mAm, &full[s], kc, m0);
-        tma_load_2d(st + 16384, &mAh, &full[s], kc, m0);
+        tma_load_2d(st, pAm, &full[s], kc, m0);
+        tma_load_2d(st + 16384, pAh, &full[s], kc, m0);
       } else {  // [64 K rows][64 M] boxes, M halves 8 KB apart
-        tma_load_2d(st, &mAm, &full[s], m0, kc);
-        tma_load_2d(st + 8192, &mAm, &full[s], m0 + 64, kc);
-        tma_load_2d(st + 16384, &mAh, &full[s], m0, kc);
-        tma_load_2d(st + 24576, &mAh, &full[s], m0 + 64, kc);
+        tma_load_2d(st, pAm, &full[s], m0, kc);
+        tma_load_2d(st + 8192, pAm, &full[s], m0 + 64, kc);
+        tma_load_2d(st + 16384, pAh, &full[s], m0, kc);
+        tma_load_2d(st + 24576, pAh, &full[s], m0 + 64, kc);
       }
       if (!g.b_mn) {
-        tma_load_2d(st + 32768, &mBm, &full[s], kc, n0);
-        tma_load_2d(st + 49152, &mBh, &full[s], kc, n0);
+        tma_load_2d(st + 32768, pBm, &full[s], kc, n0);
+        tma_load_2d(st + 49152, pBh, &full[s], kc, n0);
       } else {
-        tma_load_2d(st + 32768, &mBm, &full[s], n0, kc);
-        tma_load_2d(st + 40960, &mBm, &full[s], n0 + 64, kc);
-        tma_load_2d(st + 49152, &mBh, &full[s], n0, kc);
-        tma_load_2d(st + 57344, &mBh, &full[s], n0 + 64, kc);
+        tma_load_2d(st + 32768, pBm, &full[s], n0, kc);
+        tma_load_2d(st + 40960, pBm, &full[s], n0 + 64, kc);
+        tma_load_2d(st + 49152, pBh, &full[s], n0, kc);
+        tma_load_2d(st + 57344, pBh, &full[s], n0 + 64, kc);
       }
       last_parity[s] = use & 1;
     }
@@ -942,6 +944,17 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   if (warp == kGemmMma) tmem_dealloc(tbase, 512);
 }
 
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    gemm_kernel(const __grid_constant__ CUtensorMap mAm, const __grid_constant__ CUtensorMap mAh,
+                const __grid_constant__ CUtensorMap mBm, const __grid_constant__ CUtensorMap mBh,
+                const __grid_constant__ CUtensorMap mAl, const __grid_constant__ CUtensorMap mBl,
+                GemmArgs g) {
+  if (g.wait > 0 && g.wait < kWaitCycles)
+    gemm_body<true>(&mAm, &mAh, &mBm, &mBh, &mAl, &mBl, g);
+  else
+    gemm_body<false>(&mAm, &mAh, &mBm, &mBh, &mAl, &mBl, g);
+}
+
 // SMs of the current device (cached per device).
 int sm_count() {
   static int cached[64] = {0};
@@ -1102,7 +1115,7 @@ __device__ __forceinline__ void produce_tiles(const CUtensorMap* mYm, const CUte
 }
 
 // The kernel body: one X tile against a range of Y tiles for one role.
-template <int NP>
+template <int NP, bool kShort>
 __device__ __forceinline__ void pair_body(const CUtensorMap* mYm, const CUtensorMap* mYh,
                                           const CUtensorMap* mV, const PairArgs& a, int bx, int by,
                                           int gx) {
@@ -1120,7 +1133,7 @@ __device__ __forceinline__ void pair_body(const CUtensorMap* mYm, const CUtensor
   const int y0 = by * a.ychunk;
   const int y1 = min(a.Y, y0 + a.ychunk);
   const int T = y1 > y0 ? (y1 - y0 + 63) / 64 : 0;
-  const long long lw = wait_limit(a.wait);
+  const long long lw = kShort ? wait_limit(a.wait) : kWaitCycles;
 
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -1402,6 +1415,7 @@ __device__ __forceinline__ void red_add_f32(float* p, float v) {
   asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
 
+template <bool kShort>
 __device__ __forceinline__ void fused_body(const CUtensorMap* mYm, const CUtensorMap* mYh,
                                            const CUtensorMap* mV, const CUtensorMap* mXm,
                                            const CUtensorMap* mXh, const PairArgs& a, int bx) {
@@ -1419,7 +1433,7 @@ __device__ __forceinline__ void fused_body(const CUtensorMap* mYm, const CUtenso
   const int prod_warp = kEpiWarps, mma_warp = kEpiWarps + 1;
   const int x0 = bx * 128;
   const int T = a.Y > 0 ? (a.Y + 63) / 64 : 0;
-  const long long lw = wait_limit(a.wait);
+  const long long lw = kShort ? wait_limit(a.wait) : kWaitCycles;
 
   if (tid == 0) {
     for (int s = 0; s < kFusedStages; ++s) {
@@ -1770,7 +1784,10 @@ __global__ void __launch_bounds__(kPairThreads, 1) pair_kernel(const __grid_cons
   const CUtensorMap* mV = ri == 0 ? &job.v[0] : ri == 1 ? &job.v[1] : &job.v[2];
   const PairArgs& a = ri == 0 ? job.a[0] : ri == 1 ? job.a[1] : job.a[2];
   const int gx = ri == 0 ? job.gx[0] : ri == 1 ? job.gx[1] : job.gx[2];
-  pair_body<NP>(mYm, mYh, mV, a, blk % gx, blk / gx, gx);
+  if (short_wait(a.wait))
+    pair_body<NP, true>(mYm, mYh, mV, a, blk % gx, blk / gx, gx);
+  else
+    pair_body<NP, false>(mYm, mYh, mV, a, blk % gx, blk / gx, gx);
 }
 
 // Up to kGroupRoles roles of several builds in one launch, all in parameter
@@ -1792,11 +1809,17 @@ __global__ void __launch_bounds__(kPairThreads, 1)
   const int gx = job.gx[ri], blk = (int)blockIdx.x - job.first[ri];
   if constexpr (NP == 128) {
     if (job.kind[ri] == 1) {
-      fused_body(&job.ym[ri], &job.yh[ri], &job.v[ri], &job.xm[ri], &job.xh[ri], job.a[ri], blk);
+      if (short_wait(job.a[ri].wait))
+        fused_body<true>(&job.ym[ri], &job.yh[ri], &job.v[ri], &job.xm[ri], &job.xh[ri], job.a[ri], blk);
+      else
+        fused_body<false>(&job.ym[ri], &job.yh[ri], &job.v[ri], &job.xm[ri], &job.xh[ri], job.a[ri], blk);
       return;
     }
   }
-  pair_body<NP>(&job.ym[ri], &job.yh[ri], &job.v[ri], job.a[ri], blk % gx, blk / gx, gx);
+  if (short_wait(job.a[ri].wait))
+    pair_body<NP, true>(&job.ym[ri], &job.yh[ri], &job.v[ri], job.a[ri], blk % gx, blk / gx, gx);
+  else
+    pair_body<NP, false>(&job.ym[ri], &job.yh[ri], &job.v[ri], job.a[ri], blk % gx, blk / gx, gx);
 }
 
 // ============================================================ energy-only pair kernel
@@ -1818,7 +1841,7 @@ struct EnergyJob {
   int gx[2], nblk[2];
 };
 
-template <int NP>
+template <int NP, bool kShort>
 __device__ __forceinline__ void energy_body(const CUtensorMap* mYm, const CUtensorMap* mYh,
                                             const CUtensorMap* mV, const PairArgs& a, int bx,
                                             int by, int gx) {
@@ -1835,7 +1858,7 @@ __device__ __forceinline__ void energy_body(const CUtensorMap* mYm, const CUtens
   const int y0 = by * a.ychunk;
   const int y1 = min(a.Y, y0 + a.ychunk);
   const int T = y1 > y0 ? (y1 - y0 + 63) / 64 : 0;
-  const long long lw = wait_limit(a.wait);
+  const long long lw = kShort ? wait_limit(a.wait) : kWaitCycles;
   constexpr uint32_t T_SB = 128;  // first S buffer; the second follows 128 columns on
 
   if (tid == 0) {
@@ -1972,7 +1995,11 @@ __global__ void __launch_bounds__(kPairThreads, 1) energy_kernel(const __grid_co
   const int ri = (int)blockIdx.x >= job.nblk[0] ? 1 : 0;
   const int blk = (int)blockIdx.x - (ri ? job.nblk[0] : 0);
   const int gx = ri ? job.gx[1] : job.gx[0];
-  energy_body<NP>(ri ? &job.ym[1] : &job.ym[0], ri ? &job.yh[1] : &job.yh[0],
+  if (short_wait(ri ? job.a[1].wait : job.a[0].wait))
+    energy_body<NP, true>(ri ? &job.ym[1] : &job.ym[0], ri ? &job.yh[1] : &job.yh[0],
+                  ri ? &job.v[1] : &job.v[0], ri ? job.a[1] : job.a[0], blk % gx, blk / gx, gx);
+  else
+    energy_body<NP, false>(ri ? &job.ym[1] : &job.ym[0], ri ? &job.yh[1] : &job.yh[0],
                   ri ? &job.v[1] : &job.v[0], ri ? job.a[1] : job.a[0], blk % gx, blk / gx, gx);
 }
 
