@@ -42,9 +42,10 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # DRAM bytes per (X row, Y row) pair of the pair kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum = 1496 MB over 3.2316e8 pairs)
 PAIR_DRAM_BYTES_PER_PAIR = 1496e6 / (2.0 * 1755 * 91125 + 1755.0 * 1755)
-# The same for the fused role (one pass over V per N_aux x N_g pair): not yet
-# captured for the current kernel.
-FUSED_DRAM_BYTES_PER_PAIR = None
+# The same for the fused role (one pass over V^T per N_aux x N_g pair): one ncu
+# capture on the 27-centre cell with n = 128, 827 MB over 1.630e8 pairs
+# (profiles/pair_kernel_fused_cubic27_n128.md).
+FUSED_DRAM_BYTES_PER_PAIR = 827e6 / (1755.0 * 91125 + 1755.0 * 1755)
 # FP64 on the CUDA cores of GB300: 2 DFMA (4 flops) per clock per SM, measured
 # 3.81 flops/clock/SM with an FMA-chain probe; x 152 SMs x 2070 MHz.
 FP64_FLOPS_PER_CLK_SM = 4.0
@@ -571,6 +572,9 @@ def main():
     K_last = Kd.cpu().numpy()
     E_last = float(Ed.item())
     C_last = Cs[warm + steps - 1]
+    # per-build a-posteriori estimate |E_x - E_K| (E_K = -sum K o C of the
+    # returned K) of the last timed build; a shard's is its share's
+    err_est = h.error_estimate()
 
     # e2e through the blocking C-ABI call: host (pinned) buffers in and out
     Ch = [torch.from_numpy(C).pin_memory() for C in Cs[warm:warm + steps]]
@@ -652,7 +656,8 @@ def main():
     fp64 = None
     if mode != "fp64" and not args.no_fp64:
         hf = xk.Handle(cell.phi, cell.idx, cell.V, cell.W, cell.dV, n, mode="fp64")
-        ms64, _, _ = time_device_builds(xk, hf, Cd[warm + steps - 3:], Kd, Ed, stream, 1, 2, torch)
+        nf = min(5, len(Cd) - 1)  # FP64 builds timed after one warm-up
+        ms64, _, _ = time_device_builds(xk, hf, Cd[len(Cd) - nf - 1:], Kd, Ed, stream, 1, nf, torch)
         hf.build_device(Cd[warm + steps - 1].data_ptr(), Kd.data_ptr(), Ed.data_ptr(),
                         stream.cuda_stream)
         torch.cuda.synchronize()
@@ -676,7 +681,7 @@ def main():
             full["max_dK_vs_fp64"] = float(np.max(np.abs(Kf - Kf64)))
             full["max_abs_K"] = float(np.max(np.abs(Kf64)))
         hf.release()
-        fp64 = {"builds_per_s": 2.0 / (ms64 * 1e-3), "ms_per_build": ms64 / 2.0,
+        fp64 = {"builds_per_s": nf / (ms64 * 1e-3), "ms_per_build": ms64 / nf, "builds_timed": nf,
                 "dE_x_vs_fp64": abs(E_last - E64),
                 "max_dK_vs_fp64": float(np.max(np.abs(K_last - K64))), "coulomb_j": coul}
 
@@ -723,11 +728,9 @@ def main():
                         "bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"]),
                     # DRAM bytes of the pair launch: dram__bytes_read + write of one ncu
                     # capture of the same kernel on the 27-centre cell with n = 128,
-                    # scaled to this cell by its pair count (the traffic is per pair);
-                    # None until a capture of the current kernel exists
-                    "traffic": (None if pair_bytes is None else
-                                pair_bytes * (Na * Ng * (1.0 if npad == 128 else 2.0)
-                                              + float(Na) * Na)),
+                    # scaled to this cell by its pair count (the traffic is per pair)
+                    "traffic": pair_bytes * (Na * Ng * (1.0 if npad == 128 else 2.0)
+                                             + float(Na) * Na),
                     "traffic_source": "ncu capture of the pair kernel on the 27-centre cell "
                                       "(n = 128), scaled by pair count"}
         roof["frac"] = roof["achieved"] / roof["peak"]
@@ -753,6 +756,9 @@ def main():
             "roofline": roof,
             "gpu_launches": int(launches),
             "clocks": clocks,
+            "error_estimate": {"last_build": err_est,
+                               "definition": "|E_x - E_K|, E_K = -sum K o C of the returned K "
+                                             "(xk_poll err_est / xk_error_estimate)"},
             "e2e": {"value": job_throughput(1 if shard else world, steps, e2e_s * 1e3),
                     "unit": "builds/s",
                     "h2d_bytes_per_step": N * n * 8, "d2h_bytes_per_step": N * n * 8 + 8},
