@@ -259,6 +259,123 @@ __device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uin
       : "memory");
 }
 
+// Runs of MMAs along K issued by one elected lane of a converged warp, with
+// no branch per MMA: the whole warp executes one asm block, elect.sync picks
+// the lane and every tcgen05.mma is predicated on it.  `acc0` enables the
+// accumulator for the first MMA of the run; the others always accumulate.
+//
+// 8 TS MMAs: A in tensor memory at ta + 8 k (16-bit pairs, 8 columns per K
+// step); B a K-major 128-byte-swizzled tile whose K steps sit at
+// desc + {0, 2, 4, 6, 512, 514, 516, 518} (32 B apart within a 64-wide block,
+// 8 KB between blocks).
+__device__ __forceinline__ void mma_ts_run8_kmajor(uint32_t d, uint32_t ta, uint64_t b,
+                                                   uint32_t idesc, uint32_t acc0) {
+  asm volatile(
+      "{\n\t.reg .pred E, A, T;\n\t.reg .b64 b1, b2, b3, b4, b5, b6, b7;\n\t"
+      ".reg .b32 a1, a2, a3, a4, a5, a6, a7;\n\t"
+      "elect.sync _|E, 0xffffffff;\n\t"
+      "setp.ne.b32 A, %4, 0;\n\tsetp.eq.b32 T, 0, 0;\n\t"
+      "add.u32 a1, %1, 8;\n\tadd.u32 a2, %1, 16;\n\tadd.u32 a3, %1, 24;\n\tadd.u32 a4, %1, 32;\n\t"
+      "add.u32 a5, %1, 40;\n\tadd.u32 a6, %1, 48;\n\tadd.u32 a7, %1, 56;\n\t"
+      "add.s64 b1, %2, 2;\n\tadd.s64 b2, %2, 4;\n\tadd.s64 b3, %2, 6;\n\tadd.s64 b4, %2, 512;\n\t"
+      "add.s64 b5, %2, 514;\n\tadd.s64 b6, %2, 516;\n\tadd.s64 b7, %2, 518;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, A;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], [a1], b1, %3, T;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], [a2], b2, %3, T;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], [a3], b3, %3, T;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], [a4], b4, %3, T;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], [a5], b5, %3, T;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], [a6], b6, %3, T;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], [a7], b7, %3, T;\n\t}" ::"r"(d),
+      "r"(ta), "l"(b), "r"(idesc), "r"(acc0)
+      : "memory");
+}
+
+// 4 TS MMAs: A in tensor memory at ta + 8 k; B an MN-major tile whose K steps
+// (16 rows) sit 2048 B apart (desc + 128 k).
+__device__ __forceinline__ void mma_ts_run4_mn(uint32_t d, uint32_t ta, uint64_t b, uint32_t idesc,
+                                               uint32_t acc0) {
+  asm volatile(
+      "{\n\t.reg .pred E, A, T;\n\t.reg .b64 b1, b2, b3;\n\t.reg .b32 a1, a2, a3;\n\t"
+      "elect.sync _|E, 0xffffffff;\n\t"
+      "setp.ne.b32 A, %4, 0;\n\tsetp.eq.b32 T, 0, 0;\n\t"
+      "add.u32 a1, %1, 8;\n\tadd.u32 a2, %1, 16;\n\tadd.u32 a3, %1, 24;\n\t"
+      "add.s64 b1, %2, 128;\n\tadd.s64 b2, %2, 256;\n\tadd.s64 b3, %2, 384;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, A;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], [a1], b1, %3, T;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], [a2], b2, %3, T;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], [a3], b3, %3, T;\n\t}" ::"r"(d),
+      "r"(ta), "l"(b), "r"(idesc), "r"(acc0)
+      : "memory");
+}
+
+// 8 SS MMAs, both operands MN-major with K steps (16 rows) 2048 B apart.
+__device__ __forceinline__ void mma_ss_run8_mn(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                               uint32_t acc0) {
+  asm volatile(
+      "{\n\t.reg .pred E, A, T;\n\t.reg .b64 a1, a2, a3, a4, a5, a6, a7, b1, b2, b3, b4, b5, b6, b7;\n\t"
+      "elect.sync _|E, 0xffffffff;\n\t"
+      "setp.ne.b32 A, %4, 0;\n\tsetp.eq.b32 T, 0, 0;\n\t"
+      "add.s64 a1, %1, 128;\n\tadd.s64 a2, %1, 256;\n\tadd.s64 a3, %1, 384;\n\tadd.s64 a4, %1, 512;\n\t"
+      "add.s64 a5, %1, 640;\n\tadd.s64 a6, %1, 768;\n\tadd.s64 a7, %1, 896;\n\t"
+      "add.s64 b1, %2, 128;\n\tadd.s64 b2, %2, 256;\n\tadd.s64 b3, %2, 384;\n\tadd.s64 b4, %2, 512;\n\t"
+      "add.s64 b5, %2, 640;\n\tadd.s64 b6, %2, 768;\n\tadd.s64 b7, %2, 896;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, A;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], a1, b1, %3, T;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], a2, b2, %3, T;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], a3, b3, %3, T;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], a4, b4, %3, T;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], a5, b5, %3, T;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], a6, b6, %3, T;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], a7, b7, %3, T;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc0)
+      : "memory");
+}
+
+// 4 TS MMAs: A in tensor memory at ta + 8 k; B a K-major 128-byte-swizzled
+// tile whose K steps sit 32 B apart (desc + 2 k).
+__device__ __forceinline__ void mma_ts_run4_kmajor(uint32_t d, uint32_t ta, uint64_t b,
+                                                   uint32_t idesc, uint32_t acc0) {
+  asm volatile(
+      "{\n\t.reg .pred E, A, T;\n\t.reg .b64 b1, b2, b3;\n\t.reg .b32 a1, a2, a3;\n\t"
+      "elect.sync _|E, 0xffffffff;\n\t"
+      "setp.ne.b32 A, %4, 0;\n\tsetp.eq.b32 T, 0, 0;\n\t"
+      "add.u32 a1, %1, 8;\n\tadd.u32 a2, %1, 16;\n\tadd.u32 a3, %1, 24;\n\t"
+      "add.s64 b1, %2, 2;\n\tadd.s64 b2, %2, 4;\n\tadd.s64 b3, %2, 6;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, A;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], [a1], b1, %3, T;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], [a2], b2, %3, T;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], [a3], b3, %3, T;\n\t}" ::"r"(d),
+      "r"(ta), "l"(b), "r"(idesc), "r"(acc0)
+      : "memory");
+}
+
+// 4 SS MMAs with K steps `as` and `bs` apart in the A and B descriptors.
+__device__ __forceinline__ void mma_ss_run4(uint32_t d, uint64_t a, uint64_t b, uint64_t as,
+                                            uint64_t bs, uint32_t idesc, uint32_t acc0) {
+  asm volatile(
+      "{\n\t.reg .pred E, A, T;\n\t.reg .b64 a1, a2, a3, b1, b2, b3;\n\t"
+      "elect.sync _|E, 0xffffffff;\n\t"
+      "setp.ne.b32 A, %4, 0;\n\tsetp.eq.b32 T, 0, 0;\n\t"
+      "add.s64 a1, %1, %5;\n\tadd.s64 a2, a1, %5;\n\tadd.s64 a3, a2, %5;\n\t"
+      "add.s64 b1, %2, %6;\n\tadd.s64 b2, b1, %6;\n\tadd.s64 b3, b2, %6;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, A;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], a1, b1, %3, T;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], a2, b2, %3, T;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], a3, b3, %3, T;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc0), "l"(as), "l"(bs)
+      : "memory");
+}
+
+// One commit by an elected lane of a converged warp (no branch).
+__device__ __forceinline__ void mma_commit_elect(uint64_t* bar) {
+  asm volatile(
+      "{\n\t.reg .pred E;\n\telect.sync _|E, 0xffffffff;\n\t"
+      "@E tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
 // The mbarrier receives one arrival once every prior tcgen05 op of this thread completes.
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile(

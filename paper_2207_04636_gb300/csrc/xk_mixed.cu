@@ -713,20 +713,13 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* pAm, const CUtensor
         const uint64_t dam = dkm + s * (uint64_t)(sbytes >> 4), dah = dam + 1024, dal = dam + 2048;
         const uint64_t dbm = dam + 3072, dbh = dam + 4096, dbl = dam + 5120;
         const uint32_t t0 = tbase + set * 256, t1 = t0 + 128;
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          if (elect_one()) mma_f16(t0, dam + kk * 2, dbm + kk * 2, idesc, (first && kk == 0) ? 0u : 1u);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          if (elect_one()) mma_f16(t1, dam + kk * 2, dbh + kk * 2, idesc, (first && kk == 0) ? 0u : 1u);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) if (elect_one()) mma_f16(t1, dah + kk * 2, dbm + kk * 2, idesc, 1u);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) if (elect_one()) mma_f16(t1, dah + kk * 2, dbh + kk * 2, idesc, 1u);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) if (elect_one()) mma_f16(t1, dam + kk * 2, dbl + kk * 2, idesc, 1u);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) if (elect_one()) mma_f16(t1, dal + kk * 2, dbm + kk * 2, idesc, 1u);
+        const uint32_t a0 = first ? 0u : 1u;
+        mma_ss_run4(t0, dam, dbm, 2, 2, idesc, a0);
+        mma_ss_run4(t1, dam, dbh, 2, 2, idesc, a0);
+        mma_ss_run4(t1, dah, dbm, 2, 2, idesc, 1u);
+        mma_ss_run4(t1, dah, dbh, 2, 2, idesc, 1u);
+        mma_ss_run4(t1, dam, dbl, 2, 2, idesc, 1u);
+        mma_ss_run4(t1, dal, dbm, 2, 2, idesc, 1u);
         if (elect_one()) {
           mma_commit(&empty[s]);
           if (last) mma_commit(&set_ready[set]);
@@ -739,18 +732,11 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* pAm, const CUtensor
       const uint64_t dam = da0 + s * (G_STAGE_BYTES >> 4), dah = dam + 1024;
       const uint64_t dbm = db0 + s * (G_STAGE_BYTES >> 4) + 2048, dbh = dbm + 1024;
       const uint32_t t0 = tbase + set * 256, t1 = t0 + 128;
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk)
-        if (elect_one()) mma_f16(t0, dam + kk * ast, dbm + kk * bst, idesc, (first && kk == 0) ? 0u : 1u);
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk)
-        if (elect_one()) mma_f16(t1, dam + kk * ast, dbh + kk * bst, idesc, (first && kk == 0) ? 0u : 1u);
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk)
-        if (elect_one()) mma_f16(t1, dah + kk * ast, dbm + kk * bst, idesc, 1u);
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk)
-        if (elect_one()) mma_f16(t1, dah + kk * ast, dbh + kk * bst, idesc, 1u);
+      const uint32_t a0 = first ? 0u : 1u;
+      mma_ss_run4(t0, dam, dbm, ast, bst, idesc, a0);
+      mma_ss_run4(t1, dam, dbh, ast, bst, idesc, a0);
+      mma_ss_run4(t1, dah, dbm, ast, bst, idesc, 1u);
+      mma_ss_run4(t1, dah, dbh, ast, bst, idesc, 1u);
       if (elect_one()) {
         mma_commit(&empty[s]);
         if (last) mma_commit(&set_ready[set]);
@@ -1196,15 +1182,9 @@ __device__ __forceinline__ void pair_body(const CUtensorMap* mYm, const CUtensor
       const uint64_t bym = dy0mn + s * kStage16, byh = bym + kYh16;
       const uint32_t tuh = tbase + C::T_U + b * 64, tul = tuh + 32;
       // K step kk: 16 Y rows = 8 TMEM columns of U, 2048 bytes of the MN-major Y tile
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk)
-        if (elect_one()) mma_f16_ts(tacc, tuh + kk * 8, bym + kk * 128, id_acc, (first && kk == 0) ? 0u : 1u);
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk)
-        if (elect_one()) mma_f16_ts(tacc, tuh + kk * 8, byh + kk * 128, id_acc, 1u);
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk)
-        if (elect_one()) mma_f16_ts(tacc, tul + kk * 8, bym + kk * 128, id_acc, 1u);
+      mma_ts_run4_mn(tacc, tuh, bym, id_acc, first ? 0u : 1u);
+      mma_ts_run4_mn(tacc, tuh, byh, id_acc, 1u);
+      mma_ts_run4_mn(tacc, tul, bym, id_acc, 1u);
       if (elect_one()) {
         mma_commit(&empty[s]);
         mma_commit(&u_free[b]);
@@ -1220,18 +1200,17 @@ __device__ __forceinline__ void pair_body(const CUtensorMap* mYm, const CUtensor
       tc_fence_after();
       const uint64_t dym = dy0 + s * kStage16, dyh = dym + kYh16;
       // K step kk: 8 TMEM columns of X; Y tile offset (kk/4)*8192 + (kk%4)*32 bytes
-#pragma unroll
-      for (int kk = 0; kk < NP / 16; ++kk)
-        if (elect_one()) mma_f16_ts(ts0, txm + kk * 8, dym + (kk >> 2) * 512 + (kk & 3) * 2, id_s, kk > 0 ? 1u : 0u);
-#pragma unroll
-      for (int kk = 0; kk < NP / 16; ++kk)
-        if (elect_one()) mma_f16_ts(ts1, txm + kk * 8, dyh + (kk >> 2) * 512 + (kk & 3) * 2, id_s, kk > 0 ? 1u : 0u);
-#pragma unroll
-      for (int kk = 0; kk < NP / 16; ++kk)
-        if (elect_one()) mma_f16_ts(ts1, txh + kk * 8, dym + (kk >> 2) * 512 + (kk & 3) * 2, id_s, 1u);
-#pragma unroll
-      for (int kk = 0; kk < NP / 16; ++kk)
-        if (elect_one()) mma_f16_ts(ts1, txh + kk * 8, dyh + (kk >> 2) * 512 + (kk & 3) * 2, id_s, 1u);
+      if constexpr (NP == 128) {
+        mma_ts_run8_kmajor(ts0, txm, dym, id_s, 0u);
+        mma_ts_run8_kmajor(ts1, txm, dyh, id_s, 0u);
+        mma_ts_run8_kmajor(ts1, txh, dym, id_s, 1u);
+        mma_ts_run8_kmajor(ts1, txh, dyh, id_s, 1u);
+      } else {
+        mma_ts_run4_kmajor(ts0, txm, dym, id_s, 0u);
+        mma_ts_run4_kmajor(ts1, txm, dyh, id_s, 0u);
+        mma_ts_run4_kmajor(ts1, txh, dym, id_s, 1u);
+        mma_ts_run4_kmajor(ts1, txh, dyh, id_s, 1u);
+      }
       if (elect_one()) mma_commit(&s_full);
       __syncwarp();
       if (t > 0 && !issue_acc(t - 1)) { fail(25); good = false; break; }
@@ -1545,10 +1524,7 @@ __device__ __forceinline__ void fused_body(const CUtensorMap* mYm, const CUtenso
       for (int pass = 0; pass < 3; ++pass) {
         const uint32_t ta = pass == 2 ? tul : tuh;
         const uint64_t db = pass == 1 ? bym + kYh16 : bym;
-        const uint32_t acc0 = (first && pass == 0) ? 0u : 1u;
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          if (elect_one()) mma_f16_ts(tacc, ta + kk * 8, db + kk * 128, id_m1, kk > 0 ? 1u : acc0);
+        mma_ts_run4_mn(tacc, ta, db, id_m1, (first && pass == 0) ? 0u : 1u);
       }
       if (elect_one()) {
         mma_commit(&y_empty[s]);
@@ -1563,10 +1539,7 @@ __device__ __forceinline__ void fused_body(const CUtensorMap* mYm, const CUtenso
       for (int pass = 0; pass < 3; ++pass) {
         const uint64_t da = pass == 1 ? dxh : dxm;
         const uint64_t db = pass == 2 ? dul : duh;
-        const uint32_t acc0 = pass > 0 ? 1u : 0u;
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk)
-          if (elect_one()) mma_f16(tm2, da + kk * 128, db + kk * 128, id_m2, kk > 0 ? 1u : acc0);
+        mma_ss_run8_mn(tm2, da, db, id_m2, pass > 0 ? 1u : 0u);
       }
       if (elect_one()) {
         mma_commit(&u_free);
@@ -1587,10 +1560,8 @@ __device__ __forceinline__ void fused_body(const CUtensorMap* mYm, const CUtenso
         const uint32_t td = pass == 0 ? ts0 : ts1;
         const uint32_t ta = pass < 2 ? txm : txh;
         const uint64_t db = (pass & 1) ? dyh : dym;
-        const uint32_t acc0 = pass >= 2 ? 1u : 0u;
-#pragma unroll
-        for (int kk = 0; kk < NP / 16; ++kk)
-          if (elect_one()) mma_f16_ts(td, ta + kk * 8, db + (kk >> 2) * 512 + (kk & 3) * 2, id_s, kk > 0 ? 1u : acc0);
+        static_assert(NP / 16 == 8, "one run of eight K steps per pass");
+        mma_ts_run8_kmajor(td, ta, db, id_s, pass >= 2 ? 1u : 0u);
       }
       if (elect_one()) mma_commit(&s_full);
       __syncwarp();
@@ -1914,10 +1885,10 @@ __device__ __forceinline__ void energy_body(const CUtensorMap* mYm, const CUtens
         const uint32_t td = pass == 0 ? ts0 : ts1;
         const uint32_t ta = pass < 2 ? txm : txh;
         const uint64_t db = (pass & 1) ? dyh : dym;
-        const uint32_t acc0 = pass >= 2 ? 1u : 0u;
-#pragma unroll
-        for (int kk = 0; kk < NP / 16; ++kk)
-          if (elect_one()) mma_f16_ts(td, ta + kk * 8, db + (kk >> 2) * 512 + (kk & 3) * 2, id_s, kk > 0 ? 1u : acc0);
+        if constexpr (NP == 128)
+          mma_ts_run8_kmajor(td, ta, db, id_s, pass >= 2 ? 1u : 0u);
+        else
+          mma_ts_run4_kmajor(td, ta, db, id_s, pass >= 2 ? 1u : 0u);
       }
       if (elect_one()) {
         mma_commit(&s_full[b]);
