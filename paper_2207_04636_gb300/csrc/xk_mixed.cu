@@ -440,15 +440,18 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
   hi = s;
 }
 
+// a_scale (nullable): a power of two applied to the a terms (exact).
 __global__ void reduce_parts_kernel(const float* __restrict__ a, int na, const float* __restrict__ b,
                                     int nb, long count, double* __restrict__ out,
-                                    unsigned* __restrict__ am_slot) {
+                                    unsigned* __restrict__ am_slot,
+                                    const float* __restrict__ a_scale = nullptr) {
   float m = 0.0f;
+  const float as = a_scale ? *a_scale : 1.0f;
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < count;
        t += (long)gridDim.x * blockDim.x) {
     float hi = 0.0f, lo = 0.0f;
 #pragma unroll 8
-    for (int p = 0; p < na; ++p) ff_add(hi, lo, a[(long)p * count + t]);
+    for (int p = 0; p < na; ++p) ff_add(hi, lo, a[(long)p * count + t] * as);
     if (b) {
 #pragma unroll 8
       for (int p = 0; p < nb; ++p) ff_add(hi, lo, -b[(long)p * count + t]);
@@ -1630,13 +1633,18 @@ __device__ __forceinline__ void fused_body(const CUtensorMap* mYm, const CUtenso
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&m2_free);
+      // accumulator units (the FP64 reduction of the copies applies the scale)
       if (r < a.n) {
-        const float os = a.sc[a.out_idx];
         const int g0 = u * 64 + 16 * c;
         float* dst = a.m2acc + (long)(bx % a.ncopy) * a.m2_copy_stride + (long)g0 * a.n + r;
+        if (g0 + 16 <= a.Y) {
 #pragma unroll
-        for (int k = 0; k < 16; ++k)
-          if (g0 + k < a.Y) red_add_f32(dst + (long)k * a.n, __uint_as_float(mv[k]) * os);
+          for (int k = 0; k < 16; ++k, dst += a.n) red_add_f32(dst, __uint_as_float(mv[k]));
+        } else {
+#pragma unroll
+          for (int k = 0; k < 16; ++k, dst += a.n)
+            if (g0 + k < a.Y) red_add_f32(dst, __uint_as_float(mv[k]));
+        }
       }
       return true;
     };
@@ -2922,8 +2930,10 @@ cudaError_t mixed_enqueue_post(MixedState* m, double* K, double* Ex, cudaStream_
   cudaError_t e;
   // ---- step 4: line1^T = Phi^T M1^T and (line2 - line3)^T = Phi_g^T (M2 - M3)
   hook(4, 1);
+  // the fused role's M2 copies hold accumulator units: scaled here (exact, 2^k)
   reduce_parts_kernel<<<blocks_for(na * n), 256, 0, s>>>(m->M2p, m->partsA, m->M3p, m->partsC,
-                                                         na * n, m->D23, m->am + AM_D23);
+                                                         na * n, m->D23, m->am + AM_D23,
+                                                         m->fused ? m->sc + SC_OUT_AB : nullptr);
   e = cudaMemsetAsync(m->rowmax, 0, (size_t)n * 4, s);
   if (e != cudaSuccess) return e;
   {
