@@ -819,7 +819,7 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* pAm, const CUtensor
         if (lane == 0) atomicMax(g.rn2, __float_as_uint(wn * 1.0001f));
       }
       if (m0 + r < g.M) {
-        const float q = row_grid(mx);
+        const float q = row_grid(mx), qi = 1.0f / q;  // q a power of two: x * qi == x / q
         __half* mrow = g.pm + (long)(m0 + r) * g.ld_p + cb;
         __half* hrow = g.ph + (long)(m0 + r) * g.ld_p + cb;
 #pragma unroll
@@ -829,7 +829,7 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* pAm, const CUtensor
 #pragma unroll
           for (int j = 0; j < 8; j += 2) {
             const float x0 = run[c0 + j] * G, x1 = run[c0 + j + 1] * G;
-            const float m0v = q * rintf(x0 / q), m1v = q * rintf(x1 / q);
+            const float m0v = q * rintf(x0 * qi), m1v = q * rintf(x1 * qi);
             const __half2 hm = __floats2half2_rn(m0v, m1v);
             const __half2 hh = __floats2half2_rn(x0 - m0v, x1 - m1v);
             mw[j / 2] = *reinterpret_cast<const uint32_t*>(&hm);
@@ -2197,10 +2197,10 @@ Plan make_plan(int64_t Ng, int N, int n, int Naux, int NaT) {
   p.nt = (n + 127) / 128;
   if (!p.large) {
     // roles A and C: X = g tiles; split Y so the grid is about four waves of 152 SMs
-    p.partsA = std::max(1, std::min<int>((608 + p.xa - 1) / p.xa, (int)((Ng + 63) / 64)));
+    p.partsA = std::max(1, std::min<int>(608 / p.xa, (int)((Ng + 63) / 64)));
     p.ychunkA = (int)rup((Ng + p.partsA - 1) / p.partsA, 64);
     p.partsA = (int)((Ng + p.ychunkA - 1) / p.ychunkA);
-    p.partsC = std::max(1, std::min<int>((608 + p.xa - 1) / p.xa, (NaT + 63) / 64));
+    p.partsC = std::max(1, std::min<int>(608 / p.xa, (NaT + 63) / 64));
     p.ychunkC = (int)rup((NaT + p.partsC - 1) / p.partsC, 64);
     p.partsC = (NaT + p.ychunkC - 1) / p.ychunkC;
     p.partsA_max = p.partsA;
@@ -2215,22 +2215,24 @@ Plan make_plan(int64_t Ng, int N, int n, int Naux, int NaT) {
   } else {
     // M2 = T_A Psi and M3 = T_C Psi_g: (xa x nt) tiles, K split to about four waves
     const int t2 = p.xa * p.nt;
-    p.partsA = std::max(1, std::min<int>((608 + t2 - 1) / t2, (int)((Ng + 4095) / 4096)));
+    p.partsA = std::max(1, std::min<int>(608 / t2, (int)((Ng + 4095) / 4096)));
     p.ychunkA = (int)rup((Ng + p.partsA - 1) / p.partsA, 64);
     p.partsA = (int)((Ng + p.ychunkA - 1) / p.ychunkA);
-    p.partsC = std::max(1, std::min<int>((304 + t2 - 1) / t2, (NaT + 1023) / 1024));
+    p.partsC = std::max(1, std::min<int>(304 / t2, (NaT + 1023) / 1024));
     p.ychunkC = (int)rup((NaT + p.partsC - 1) / p.partsC, 64);
     p.partsC = (NaT + p.ychunkC - 1) / p.ychunkC;
     p.epA = (long)p.xa * ((Ng + 127) / 128);
     p.epC = (long)p.xa * ((NaT + 127) / 128);
     p.partsA_max = p.partsA;
   }
-  // line GEMMs: (N / 128) x (n / 128) tiles x K splits of >= 1024
+  // line GEMMs: (N / 128) x (n / 128) tiles x K splits of >= 1024; split
+  // counts round down, so the tiles fill whole waves of CTAs (a wave plus one
+  // tile would run a whole extra tile time)
   const int tiles = ((N + 127) / 128) * ((n + 127) / 128);
-  p.splitsL1 = std::max(1, std::min<int>((int)((Ng + 1023) / 1024), (608 + tiles - 1) / tiles));
+  p.splitsL1 = std::max(1, std::min<int>((int)((Ng + 1023) / 1024), 608 / tiles));
   p.kchunkL1 = (int)rup((Ng + p.splitsL1 - 1) / p.splitsL1, 64);
   p.splitsL1 = (int)((Ng + p.kchunkL1 - 1) / p.kchunkL1);
-  p.splitsL23 = std::max(1, std::min<int>((Naux + 511) / 512, (304 + tiles - 1) / tiles));
+  p.splitsL23 = std::max(1, std::min<int>((Naux + 511) / 512, 304 / tiles));
   p.kchunkL23 = (int)rup((Naux + p.splitsL23 - 1) / p.splitsL23, 64);
   p.splitsL23 = (Naux + p.kchunkL23 - 1) / p.kchunkL23;
   return p;
@@ -2251,7 +2253,7 @@ struct FullPlan {
 FullPlan make_full_plan(int64_t Ng, int N, int Naux) {
   const int xa = (Naux + 127) / 128, tn = (N + 127) / 128;
   auto split = [](long K, int tiles, int& kchunk) {
-    int sp = (int)std::max<long>(1, std::min<long>((K + 1023) / 1024, (608 + tiles - 1) / tiles));
+    int sp = (int)std::max<long>(1, std::min<long>((K + 1023) / 1024, 608 / tiles));
     kchunk = (int)rup((K + sp - 1) / sp, 64);
     return (int)((K + kchunk - 1) / kchunk);
   };
