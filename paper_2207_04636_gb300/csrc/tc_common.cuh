@@ -158,6 +158,38 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// Tiled store of a shared-memory box to global memory (bulk async group of
+// the issuing thread); elements outside the tensor map's extent are dropped.
+// The writers of the box execute fence_async_smem() and synchronise first.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int c0,
+                                             int c1) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(smem_u32(src)), "r"(c0), "r"(c1)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// Waits until every committed bulk store of this thread has read its source
+// (the shared memory may then be rewritten).
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// Waits until every committed bulk store of this thread has completed.
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
 // Brings a tile of a tensor map into L2 (no shared-memory destination).
 __device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int c0, int c1) {
   asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
@@ -196,6 +228,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
         "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
+}
+// Thread t of warp w reads TMEM lane 32*(w%4)+t, columns [col, col+8).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -373,6 +412,21 @@ __device__ __forceinline__ void mma_ss_run4(uint32_t d, uint64_t a, uint64_t b, 
       : "memory");
 }
 
+// Two SS MMAs over successive K=16 slices (steps as / bs), issued by one
+// elected lane; acc0 = 0 starts the accumulator with the first.
+__device__ __forceinline__ void mma_ss_run2(uint32_t d, uint64_t a, uint64_t b, uint64_t as,
+                                            uint64_t bs, uint32_t idesc, uint32_t acc0) {
+  asm volatile(
+      "{\n\t.reg .pred E, A, T;\n\t.reg .b64 a1, b1;\n\t"
+      "elect.sync _|E, 0xffffffff;\n\t"
+      "setp.ne.b32 A, %4, 0;\n\tsetp.eq.b32 T, 0, 0;\n\t"
+      "add.s64 a1, %1, %5;\n\tadd.s64 b1, %2, %6;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, A;\n\t"
+      "@E tcgen05.mma.cta_group::1.kind::f16 [%0], a1, b1, %3, T;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc0), "l"(as), "l"(bs)
+      : "memory");
+}
+
 // One commit by an elected lane of a converged warp (no branch).
 __device__ __forceinline__ void mma_commit_elect(uint64_t* bar) {
   asm volatile(
@@ -395,6 +449,15 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr, uint32_t lbo, ui
   return static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4) |
          (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
          (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+// The same for the 64-byte swizzled layout (CU_TENSOR_MAP_SWIZZLE_64B): rows
+// of 32 16-bit elements (64 B), 8-row atoms of 512 B (SBO = 512 for a K-major
+// tile), tile bases 512-B aligned; successive K=16 slices start 32 B apart.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4) |
+         (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
+         (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (4ull << 61);
 }
 
 // Instruction descriptor of kind::f16 with an FP32 accumulator.

@@ -481,26 +481,40 @@ __global__ void final_k_kernel(const float* __restrict__ L1, int n1, const float
 
 // E_x = -dV (2 sum_k ea[k] - sum_k ec[k]) / G^4 with G the orbital scale, in
 // a fixed summation order (one block of 256 threads).
-__global__ void final_ex_kernel(const double* __restrict__ ea, int na_, const double* __restrict__ ec,
-                                int nc_, const float* __restrict__ sc, double dV, double* Ex) {
-  __shared__ double sa[256], sb[256];
-  double a = 0.0, b = 0.0;
-  for (int t = threadIdx.x; t < na_; t += blockDim.x) a += ea[t];
-  for (int t = threadIdx.x; t < nc_; t += blockDim.x) b += ec[t];
-  sa[threadIdx.x] = a;
-  sb[threadIdx.x] = b;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      sa[threadIdx.x] += sa[threadIdx.x + w];
-      sb[threadIdx.x] += sb[threadIdx.x + w];
-    }
-    __syncthreads();
+__global__ void __launch_bounds__(1024) final_ex_kernel(const double* __restrict__ ea, int na_,
+                                                       const double* __restrict__ ec, int nc_,
+                                                       const float* __restrict__ sc, double dV,
+                                                       double* Ex) {
+  // one block of 1024 threads; four independent sums per thread keep several
+  // loads in flight (the n > 128 path has ~10^5 partials per launch); the
+  // order is fixed by the launch shape, so a build repeats bit for bit
+  __shared__ double sa[32], sb[32];
+  double a[4] = {0.0, 0.0, 0.0, 0.0}, b[4] = {0.0, 0.0, 0.0, 0.0};
+  const int T = blockDim.x;
+  int t = threadIdx.x;
+  for (; t + 3 * T < na_; t += 4 * T) {
+    a[0] += ea[t]; a[1] += ea[t + T]; a[2] += ea[t + 2 * T]; a[3] += ea[t + 3 * T];
   }
+  for (; t < na_; t += T) a[0] += ea[t];
+  t = threadIdx.x;
+  for (; t + 3 * T < nc_; t += 4 * T) {
+    b[0] += ec[t]; b[1] += ec[t + T]; b[2] += ec[t + 2 * T]; b[3] += ec[t + 3 * T];
+  }
+  for (; t < nc_; t += T) b[0] += ec[t];
+  double x = (a[0] + a[1]) + (a[2] + a[3]), y = (b[0] + b[1]) + (b[2] + b[3]);
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_xor_sync(0xffffffffu, x, o);
+    y += __shfl_xor_sync(0xffffffffu, y, o);
+  }
+  const int w = threadIdx.x >> 5, nw = T >> 5;
+  if ((threadIdx.x & 31) == 0) { sa[w] = x; sb[w] = y; }
+  __syncthreads();
   if (threadIdx.x == 0) {
+    double u = 0.0, v = 0.0;
+    for (int k = 0; k < nw; ++k) { u += sa[k]; v += sb[k]; }
     const double g = (double)sc[SC_PSI];
     const double g4 = (g * g) * (g * g);
-    *Ex = -dV * (2.0 * sa[0] - sb[0]) / g4;
+    *Ex = -dV * (2.0 * u - v) / g4;
   }
 }
 
@@ -549,17 +563,6 @@ struct GemmArgs {
   // K-major ([M][K], [N][K]; 128 x 64 boxes).
   int a_mn, b_mn;
   int transposed;  // write out[col][row] (stride ldo) instead of out[row][col]
-  // T mode (tv set, one split): the tile is S = A B^T (both in piece units);
-  // write the hi/lo FP16 split of f V'[row][col] S into th / tl [M][ld_t]
-  // (zero for Ncols <= col < ld_t) and the tile's sum V' S^2 into
-  // epart[by * tiles_x + bx] for the tile (bx, by).
-  const float* tv;
-  long ldv;
-  int f_idx;
-  __half* th;
-  __half* tl;
-  long ld_t;
-  double* epart;
   int kdrain;  // k-blocks per accumulator drain (0: kDrain)
   // Three pieces per operand (K-major only): x = m + h + l, l = fp16(x - m - h);
   // A1 adds m l' + l m' (products below 2^-30 of the row maxima are dropped).
@@ -758,7 +761,6 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* pAm, const CUtensor
     const int cb = 64 * half;
     const uint32_t lane_off = static_cast<uint32_t>(quad * 32) << 16;
     __shared__ float prow_mx[2][128], prow_nrm[2][128];
-    __shared__ double ered[kGemmEpi];
     // Every epilogue warp walks all of the CTA's tiles (after a failed wait
     // without waiting further), so the named barriers below match up.
     int G0 = 0;
@@ -839,59 +841,6 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* pAm, const CUtensor
           *reinterpret_cast<uint4*>(hrow + c0) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
         }
       }
-    } else if (g.tv) {
-      // T mode: V' o S and its hi/lo split, 8 columns at a time
-      const long x = (long)m0 + r;
-      const bool xok = x < g.M;
-      const float f = g.sc[g.f_idx];
-      const float* vrow = g.tv + x * g.ldv;
-      double esum = 0.0;
-#pragma unroll
-      for (int c0 = 0; c0 < 64; c0 += 8) {
-        const long col = (long)n0 + cb + c0;
-        if (col >= g.ld_t) break;
-        float v[8];
-        if (xok && col + 8 <= g.Ncols) {
-          const float4 v0 = *reinterpret_cast<const float4*>(vrow + col);
-          const float4 v1 = *reinterpret_cast<const float4*>(vrow + col + 4);
-          v[0] = v0.x; v[1] = v0.y; v[2] = v0.z; v[3] = v0.w;
-          v[4] = v1.x; v[5] = v1.y; v[6] = v1.z; v[7] = v1.w;
-        } else {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) v[j] = (xok && col + j < g.Ncols) ? vrow[col + j] : 0.0f;
-        }
-        uint32_t hw[4], lw[4];
-        float e = 0.0f;
-#pragma unroll
-        for (int j = 0; j < 8; j += 2) {
-          const float s0 = ok ? run[c0 + j] : 0.0f, s1 = ok ? run[c0 + j + 1] : 0.0f;
-          const float p0 = v[j] * s0, p1 = v[j + 1] * s1;
-          e = fmaf(p0, s0, e);
-          e = fmaf(p1, s1, e);
-          const float t0 = p0 * f, t1 = p1 * f;
-          const __half2 h01 = __floats2half2_rn(t0, t1);
-          const float2 b01 = __half22float2(h01);
-          const __half2 l01 = __floats2half2_rn(t0 - b01.x, t1 - b01.y);
-          hw[j / 2] = *reinterpret_cast<const uint32_t*>(&h01);
-          lw[j / 2] = *reinterpret_cast<const uint32_t*>(&l01);
-        }
-        esum += (double)e;
-        if (xok && g.th) {
-          *reinterpret_cast<uint4*>(g.th + x * g.ld_t + col) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-          *reinterpret_cast<uint4*>(g.tl + x * g.ld_t + col) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-        }
-      }
-      if (g.epart) {
-        for (int o = 16; o > 0; o >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, o);
-        if (lane == 0) ered[warp] = esum;
-        asm volatile("bar.sync 1, %0;" ::"n"(32 * kGemmEpi) : "memory");
-        if (warp == 0 && lane == 0) {
-          double t = 0.0;
-          for (int w = 0; w < kGemmEpi; ++w) t += ered[w];
-          g.epart[(long)by * g.tiles_x + bx] = t;
-        }
-        asm volatile("bar.sync 1, %0;" ::"n"(32 * kGemmEpi) : "memory");  // rewritten by the next tile
-      }
     } else if (g.transposed) {
       const long row = (long)m0 + r;
       if (row < g.M) {
@@ -969,6 +918,549 @@ void launch_gemm(const CUtensorMap& mAm, const CUtensorMap& mAh, const CUtensorM
   const long total = (long)tiles.x * tiles.y * tiles.z;
   const unsigned ctas = (unsigned)std::max<long>(1, std::min<long>(total, sm_count()));
   gemm_kernel<<<ctas, kGemmThreads, G_SMEM, s>>>(mAm, mAh, mBm, mBh, mAl, mBl, g);
+}
+
+// ============================================================ wide gemm
+// The same contraction as gemm_kernel over 128 x 256 output tiles (for the
+// n > 128 back-contractions M2 = T_A Psi, M3 = T_C Psi_g, M1^T = T_A^T
+// Psi_g): each 96 KB stage of operands (A m, h [128][64]; B m, h [256][64]
+// or [64][4 x 64]) feeds twice the MMA work of a 128 x 128 stage, so the
+// TMA ring needs 47 instead of 64 bytes per tensor-core cycle.  A0 and A1
+// fill the 512 columns of tensor memory (one set): the MMA warp waits for the
+// drain of each 192-term group before it starts the next, and 16 epilogue
+// warps (lane quadrant w % 4, 64 columns (w / 4)) keep that drain short.
+// Output: plain (splits) or transposed, as in gemm_kernel.
+constexpr int GW_STAGES = 2;
+constexpr int GW_STAGE_BYTES = 2 * 16384 + 2 * 32768;
+constexpr int GW_SMEM = GW_STAGES * GW_STAGE_BYTES + 1024;
+constexpr int kWideEpi = 16;
+constexpr int kWideTma = kWideEpi, kWideMma = kWideEpi + 1;
+constexpr int kWideThreads = 32 * (kWideEpi + 2);
+
+template <bool kShort>
+__device__ __forceinline__ void gemm_wide_body(const CUtensorMap* pAm, const CUtensorMap* pAh,
+                                               const CUtensorMap* pBm, const CUtensorMap* pBh,
+                                               const GemmArgs& g) {
+  extern __shared__ uint8_t gw_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gw_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ uint64_t full[GW_STAGES], empty[GW_STAGES], set_ready, set_free, drain;
+  __shared__ uint32_t tslot;
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntiles = g.tiles_x * g.tiles_y * g.tiles_z;
+  auto tile_at = [&](int t, int& bx, int& by, int& bz) {
+    bx = t % g.tiles_x;
+    by = (t / g.tiles_x) % g.tiles_y;
+    bz = t / (g.tiles_x * g.tiles_y);
+  };
+  auto kblocks = [&](int bz) {
+    const int kb0 = bz * g.kchunk, ke = min(g.K, kb0 + g.kchunk);
+    return ke > kb0 ? (ke - kb0 + 63) / 64 : 0;
+  };
+  const long long lw = kShort ? wait_limit(g.wait) : kWaitCycles;
+  const int ns = GW_STAGES, sbytes = GW_STAGE_BYTES;
+
+  if (tid == 0) {
+    for (int s = 0; s < GW_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&set_ready, 1);
+    mbar_init(&set_free, kWideEpi);  // one arrival per epilogue warp
+    mbar_init(&drain, 1);
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == kWideMma) {
+    tmem_alloc(&tslot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tslot;
+
+  if (warp == kWideTma && lane == 0) {
+    prefetch_tmap(pAm); prefetch_tmap(pAh); prefetch_tmap(pBm); prefetch_tmap(pBh);
+    int last_parity[GW_STAGES] = {-1, -1};
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x) {
+      int bx, by, bz;
+      tile_at(tile, bx, by, bz);
+      const int m0 = bx * 128, n0 = by * 256, kbeg = bz * g.kchunk, nkb = kblocks(bz);
+      for (int kb = 0; kb < nkb && !abort_flag; ++kb, ++it) {
+        const int s = it % ns, use = it / ns;
+        if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1, lw)) {
+          atomicExch(g.status, 31); abort_flag = 1; break;
+        }
+        uint8_t* st = sm + s * sbytes;  // A m +0, A h +16 KB, B m +32 KB, B h +64 KB
+        mbar_expect_tx(&full[s], sbytes);
+        const int kc = kbeg + kb * 64;
+        if (!g.a_mn) {
+          tma_load_2d(st, pAm, &full[s], kc, m0);
+          tma_load_2d(st + 16384, pAh, &full[s], kc, m0);
+        } else {  // [64 K rows][64 M] boxes, M halves 8 KB apart
+          tma_load_2d(st, pAm, &full[s], m0, kc);
+          tma_load_2d(st + 8192, pAm, &full[s], m0 + 64, kc);
+          tma_load_2d(st + 16384, pAh, &full[s], m0, kc);
+          tma_load_2d(st + 24576, pAh, &full[s], m0 + 64, kc);
+        }
+        if (!g.b_mn) {  // [256 N rows][64 K] boxes
+          tma_load_2d(st + 32768, pBm, &full[s], kc, n0);
+          tma_load_2d(st + 65536, pBh, &full[s], kc, n0);
+        } else {  // [64 K rows][64 N] boxes, four N blocks 8 KB apart
+          for (int q = 0; q < 4; ++q) {
+            tma_load_2d(st + 32768 + 8192 * q, pBm, &full[s], n0 + 64 * q, kc);
+            tma_load_2d(st + 65536 + 8192 * q, pBh, &full[s], n0 + 64 * q, kc);
+          }
+        }
+        last_parity[s] = use & 1;
+      }
+    }
+    for (int s = 0; s < ns; ++s)
+      if (last_parity[s] >= 0) mbar_wait(&full[s], last_parity[s]);
+  } else if (warp == kWideMma) {
+    const uint32_t idesc = idesc_f16(128, 256, false, g.a_mn != 0, g.b_mn != 0);
+    const uint64_t dkm = sdesc_sw128(smem_u32(sm), 16, 1024);
+    const uint64_t dmn = sdesc_sw128(smem_u32(sm), 8192, 1024);
+    const uint64_t da0 = g.a_mn ? dmn : dkm, db0 = g.b_mn ? dmn : dkm;
+    const uint32_t ast = g.a_mn ? 128 : 2, bst = g.b_mn ? 128 : 2;
+    auto fail = [&](int code) {
+      if (lane == 0) { atomicExch(g.status, code); abort_flag = 1; }
+      __syncwarp();
+    };
+    int it = 0, G = 0;  // G: drain groups issued over all tiles
+    bool good = true;
+    for (int tile = blockIdx.x; good && tile < ntiles; tile += gridDim.x) {
+      int bx, by, bz;
+      tile_at(tile, bx, by, bz);
+      const int nkb = kblocks(bz);
+      for (int kb = 0; kb < nkb; ++kb, ++it) {
+        if (__shfl_sync(0xffffffffu, (int)abort_flag, 0)) { good = false; break; }
+        const int s = it % ns;
+        const bool first = (kb % kDrain) == 0;
+        const bool last = (kb % kDrain) == kDrain - 1 || kb == nkb - 1;
+        // one accumulator set: group G starts once the epilogue drained group G - 1
+        if (first && G >= 1 && !mbar_wait_warp(&set_free, (G - 1) & 1, lw)) {
+          fail(34); good = false; break;
+        }
+        if (!mbar_wait_warp(&full[s], (it / ns) & 1, lw)) { fail(32); good = false; break; }
+        tc_fence_after();
+        const uint64_t dam = da0 + s * (GW_STAGE_BYTES >> 4), dah = dam + 1024;
+        const uint64_t dbm = db0 + s * (GW_STAGE_BYTES >> 4) + 2048, dbh = dbm + 2048;
+        const uint32_t t0 = tbase, t1 = tbase + 256;
+        const uint32_t a0 = first ? 0u : 1u;
+        mma_ss_run4(t0, dam, dbm, ast, bst, idesc, a0);
+        mma_ss_run4(t1, dam, dbh, ast, bst, idesc, a0);
+        mma_ss_run4(t1, dah, dbm, ast, bst, idesc, 1u);
+        mma_ss_run4(t1, dah, dbh, ast, bst, idesc, 1u);
+        if (elect_one()) {
+          mma_commit(&empty[s]);
+          if (last) mma_commit(&set_ready);
+        }
+        __syncwarp();
+        if (last) ++G;
+      }
+    }
+    if (elect_one()) mma_commit(&drain);
+    __syncwarp();
+    mbar_wait_warp(&drain, 0);
+  } else if (warp < kWideEpi) {
+    const int quad = warp & 3, qc = warp >> 2;
+    const int r = quad * 32 + lane;
+    const int cb = 64 * qc;
+    const uint32_t lane_off = static_cast<uint32_t>(quad * 32) << 16;
+    int G = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      int bx, by, bz;
+      tile_at(tile, bx, by, bz);
+      const int m0 = bx * 128, n0 = by * 256;
+      const int ngroups = (kblocks(bz) + kDrain - 1) / kDrain;
+      float run[64];
+#pragma unroll
+      for (int c = 0; c < 64; ++c) run[c] = 0.0f;
+      bool ok = true;
+      for (int gi = 0; gi < ngroups; ++gi, ++G) {
+        if (__shfl_sync(0xffffffffu, (int)abort_flag, 0) || !mbar_wait_warp(&set_ready, G & 1, lw)) {
+          ok = false;
+          if (lane == 0 && !abort_flag) { atomicExch(g.status, 33); abort_flag = 1; }
+          __syncwarp();
+          break;
+        }
+        tc_fence_after();
+#pragma unroll
+        for (int c = 0; c < 64; c += 8) {
+          uint32_t a0[8], a1[8];
+          tmem_ld8(tbase + lane_off + cb + c, a0);
+          tmem_ld8(tbase + lane_off + 256 + cb + c, a1);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 8; ++j) run[c + j] += __uint_as_float(a0[j]) + __uint_as_float(a1[j]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&set_free);
+      }
+      ok = ok && !abort_flag;
+      const float scale = g.sc[g.scale_idx];
+      const long row = (long)m0 + r;
+      if (row < g.M) {
+        if (g.transposed) {
+#pragma unroll
+          for (int c = 0; c < 64; ++c) {
+            const int col = n0 + cb + c;
+            if (col < g.Ncols) g.out[(long)col * g.ldo + row] = ok ? run[c] * scale : 0.0f;
+          }
+        } else {
+          float* orow = g.out + (long)bz * g.split_stride + row * g.ldo;
+          if (((g.ldo | g.split_stride) & 3) == 0) {
+#pragma unroll
+            for (int c = 0; c < 64; c += 4) {
+              const int col = n0 + cb + c;
+              if (col + 4 <= g.Ncols) {
+                *reinterpret_cast<float4*>(orow + col) =
+                    ok ? make_float4(run[c] * scale, run[c + 1] * scale, run[c + 2] * scale,
+                                     run[c + 3] * scale)
+                       : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+              } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                  if (col + j < g.Ncols) orow[col + j] = ok ? run[c + j] * scale : 0.0f;
+              }
+            }
+          } else {
+#pragma unroll
+            for (int c = 0; c < 64; ++c) {
+              const int col = n0 + cb + c;
+              if (col < g.Ncols) orow[col] = ok ? run[c] * scale : 0.0f;
+            }
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == kWideMma) tmem_dealloc(tbase, 512);
+}
+
+__global__ void __launch_bounds__(kWideThreads, 1)
+    gemm_wide_kernel(const __grid_constant__ CUtensorMap mAm, const __grid_constant__ CUtensorMap mAh,
+                     const __grid_constant__ CUtensorMap mBm, const __grid_constant__ CUtensorMap mBh,
+                     GemmArgs g) {
+  if (g.wait > 0 && g.wait < kWaitCycles)
+    gemm_wide_body<true>(&mAm, &mAh, &mBm, &mBh, g);
+  else
+    gemm_wide_body<false>(&mAm, &mAh, &mBm, &mBh, g);
+}
+
+// gemm_wide_kernel over tiles (x: 128-row M tiles, y: 256-column N tiles,
+// z: K splits) with at most one CTA per SM.
+void launch_gemm_wide(const CUtensorMap& mAm, const CUtensorMap& mAh, const CUtensorMap& mBm,
+                      const CUtensorMap& mBh, GemmArgs g, dim3 tiles, cudaStream_t s,
+                      long long wait = 0) {
+  g.wait = wait;
+  g.tiles_x = (int)tiles.x;
+  g.tiles_y = (int)tiles.y;
+  g.tiles_z = (int)tiles.z;
+  const long total = (long)tiles.x * tiles.y * tiles.z;
+  const unsigned ctas = (unsigned)std::max<long>(1, std::min<long>(total, sm_count()));
+  gemm_wide_kernel<<<ctas, kWideThreads, GW_SMEM, s>>>(mAm, mAh, mBm, mBh, g);
+}
+
+// ============================================================ T products
+// One 128 x 128 tile of T = f V' o S, S = A B^T over K = the pieces' width
+// (n rounded up to 64): A (rows: the slice's interpolation points) and B
+// (rows: grid points, or every interpolation point for T_C) as per-row FP16
+// pieces (m, h[, l]), K-major, streamed by TMA in 32-wide K blocks with the
+// 64-byte swizzle (one box per operand spans its pieces).  A0 = m.m' and A1 = the cross terms (m.h' + h.m' + h.h'
+// [+ m.l' + l.m']) accumulate in one of two tensor-memory sets, drained
+// every 6 K blocks (192 terms) into FP32 sums held in registers, as in
+// gemm_body.  The epilogue takes the V' tile (FP32, four [128][32] boxes)
+// from shared memory, where it loads it by TMA as soon as the previous
+// tile's T has left shared memory.  Each thread (one row, 64
+// columns) forms V' o S, the energy term V' S^2 and the FP16 hi/lo split of
+// f V' S, writes the split in place of the V' boxes its column half has read,
+// and one thread per half stores the four [128][32] FP16 boxes with TMA and
+// writes the half's energy partial.  V' and T thus cross between HBM and the
+// SM in whole lines, no thread waits on a global load or store, and the two
+// column halves run without synchronising with each other.
+// Warps 0-7: epilogue (warp w: rows 32 (w % 4) .. +31, columns 64 (w / 4)
+// .. +63); warp 8: TMA producer; warp 9: MMA.
+
+struct TprodMaps {
+  CUtensorMap a, b;        // A and B over (K, rows, piece): [piece][128][32] boxes, 64-byte swizzle
+  CUtensorMap v;           // V' FP32 [M][Ncols]: [128][32] boxes, 128-byte swizzle
+  CUtensorMap th, tl;      // T hi / lo FP16 [M][ld]: [128][32] boxes, 64-byte swizzle
+};
+
+struct TprodArgs {
+  int M, Ncols, K;  // rows of A, rows of B (columns of T), K (a multiple of 32)
+  const float* sc;
+  int f_idx;
+  double* epart;    // [2 (by * tiles_x + bx) + column half]: sum V' S^2; nullable
+  int store;        // write T (hi, lo) through the maps th, tl
+  int ld_t;         // columns of T's rows (the maps' extent): boxes past it are not stored
+  int pieces3;      // three pieces per operand (else two)
+  int tiles_x, tiles_y;
+  int* status;
+  long long wait;   // pipeline-wait limit in SM cycles (0: the default)
+};
+
+constexpr int TP_KB = 32;                    // K per block
+constexpr int TP_BOX = 128 * TP_KB * 2;      // one [128][32] FP16 box: 8 KB
+constexpr int TP_RING = 6 * TP_BOX * 3;      // 3 stages of 6 boxes (or 4 stages of 4)
+constexpr int TP_VBUF = 128 * 128 * 4;       // the V' tile, rewritten as T hi / lo
+constexpr int TP_SMEM = TP_RING + TP_VBUF + 1024;
+constexpr int TP_DRAIN = 6;                  // K blocks per accumulator drain (192 terms)
+
+template <bool kShort>
+__device__ __forceinline__ void tprod_body(const TprodMaps& mp, const TprodArgs& g) {
+  extern __shared__ uint8_t tp_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tp_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* vbuf = sm + TP_RING;
+  __shared__ uint64_t full[4], empty[4], set_ready[2], set_free[2], drain, vfull[2];
+  __shared__ uint32_t tslot;
+  __shared__ volatile int abort_flag;
+  __shared__ double ered[kGemmEpi];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntiles = g.tiles_x * g.tiles_y;
+  const int npc = g.pieces3 ? 3 : 2;      // pieces per operand
+  const int ns = g.pieces3 ? 3 : 4;       // stages
+  const int sbytes = 2 * npc * TP_BOX;    // bytes per stage
+  const int nkb = g.K / TP_KB;            // K blocks per tile
+  const int ngroups = (nkb + TP_DRAIN - 1) / TP_DRAIN;
+  const long long lw = kShort ? wait_limit(g.wait) : kWaitCycles;
+
+  if (tid == 0) {
+    for (int s = 0; s < 4; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&set_ready[s], 1);
+      mbar_init(&set_free[s], kGemmEpi);  // one arrival per epilogue warp
+      mbar_init(&vfull[s], 1);
+    }
+    mbar_init(&drain, 1);
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == kGemmMma) {
+    tmem_alloc(&tslot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tslot;
+
+  if (warp == kGemmTma && lane == 0) {
+    prefetch_tmap(&mp.a);
+    prefetch_tmap(&mp.b);
+    prefetch_tmap(&mp.v);
+    int last_parity[4] = {-1, -1, -1, -1};
+    int it = 0;  // K blocks issued by this CTA over all its tiles
+    for (int tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x) {
+      const int m0 = (tile % g.tiles_x) * 128, n0 = (tile / g.tiles_x) * 128;
+      for (int kb = 0; kb < nkb && !abort_flag; ++kb, ++it) {
+        const int s = it % ns, use = it / ns;
+        if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1, lw)) {
+          atomicExch(g.status, 21); abort_flag = 1; break;
+        }
+        uint8_t* st = sm + s * sbytes;  // A pieces at p * 8 KB, B pieces at (npc + p) * 8 KB
+        mbar_expect_tx(&full[s], sbytes);
+        const int kc = kb * TP_KB;
+        tma_load_3d(st, &mp.a, &full[s], kc, m0, 0);  // every piece in one box
+        tma_load_3d(st + npc * TP_BOX, &mp.b, &full[s], kc, n0, 0);
+        last_parity[s] = use & 1;
+      }
+    }
+    for (int s = 0; s < ns; ++s)
+      if (last_parity[s] >= 0) mbar_wait(&full[s], last_parity[s]);
+  } else if (warp == kGemmMma) {
+    const uint32_t idesc = idesc_f16(128, 128, false, false, false);
+    const uint64_t d0 = sdesc_sw64(smem_u32(sm), 16, 512);
+    auto fail = [&](int code) {
+      if (lane == 0) { atomicExch(g.status, code); abort_flag = 1; }
+      __syncwarp();
+    };
+    int it = 0, G0 = 0;
+    bool good = true;
+    for (int tile = blockIdx.x; good && tile < ntiles; tile += gridDim.x) {
+      for (int kb = 0; kb < nkb; ++kb, ++it) {
+        if (__shfl_sync(0xffffffffu, (int)abort_flag, 0)) { good = false; break; }
+        const int s = it % ns, grp = G0 + kb / TP_DRAIN, set = grp & 1;
+        const bool first = (kb % TP_DRAIN) == 0;
+        const bool last = (kb % TP_DRAIN) == TP_DRAIN - 1 || kb == nkb - 1;
+        if (first && grp >= 2 && !mbar_wait_warp(&set_free[set], ((grp >> 1) - 1) & 1, lw)) {
+          fail(24); good = false; break;
+        }
+        if (!mbar_wait_warp(&full[s], (it / ns) & 1, lw)) { fail(22); good = false; break; }
+        tc_fence_after();
+        // descriptor address field in 16-byte units: 512 per 8 KB box, 2 per K step
+        const uint64_t am = d0 + (uint64_t)((s * sbytes) >> 4), ah = am + 512, al = am + 1024;
+        const uint64_t bm = am + 512 * npc, bh = bm + 512, bl = bm + 1024;
+        const uint32_t t0 = tbase + set * 256, t1 = t0 + 128;
+        const uint32_t a0 = first ? 0u : 1u;
+        mma_ss_run2(t0, am, bm, 2, 2, idesc, a0);
+        mma_ss_run2(t1, am, bh, 2, 2, idesc, a0);
+        mma_ss_run2(t1, ah, bm, 2, 2, idesc, 1u);
+        mma_ss_run2(t1, ah, bh, 2, 2, idesc, 1u);
+        if (npc == 3) {
+          mma_ss_run2(t1, am, bl, 2, 2, idesc, 1u);
+          mma_ss_run2(t1, al, bm, 2, 2, idesc, 1u);
+        }
+        if (elect_one()) {
+          mma_commit(&empty[s]);
+          if (last) mma_commit(&set_ready[set]);
+        }
+        __syncwarp();
+      }
+      G0 += ngroups;
+    }
+    if (elect_one()) mma_commit(&drain);
+    __syncwarp();
+    mbar_wait_warp(&drain, 0);
+  } else if (warp < kGemmEpi) {
+    const int quad = warp & 3, half = warp >> 2;
+    const int r = quad * 32 + lane;
+    const int cb = 64 * half;
+    const uint32_t lane_off = static_cast<uint32_t>(quad * 32) << 16;
+    const bool leader = quad == 0 && lane == 0;  // issues the half's V' loads and T stores
+    uint8_t* vb = vbuf + half * 32768;           // V' boxes of columns cb .. cb + 63
+    const float f = g.sc[g.f_idx];
+    auto load_v = [&](int tile) {
+      const int m0 = (tile % g.tiles_x) * 128, n0 = (tile / g.tiles_x) * 128;
+      mbar_expect_tx(&vfull[half], 32768);
+      tma_load_2d(vb, &mp.v, &vfull[half], n0 + cb, m0);
+      tma_load_2d(vb + 16384, &mp.v, &vfull[half], n0 + cb + 32, m0);
+    };
+    if (leader && (int)blockIdx.x < ntiles) load_v(blockIdx.x);
+    int G0 = 0, j = 0, vlost = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
+      const int bx = tile % g.tiles_x, by = tile / g.tiles_x;
+      const int m0 = bx * 128, n0 = by * 128;
+      float run[64];
+#pragma unroll
+      for (int c = 0; c < 64; ++c) run[c] = 0.0f;
+      bool ok = true;
+      for (int gi = 0; gi < ngroups; ++gi) {
+        const int grp = G0 + gi, set = grp & 1;
+        if (__shfl_sync(0xffffffffu, (int)abort_flag, 0) || !mbar_wait_warp(&set_ready[set], (grp >> 1) & 1, lw)) {
+          ok = false;
+          if (lane == 0 && !abort_flag) { atomicExch(g.status, 23); abort_flag = 1; }
+          __syncwarp();
+          break;
+        }
+        tc_fence_after();
+#pragma unroll
+        for (int c = 0; c < 64; c += 16) {
+          uint32_t a0[16], a1[16];
+          tmem_ld16(tbase + lane_off + set * 256 + cb + c, a0);
+          tmem_ld16(tbase + lane_off + set * 256 + 128 + cb + c, a1);
+          tmem_wait_ld();
+#pragma unroll
+          for (int q = 0; q < 16; ++q) run[c + q] += __uint_as_float(a0[q]) + __uint_as_float(a1[q]);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&set_free[set]);
+      }
+      G0 += ngroups;
+      // the V' boxes of this tile (issued when the previous tile's T had been read out)
+      if (!mbar_wait_warp(&vfull[half], j & 1, lw)) {
+        ok = false;
+        vlost = 1;
+        if (lane == 0) { atomicExch(g.status, 25); abort_flag = 1; }
+      }
+      ok = ok && !abort_flag;
+      // row r of the two [128][32] FP32 boxes: 16-byte chunk c sits at c ^ (r % 8)
+      float v[64];
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const float4 x = *reinterpret_cast<const float4*>(vb + b * 16384 + r * 128 + 16 * (c ^ (r & 7)));
+          v[b * 32 + c * 4 + 0] = x.x; v[b * 32 + c * 4 + 1] = x.y;
+          v[b * 32 + c * 4 + 2] = x.z; v[b * 32 + c * 4 + 3] = x.w;
+        }
+      asm volatile("bar.sync %0, 128;" ::"r"(2 + half) : "memory");  // the half's V' is read
+      double esum = 0.0;
+#pragma unroll
+      for (int c0 = 0; c0 < 64; c0 += 8) {
+        uint32_t hw[4], lw4[4];
+        float e = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 8; q += 2) {
+          const float s0 = ok ? run[c0 + q] : 0.0f, s1 = ok ? run[c0 + q + 1] : 0.0f;
+          const float p0 = v[c0 + q] * s0, p1 = v[c0 + q + 1] * s1;
+          e = fmaf(p0, s0, e);
+          e = fmaf(p1, s1, e);
+          const float t0 = p0 * f, t1 = p1 * f;
+          const __half2 h01 = __floats2half2_rn(t0, t1);
+          const float2 b01 = __half22float2(h01);
+          const __half2 l01 = __floats2half2_rn(t0 - b01.x, t1 - b01.y);
+          hw[q / 2] = *reinterpret_cast<const uint32_t*>(&h01);
+          lw4[q / 2] = *reinterpret_cast<const uint32_t*>(&l01);
+        }
+        esum += (double)e;
+        if (g.store) {
+          // box c0 / 32 of the half: hi [128][32] at +0, lo at +8 KB; row r is
+          // 64 B and its 16-byte chunk c sits at c ^ ((r / 2) % 4)
+          uint8_t* bb = vb + (c0 >> 5) * 16384 + r * 64 + 16 * (((c0 & 31) >> 3) ^ ((r >> 1) & 3));
+          *reinterpret_cast<uint4*>(bb) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          *reinterpret_cast<uint4*>(bb + 8192) = make_uint4(lw4[0], lw4[1], lw4[2], lw4[3]);
+        }
+      }
+      if (g.epart) {
+        for (int o = 16; o > 0; o >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, o);
+        if (lane == 0) ered[warp] = esum;  // read by the leader after the barrier below
+      }
+      if (g.store) fence_async_smem();
+      asm volatile("bar.sync %0, 128;" ::"r"(2 + half) : "memory");  // the half's T is written
+      if (leader) {
+        if (g.epart)  // per tile and column half, in a fixed order
+          g.epart[2 * ((long)by * g.tiles_x + bx) + half] =
+              ((ered[4 * half] + ered[4 * half + 1]) + ered[4 * half + 2]) + ered[4 * half + 3];
+        if (g.store) {
+          for (int b = 0; b < 2; ++b) {
+            const int x = n0 + cb + 32 * b;
+            if (x >= g.ld_t) break;
+            tma_store_2d(&mp.th, vb + b * 16384, x, m0);
+            tma_store_2d(&mp.tl, vb + b * 16384 + 8192, x, m0);
+          }
+          bulk_commit();
+          bulk_wait_read();
+        }
+        if (tile + (int)gridDim.x < ntiles) load_v(tile + gridDim.x);
+      }
+    }
+    if (leader) {
+      bulk_wait_all();
+      // a V' load whose wait ran out may still be in flight: let it land
+      if (vlost && j > 0) mbar_wait(&vfull[half], (j - 1) & 1);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == kGemmMma) tmem_dealloc(tbase, 512);
+}
+
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    tprod_kernel(const __grid_constant__ TprodMaps mp, TprodArgs g) {
+  if (g.wait > 0 && g.wait < kWaitCycles)
+    tprod_body<true>(mp, g);
+  else
+    tprod_body<false>(mp, g);
+}
+
+// tprod_kernel over tiles_x x tiles_y tiles with at most one CTA per SM.
+void launch_tprod(const TprodMaps& mp, TprodArgs g, cudaStream_t s, long long wait = 0) {
+  g.wait = wait;
+  const long total = (long)g.tiles_x * g.tiles_y;
+  const unsigned ctas = (unsigned)std::max<long>(1, std::min<long>(total, sm_count()));
+  tprod_kernel<<<ctas, kGemmThreads, TP_SMEM, s>>>(mp, g);
 }
 
 // ============================================================ pair kernel
@@ -2048,15 +2540,35 @@ cudaError_t get_encode() {
   return cudaSuccess;
 }
 
-// 2-D map of a row-major [rows][ld] array, box [box_rows][box_cols], 128-B swizzle.
+// 2-D map of a row-major [rows][ld] array, box [box_rows][box_cols], 128-B
+// swizzle by default; cols > 0 limits the map to the first cols columns of
+// each row (a box reaching past them reads zeros, a store there is dropped).
 cudaError_t make_map(CUtensorMap* m, const void* ptr, CUtensorMapDataType dt, int esize, long rows,
                      long ld, int box_rows, int box_cols,
-                     CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
-  cuuint64_t dims[2] = {static_cast<cuuint64_t>(ld), static_cast<cuuint64_t>(rows)};
+                     CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B, long cols = 0) {
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols > 0 ? cols : ld), static_cast<cuuint64_t>(rows)};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * esize};
   cuuint32_t box[2] = {static_cast<cuuint32_t>(box_cols), static_cast<cuuint32_t>(box_rows)};
   cuuint32_t es[2] = {1, 1};
   CUresult r = g_encode(m, dt, 2, const_cast<void*>(ptr), dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// 3-D map of `pieces` row-major [rows][ld] arrays piece_stride elements apart:
+// a box [pieces][box_rows][box_cols] brings the same tile of every piece.
+cudaError_t make_map3(CUtensorMap* m, const void* ptr, CUtensorMapDataType dt, int esize, long rows,
+                      long ld, int pieces, long piece_stride, int box_rows, int box_cols,
+                      CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(ld), static_cast<cuuint64_t>(rows),
+                        static_cast<cuuint64_t>(pieces)};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld) * esize,
+                           static_cast<cuuint64_t>(piece_stride) * esize};
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(box_cols), static_cast<cuuint32_t>(box_rows),
+                       static_cast<cuuint32_t>(pieces)};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = g_encode(m, dt, 3, const_cast<void*>(ptr), dims, strides, box, es,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
@@ -2117,6 +2629,10 @@ struct MixedState {
   CUtensorMap m_psigA64_m, m_psigA64_h, m_psigA128_m, m_psigA128_h, m_psigA128_l;
   CUtensorMap m_TA_h, m_TA_l, m_TAmn_h, m_TAmn_l, m_TC_h, m_TC_l, m_psi128_l, m_psig128_l,
       m_phi_l, m_CT_l;
+  // The T-product launches (tprod_kernel): T_A = f_AB V o (Psi_g Psi^T) and
+  // T_C = f_C W o (Psi_g Psi_g^T); set up with T_A, T_C (n > 128: at
+  // creation; otherwise with the full-K scratch)
+  TprodMaps tpA, tpC;
   // Full K_{mu nu} (mixed_enqueue_full): scratch allocated on first use
   bool full_ready = false;
   int splitsF = 1, splitsFC = 1, splitsY = 1, kchunkF = 64, kchunkFC = 64, kchunkY = 64;
@@ -2138,6 +2654,8 @@ struct MixedState {
       m_psig128_m, m_psig128_h, m_psig64_m, m_psig64_h, m_VA, m_VB, m_VC, m_phiT_m, m_phiT_h,
       m_M1_m, m_M1_h, m_phigT_m, m_phigT_h, m_D23T_m, m_D23T_h;
 };
+
+cudaError_t make_tprod_maps(MixedState* m);
 
 namespace {
 
@@ -2213,16 +2731,18 @@ Plan make_plan(int64_t Ng, int N, int n, int Naux, int NaT) {
       p.epA = (Ng + 127) / 128;
     }
   } else {
-    // M2 = T_A Psi and M3 = T_C Psi_g: (xa x nt) tiles, K split to about four waves
-    const int t2 = p.xa * p.nt;
+    // M2 = T_A Psi and M3 = T_C Psi_g: xa x (n / 256) wide tiles, K split to
+    // about four waves
+    const int t2 = p.xa * ((n + 255) / 256);
     p.partsA = std::max(1, std::min<int>(608 / t2, (int)((Ng + 4095) / 4096)));
     p.ychunkA = (int)rup((Ng + p.partsA - 1) / p.partsA, 64);
     p.partsA = (int)((Ng + p.ychunkA - 1) / p.ychunkA);
     p.partsC = std::max(1, std::min<int>(304 / t2, (NaT + 1023) / 1024));
     p.ychunkC = (int)rup((NaT + p.partsC - 1) / p.partsC, 64);
     p.partsC = (NaT + p.ychunkC - 1) / p.ychunkC;
-    p.epA = (long)p.xa * ((Ng + 127) / 128);
-    p.epC = (long)p.xa * ((NaT + 127) / 128);
+    // energy partials of the T products: one per tile and column half
+    p.epA = 2L * p.xa * ((Ng + 127) / 128);
+    p.epC = 2L * p.xa * ((NaT + 127) / 128);
     p.partsA_max = p.partsA;
   }
   // line GEMMs: (N / 128) x (n / 128) tiles x K splits of >= 1024; split
@@ -2416,6 +2936,10 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int NaT, int g0, int g1, cons
     e = cudaFuncSetAttribute(energy_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, PairCfg<128>::SMEM);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, G_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tprod_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TP_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gemm_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, GW_SMEM);
   if (e != cudaSuccess) return e;
 
   MixedState* m = new MixedState();
@@ -2443,16 +2967,26 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int NaT, int g0, int g1, cons
   if (p.large) {
     MX(m->TA_h, na * p.Ng8); MX(m->TA_l, na * p.Ng8);
     MX(m->TC_h, na * p.NaT8); MX(m->TC_l, na * p.NaT8);
-    MX(m->psi_l, ng * p.np); MX(m->psigA_l, nat * p.np);
-    m->psig_l = m->psigA_l + (size_t)g0 * p.np;
   }
   // third pieces of Phi' and Q for every n: with two pieces the orbital split
   // alone moves E_x by up to ~1e-6 Ha on the 64-centre cell
   MX(m->phi_l, ng * p.Np); MX(m->CT_l, (size_t)n * p.Np);
   MX(m->idx, nat);
   MX(m->CT_m, (size_t)n * p.Np); MX(m->CT_h, (size_t)n * p.Np); MX(m->CT64, (size_t)n * p.Np);
-  MX(m->psi_m, ng * p.np); MX(m->psi_h, ng * p.np);
-  MX(m->psigA_m, nat * p.np); MX(m->psigA_h, nat * p.np);
+  // the pieces m, h[, l] of Psi and of Psi at all NaT points, each set in one
+  // block with a fixed piece stride (one TMA box can span the pieces)
+  {
+    const size_t npc = p.large ? 3 : 2, ps = ng * p.np, pa = nat * p.np;
+    MX(m->psi_m, npc * ps);
+    m->psi_h = m->psi_m + ps;
+    MX(m->psigA_m, npc * pa);
+    m->psigA_h = m->psigA_m + pa;
+    if (p.large) {
+      m->psi_l = m->psi_m + 2 * ps;
+      m->psigA_l = m->psigA_m + 2 * pa;
+      m->psig_l = m->psigA_l + (size_t)g0 * p.np;
+    }
+  }
   m->psig_m = m->psigA_m + (size_t)g0 * p.np;  // the slice's rows
   m->psig_h = m->psigA_h + (size_t)g0 * p.np;
   MX(m->M2p, (size_t)p.partsA_max * na * n); MX(m->M3p, (size_t)p.partsC * na * n);
@@ -2619,6 +3153,7 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int NaT, int g0, int g1, cons
     if (m->V32) e = make_map(&m->m_VA, m->V32, F32, 4, (long)na, p.Ng4, 128, 32);
     if (e == cudaSuccess && m->VT32) e = make_map(&m->m_VB, m->VT32, F32, 4, (long)ng, p.Na4, 128, 32);
     if (e == cudaSuccess) e = make_map(&m->m_VC, m->W32, F32, 4, (long)na, p.NaT4, 128, 32);
+    if (e == cudaSuccess && p.large) e = make_tprod_maps(m);
     if (e != cudaSuccess) return fin(e);
   }
   if (!p.large) {
@@ -2673,7 +3208,7 @@ void mixed_destroy(MixedState* m) {
 }
 
 cudaError_t mixed_enqueue_pre(MixedState* m, const double* C, cudaStream_t s, const StepHook& hook) {
-  const long ng = m->Ng, na = m->Naux;
+  const long ng = m->Ng;
   const int N = m->N, n = m->n, np = m->np;
   cudaError_t e;
   // ---- step 1: Psi = Phi C
@@ -2731,24 +3266,45 @@ cudaError_t mixed_enqueue_pre(MixedState* m, const double* C, cudaStream_t s, co
 // for n > 128, two for n <= 128): T = f V' o S and f W' o S as hi/lo FP16
 // when `store`, and the energy sums sum V' o S^2, sum W' o S^2 when `energy`
 // (n > 128 only: the per-tile sums fill EpA / EpC).
+// Tensor maps of the two T-product launches: A = the slice's Psi_g pieces,
+// B = Psi (T_A) or the pieces at all NaT points (T_C), in [128][32] boxes with
+// the 64-byte swizzle; V and W limited to their N_g and NaT columns (the
+// padding of a last tile reads zeros, so T is zero there); T_A and T_C hi/lo
+// as store targets over their padded rows.
+cudaError_t make_tprod_maps(MixedState* m) {
+  const auto F16 = CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  const auto F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const auto S64 = CU_TENSOR_MAP_SWIZZLE_64B;
+  const long ng = m->Ng, na = m->Naux, nat = m->NaT, np = m->np;
+  const int npc = m->large ? 3 : 2;  // pieces; psig is a view of psigA: the same piece stride
+  cudaError_t e = make_map3(&m->tpA.a, m->psig_m, F16, 2, na, np, npc, nat * np, 128, 32, S64);
+  if (e == cudaSuccess) e = make_map3(&m->tpA.b, m->psi_m, F16, 2, ng, np, npc, ng * np, 128, 32, S64);
+  if (e == cudaSuccess) e = make_map3(&m->tpC.b, m->psigA_m, F16, 2, nat, np, npc, nat * np, 128, 32, S64);
+  m->tpC.a = m->tpA.a;
+  if (e == cudaSuccess)
+    e = make_map(&m->tpA.v, m->V32, F32, 4, na, m->Ng4, 128, 32, CU_TENSOR_MAP_SWIZZLE_128B, ng);
+  if (e == cudaSuccess)
+    e = make_map(&m->tpC.v, m->W32, F32, 4, na, m->NaT4, 128, 32, CU_TENSOR_MAP_SWIZZLE_128B, nat);
+  if (e == cudaSuccess) e = make_map(&m->tpA.th, m->TA_h, F16, 2, na, m->Ng8, 128, 32, S64);
+  if (e == cudaSuccess) e = make_map(&m->tpA.tl, m->TA_l, F16, 2, na, m->Ng8, 128, 32, S64);
+  if (e == cudaSuccess) e = make_map(&m->tpC.th, m->TC_h, F16, 2, na, m->NaT8, 128, 32, S64);
+  if (e == cudaSuccess) e = make_map(&m->tpC.tl, m->TC_l, F16, 2, na, m->NaT8, 128, 32, S64);
+  return e;
+}
+
 void enqueue_t_products(MixedState* m, cudaStream_t s, bool store, bool energy) {
   const long ng = m->Ng, na = m->Naux;
-  const bool p3 = m->large;
-  GemmArgs t{};
-  t.M = (int)na; t.Ncols = (int)ng; t.K = m->np; t.kchunk = m->np; t.sc = m->sc;
-  t.status = m->status; t.tv = m->V32; t.ldv = m->Ng4; t.f_idx = SC_F_AB;
-  t.th = store ? m->TA_h : nullptr; t.tl = store ? m->TA_l : nullptr;
-  t.ld_t = m->Ng8; t.epart = energy ? m->EpA : nullptr; t.pieces3 = p3 ? 1 : 0;
-  launch_gemm(m->m_psig128_m, m->m_psig128_h, m->m_psi128_m, m->m_psi128_h,
-              p3 ? m->m_psig128_l : m->m_psig128_m, p3 ? m->m_psi128_l : m->m_psi128_m, t,
-              dim3((unsigned)m->xa, (unsigned)((ng + 127) / 128), 1), s, m->wait_cycles);
-  GemmArgs tc = t;  // rows: the slice's points; columns: all NaT points
-  tc.Ncols = m->NaT; tc.tv = m->W32; tc.ldv = m->NaT4; tc.f_idx = SC_F_C;
-  tc.th = store ? m->TC_h : nullptr; tc.tl = store ? m->TC_l : nullptr;
-  tc.ld_t = m->NaT8; tc.epart = energy ? m->EpC : nullptr;
-  launch_gemm(m->m_psig128_m, m->m_psig128_h, m->m_psigA128_m, m->m_psigA128_h,
-              p3 ? m->m_psig128_l : m->m_psig128_m, p3 ? m->m_psigA128_l : m->m_psigA128_m, tc,
-              dim3((unsigned)m->xa, (unsigned)((m->NaT + 127) / 128), 1), s, m->wait_cycles);
+  TprodArgs t{};
+  t.M = (int)na; t.Ncols = (int)ng; t.K = m->np; t.sc = m->sc; t.f_idx = SC_F_AB;
+  t.epart = energy ? m->EpA : nullptr; t.store = store ? 1 : 0; t.pieces3 = m->large ? 1 : 0;
+  t.ld_t = (int)m->Ng8;
+  t.tiles_x = m->xa; t.tiles_y = (int)((ng + 127) / 128); t.status = m->status;
+  launch_tprod(m->tpA, t, s, m->wait_cycles);
+  TprodArgs tc = t;  // rows: the slice's points; columns: all NaT points
+  tc.Ncols = m->NaT; tc.f_idx = SC_F_C; tc.epart = energy ? m->EpC : nullptr;
+  tc.ld_t = (int)m->NaT8;
+  tc.tiles_y = (m->NaT + 127) / 128;
+  launch_tprod(m->tpC, tc, s, m->wait_cycles);
   count_launch(2);
 }
 
@@ -2792,6 +3348,7 @@ cudaError_t mixed_full_prepare(MixedState* m) {
     if (e == cudaSuccess) e = make_map(&m->m_TA_l, m->TA_l, F16, 2, na, m->Ng8, 128, 64);
     if (e == cudaSuccess) e = make_map(&m->m_TC_h, m->TC_h, F16, 2, na, m->Na8, 128, 64);
     if (e == cudaSuccess) e = make_map(&m->m_TC_l, m->TC_l, F16, 2, na, m->Na8, 128, 64);
+    if (e == cudaSuccess) e = make_tprod_maps(m);
     if (e != cudaSuccess) return e;
   }
   e = make_map(&m->m_DAT_m, m->DAT_m, F16, 2, N, m->Na8, 128, 64);
@@ -2876,7 +3433,7 @@ cudaError_t mixed_enqueue_energy(MixedState* m, const double* C, double* Ex, cud
   if (e != cudaSuccess) return e;
   hook(1, 0);
   hook(7, 1);
-  final_ex_kernel<<<1, 256, 0, s>>>(m->EpA, (int)m->epA, m->EpC, (int)m->epC, m->sc, m->dV, Ex);
+  final_ex_kernel<<<1, 1024, 0, s>>>(m->EpA, (int)m->epA, m->EpC, (int)m->epC, m->sc, m->dV, Ex);
   count_launch();
   e = cudaGetLastError();
   hook(7, 0);
@@ -2898,18 +3455,20 @@ cudaError_t mixed_enqueue_pair(MixedState* m, cudaStream_t s, const StepHook& ho
     g2.M = (int)na; g2.Ncols = n; g2.K = (int)ng; g2.kchunk = m->ychunkA; g2.out = m->M2p;
     g2.ldo = n; g2.split_stride = na * n; g2.sc = m->sc; g2.scale_idx = SC_OUT_AB;
     g2.status = m->status; g2.b_mn = 1;
-    launch_gemm(m->m_TA_h, m->m_TA_l, m->m_psi64_m, m->m_psi64_h, m->m_TA_h, m->m_psi64_m, g2,
-                dim3((unsigned)m->xa, (unsigned)m->nt, (unsigned)m->partsA), s, m->wait_cycles);
+    // (128 x 256 output tiles: half the operand bytes per MMA of 128 x 128 ones)
+    const unsigned ntw = (unsigned)((n + 255) / 256);
+    launch_gemm_wide(m->m_TA_h, m->m_TA_l, m->m_psi64_m, m->m_psi64_h, g2,
+                     dim3((unsigned)m->xa, ntw, (unsigned)m->partsA), s, m->wait_cycles);
     GemmArgs g3 = g2;
     g3.K = m->NaT; g3.kchunk = m->ychunkC; g3.out = m->M3p; g3.scale_idx = SC_OUT_C;
-    launch_gemm(m->m_TC_h, m->m_TC_l, m->m_psigA64_m, m->m_psigA64_h, m->m_TC_h, m->m_psigA64_m, g3,
-                dim3((unsigned)m->xa, (unsigned)m->nt, (unsigned)m->partsC), s, m->wait_cycles);
+    launch_gemm_wide(m->m_TC_h, m->m_TC_l, m->m_psigA64_m, m->m_psigA64_h, g3,
+                     dim3((unsigned)m->xa, ntw, (unsigned)m->partsC), s, m->wait_cycles);
     GemmArgs g1{};
     g1.M = (int)ng; g1.Ncols = n; g1.K = (int)na; g1.kchunk = (int)rup(na, 64); g1.out = m->M1;
     g1.ldo = m->Ng4; g1.sc = m->sc; g1.scale_idx = SC_OUT_AB; g1.status = m->status;
     g1.a_mn = 1; g1.b_mn = 1; g1.transposed = 1;
-    launch_gemm(m->m_TAmn_h, m->m_TAmn_l, m->m_psig64_m, m->m_psig64_h, m->m_TAmn_h, m->m_psig64_m,
-                g1, dim3((unsigned)((ng + 127) / 128), (unsigned)m->nt, 1), s, m->wait_cycles);
+    launch_gemm_wide(m->m_TAmn_h, m->m_TAmn_l, m->m_psig64_m, m->m_psig64_h, g1,
+                     dim3((unsigned)((ng + 127) / 128), ntw, 1), s, m->wait_cycles);
     count_launch(3);
   } else if (m->fused) {
     // M1 and M2 from one pass over V^T (M2 reduced into the copies), and M3
@@ -2971,7 +3530,7 @@ cudaError_t mixed_enqueue_post(MixedState* m, double* K, double* Ex, cudaStream_
   hook(7, 1);
   final_k_kernel<<<blocks_for((long)N * n), 256, 0, s>>>(m->L1p, m->splitsL1, m->L23p,
                                                          m->splitsL23, (long)N * n, m->dV, K);
-  final_ex_kernel<<<1, 256, 0, s>>>(m->EpA, (int)m->epA, m->EpC, (int)m->epC, m->sc, m->dV, Ex);
+  final_ex_kernel<<<1, 1024, 0, s>>>(m->EpA, (int)m->epA, m->EpC, (int)m->epC, m->sc, m->dV, Ex);
   count_launch(2);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -217,3 +217,31 @@ def test_config2_scf_steps(xk):
     finally:
         hf.release()
         h.release()
+
+
+@pytest.mark.slow
+def test_config2_n256(xk):
+    """The n > 128 path (stored T = f V o P as FP16 hi/lo, three tensor-core
+    GEMMs, three-piece orbitals) at a full-size grid: the 64-centre cell
+    (N_g = 60^3, N_aux = 4000) with n = 256, against the FP64 path on the same
+    tables (the FP64 path is held to the oracle at 1e-8 Ha on these cells):
+    |dE_x| <= 1e-6 Ha, max|dK| <= 1e-6, and the per-build error estimate."""
+    from cellgen.cells import draw_coefficients
+    c = load_cell(config_spec(2))
+    C = draw_coefficients(c.S, 256, 2256)  # 256 S-orthonormal columns on the same tables
+    hf = xk.Handle(c.phi, c.idx, c.V, c.W, c.dV, 256, mode="fp64")
+    h = xk.Handle(c.phi, c.idx, c.V, c.W, c.dV, 256, mode="f16x3")
+    try:
+        K0, E0 = hf.build(C)
+        K, E = h.build(C)
+        est = h.error_estimate()
+        Ee = h.energy(C)
+        K2, E2 = h.build(C)
+    finally:
+        hf.release()
+        h.release()
+    assert abs(E - E0) <= TOL_E, (E, E0)
+    assert np.max(np.abs(K - K0)) <= TOL_K, np.max(np.abs(K - K0))
+    assert Ee == E
+    assert np.array_equal(K, K2) and E == E2
+    assert abs(est - abs(E + float(np.sum(K * C)))) <= 1e-10
