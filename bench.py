@@ -91,6 +91,16 @@ def peaks():
     return FALLBACK_PEAKS, "fallback"
 
 
+def large_pair_issued(n, Ng, Na):
+    """Split MMA FLOPs issued by the n > 128 pair step: the T products (six
+    piece products of K = npad), then M2 = T_A Psi, M3 = T_C Psi_g and
+    M1^T = T_A^T Psi_g (four products each, N padded to 256-column tiles)."""
+    npad = -(-n // 64) * 64
+    nw = -(-n // 256) * 256
+    return (6 * 2.0 * Na * (Ng + Na) * npad
+            + 4 * 2.0 * Na * Ng * nw + 4 * 2.0 * Na * Na * nw + 4 * 2.0 * Ng * Na * nw)
+
+
 def step_flops(N, n, Ng, Na):
     """Algorithmic FLOPs of each build step (the contraction counts of the
     steps listed in include/xk.h); the pair kernel counts P once."""
@@ -402,6 +412,105 @@ def batch_and_mixed_serving(xk, cell64, count, seed=4000):
     return out
 
 
+def scf_runs_queued(xk, cell64, count=48, builds=6, seed=4800, budget_runs=12):
+    """Config-5 shaped serving with queued admission: `count` SCF runs drawn
+    with the seed from {8, 27, 64} centres arrive as a Poisson process; each
+    run is admitted by xk_setup_queued against an HBM budget that holds about
+    `budget_runs` runs of the mix (XK_HBM_BUDGET_BYTES over what is already
+    admitted), does `builds` builds of its own pseudo-SCF sequence (xk_build,
+    one thread per run, so builds of different runs overlap on the device) and
+    releases its tables, which admits the next waiting run.
+    Arrival rates 0.25, 0.5 and 1.0 x the budget's capacity (budget_runs
+    64-centre runs live at a time, each as long as one alone takes).  Reports
+    admission waits and build latencies (request to K on the host)."""
+    import threading
+    rng = np.random.default_rng(seed)
+    sizes = rng.choice([8, 27, 64], size=count)
+    cells = {8: load_cell(config_spec(4, k=2)), 27: load_cell(config_spec(4, k=3)), 64: cell64}
+    seqs = [pseudo_scf_sequence(cells[int(z)].S, cells[int(z)].C, builds, 6000 + i)
+            for i, z in enumerate(sizes)]
+    fp = {z: xk.footprint(c.Ng, c.N, c.n, c.Naux, "f16x3") for z, c in cells.items()}
+    mean_fp = float(np.mean([fp[int(z)] for z in sizes]))
+    # one 64-centre run alone (set-up, builds, release): the capacity of the
+    # budget is budget_runs such runs live at a time
+    c = cells[64]
+    t0 = time.perf_counter()
+    h = xk.Handle(c.phi, c.idx, c.V, c.W, c.dV, c.n, mode="f16x3")
+    for k in range(builds):
+        h.build(c.C)
+    h.release()
+    run_s = time.perf_counter() - t0
+    base, _ = xk.admit_state()
+    budget = int(budget_runs * mean_fp)
+    sustain = budget_runs / run_s  # runs/s at which the budget is full on average
+    old = os.environ.get("XK_HBM_BUDGET_BYTES")
+    os.environ["XK_HBM_BUDGET_BYTES"] = str(base + budget)
+    out = {"runs": int(count), "sizes": {str(z): int(np.sum(sizes == z)) for z in (8, 27, 64)},
+           "builds_per_run": builds, "budget_bytes": budget, "run_alone_s_64": run_s,
+           "budget_in_runs_of_the_mix": budget_runs, "rates": []}
+    try:
+        for frac in (0.25, 0.5, 1.0):
+            rate = frac * sustain
+            arrivals = np.cumsum(rng.exponential(1.0 / rate, size=count))
+            waits, lats, errs = [], [], []
+            lock = threading.Lock()
+            t_start = time.perf_counter()
+
+            def run(i):
+                z = int(sizes[i])
+                cc = cells[z]
+                delay = arrivals[i] - (time.perf_counter() - t_start)
+                if delay > 0:
+                    time.sleep(delay)
+                ta = time.perf_counter()
+                try:
+                    hh = xk.Handle(cc.phi, cc.idx, cc.V, cc.W, cc.dV, cc.n, mode="f16x3",
+                                   queue_timeout_ms=120000.0)
+                except xk.XKError as e:
+                    with lock:
+                        errs.append(str(e))
+                    return
+                tw = time.perf_counter() - ta
+                my = []
+                try:
+                    for k in range(builds):
+                        tr = time.perf_counter()
+                        hh.build(seqs[i][k])
+                        my.append(1e3 * (time.perf_counter() - tr))
+                finally:
+                    hh.release()
+                with lock:
+                    waits.append(1e3 * tw)
+                    lats.extend(my)
+
+            ths = [threading.Thread(target=run, args=(i,)) for i in range(count)]
+            for t in ths:
+                t.start()
+            for t in ths:
+                t.join()
+            total = time.perf_counter() - t_start
+            lats = np.array(lats)
+            waits = np.array(waits)
+            out["rates"].append({
+                "run_arrival_rate_per_s": rate, "x_sustained": frac,
+                "admission_wait_ms": {"p50": float(np.percentile(waits, 50)),
+                                      "p99": float(np.percentile(waits, 99)),
+                                      "max": float(waits.max())} if waits.size else None,
+                "build_latency_ms": {"p50": float(np.percentile(lats, 50)),
+                                     "p99": float(np.percentile(lats, 99))} if lats.size else None,
+                "builds_per_s": float(lats.size / total), "seconds": total,
+                "errors": errs[:3]})
+    finally:
+        if old is None:
+            del os.environ["XK_HBM_BUDGET_BYTES"]
+        else:
+            os.environ["XK_HBM_BUDGET_BYTES"] = old
+    out["note"] = ("xk_setup_queued admission (arrival order, woken by xk_release), one thread "
+                   "per run doing blocking xk_build calls; 125- and 216-centre members left out "
+                   "(host generation of their tables takes minutes)")
+    return out
+
+
 def gpu_points(xk, cell):
     """The two-stage point selection of Sec. IV.C with the pivoting on the GPU
     (xk_isdf_points): per-atom candidates from each Voronoi cell of the grid,
@@ -485,6 +594,15 @@ def run_config3(args):
             "fp64_path": {"s_per_build": t_fp64, "dE_x_vs_fp64": abs(E - E64),
                           "max_dK_vs_fp64": float(np.max(np.abs(K - K64))), "E_x_fp64": E64},
             "E_x": E}
+    pk, pk_src = peaks()
+    pair_ms = st["pair"][0] / max(1, st["pair"][1])
+    issued = large_pair_issued(n, Ng, Na)
+    line["pair_roofline"] = {
+        "bound": "tensor", "pair_ms": pair_ms,
+        "issued_tensor_tflops": issued / (pair_ms * 1e-3) / 1e12,
+        "issued_frac": issued / (pair_ms * 1e-3) / 1e12 / pk.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]),
+        "algorithmic_tflops": 6.0 * Na * Ng * n / (pair_ms * 1e-3) / 1e12,
+        "peak_source": f"dense bf16/fp16 tensor rate ({pk_src})"}
     if not args.no_cpu_baseline:
         t0 = time.perf_counter()
         E0 = oracle.exx_energy_direct(cell.phi, cell.idx, V, W, C_last, cell.dV)
@@ -652,6 +770,8 @@ def main():
     mixed = None
     if mode != "fp64" and args.batch > 0 and world == 1:
         mixed = batch_and_mixed_serving(xk, cell, args.batch)
+        if not args.no_serve:
+            mixed["scf_runs_queued"] = scf_runs_queued(xk, cell)
 
     fp64 = None
     if mode != "fp64" and not args.no_fp64:
@@ -708,6 +828,10 @@ def main():
                 issued = 10 * 2.0 * Na * Ng * npad + 7 * 2.0 * Na * Na * npad
                 kname = ("pair kernel (fused role: S = Psi Psi_g^T once, V^T o S, M1 and M2 "
                          "from one pass over V; role C in the same launch)")
+            elif n > 128:
+                issued = large_pair_issued(n, Ng, Na)
+                kname = ("pair step (n > 128): T products (tprod_kernel) and the three "
+                         "back-contractions on 128 x 256 tiles (gemm_wide_kernel)")
             else:
                 # roles A and B each form S (4 passes) and one product (3 passes)
                 issued = 7 * 2.0 * 2 * Na * Ng * npad + 7 * 2.0 * Na * Na * npad
@@ -729,10 +853,11 @@ def main():
                     # DRAM bytes of the pair launch: dram__bytes_read + write of one ncu
                     # capture of the same kernel on the 27-centre cell with n = 128,
                     # scaled to this cell by its pair count (the traffic is per pair)
-                    "traffic": pair_bytes * (Na * Ng * (1.0 if npad == 128 else 2.0)
-                                             + float(Na) * Na),
-                    "traffic_source": "ncu capture of the pair kernel on the 27-centre cell "
-                                      "(n = 128), scaled by pair count"}
+                    "traffic": (pair_bytes * (Na * Ng * (1.0 if npad == 128 else 2.0)
+                                              + float(Na) * Na) if n <= 128 else None),
+                    "traffic_source": ("ncu capture of the pair kernel on the 27-centre cell "
+                                       "(n = 128), scaled by pair count" if n <= 128 else
+                                       "not captured for this n")}
         roof["frac"] = roof["achieved"] / roof["peak"]
         roof["ms_per_build"] = dom_ms
         # a sharded job completes one build per step across all ranks (strong

@@ -18,7 +18,8 @@
  * computed once per geometry by the caller (Eq. rpsPot, Eq. thcpot).
  *
  * Entry points: set-up and release (xk_footprint, xk_setup, xk_setup_shard, xk_setup_isdf,
- * xk_isdf_points, xk_tables, xk_release); builds (xk_build, xk_build_device,
+ * xk_isdf_points, xk_tables, xk_release); admission (xk_setup_queued,
+ * xk_admit_reserve, xk_admit_release, xk_admit_state); builds (xk_build, xk_build_device,
  * xk_ace); serving (xk_submit, xk_poll) and batches (xk_batch_create,
  * xk_batch_build, xk_batch_release); other products on the same tables
  * (xk_energy, xk_energy_device, xk_build_full, xk_coulomb,
@@ -131,6 +132,50 @@ int xk_setup_shard(int64_t Ng, int32_t N, int32_t n, int32_t Naux, int32_t g0, i
                    const double* basis_on_points, const int32_t* interp_idx,
                    const double* V_rows, const double* W_rows, double dV, int mode,
                    xk_handle** out);
+
+/*
+ * Queued admission for serving many SCF runs on one device (each run holds
+ * its tables for its lifetime; the paper's SCF loop, Sec. IV.F).  Every
+ * handle's footprint (xk_footprint) counts against an admission budget: the
+ * device's free memory less a 1 GiB reserve and, when the environment
+ * variable XK_HBM_BUDGET_BYTES is set, that many bytes less the footprints of
+ * the live handles and reservations (checked first, with no device call).
+ * xk_setup and the other set-ups refuse a footprint above the budget at once
+ * (XK_ENOMEM).  xk_setup_queued instead waits: requests queue in arrival
+ * order, the oldest is admitted as soon as its footprint fits (xk_release and
+ * xk_admit_release wake the queue; device memory freed elsewhere is seen
+ * within 50 ms), later ones wait behind it, and a request still waiting after
+ * timeout_ms milliseconds leaves the queue with XK_ETIMEDOUT.  Arguments
+ * otherwise as xk_setup; the calling thread blocks while it waits.
+ * Errors: as xk_setup; XK_EINVAL for a negative or non-finite timeout_ms;
+ * XK_ENOMEM at once for a footprint above XK_HBM_BUDGET_BYTES itself;
+ * XK_ETIMEDOUT when not admitted in time.
+ */
+int xk_setup_queued(int64_t Ng, int32_t N, int32_t n, int32_t Naux,
+                    const double* basis_on_points, const int32_t* interp_idx,
+                    const double* V_aux, const double* W_aux, double dV, int mode,
+                    double timeout_ms, xk_handle** out);
+
+/*
+ * A reservation of `bytes` against the same admission budget (host
+ * bookkeeping, no device memory): for memory the caller allocates itself
+ * next to the handles.  timeout_ms < 0 admits now or fails with XK_ENOMEM;
+ * otherwise the request queues with the set-ups as in xk_setup_queued.
+ * Without XK_HBM_BUDGET_BYTES the budget is the current device's free memory
+ * less 1 GiB and less the live reservations.  *token identifies the
+ * reservation for xk_admit_release, which returns its bytes and wakes the
+ * queue.  Errors: XK_EINVAL (NULL token, non-finite timeout, unknown token),
+ * XK_ENOMEM, XK_ETIMEDOUT, XK_ECUDA (device query).
+ */
+int xk_admit_reserve(uint64_t bytes, double timeout_ms, uint64_t* token);
+int xk_admit_release(uint64_t token);
+
+/*
+ * Bytes currently admitted (live handles, their extra buffers and the
+ * reservations) and the number of requests waiting in the admission queue.
+ * Errors: XK_EINVAL (NULL argument).
+ */
+int xk_admit_state(uint64_t* admitted_bytes, uint32_t* waiting);
 
 /*
  * The same set-up with the ISDF tables formed on the device in FP64 from the

@@ -9,6 +9,9 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <cstdlib>
+#include <deque>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -64,8 +67,115 @@ struct Slot {
   bool has_deadline = false;
 };
 
-size_t g_admitted = 0;    // bytes held by live handles (all devices)
+size_t g_admitted = 0;    // bytes held by live handles and reservations (all devices)
 std::mutex g_admit_mu;
+
+// Queued admission: a request that does not fit waits, in arrival order,
+// until the bytes it needs are free; releasing a handle or a reservation
+// wakes the waiters.  Reservations (xk_admit_reserve) are host bookkeeping
+// only: they count against the budget until released.
+std::condition_variable g_admit_cv;
+std::deque<uint64_t> g_admit_queue;                   // waiting requests, oldest first
+uint64_t g_admit_seq = 0;                             // ids of requests and reservation tokens
+std::unordered_map<uint64_t, size_t> g_reservations;  // token -> bytes
+size_t g_reserved = 0;                                // bytes of live reservations
+
+// Bytes the budget admits now (g_admit_mu held): XK_HBM_BUDGET_BYTES less
+// everything admitted, checked first and without any device call; then, if
+// `device`, the current device's free memory less 1 GiB and less the
+// reservations (which hold no device memory of their own).
+int admit_left(bool device, size_t* left, bool* env_short) {
+  *left = SIZE_MAX;
+  *env_short = false;
+  if (const char* env = std::getenv("XK_HBM_BUDGET_BYTES")) {
+    const size_t cap = (size_t)std::strtoull(env, nullptr, 10);
+    *left = cap > g_admitted ? cap - g_admitted : 0;
+    *env_short = true;
+  }
+  if (device) {
+    size_t freeb = 0, totalb = 0;
+    cudaError_t e = cudaMemGetInfo(&freeb, &totalb);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemGetInfo");
+    const size_t reserve = (size_t)1 << 30;
+    size_t dev = freeb > reserve ? freeb - reserve : 0;
+    dev = dev > g_reserved ? dev - g_reserved : 0;
+    if (dev < *left) {
+      *left = dev;
+      *env_short = false;
+    }
+  }
+  return XK_OK;
+}
+
+// Admits `bytes` (adds them to g_admitted) or fails.  timeout_ms < 0: now or
+// XK_ENOMEM.  Otherwise the request queues behind earlier ones and waits up to
+// timeout_ms for the bytes (re-checking the device every 50 ms, since other
+// processes free memory without waking us): XK_ETIMEDOUT when the wait runs
+// out.  A request above XK_HBM_BUDGET_BYTES itself fails at once.
+int admit_bytes(size_t bytes, double timeout_ms, bool device, const char* who) {
+  std::unique_lock<std::mutex> lk(g_admit_mu);
+  if (const char* env = std::getenv("XK_HBM_BUDGET_BYTES")) {
+    const size_t cap = (size_t)std::strtoull(env, nullptr, 10);
+    if (bytes > cap)
+      return fail(XK_ENOMEM, std::string(who) + ": footprint " + std::to_string(bytes) +
+                                 " bytes exceeds XK_HBM_BUDGET_BYTES (" + std::to_string(cap) +
+                                 " bytes)");
+  }
+  size_t left = 0;
+  bool env_short = false;
+  if (timeout_ms < 0.0) {
+    // the caller's budget first, before any device call
+    int rc = admit_left(false, &left, &env_short);
+    if (rc == XK_OK && bytes > left)
+      return fail(XK_ENOMEM, std::string(who) + ": footprint " + std::to_string(bytes) +
+                                 " bytes exceeds XK_HBM_BUDGET_BYTES less the live handles (" +
+                                 std::to_string(left) + " bytes)");
+    rc = admit_left(device, &left, &env_short);
+    if (rc != XK_OK) return rc;
+    if (bytes > left)
+      return fail(XK_ENOMEM, std::string(who) + ": footprint " + std::to_string(bytes) +
+                                 " bytes exceeds the admission budget " + std::to_string(left));
+    g_admitted += bytes;
+    return XK_OK;
+  }
+  const uint64_t id = ++g_admit_seq;
+  g_admit_queue.push_back(id);
+  const auto deadline = std::chrono::steady_clock::now() +
+                        std::chrono::microseconds((long long)(timeout_ms * 1000.0));
+  auto leave = [&]() {
+    for (auto it = g_admit_queue.begin(); it != g_admit_queue.end(); ++it)
+      if (*it == id) { g_admit_queue.erase(it); break; }
+    g_admit_cv.notify_all();
+  };
+  for (;;) {
+    if (g_admit_queue.front() == id) {
+      int rc = admit_left(false, &left, &env_short);
+      if (rc == XK_OK && bytes <= left) rc = admit_left(device, &left, &env_short);
+      if (rc != XK_OK) { leave(); return rc; }
+      if (bytes <= left) {
+        g_admit_queue.pop_front();
+        g_admitted += bytes;
+        g_admit_cv.notify_all();  // the next in line may fit too
+        return XK_OK;
+      }
+    }
+    const auto now = std::chrono::steady_clock::now();
+    if (now >= deadline) {
+      leave();
+      return fail(XK_ETIMEDOUT, std::string(who) + ": " + std::to_string(bytes) +
+                                    " bytes not admitted within the timeout");
+    }
+    g_admit_cv.wait_for(lk, std::min<std::chrono::steady_clock::duration>(
+                                deadline - now, std::chrono::milliseconds(50)));
+  }
+}
+
+// Returns bytes to the budget and wakes the waiters.
+void unadmit_bytes(size_t bytes) {
+  std::lock_guard<std::mutex> lk(g_admit_mu);
+  g_admitted -= std::min(g_admitted, bytes);
+  g_admit_cv.notify_all();
+}
 
 }  // namespace
 
@@ -209,10 +319,7 @@ void free_handle(xk_handle* h) {
   fold_marks(h);
   for (void* p : h->allocs) cudaFree(p);
   if (h->stream) cudaStreamDestroy(h->stream);
-  {
-    std::lock_guard<std::mutex> lk(g_admit_mu);
-    g_admitted -= std::min(g_admitted, h->footprint);
-  }
+  unadmit_bytes(h->footprint);
   delete h;
 }
 
@@ -453,7 +560,8 @@ int xk_footprint(int64_t Ng, int32_t N, int32_t n, int32_t Naux, int mode, size_
 // point at those g1 - g0 rows (V: N_g columns, W: all Naux columns).
 static int setup_impl(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* phi,
                const int32_t* idx, const double* V, const double* W, double dV, int mode,
-               int32_t grid, double L, xk_handle** out, int32_t g0 = 0, int32_t g1 = -1) {
+               int32_t grid, double L, xk_handle** out, int32_t g0 = 0, int32_t g1 = -1,
+               double queue_ms = -1.0) {
   if (!out) return fail(XK_EINVAL, "xk_setup: out is NULL");
   *out = nullptr;
   if (g1 < 0) g1 = Naux;
@@ -502,39 +610,24 @@ static int setup_impl(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const doub
          max_work(Ng, N, n, Naux) + (size_t)Naux) * 8 + (size_t)Naux * 4
       : 0;
 
-  if (const char* env = std::getenv("XK_HBM_BUDGET_BYTES")) {
-    // a budget set by the caller is checked before any device call
-    std::lock_guard<std::mutex> lk(g_admit_mu);
-    const size_t cap = (size_t)std::strtoull(env, nullptr, 10);
-    const size_t left = cap > g_admitted ? cap - g_admitted : 0;
-    if (need + isdf_tmp > left)
-      return fail(XK_ENOMEM, "xk_setup: footprint " + std::to_string(need + isdf_tmp) +
-                                 " bytes exceeds XK_HBM_BUDGET_BYTES less the live handles (" +
-                                 std::to_string(left) + " bytes)");
+  // admission: now (queue_ms < 0) or in arrival order within queue_ms
+  {
+    int rc = admit_bytes(need + isdf_tmp, queue_ms, true, "xk_setup");
+    if (rc != XK_OK) return rc;
   }
   int dev = 0;
-  XK_CUDA(cudaGetDevice(&dev));
-  size_t freeb = 0, totalb = 0;
-  XK_CUDA(cudaMemGetInfo(&freeb, &totalb));
   {
-    std::lock_guard<std::mutex> lk(g_admit_mu);
-    const size_t reserve = (size_t)1 << 30;
-    size_t budget = freeb > reserve ? freeb - reserve : 0;
-    if (const char* env = std::getenv("XK_HBM_BUDGET_BYTES")) {
-      const size_t cap = (size_t)std::strtoull(env, nullptr, 10);
-      const size_t left = cap > g_admitted ? cap - g_admitted : 0;
-      budget = std::min(budget, left);
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+      unadmit_bytes(need + isdf_tmp);
+      return cuda_fail(e, "cudaGetDevice");
     }
-    if (need + isdf_tmp > budget)
-      return fail(XK_ENOMEM, "xk_setup: footprint " + std::to_string(need + isdf_tmp) +
-                                 " bytes exceeds the admission budget " + std::to_string(budget));
-    g_admitted += need;
   }
 
   xk_handle* h = new xk_handle();
   h->Ng = Ng; h->N = N; h->n = n; h->Naux = Naux; h->dV = dV; h->mode = mode; h->device = dev;
   h->g0 = g0; h->ga = ga;
-  h->footprint = need;
+  h->footprint = need + isdf_tmp;  // the ISDF temporaries are returned at the end
   auto bail = [&](int code) { free_handle(h); return code; };
   cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate"));
@@ -653,6 +746,10 @@ static int setup_impl(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const doub
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
     if (e != cudaSuccess) return bail(cuda_fail(e, "xk_setup slots"));
   }
+  if (isdf_tmp) {  // the ISDF set-up's temporaries are freed: return their bytes
+    h->footprint = need;
+    unadmit_bytes(isdf_tmp);
+  }
   *out = h;
   return XK_OK;
 }
@@ -677,6 +774,58 @@ int xk_setup_shard(int64_t Ng, int32_t N, int32_t n, int32_t Naux, int32_t g0, i
   }
   return setup_impl(Ng, N, n, Naux, basis_on_points, interp_idx, V_rows, W_rows, dV, mode, 0, 0.0,
                     out, g0, g1);
+}
+
+int xk_setup_queued(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* phi,
+                    const int32_t* idx, const double* V, const double* W, double dV, int mode,
+                    double timeout_ms, xk_handle** out) {
+  if (!V || !W) {
+    if (out) *out = nullptr;
+    return fail(XK_EINVAL, "xk_setup_queued: NULL table pointer");
+  }
+  if (!(timeout_ms >= 0.0) || !std::isfinite(timeout_ms)) {
+    if (out) *out = nullptr;
+    return fail(XK_EINVAL, "xk_setup_queued: timeout_ms must be finite and >= 0");
+  }
+  return setup_impl(Ng, N, n, Naux, phi, idx, V, W, dV, mode, 0, 0.0, out, 0, -1, timeout_ms);
+}
+
+int xk_admit_reserve(uint64_t bytes, double timeout_ms, uint64_t* token) {
+  if (!token) return fail(XK_EINVAL, "xk_admit_reserve: token is NULL");
+  *token = 0;
+  if (!std::isfinite(timeout_ms)) return fail(XK_EINVAL, "xk_admit_reserve: timeout_ms is not finite");
+  // without XK_HBM_BUDGET_BYTES the budget is the current device's free memory
+  const bool device = std::getenv("XK_HBM_BUDGET_BYTES") == nullptr;
+  int rc = admit_bytes((size_t)bytes, timeout_ms, device, "xk_admit_reserve");
+  if (rc != XK_OK) return rc;
+  std::lock_guard<std::mutex> lk(g_admit_mu);
+  const uint64_t t = ++g_admit_seq;
+  g_reservations[t] = (size_t)bytes;
+  g_reserved += (size_t)bytes;
+  *token = t;
+  return XK_OK;
+}
+
+int xk_admit_release(uint64_t token) {
+  size_t bytes = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_admit_mu);
+    auto it = g_reservations.find(token);
+    if (it == g_reservations.end()) return fail(XK_EINVAL, "xk_admit_release: unknown token");
+    bytes = it->second;
+    g_reserved -= std::min(g_reserved, bytes);
+    g_reservations.erase(it);
+  }
+  unadmit_bytes(bytes);
+  return XK_OK;
+}
+
+int xk_admit_state(uint64_t* admitted_bytes, uint32_t* waiting) {
+  if (!admitted_bytes || !waiting) return fail(XK_EINVAL, "xk_admit_state: NULL argument");
+  std::lock_guard<std::mutex> lk(g_admit_mu);
+  *admitted_bytes = (uint64_t)g_admitted;
+  *waiting = (uint32_t)g_admit_queue.size();
+  return XK_OK;
 }
 
 int xk_setup_isdf(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const double* phi,

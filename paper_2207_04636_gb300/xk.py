@@ -45,6 +45,12 @@ def lib():
                                c_int, ctypes.POINTER(ctypes.c_void_p)]
         L.xk_setup_isdf.argtypes = [c_i64, c_i32, c_i32, c_i32, c_d, c_d, c_i32, ctypes.c_double,
                                     c_int, ctypes.POINTER(ctypes.c_void_p)]
+        L.xk_setup_queued.argtypes = [c_i64, c_i32, c_i32, c_i32, c_d, c_d, c_d, c_d,
+                                      ctypes.c_double, c_int, ctypes.c_double, c_d]
+        L.xk_admit_reserve.argtypes = [ctypes.c_uint64, ctypes.c_double,
+                                       ctypes.POINTER(ctypes.c_uint64)]
+        L.xk_admit_release.argtypes = [ctypes.c_uint64]
+        L.xk_admit_state.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32)]
         L.xk_setup_shard.argtypes = [c_i64, c_i32, c_i32, c_i32, c_i32, c_i32, c_d, c_d, c_d, c_d,
                                      ctypes.c_double, c_int, ctypes.POINTER(ctypes.c_void_p)]
         L.xk_tables.argtypes = [c_d, c_d, c_d, c_i32, c_d, c_d]
@@ -115,10 +121,34 @@ def footprint(Ng, N, n, Naux, mode="fp64") -> int:
     return int(out.value)
 
 
+def admit_reserve(nbytes, timeout_ms=-1.0):
+    """Reserve nbytes against the admission budget (xk_admit_reserve); returns
+    the token.  timeout_ms < 0: now or XKError(XK_ENOMEM); else wait in the
+    admission queue (XKError(XK_ETIMEDOUT) when not admitted in time)."""
+    tok = ctypes.c_uint64()
+    _check(lib().xk_admit_reserve(int(nbytes), float(timeout_ms), ctypes.byref(tok)))
+    return tok.value
+
+
+def admit_release(token):
+    """Return a reservation's bytes and wake the admission queue (xk_admit_release)."""
+    _check(lib().xk_admit_release(int(token)))
+
+
+def admit_state():
+    """(bytes admitted, requests waiting) of the admission queue (xk_admit_state)."""
+    b = ctypes.c_uint64()
+    w = ctypes.c_uint32()
+    _check(lib().xk_admit_state(ctypes.byref(b), ctypes.byref(w)))
+    return b.value, w.value
+
+
 class Handle:
     """Per-geometry device tables plus build scratch (xk_setup / xk_release)."""
 
-    def __init__(self, phi, idx, V, W, dV, n, mode="fp64"):
+    def __init__(self, phi, idx, V, W, dV, n, mode="fp64", queue_timeout_ms=None):
+        """queue_timeout_ms: None admits now or raises (xk_setup); a number waits
+        in the admission queue up to that many milliseconds (xk_setup_queued)."""
         phi = np.asarray(phi)
         Ng, N = phi.shape
         idx = np.ascontiguousarray(idx, dtype=np.int32)
@@ -128,8 +158,13 @@ class Handle:
         V = _f64(V, (Naux, Ng), "V")
         W = _f64(W, (Naux, Naux), "W")
         h = ctypes.c_void_p()
-        _check(lib().xk_setup(Ng, N, self.n, Naux, _ptr(phi), _ptr(idx), _ptr(V), _ptr(W),
-                              float(dV), MODES[mode], ctypes.byref(h)))
+        if queue_timeout_ms is None:
+            _check(lib().xk_setup(Ng, N, self.n, Naux, _ptr(phi), _ptr(idx), _ptr(V), _ptr(W),
+                                  float(dV), MODES[mode], ctypes.byref(h)))
+        else:
+            _check(lib().xk_setup_queued(Ng, N, self.n, Naux, _ptr(phi), _ptr(idx), _ptr(V),
+                                         _ptr(W), float(dV), MODES[mode], float(queue_timeout_ms),
+                                         ctypes.byref(h)))
         self._h = h
 
     @classmethod
