@@ -1304,6 +1304,11 @@ struct xk_batch {
   std::vector<xk_handle*> hs;
   int device = 0;
   cudaStream_t stream = nullptr;
+  // capture-time fork/join: the members' orbital and line steps run on up to
+  // kBatchSide streams side by side (their small kernels overlap), the
+  // grouped pair launch on `stream` between them
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> evs;  // 2 forks, then 2 x side.size() joins
   xk::PairGroup* group = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -1333,10 +1338,24 @@ int xk_batch_create(xk_handle* const* handles, int count, xk_batch** out) {
   b->hs = hs;
   b->device = hs[0]->device;
   cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  constexpr int kBatchSide = 8;
+  const int nside = std::min(count, kBatchSide);
+  for (int k = 0; k < nside && e == cudaSuccess; ++k) {
+    cudaStream_t st = nullptr;
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) b->side.push_back(st);
+  }
+  for (int k = 0; k < 2 + 2 * nside && e == cudaSuccess; ++k) {
+    cudaEvent_t ev = nullptr;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->evs.push_back(ev);
+  }
   std::vector<xk::MixedState*> ms;
   for (xk_handle* h : hs) ms.push_back(h->mixed);
   if (e == cudaSuccess) e = xk::mixed_group_create(ms.data(), count, &b->group);
   if (e != cudaSuccess) {
+    for (cudaEvent_t ev : b->evs) cudaEventDestroy(ev);
+    for (cudaStream_t st : b->side) cudaStreamDestroy(st);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
     return cuda_fail(e, "xk_batch_create");
@@ -1375,11 +1394,30 @@ int xk_batch_build(xk_batch* b, const double* const* C, double* const* K_out, do
     XK_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     xk::StepHook none{nullptr, nullptr};
     cudaError_t e = cudaSuccess;
-    for (xk_handle* h : b->hs)
-      if (e == cudaSuccess) e = xk::mixed_enqueue_pre(h->mixed, h->C, b->stream, none);
+    const size_t ns = b->side.size();
+    // the side streams start after `stream` (fork) and `stream` continues
+    // after all of them (join)
+    auto fork = [&](int f) {
+      if (e == cudaSuccess) e = cudaEventRecord(b->evs[f], b->stream);
+      for (size_t k = 0; k < ns && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->side[k], b->evs[f], 0);
+    };
+    auto join = [&](int f) {
+      for (size_t k = 0; k < ns && e == cudaSuccess; ++k) {
+        cudaEvent_t ev = b->evs[2 + f * ns + k];
+        e = cudaEventRecord(ev, b->side[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, ev, 0);
+      }
+    };
+    fork(0);
+    for (size_t i = 0; i < b->hs.size(); ++i)
+      if (e == cudaSuccess) e = xk::mixed_enqueue_pre(b->hs[i]->mixed, b->hs[i]->C, b->side[i % ns], none);
+    join(0);
     if (e == cudaSuccess) e = xk::mixed_group_enqueue_pair(b->group, b->stream);
-    for (xk_handle* h : b->hs)
-      if (e == cudaSuccess) e = xk::mixed_enqueue_post(h->mixed, h->K, h->Ex, b->stream, none);
+    fork(1);
+    for (size_t i = 0; i < b->hs.size(); ++i)
+      if (e == cudaSuccess)
+        e = xk::mixed_enqueue_post(b->hs[i]->mixed, b->hs[i]->K, b->hs[i]->Ex, b->side[i % ns], none);
+    join(1);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(b->stream, &graph);
     if (e == cudaSuccess) e = ec;
@@ -1423,6 +1461,8 @@ int xk_batch_release(xk_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   xk::mixed_group_destroy(b->group);
+  for (cudaEvent_t ev : b->evs) cudaEventDestroy(ev);
+  for (cudaStream_t st : b->side) cudaStreamDestroy(st);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
   return XK_OK;
