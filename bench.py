@@ -440,6 +440,12 @@ def scf_runs_queued(xk, cell64, count=48, builds=6, seed=4800, budget_runs=12):
         h.build(c.C)
     h.release()
     run_s = time.perf_counter() - t0
+    setup_alone = {}
+    for z, cz in cells.items():  # one set-up of each size with nothing else running
+        t1 = time.perf_counter()
+        hz = xk.Handle(cz.phi, cz.idx, cz.V, cz.W, cz.dV, cz.n, mode="f16x3")
+        setup_alone[str(z)] = time.perf_counter() - t1
+        hz.release()
     base, _ = xk.admit_state()
     budget = int(budget_runs * mean_fp)
     sustain = budget_runs / run_s  # runs/s at which the budget is full on average
@@ -447,6 +453,7 @@ def scf_runs_queued(xk, cell64, count=48, builds=6, seed=4800, budget_runs=12):
     os.environ["XK_HBM_BUDGET_BYTES"] = str(base + budget)
     out = {"runs": int(count), "sizes": {str(z): int(np.sum(sizes == z)) for z in (8, 27, 64)},
            "builds_per_run": builds, "budget_bytes": budget, "run_alone_s_64": run_s,
+           "setup_alone_s": setup_alone,
            "budget_in_runs_of_the_mix": budget_runs, "rates": []}
     try:
         for frac in (0.25, 0.5, 1.0):
@@ -506,8 +513,11 @@ def scf_runs_queued(xk, cell64, count=48, builds=6, seed=4800, budget_runs=12):
         else:
             os.environ["XK_HBM_BUDGET_BYTES"] = old
     out["note"] = ("xk_setup_queued admission (arrival order, woken by xk_release), one thread "
-                   "per run doing blocking xk_build calls; 125- and 216-centre members left out "
-                   "(host generation of their tables takes minutes)")
+                   "per run doing blocking xk_build calls; admission_wait_ms is the whole "
+                   "xk_setup_queued call: the wait in the queue plus the set-up itself (the "
+                   "upload and conversion of the run's tables from pageable host memory, shared "
+                   "by the set-ups that run at the same time); 125- and 216-centre members left "
+                   "out (host generation of their tables takes minutes)")
     return out
 
 
