@@ -74,6 +74,9 @@ def parse():
     p.add_argument("--isdf", action="store_true",
                    help="form the handle's ISDF tables on the GPU (xk_setup_isdf) instead of "
                         "taking the generator's, and report the set-up time")
+    p.add_argument("--mix125", type=int, default=0,
+                   help="run only the config-4 mix with 125-centre members: this many cells "
+                        "drawn from 8/27/64/125 centres (batch and serving), one JSON line")
     p.add_argument("--batch", type=int, default=32,
                    help="cells in the grouped batch / mixed serving run (0 skips both)")
     p.add_argument("--shard", action="store_true",
@@ -366,13 +369,20 @@ def batch_and_mixed_serving(xk, cell64, count, seed=4000):
     rng = np.random.default_rng(seed)
     sizes = rng.choice([8, 27, 64], size=count)
     cells = {8: load_cell(config_spec(4, k=2)), 27: load_cell(config_spec(4, k=3)), 64: cell64}
+    return batch_and_serve(xk, cells, sizes)
+
+
+def batch_and_serve(xk, cells, sizes):
+    """(a) and (b) of batch_and_mixed_serving over the given cells (size ->
+    cell) and member sizes."""
+    count = len(sizes)
     handles, seqs = [], []
     for i, z in enumerate(sizes):
         c = cells[int(z)]
         handles.append(xk.Handle(c.phi, c.idx, c.V, c.W, c.dV, c.n, mode="f16x3"))
         seqs.append(pseudo_scf_sequence(c.S, c.C, 8, 5000 + i))
     footprint = sum(xk.footprint(h.Ng, h.N, h.n, h.Naux, "f16x3") for h in handles)
-    out = {"cells": int(count), "sizes": {str(z): int(np.sum(sizes == z)) for z in (8, 27, 64)},
+    out = {"cells": int(count), "sizes": {str(z): int(np.sum(sizes == z)) for z in sorted(cells)},
            "device_bytes": int(footprint)}
     try:
         b = xk.Batch(handles)
@@ -404,8 +414,9 @@ def batch_and_mixed_serving(xk, cell64, count, seed=4000):
                           "p50_ms": float(np.percentile(lat, 50)),
                           "p99_ms": float(np.percentile(lat, 99)), "builds_per_s": got})
         out["serving"] = {"runs": int(count), "rates": rates,
-                          "note": "xk_submit/xk_poll, four slots per run, runs of 8, 27 and "
-                                  "64 centres overlapping on the GPU"}
+                          "note": "xk_submit/xk_poll, four slots per run, runs of " +
+                                  ", ".join(str(z) for z in sorted(cells)) +
+                                  " centres overlapping on the GPU"}
     finally:
         for h in handles:
             h.release()
@@ -521,6 +532,51 @@ def scf_runs_queued(xk, cell64, count=48, builds=6, seed=4800, budget_runs=12):
     return out
 
 
+def run_mix125(args):
+    """Config 4 with its largest size: `args.mix125` cells drawn with seed 4125
+    from {8, 27, 64, 125} centres.  The 125-centre cell (N = 1625, n = 250,
+    75^3 grid, N_aux = 8125) gets its ISDF tables on the GPU (xk_setup_isdf,
+    FP64; the host fit would take hours), read back and handed to its f16x3
+    members like any caller's tables.  Then the grouped batch against one
+    build at a time, and serving at three rates (batch_and_serve).  32 cells
+    drawn the same way would need the footprint reported as
+    `footprint_of_32_cells`, more than one GPU holds."""
+    import dataclasses
+    import torch
+    import paper_2207_04636_gb300 as xk
+    from paper_2207_04636_gb300 import build as xkbuild
+    from cellgen import build_cell
+    xkbuild.build_library()
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    c125 = build_cell(config_spec(4, k=5), fit=False)
+    t_inputs = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hf = xk.Handle.isdf(c125.phi, c125.idx, c125.grid, c125.L, c125.n, mode="fp64")
+    t_isdf = time.perf_counter() - t0
+    W, V, ridge = hf.tables(np.arange(c125.Naux))
+    hf.release()
+    c125 = dataclasses.replace(c125, V=V, W=W)
+    cells = {8: load_cell(config_spec(4, k=2)), 27: load_cell(config_spec(4, k=3)),
+             64: load_cell(config_spec(2)), 125: c125}
+    fp = {z: xk.footprint(c.Ng, c.N, c.n, c.Naux, "f16x3") for z, c in cells.items()}
+    rng = np.random.default_rng(4125)
+    sizes = rng.choice([8, 27, 64, 125], size=args.mix125)
+    fp32 = sum(fp[int(z)] for z in np.random.default_rng(4125).choice([8, 27, 64, 125], size=32))
+    res = batch_and_serve(xk, cells, sizes)
+    line = {"metric": "K builds/s (config 4 mix with 125-centre members)",
+            "value": res.get("batch", {}).get("builds_per_s"), "unit": "builds/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f16x3",
+            "data": "synthetic (seeded cell generator; 125-centre ISDF tables formed on the GPU)",
+            "config": {"workload": f"{args.mix125} cells drawn from 8/27/64/125 centres (seed 4125)"},
+            "footprint_bytes": {str(z): int(v) for z, v in fp.items()},
+            "footprint_of_32_cells": int(fp32),
+            "device_memory_bytes": int(torch.cuda.get_device_properties(0).total_memory),
+            "setup_125_s": {"host_inputs": t_inputs, "isdf_fp64_on_gpu": t_isdf},
+            "isdf_ridge_125": ridge, "mix": res}
+    print(json.dumps(line), flush=True)
+
+
 def gpu_points(xk, cell):
     """The two-stage point selection of Sec. IV.C with the pivoting on the GPU
     (xk_isdf_points): per-atom candidates from each Voronoi cell of the grid,
@@ -631,6 +687,9 @@ def main():
         return
     if args.config == 3:
         run_config3(args)
+        return
+    if args.mix125:
+        run_mix125(args)
         return
     import torch
     import paper_2207_04636_gb300 as xk
