@@ -644,6 +644,7 @@ def run_config3(args):
     ms, launches, st = time_device_builds(xk, h, Cd, Kd, Ed, stream, warm, steps, torch)
     clocks = sampler.stop()
     K, E = Kd.cpu().numpy(), float(Ed.item())
+    tuned = h.autotune_info()
     h.release()
     line = {"metric": "K builds/s (216-centre cell)", "value": steps / (ms * 1e-3),
             "unit": "builds/s", "n_gpus": 1, "steps": steps, "warmup": warm,
@@ -653,7 +654,7 @@ def run_config3(args):
                                    "n_occ=432, 90^3 grid, N_aux=13500", "N": N, "n": n,
                        "N_g": Ng, "N_aux": Na},
             "step_ms": {k: v[0] / max(1, v[1]) for k, v in st.items() if v[1]},
-            "gpu_launches": int(launches), "clocks": clocks,
+            "gpu_launches": int(launches), "clocks": clocks, "autotune": tuned,
             "setup_s": {"host_inputs": t_inputs, "isdf_fp64_on_gpu": t_isdf,
                         "tensor_handle_from_tables": t_mixed_setup},
             "isdf_ridge": ridge,
@@ -762,6 +763,7 @@ def main():
     # per-build a-posteriori estimate |E_x - E_K| (E_K = -sum K o C of the
     # returned K) of the last timed build; a shard's is its share's
     err_est = h.error_estimate()
+    tuned = h.autotune_info() if mode != "fp64" else None
 
     # e2e through the blocking C-ABI call: host (pinned) buffers in and out
     Ch = [torch.from_numpy(C).pin_memory() for C in Cs[warm:warm + steps]]
@@ -953,6 +955,7 @@ def main():
             "error_estimate": {"last_build": err_est,
                                "definition": "|E_x - E_K|, E_K = -sum K o C of the returned K "
                                              "(xk_poll err_est / xk_error_estimate)"},
+            "autotune": tuned,
             "e2e": {"value": job_throughput(1 if shard else world, steps, e2e_s * 1e3),
                     "unit": "builds/s",
                     "h2d_bytes_per_step": N * n * 8, "d2h_bytes_per_step": N * n * 8 + 8},

@@ -24,7 +24,8 @@
  * xk_batch_build, xk_batch_release); other products on the same tables
  * (xk_energy, xk_energy_device, xk_build_full, xk_coulomb,
  * xk_exchange_energy_noalloc); diagnostics and control (xk_last_error,
- * xk_kernel_launches, xk_timing_enable, xk_timing_read, xk_set_wait_limit).
+ * xk_kernel_launches, xk_timing_enable, xk_timing_read, xk_set_wait_limit,
+ * xk_autotune_info).
  *
  * Conventions for every entry point:
  *   - All matrices are row-major, double precision, densely packed.
@@ -354,6 +355,20 @@ int xk_poll(xk_ticket t, double* K_out, double* Ex, double* err_est);
  * (NULL argument, no build yet), XK_ECUDA.
  */
 int xk_error_estimate(xk_handle* h, double* est);
+
+/*
+ * What the set-up's autotuner chose for an XK_F16X3 handle (it times its own
+ * launches on its own sizes when the handle is created):
+ *   info[0]  width of the n > 128 back-contraction tiles, 128 or 256 (0 for
+ *            n <= 128); the faster of the two, 256 unless 128 is 3 % faster;
+ *            XK_BACK_TILES=128 or 256 in the environment fixes it
+ *   info[1]  the K split of M2 (the role-A split for n <= 64)
+ *   ms[0..2] set-up timing (ms) of the 128- and 256-column back-contraction
+ *            shapes, and of the tuned pair launch for n <= 64 (0 when not timed)
+ * info: 2 int32, ms: 3 doubles, caller-owned.  Errors: XK_EINVAL (NULL
+ * argument, XK_FP64 handle).
+ */
+int xk_autotune_info(xk_handle* h, int32_t* info, double* ms);
 
 /*
  * Free every device and host resource of the handle (waits for its work).

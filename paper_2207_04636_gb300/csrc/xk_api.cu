@@ -1291,6 +1291,19 @@ int xk_error_estimate(xk_handle* h, double* est) {
   return XK_OK;
 }
 
+int xk_autotune_info(xk_handle* h, int32_t* info, double* ms) {
+  if (!h || !info || !ms) return fail(XK_EINVAL, "xk_autotune_info: NULL argument");
+  if (!h->mixed) return fail(XK_EINVAL, "xk_autotune_info: not an XK_F16X3 handle");
+  std::lock_guard<std::mutex> lk(h->mu);
+  int in[2] = {0, 0};
+  double t[3] = {0.0, 0.0, 0.0};
+  xk::mixed_autotune_info(h->mixed, in, t);
+  info[0] = in[0];
+  info[1] = in[1];
+  ms[0] = t[0]; ms[1] = t[1]; ms[2] = t[2];
+  return XK_OK;
+}
+
 int xk_set_wait_limit(xk_handle* h, int64_t cycles) {
   if (!h || cycles < 0) return fail(XK_EINVAL, "xk_set_wait_limit: NULL handle or negative limit");
   std::lock_guard<std::mutex> lk(h->mu);

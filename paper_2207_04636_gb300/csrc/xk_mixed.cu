@@ -2616,6 +2616,11 @@ struct MixedState {
   int* status = nullptr;
   int xa = 1, partsA = 1, partsC = 1, splitsL1 = 1, splitsL23 = 1;
   int ychunkA = 64, ychunkC = 64;
+  // n > 128: shape of the back-contraction tiles (true: 128 x 256, gemm_wide_kernel;
+  // false: 128 x 128, gemm_kernel) and the splits of each (index 0: 128 x 128)
+  bool wide = true;
+  int partsA_s[2] = {1, 1}, partsC_s[2] = {1, 1}, ychunkA_s[2] = {64, 64}, ychunkC_s[2] = {64, 64};
+  float shape_ms[2] = {0.0f, 0.0f};  // the set-up's timing of each shape (ms)
   // n > 128: the pair contractions run through a stored T = f V o P (hi/lo
   // FP16, [N_aux][N_g] and [N_aux][N_aux]) and three GEMMs over it
   bool large = false;
@@ -2656,6 +2661,7 @@ struct MixedState {
 };
 
 cudaError_t make_tprod_maps(MixedState* m);
+cudaError_t autotune_back_shape(MixedState* m, cudaStream_t s);
 
 namespace {
 
@@ -2677,6 +2683,10 @@ struct Plan {
   int nt;
   long epA, epC;
   int partsA_max;  // largest role-A split the autotuner may pick (buffer sizes)
+  int partsC_max;  // largest role-C split (buffer sizes)
+  // n > 128: splits of M2 and M3 for 128 x 128 tiles (partsA / partsC are those
+  // of the 128 x 256 tiles); the handle times both shapes at set-up
+  int partsA_n = 1, partsC_n = 1, ychunkA_n = 64, ychunkC_n = 64;
 };
 
 // FP32 copies of M2 the fused role reduces into (X tile % kM2Copies): each
@@ -2723,6 +2733,7 @@ Plan make_plan(int64_t Ng, int N, int n, int Naux, int NaT) {
     p.partsC = (NaT + p.ychunkC - 1) / p.ychunkC;
     p.partsA_max = p.partsA;
     for (int c : tune_candidates(Ng, p.xa)) p.partsA_max = std::max(p.partsA_max, c);
+    p.partsC_max = p.partsC;
     p.epA = (long)p.partsA_max * p.xa;
     p.epC = (long)p.partsC * p.xa;
     if (p.fused) {  // one CTA per 128 grid points over every g; M2 in kM2Copies copies
@@ -2731,19 +2742,24 @@ Plan make_plan(int64_t Ng, int N, int n, int Naux, int NaT) {
       p.epA = (Ng + 127) / 128;
     }
   } else {
-    // M2 = T_A Psi and M3 = T_C Psi_g: xa x (n / 256) wide tiles, K split to
-    // about four waves
-    const int t2 = p.xa * ((n + 255) / 256);
-    p.partsA = std::max(1, std::min<int>(608 / t2, (int)((Ng + 4095) / 4096)));
-    p.ychunkA = (int)rup((Ng + p.partsA - 1) / p.partsA, 64);
-    p.partsA = (int)((Ng + p.ychunkA - 1) / p.ychunkA);
-    p.partsC = std::max(1, std::min<int>(304 / t2, (NaT + 1023) / 1024));
-    p.ychunkC = (int)rup((NaT + p.partsC - 1) / p.partsC, 64);
-    p.partsC = (NaT + p.ychunkC - 1) / p.ychunkC;
+    // M2 = T_A Psi and M3 = T_C Psi_g: K split to about four waves of the
+    // 128 x 256 tiles (xa x n / 256) and, for the other shape the autotuner
+    // tries, of 128 x 128 tiles (xa x n / 128)
+    auto split = [&](int tiles, long K, long kmin, int cap, int& chunk) {
+      int sp = std::max(1, std::min<int>(cap / tiles, (int)((K + kmin - 1) / kmin)));
+      chunk = (int)rup((K + sp - 1) / sp, 64);
+      return (int)((K + chunk - 1) / chunk);
+    };
+    const int tw = p.xa * ((n + 255) / 256), tn = p.xa * p.nt;
+    p.partsA = split(tw, Ng, 4096, 608, p.ychunkA);
+    p.partsC = split(tw, NaT, 1024, 304, p.ychunkC);
+    p.partsA_n = split(tn, Ng, 4096, 608, p.ychunkA_n);
+    p.partsC_n = split(tn, NaT, 1024, 304, p.ychunkC_n);
     // energy partials of the T products: one per tile and column half
     p.epA = 2L * p.xa * ((Ng + 127) / 128);
     p.epC = 2L * p.xa * ((NaT + 127) / 128);
-    p.partsA_max = p.partsA;
+    p.partsA_max = std::max(p.partsA, p.partsA_n);
+    p.partsC_max = std::max(p.partsC, p.partsC_n);
   }
   // line GEMMs: (N / 128) x (n / 128) tiles x K splits of >= 1024; split
   // counts round down, so the tiles fill whole waves of CTAs (a wave plus one
@@ -2813,7 +2829,7 @@ size_t mixed_footprint(int64_t Ng, int N, int n, int Naux, int NaT) {
     b += 2 * na * p.Ng8 * 2 + 2 * na * p.NaT8 * 2 + (ng + nat) * p.np * 2;
   b += (ng + n) * p.Np * 2;  // third pieces of Phi' and Q
   b += 2 * (size_t)n * p.Np * 2 + (size_t)n * p.Np * 8 + 2 * ng * p.np * 2 + 2 * nat * p.np * 2;
-  b += (size_t)p.partsA_max * na * n * 4 + (size_t)p.partsC * na * n * 4 + (size_t)n * p.Ng4 * 4;
+  b += (size_t)p.partsA_max * na * n * 4 + (size_t)p.partsC_max * na * n * 4 + (size_t)n * p.Ng4 * 4;
   b += na * n * 8 + (size_t)n * p.Na8 * 8 + 2 * (size_t)n * p.Ng8 * 2 + 2 * (size_t)n * p.Na8 * 2;
   b += (size_t)p.splitsL1 * N * n * 4 + (size_t)p.splitsL23 * N * n * 4;
   b += (size_t)(p.epA + p.epC) * 8;
@@ -2949,6 +2965,10 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int NaT, int g0, int g1, cons
   m->Np = p.Np; m->Ng8 = p.Ng8; m->Na8 = p.Na8; m->Ng4 = p.Ng4; m->Na4 = p.Na4;
   m->xa = p.xa; m->partsA = p.partsA; m->partsC = p.partsC;
   m->ychunkA = p.ychunkA; m->ychunkC = p.ychunkC;
+  m->partsA_s[0] = p.partsA_n; m->partsC_s[0] = p.partsC_n;
+  m->ychunkA_s[0] = p.ychunkA_n; m->ychunkC_s[0] = p.ychunkC_n;
+  m->partsA_s[1] = p.partsA; m->partsC_s[1] = p.partsC;
+  m->ychunkA_s[1] = p.ychunkA; m->ychunkC_s[1] = p.ychunkC;
   m->splitsL1 = p.splitsL1; m->splitsL23 = p.splitsL23;
   m->kchunkL1 = p.kchunkL1; m->kchunkL23 = p.kchunkL23;
   m->large = p.large; m->fused = p.fused; m->nt = p.nt; m->epA = p.epA; m->epC = p.epC;
@@ -2989,7 +3009,7 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int NaT, int g0, int g1, cons
   }
   m->psig_m = m->psigA_m + (size_t)g0 * p.np;  // the slice's rows
   m->psig_h = m->psigA_h + (size_t)g0 * p.np;
-  MX(m->M2p, (size_t)p.partsA_max * na * n); MX(m->M3p, (size_t)p.partsC * na * n);
+  MX(m->M2p, (size_t)p.partsA_max * na * n); MX(m->M3p, (size_t)p.partsC_max * na * n);
   MX(m->M1, (size_t)n * p.Ng4);
   MX(m->D23, na * n); MX(m->D23T64, (size_t)n * p.Na8);
   MX(m->M1_m, (size_t)n * p.Ng8); MX(m->M1_h, (size_t)n * p.Ng8);
@@ -3195,6 +3215,9 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int NaT, int g0, int g1, cons
       e = autotune_split_a(m, s);
       if (e != cudaSuccess) return fin(e);
     }
+  } else {
+    e = autotune_back_shape(m, s);
+    if (e != cudaSuccess) return fin(e);
   }
   fin(cudaSuccess);
   *out = m;
@@ -3440,8 +3463,100 @@ cudaError_t mixed_enqueue_energy(MixedState* m, const double* C, double* Ex, cud
   return e;
 }
 
-cudaError_t mixed_enqueue_pair(MixedState* m, cudaStream_t s, const StepHook& hook) {
+// n > 128: M2 = T_A Psi, M3 = T_C Psi_g and M1^T = T_A^T Psi_g (written
+// transposed) over the stored T, on 128 x 256 tiles (wide) or 128 x 128
+// tiles, with the splits of that shape (m->partsA, m->partsC, chunks).
+void enqueue_back_contractions(MixedState* m, cudaStream_t s, bool wide) {
   const long ng = m->Ng, na = m->Naux;
+  const int n = m->n;
+  GemmArgs g2{};
+  g2.M = (int)na; g2.Ncols = n; g2.K = (int)ng; g2.kchunk = m->ychunkA; g2.out = m->M2p;
+  g2.ldo = n; g2.split_stride = na * n; g2.sc = m->sc; g2.scale_idx = SC_OUT_AB;
+  g2.status = m->status; g2.b_mn = 1;
+  GemmArgs g3 = g2;
+  g3.K = m->NaT; g3.kchunk = m->ychunkC; g3.out = m->M3p; g3.scale_idx = SC_OUT_C;
+  GemmArgs g1{};
+  g1.M = (int)ng; g1.Ncols = n; g1.K = (int)na; g1.kchunk = (int)rup(na, 64); g1.out = m->M1;
+  g1.ldo = m->Ng4; g1.sc = m->sc; g1.scale_idx = SC_OUT_AB; g1.status = m->status;
+  g1.a_mn = 1; g1.b_mn = 1; g1.transposed = 1;
+  const unsigned gx1 = (unsigned)((ng + 127) / 128);
+  if (wide) {
+    const unsigned ntw = (unsigned)((n + 255) / 256);
+    launch_gemm_wide(m->m_TA_h, m->m_TA_l, m->m_psi64_m, m->m_psi64_h, g2,
+                     dim3((unsigned)m->xa, ntw, (unsigned)m->partsA), s, m->wait_cycles);
+    launch_gemm_wide(m->m_TC_h, m->m_TC_l, m->m_psigA64_m, m->m_psigA64_h, g3,
+                     dim3((unsigned)m->xa, ntw, (unsigned)m->partsC), s, m->wait_cycles);
+    launch_gemm_wide(m->m_TAmn_h, m->m_TAmn_l, m->m_psig64_m, m->m_psig64_h, g1,
+                     dim3(gx1, ntw, 1), s, m->wait_cycles);
+  } else {
+    const unsigned nt = (unsigned)m->nt;
+    launch_gemm(m->m_TA_h, m->m_TA_l, m->m_psi64_m, m->m_psi64_h, m->m_TA_h, m->m_psi64_m, g2,
+                dim3((unsigned)m->xa, nt, (unsigned)m->partsA), s, m->wait_cycles);
+    launch_gemm(m->m_TC_h, m->m_TC_l, m->m_psigA64_m, m->m_psigA64_h, m->m_TC_h, m->m_psigA64_m,
+                g3, dim3((unsigned)m->xa, nt, (unsigned)m->partsC), s, m->wait_cycles);
+    launch_gemm(m->m_TAmn_h, m->m_TAmn_l, m->m_psig64_m, m->m_psig64_h, m->m_TAmn_h,
+                m->m_psig64_m, g1, dim3(gx1, nt, 1), s, m->wait_cycles);
+  }
+  count_launch(3);
+}
+
+// Sets the back-contraction shape of an n > 128 handle and its splits.
+void set_back_shape(MixedState* m, bool wide) {
+  const int k = wide ? 1 : 0;
+  m->wide = wide;
+  m->partsA = m->partsA_s[k]; m->partsC = m->partsC_s[k];
+  m->ychunkA = m->ychunkA_s[k]; m->ychunkC = m->ychunkC_s[k];
+}
+
+// Autotuner of the n > 128 back-contractions: times the three GEMMs with each
+// tile shape (and its own whole-wave split) on zeroed operands, best of two
+// launches each, and keeps the faster; 128 x 256 stays unless 128 x 128 is 3 %
+// faster.  XK_BACK_TILES=128 or 256 in the environment fixes the shape (tests).
+cudaError_t autotune_back_shape(MixedState* m, cudaStream_t s) {
+  if (const char* env = std::getenv("XK_BACK_TILES")) {
+    set_back_shape(m, std::atoi(env) != 128);
+    return cudaSuccess;
+  }
+  const long ng = m->Ng, na = m->Naux, nat = m->NaT;
+  cudaError_t e = cudaMemsetAsync(m->TA_h, 0, (size_t)na * m->Ng8 * 2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->TA_l, 0, (size_t)na * m->Ng8 * 2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->TC_h, 0, (size_t)na * m->NaT8 * 2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->TC_l, 0, (size_t)na * m->NaT8 * 2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->psi_m, 0, (size_t)3 * ng * m->np * 2, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->psigA_m, 0, (size_t)3 * nat * m->np * 2, s);
+  if (e == cudaSuccess) set_tune_scales_kernel<<<1, 32, 0, s>>>(m->sc);
+  count_launch();
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0, e1;
+  e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return e;
+  e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) { cudaEventDestroy(e0); return e; }
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    set_back_shape(m, k == 1);
+    enqueue_back_contractions(m, s, m->wide);  // warm-up
+    float ms = 1e30f;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+      e = cudaEventRecord(e0, s);
+      enqueue_back_contractions(m, s, m->wide);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float t = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+      ms = std::min(ms, t);
+    }
+    m->shape_ms[k] = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  set_back_shape(m, !(e == cudaSuccess && m->shape_ms[0] < 0.97f * m->shape_ms[1]));
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->status, 0, 16, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
+}
+
+cudaError_t mixed_enqueue_pair(MixedState* m, cudaStream_t s, const StepHook& hook) {
+  const long na = m->Naux;
   const int n = m->n, np = m->np;
   cudaError_t e;
   // ---- steps 2-3: the three fused pair contractions
@@ -3451,25 +3566,7 @@ cudaError_t mixed_enqueue_pair(MixedState* m, cudaStream_t s, const StepHook& ho
     // as hi/lo FP16 with their energy sums, then M2 = T_A Psi, M3 = T_C Psi_g
     // and M1^T = T_A^T Psi_g (written transposed) on the tensor cores.
     enqueue_t_products(m, s, true, true);
-    GemmArgs g2{};
-    g2.M = (int)na; g2.Ncols = n; g2.K = (int)ng; g2.kchunk = m->ychunkA; g2.out = m->M2p;
-    g2.ldo = n; g2.split_stride = na * n; g2.sc = m->sc; g2.scale_idx = SC_OUT_AB;
-    g2.status = m->status; g2.b_mn = 1;
-    // (128 x 256 output tiles: half the operand bytes per MMA of 128 x 128 ones)
-    const unsigned ntw = (unsigned)((n + 255) / 256);
-    launch_gemm_wide(m->m_TA_h, m->m_TA_l, m->m_psi64_m, m->m_psi64_h, g2,
-                     dim3((unsigned)m->xa, ntw, (unsigned)m->partsA), s, m->wait_cycles);
-    GemmArgs g3 = g2;
-    g3.K = m->NaT; g3.kchunk = m->ychunkC; g3.out = m->M3p; g3.scale_idx = SC_OUT_C;
-    launch_gemm_wide(m->m_TC_h, m->m_TC_l, m->m_psigA64_m, m->m_psigA64_h, g3,
-                     dim3((unsigned)m->xa, ntw, (unsigned)m->partsC), s, m->wait_cycles);
-    GemmArgs g1{};
-    g1.M = (int)ng; g1.Ncols = n; g1.K = (int)na; g1.kchunk = (int)rup(na, 64); g1.out = m->M1;
-    g1.ldo = m->Ng4; g1.sc = m->sc; g1.scale_idx = SC_OUT_AB; g1.status = m->status;
-    g1.a_mn = 1; g1.b_mn = 1; g1.transposed = 1;
-    launch_gemm_wide(m->m_TAmn_h, m->m_TAmn_l, m->m_psig64_m, m->m_psig64_h, g1,
-                     dim3((unsigned)((ng + 127) / 128), ntw, 1), s, m->wait_cycles);
-    count_launch(3);
+    enqueue_back_contractions(m, s, m->wide);
   } else if (m->fused) {
     // M1 and M2 from one pass over V^T (M2 reduced into the copies), and M3
     e = cudaMemsetAsync(m->M2p, 0, (size_t)kM2Copies * na * n * 4, s);
@@ -3595,5 +3692,13 @@ void mixed_set_wait_limit(MixedState* m, long long cycles) {
 }
 
 int* mixed_status_ptr(MixedState* m) { return m->status; }
+
+void mixed_autotune_info(const MixedState* m, int* info, double* ms) {
+  info[0] = m->large ? (m->wide ? 256 : 128) : 0;
+  info[1] = m->partsA;
+  ms[0] = m->shape_ms[0];
+  ms[1] = m->shape_ms[1];
+  ms[2] = m->tuned_ms;
+}
 
 }  // namespace xk

@@ -82,5 +82,11 @@ int* mixed_status_ptr(MixedState* m);
 // enqueued afterwards.
 void mixed_set_wait_limit(MixedState* m, long long cycles);
 
+// The set-up autotuner's choices: info[0] = width of the n > 128
+// back-contraction tiles (128 or 256, 0 otherwise), info[1] = the K split of
+// M2 (role A for n <= 64); ms[0], ms[1] = timing of the 128- and 256-column
+// shapes at set-up (0 when not timed), ms[2] = the tuned pair launch (n <= 64).
+void mixed_autotune_info(const MixedState* m, int* info, double* ms);
+
 
 }  // namespace xk

@@ -50,6 +50,7 @@ def lib():
         L.xk_admit_reserve.argtypes = [ctypes.c_uint64, ctypes.c_double,
                                        ctypes.POINTER(ctypes.c_uint64)]
         L.xk_admit_release.argtypes = [ctypes.c_uint64]
+        L.xk_autotune_info.argtypes = [c_d, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
         L.xk_admit_state.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32)]
         L.xk_setup_shard.argtypes = [c_i64, c_i32, c_i32, c_i32, c_i32, c_i32, c_d, c_d, c_d, c_d,
                                      ctypes.c_double, c_int, ctypes.POINTER(ctypes.c_void_p)]
@@ -275,6 +276,15 @@ class Handle:
         est = np.empty(1)
         _check(lib().xk_error_estimate(self._h, _ptr(est)))
         return float(est[0])
+
+    def autotune_info(self):
+        """The set-up autotuner's choices (xk_autotune_info): {"back_tiles": 128 |
+        256 | 0, "m2_split": int, "ms_128": t, "ms_256": t, "ms_tuned_pair": t}."""
+        info = (ctypes.c_int32 * 2)()
+        ms = (ctypes.c_double * 3)()
+        _check(lib().xk_autotune_info(self._h, info, ms))
+        return {"back_tiles": info[0], "m2_split": info[1], "ms_128": ms[0], "ms_256": ms[1],
+                "ms_tuned_pair": ms[2]}
 
     def set_wait_limit(self, cycles: int):
         """Bound (SM cycles) on the pipeline waits of this handle's kernels; 0 = default."""

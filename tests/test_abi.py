@@ -127,6 +127,7 @@ def test_null_handles_and_tickets(L):
     assert L.xk_batch_build(None, p, p, p) == xk.XK_EINVAL
     assert L.xk_batch_release(None) == xk.XK_EINVAL
     assert L.xk_set_wait_limit(None, 0) == xk.XK_EINVAL
+    assert L.xk_autotune_info(None, None, None) == xk.XK_EINVAL
 
 
 def test_setup_refused_beyond_budget(L, monkeypatch):

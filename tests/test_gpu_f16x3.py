@@ -93,16 +93,45 @@ def test_fused_role(xk, n_occ):
     _check(xk, load_cell(spec))
 
 
+@pytest.mark.parametrize("tiles", [None, "128", "256"])
 @pytest.mark.parametrize("n_occ", [150, 200])
-def test_large_n(xk, n_occ):
+def test_large_n(xk, n_occ, tiles, monkeypatch):
     """n > 128 (27-centre cell, N = 351): the pair contractions go through the
     stored T = V o P and three tensor-core GEMMs; n = 150 leaves a ragged
     64-wide piece block and a ragged 128-wide output tile.  With n = 200 on
     27 centres E_x = -117.8 Ha: the three-piece orbitals of the S product keep
     its error far inside 1e-6 Ha (two pieces missed by 4e-6)."""
+    # tiles: the back-contraction shape the set-up's autotuner would choose
+    # (None), or either shape forced (XK_BACK_TILES), so that both stay tested
+    if tiles is not None:
+        monkeypatch.setenv("XK_BACK_TILES", tiles)
     spec = config_spec(4, k=3)
     spec.n_occ = n_occ
     _check(xk, load_cell(spec))
+
+
+def test_back_shape_autotune(xk, monkeypatch):
+    """The set-up times the n > 128 back-contractions with 128- and 256-column
+    tiles and keeps the faster (256 unless 128 is 3 % faster); XK_BACK_TILES
+    fixes the shape without timing."""
+    spec = config_spec(4, k=3)
+    spec.n_occ = 150
+    c = load_cell(spec)
+    h = xk.Handle(c.phi, c.idx, c.V, c.W, c.dV, c.n, mode="f16x3")
+    try:
+        info = h.autotune_info()
+    finally:
+        h.release()
+    assert info["ms_128"] > 0 and info["ms_256"] > 0
+    want = 128 if info["ms_128"] < 0.97 * info["ms_256"] else 256
+    assert info["back_tiles"] == want, info
+    monkeypatch.setenv("XK_BACK_TILES", "128")
+    h = xk.Handle(c.phi, c.idx, c.V, c.W, c.dV, c.n, mode="f16x3")
+    try:
+        info = h.autotune_info()
+    finally:
+        h.release()
+    assert info["back_tiles"] == 128 and info["ms_128"] == 0 and info["ms_256"] == 0
 
 
 def _full_cells(cell1):
