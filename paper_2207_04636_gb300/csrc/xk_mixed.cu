@@ -2761,10 +2761,11 @@ Plan make_plan(int64_t Ng, int N, int n, int Naux, int NaT) {
     p.partsA_max = std::max(p.partsA, p.partsA_n);
     p.partsC_max = std::max(p.partsC, p.partsC_n);
   }
-  // line GEMMs: (N / 128) x (n / 128) tiles x K splits of >= 1024; split
-  // counts round down, so the tiles fill whole waves of CTAs (a wave plus one
-  // tile would run a whole extra tile time)
-  const int tiles = ((N + 127) / 128) * ((n + 127) / 128);
+  // line GEMMs: (N / 128) x (n / 128) tiles (n / 256 for n > 128, which runs
+  // them on 128 x 256 tiles) x K splits of >= 1024; split counts round down,
+  // so the tiles fill whole waves of CTAs (a wave plus one tile would run a
+  // whole extra tile time)
+  const int tiles = ((N + 127) / 128) * (p.large ? (n + 255) / 256 : (n + 127) / 128);
   p.splitsL1 = std::max(1, std::min<int>((int)((Ng + 1023) / 1024), 608 / tiles));
   p.kchunkL1 = (int)rup((Ng + p.splitsL1 - 1) / p.splitsL1, 64);
   p.splitsL1 = (int)((Ng + p.kchunkL1 - 1) / p.kchunkL1);
@@ -3140,12 +3141,13 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int NaT, int g0, int g1, cons
       {&m->m_psigA128_h, m->psigA_h, F16, 2, (long)nat, np_, 128, 64},
       {&m->m_phiT_m, m->phiT_m, F16, 2, N, p.Ng8, 128, 64},
       {&m->m_phiT_h, m->phiT_h, F16, 2, N, p.Ng8, 128, 64},
-      {&m->m_M1_m, m->M1_m, F16, 2, n, p.Ng8, 128, 64},
-      {&m->m_M1_h, m->M1_h, F16, 2, n, p.Ng8, 128, 64},
+      // the line GEMMs' B operands: [256][64] boxes for the 128 x 256 tiles (n > 128)
+      {&m->m_M1_m, m->M1_m, F16, 2, n, p.Ng8, p.large ? 256 : 128, 64},
+      {&m->m_M1_h, m->M1_h, F16, 2, n, p.Ng8, p.large ? 256 : 128, 64},
       {&m->m_phigT_m, m->phigT_m, F16, 2, N, p.Na8, 128, 64},
       {&m->m_phigT_h, m->phigT_h, F16, 2, N, p.Na8, 128, 64},
-      {&m->m_D23T_m, m->D23T_m, F16, 2, n, p.Na8, 128, 64},
-      {&m->m_D23T_h, m->D23T_h, F16, 2, n, p.Na8, 128, 64},
+      {&m->m_D23T_m, m->D23T_m, F16, 2, n, p.Na8, p.large ? 256 : 128, 64},
+      {&m->m_D23T_h, m->D23T_h, F16, 2, n, p.Na8, p.large ? 256 : 128, 64},
   };
   for (const MapSpec& ms : specs) {
     e = make_map(ms.m, ms.p, ms.t, ms.es, ms.rows, ms.ld, ms.br, ms.bc);
@@ -3609,14 +3611,24 @@ cudaError_t mixed_enqueue_post(MixedState* m, double* K, double* Ex, cudaStream_
   {
     GemmArgs g{N, n, (int)ng, m->kchunkL1, m->L1p, n, (long)N * n, m->sc, SC_OUT_L1, m->status,
                nullptr, nullptr, 0, 0, nullptr};
-    launch_gemm(m->m_phiT_m, m->m_phiT_h, m->m_M1_m, m->m_M1_h, m->m_phiT_m, m->m_M1_m, g,
-                dim3((unsigned)((N + 127) / 128), (unsigned)((n + 127) / 128), (unsigned)m->splitsL1), s, m->wait_cycles);
+    if (m->large)
+      launch_gemm_wide(m->m_phiT_m, m->m_phiT_h, m->m_M1_m, m->m_M1_h, g,
+                       dim3((unsigned)((N + 127) / 128), (unsigned)((n + 255) / 256), (unsigned)m->splitsL1),
+                       s, m->wait_cycles);
+    else
+      launch_gemm(m->m_phiT_m, m->m_phiT_h, m->m_M1_m, m->m_M1_h, m->m_phiT_m, m->m_M1_m, g,
+                  dim3((unsigned)((N + 127) / 128), (unsigned)((n + 127) / 128), (unsigned)m->splitsL1), s, m->wait_cycles);
   }
   {
     GemmArgs g{N, n, (int)na, m->kchunkL23, m->L23p, n, (long)N * n, m->sc, SC_OUT_L23, m->status,
                nullptr, nullptr, 0, 0, nullptr};
-    launch_gemm(m->m_phigT_m, m->m_phigT_h, m->m_D23T_m, m->m_D23T_h, m->m_phigT_m, m->m_D23T_m, g,
-                dim3((unsigned)((N + 127) / 128), (unsigned)((n + 127) / 128), (unsigned)m->splitsL23), s, m->wait_cycles);
+    if (m->large)
+      launch_gemm_wide(m->m_phigT_m, m->m_phigT_h, m->m_D23T_m, m->m_D23T_h, g,
+                       dim3((unsigned)((N + 127) / 128), (unsigned)((n + 255) / 256), (unsigned)m->splitsL23),
+                       s, m->wait_cycles);
+    else
+      launch_gemm(m->m_phigT_m, m->m_phigT_h, m->m_D23T_m, m->m_D23T_h, m->m_phigT_m, m->m_D23T_m, g,
+                  dim3((unsigned)((N + 127) / 128), (unsigned)((n + 127) / 128), (unsigned)m->splitsL23), s, m->wait_cycles);
   }
   count_launch(2);
   e = cudaGetLastError();
