@@ -937,13 +937,18 @@ constexpr int kWideEpi = 16;
 constexpr int kWideTma = kWideEpi, kWideMma = kWideEpi + 1;
 constexpr int kWideThreads = 32 * (kWideEpi + 2);
 
-template <bool kShort>
+// kP3: three pieces per operand (K-major only; the n > 128 orbital product):
+// 32-wide K blocks with the 64-byte swizzle, stages of A m, h, l [128][32]
+// and B m, h, l [256][32] (72 KB, three stages), six products per K step
+// (A1 adds m.l' + l.m'), a drain every 6 K blocks (192 terms).
+template <bool kShort, bool kP3>
 __device__ __forceinline__ void gemm_wide_body(const CUtensorMap* pAm, const CUtensorMap* pAh,
                                                const CUtensorMap* pBm, const CUtensorMap* pBh,
+                                               const CUtensorMap* pAl, const CUtensorMap* pBl,
                                                const GemmArgs& g) {
   extern __shared__ uint8_t gw_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gw_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ uint64_t full[GW_STAGES], empty[GW_STAGES], set_ready, set_free, drain;
+  __shared__ uint64_t full[3], empty[3], set_ready, set_free, drain;
   __shared__ uint32_t tslot;
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -953,15 +958,18 @@ __device__ __forceinline__ void gemm_wide_body(const CUtensorMap* pAm, const CUt
     by = (t / g.tiles_x) % g.tiles_y;
     bz = t / (g.tiles_x * g.tiles_y);
   };
+  constexpr int KB = kP3 ? 32 : 64;                  // K per block
+  constexpr int kd = kP3 ? 2 * kDrain : kDrain;      // blocks per drain (192 terms)
   auto kblocks = [&](int bz) {
     const int kb0 = bz * g.kchunk, ke = min(g.K, kb0 + g.kchunk);
-    return ke > kb0 ? (ke - kb0 + 63) / 64 : 0;
+    return ke > kb0 ? (ke - kb0 + KB - 1) / KB : 0;
   };
   const long long lw = kShort ? wait_limit(g.wait) : kWaitCycles;
-  const int ns = GW_STAGES, sbytes = GW_STAGE_BYTES;
+  constexpr int ns = kP3 ? 3 : GW_STAGES;
+  constexpr int sbytes = kP3 ? 3 * 8192 + 3 * 16384 : GW_STAGE_BYTES;
 
   if (tid == 0) {
-    for (int s = 0; s < GW_STAGES; ++s) {
+    for (int s = 0; s < ns; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -982,7 +990,7 @@ __device__ __forceinline__ void gemm_wide_body(const CUtensorMap* pAm, const CUt
 
   if (warp == kWideTma && lane == 0) {
     prefetch_tmap(pAm); prefetch_tmap(pAh); prefetch_tmap(pBm); prefetch_tmap(pBh);
-    int last_parity[GW_STAGES] = {-1, -1};
+    int last_parity[3] = {-1, -1, -1};
     int it = 0;
     for (int tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x) {
       int bx, by, bz;
@@ -995,7 +1003,17 @@ __device__ __forceinline__ void gemm_wide_body(const CUtensorMap* pAm, const CUt
         }
         uint8_t* st = sm + s * sbytes;  // A m +0, A h +16 KB, B m +32 KB, B h +64 KB
         mbar_expect_tx(&full[s], sbytes);
-        const int kc = kbeg + kb * 64;
+        const int kc = kbeg + kb * KB;
+        if constexpr (kP3) {  // A m, h, l at 0, 8, 16 KB; B m, h, l at 24, 40, 56 KB
+          tma_load_2d(st, pAm, &full[s], kc, m0);
+          tma_load_2d(st + 8192, pAh, &full[s], kc, m0);
+          tma_load_2d(st + 16384, pAl, &full[s], kc, m0);
+          tma_load_2d(st + 24576, pBm, &full[s], kc, n0);
+          tma_load_2d(st + 40960, pBh, &full[s], kc, n0);
+          tma_load_2d(st + 57344, pBl, &full[s], kc, n0);
+          last_parity[s] = use & 1;
+          continue;
+        }
         if (!g.a_mn) {
           tma_load_2d(st, pAm, &full[s], kc, m0);
           tma_load_2d(st + 16384, pAh, &full[s], kc, m0);
@@ -1025,6 +1043,7 @@ __device__ __forceinline__ void gemm_wide_body(const CUtensorMap* pAm, const CUt
     const uint64_t dmn = sdesc_sw128(smem_u32(sm), 8192, 1024);
     const uint64_t da0 = g.a_mn ? dmn : dkm, db0 = g.b_mn ? dmn : dkm;
     const uint32_t ast = g.a_mn ? 128 : 2, bst = g.b_mn ? 128 : 2;
+    const uint64_t d64 = sdesc_sw64(smem_u32(sm), 16, 512);  // three-piece K-major tiles
     auto fail = [&](int code) {
       if (lane == 0) { atomicExch(g.status, code); abort_flag = 1; }
       __syncwarp();
@@ -1038,22 +1057,34 @@ __device__ __forceinline__ void gemm_wide_body(const CUtensorMap* pAm, const CUt
       for (int kb = 0; kb < nkb; ++kb, ++it) {
         if (__shfl_sync(0xffffffffu, (int)abort_flag, 0)) { good = false; break; }
         const int s = it % ns;
-        const bool first = (kb % kDrain) == 0;
-        const bool last = (kb % kDrain) == kDrain - 1 || kb == nkb - 1;
+        const bool first = (kb % kd) == 0;
+        const bool last = (kb % kd) == kd - 1 || kb == nkb - 1;
         // one accumulator set: group G starts once the epilogue drained group G - 1
         if (first && G >= 1 && !mbar_wait_warp(&set_free, (G - 1) & 1, lw)) {
           fail(34); good = false; break;
         }
         if (!mbar_wait_warp(&full[s], (it / ns) & 1, lw)) { fail(32); good = false; break; }
         tc_fence_after();
-        const uint64_t dam = da0 + s * (GW_STAGE_BYTES >> 4), dah = dam + 1024;
-        const uint64_t dbm = db0 + s * (GW_STAGE_BYTES >> 4) + 2048, dbh = dbm + 2048;
         const uint32_t t0 = tbase, t1 = tbase + 256;
         const uint32_t a0 = first ? 0u : 1u;
-        mma_ss_run4(t0, dam, dbm, ast, bst, idesc, a0);
-        mma_ss_run4(t1, dam, dbh, ast, bst, idesc, a0);
-        mma_ss_run4(t1, dah, dbm, ast, bst, idesc, 1u);
-        mma_ss_run4(t1, dah, dbh, ast, bst, idesc, 1u);
+        if constexpr (kP3) {
+          // descriptor address field in 16-byte units: 512 per 8 KB
+          const uint64_t am = d64 + (uint64_t)((s * sbytes) >> 4), ah = am + 512, al = am + 1024;
+          const uint64_t bm = am + 1536, bh = bm + 1024, bl = bm + 2048;
+          mma_ss_run2(t0, am, bm, 2, 2, idesc, a0);
+          mma_ss_run2(t1, am, bh, 2, 2, idesc, a0);
+          mma_ss_run2(t1, ah, bm, 2, 2, idesc, 1u);
+          mma_ss_run2(t1, ah, bh, 2, 2, idesc, 1u);
+          mma_ss_run2(t1, am, bl, 2, 2, idesc, 1u);
+          mma_ss_run2(t1, al, bm, 2, 2, idesc, 1u);
+        } else {
+          const uint64_t dam = da0 + s * (GW_STAGE_BYTES >> 4), dah = dam + 1024;
+          const uint64_t dbm = db0 + s * (GW_STAGE_BYTES >> 4) + 2048, dbh = dbm + 2048;
+          mma_ss_run4(t0, dam, dbm, ast, bst, idesc, a0);
+          mma_ss_run4(t1, dam, dbh, ast, bst, idesc, a0);
+          mma_ss_run4(t1, dah, dbm, ast, bst, idesc, 1u);
+          mma_ss_run4(t1, dah, dbh, ast, bst, idesc, 1u);
+        }
         if (elect_one()) {
           mma_commit(&empty[s]);
           if (last) mma_commit(&set_ready);
@@ -1075,7 +1106,7 @@ __device__ __forceinline__ void gemm_wide_body(const CUtensorMap* pAm, const CUt
       int bx, by, bz;
       tile_at(tile, bx, by, bz);
       const int m0 = bx * 128, n0 = by * 256;
-      const int ngroups = (kblocks(bz) + kDrain - 1) / kDrain;
+      const int ngroups = (kblocks(bz) + kd - 1) / kd;
       float run[64];
 #pragma unroll
       for (int c = 0; c < 64; ++c) run[c] = 0.0f;
@@ -1149,9 +1180,36 @@ __global__ void __launch_bounds__(kWideThreads, 1)
                      const __grid_constant__ CUtensorMap mBm, const __grid_constant__ CUtensorMap mBh,
                      GemmArgs g) {
   if (g.wait > 0 && g.wait < kWaitCycles)
-    gemm_wide_body<true>(&mAm, &mAh, &mBm, &mBh, g);
+    gemm_wide_body<true, false>(&mAm, &mAh, &mBm, &mBh, &mAm, &mBm, g);
   else
-    gemm_wide_body<false>(&mAm, &mAh, &mBm, &mBh, g);
+    gemm_wide_body<false, false>(&mAm, &mAh, &mBm, &mBh, &mAm, &mBm, g);
+}
+
+// Three pieces per operand, K-major, [128][32] / [256][32] boxes with the
+// 64-byte swizzle (the n > 128 orbital product).
+__global__ void __launch_bounds__(kWideThreads, 1)
+    gemm_wide3_kernel(const __grid_constant__ CUtensorMap mAm, const __grid_constant__ CUtensorMap mAh,
+                      const __grid_constant__ CUtensorMap mAl, const __grid_constant__ CUtensorMap mBm,
+                      const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
+                      GemmArgs g) {
+  if (g.wait > 0 && g.wait < kWaitCycles)
+    gemm_wide_body<true, true>(&mAm, &mAh, &mBm, &mBh, &mAl, &mBl, g);
+  else
+    gemm_wide_body<false, true>(&mAm, &mAh, &mBm, &mBh, &mAl, &mBl, g);
+}
+
+constexpr int GW3_SMEM = 3 * (3 * 8192 + 3 * 16384) + 1024;
+
+void launch_gemm_wide3(const CUtensorMap& mAm, const CUtensorMap& mAh, const CUtensorMap& mAl,
+                       const CUtensorMap& mBm, const CUtensorMap& mBh, const CUtensorMap& mBl,
+                       GemmArgs g, dim3 tiles, cudaStream_t s, long long wait = 0) {
+  g.wait = wait;
+  g.tiles_x = (int)tiles.x;
+  g.tiles_y = (int)tiles.y;
+  g.tiles_z = (int)tiles.z;
+  const long total = (long)tiles.x * tiles.y * tiles.z;
+  const unsigned ctas = (unsigned)std::max<long>(1, std::min<long>(total, sm_count()));
+  gemm_wide3_kernel<<<ctas, kWideThreads, GW3_SMEM, s>>>(mAm, mAh, mAl, mBm, mBh, mBl, g);
 }
 
 // gemm_wide_kernel over tiles (x: 128-row M tiles, y: 256-column N tiles,
@@ -2638,6 +2696,9 @@ struct MixedState {
   // T_C = f_C W o (Psi_g Psi_g^T); set up with T_A, T_C (n > 128: at
   // creation; otherwise with the full-K scratch)
   TprodMaps tpA, tpC;
+  // n > 128, orbital product on 128 x 256 tiles: Phi' and Q^T pieces as
+  // [128][32] / [256][32] boxes with the 64-byte swizzle
+  CUtensorMap m_phi32_m, m_phi32_h, m_phi32_l, m_CT32_m, m_CT32_h, m_CT32_l;
   // Full K_{mu nu} (mixed_enqueue_full): scratch allocated on first use
   bool full_ready = false;
   int splitsF = 1, splitsFC = 1, splitsY = 1, kchunkF = 64, kchunkFC = 64, kchunkY = 64;
@@ -2957,6 +3018,8 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int NaT, int g0, int g1, cons
     e = cudaFuncSetAttribute(tprod_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TP_SMEM);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(gemm_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, GW_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gemm_wide3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, GW3_SMEM);
   if (e != cudaSuccess) return e;
 
   MixedState* m = new MixedState();
@@ -3176,6 +3239,15 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int NaT, int g0, int g1, cons
     if (e == cudaSuccess && m->VT32) e = make_map(&m->m_VB, m->VT32, F32, 4, (long)ng, p.Na4, 128, 32);
     if (e == cudaSuccess) e = make_map(&m->m_VC, m->W32, F32, 4, (long)na, p.NaT4, 128, 32);
     if (e == cudaSuccess && p.large) e = make_tprod_maps(m);
+    if (e == cudaSuccess && p.large) {
+      const auto S64 = CU_TENSOR_MAP_SWIZZLE_64B;
+      const struct { CUtensorMap* mp; const __half* ptr; long rows; int br; } w3[] = {
+          {&m->m_phi32_m, m->phi_m, (long)ng, 128}, {&m->m_phi32_h, m->phi_h, (long)ng, 128},
+          {&m->m_phi32_l, m->phi_l, (long)ng, 128}, {&m->m_CT32_m, m->CT_m, (long)n, 256},
+          {&m->m_CT32_h, m->CT_h, (long)n, 256}, {&m->m_CT32_l, m->CT_l, (long)n, 256}};
+      for (const auto& q : w3)
+        if (e == cudaSuccess) e = make_map(q.mp, q.ptr, F16, 2, q.rows, p.Np, q.br, 32, S64);
+    }
     if (e != cudaSuccess) return fin(e);
   }
   if (!p.large) {
@@ -3265,9 +3337,11 @@ cudaError_t mixed_enqueue_pre(MixedState* m, const double* C, cudaStream_t s, co
     GemmArgs g{};
     g.M = (int)ng; g.Ncols = n; g.K = N; g.kchunk = (int)m->Np;
     g.out = m->M1; g.ldo = n; g.sc = m->sc; g.scale_idx = SC_OUT_ORB; g.status = m->status;
-    g.pieces3 = 1;  // three pieces: the orbital split error would dominate E_x at this n
-    launch_gemm(m->m_phi_m, m->m_phi_h, m->m_CT_m, m->m_CT_h, m->m_phi_l, m->m_CT_l, g,
-                dim3((unsigned)((ng + 127) / 128), (unsigned)m->nt, 1), s, m->wait_cycles);
+    // three pieces (the orbital split error would dominate E_x at this n), on
+    // 128 x 256 tiles
+    launch_gemm_wide3(m->m_phi32_m, m->m_phi32_h, m->m_phi32_l, m->m_CT32_m, m->m_CT32_h,
+                      m->m_CT32_l, g, dim3((unsigned)((ng + 127) / 128), (unsigned)((n + 255) / 256), 1),
+                      s, m->wait_cycles);
     split_rows_f32_kernel<<<152 * 4, 256, 0, s>>>(m->M1, ng, n, n, m->sc, SC_PSI, m->psi_m,
                                                   m->psi_h, m->psi_l, np, m->am + AM_RN2);
     count_launch();
