@@ -533,7 +533,7 @@ def scf_runs_queued(xk, cell64, count=48, builds=6, seed=4800, budget_runs=12):
 
 
 def run_mix125(args):
-    """Config 4 with its largest size: `args.mix125` cells drawn with seed 4125
+    """The grouped batch with its largest cell size: `args.mix125` cells drawn with seed 4125
     from {8, 27, 64, 125} centres.  The 125-centre cell (N = 1625, n = 250,
     75^3 grid, N_aux = 8125) gets its ISDF tables on the GPU (xk_setup_isdf,
     FP64; the host fit would take hours), read back and handed to its f16x3
@@ -564,7 +564,7 @@ def run_mix125(args):
     sizes = rng.choice([8, 27, 64, 125], size=args.mix125)
     fp32 = sum(fp[int(z)] for z in np.random.default_rng(4125).choice([8, 27, 64, 125], size=32))
     res = batch_and_serve(xk, cells, sizes)
-    line = {"metric": "K builds/s (config 4 mix with 125-centre members)",
+    line = {"metric": "K builds/s (grouped batch of 8- to 125-centre cells)",
             "value": res.get("batch", {}).get("builds_per_s"), "unit": "builds/s", "n_gpus": 1,
             "higher_is_better": True, "dtype": "f16x3",
             "data": "synthetic (seeded cell generator; 125-centre ISDF tables formed on the GPU)",
