@@ -241,13 +241,15 @@ def job_throughput(world, steps, ms):
 
 def time_device_builds(xk, h, Cd, Kd, Ed, stream, warm, steps, torch, dist=None):
     """Warm-up, then `steps` builds between CUDA events on `stream` (with
-    `dist`, each build is a shard's and its share is allreduced in the step).
+    `dist`, each build is a shard's and its share is allreduced in the step),
+    as a caller runs them (the tensor path replays its captured build graph);
+    then the same builds again with the per-step event timing on (which
+    enqueues the kernels one by one between events) for the step times.
     Returns (ms, launches, step times)."""
     for i in range(warm):
         h.build_device(Cd[i].data_ptr(), Kd.data_ptr(), Ed.data_ptr(), stream.cuda_stream)
         reduce_partials(Kd, Ed, dist)
     torch.cuda.synchronize()
-    h.timing(True)
     launches0 = xk.kernel_launches()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -257,9 +259,20 @@ def time_device_builds(xk, h, Cd, Kd, Ed, stream, warm, steps, torch, dist=None)
         reduce_partials(Kd, Ed, dist)
     e1.record(stream)
     torch.cuda.synchronize()
+    launches = xk.kernel_launches() - launches0
+    ms = e0.elapsed_time(e1)
+    h.timing(True)
+    for i in range(min(steps, 20)):
+        h.build_device(Cd[warm + i].data_ptr(), Kd.data_ptr(), Ed.data_ptr(), stream.cuda_stream)
+        reduce_partials(Kd, Ed, dist)
+    torch.cuda.synchronize()
     st = h.step_times()
     h.timing(False)
-    return e0.elapsed_time(e1), xk.kernel_launches() - launches0, st
+    # the step-timed builds must leave the same K and E_x as the last timed one
+    h.build_device(Cd[warm + steps - 1].data_ptr(), Kd.data_ptr(), Ed.data_ptr(), stream.cuda_stream)
+    reduce_partials(Kd, Ed, dist)
+    torch.cuda.synchronize()
+    return ms, launches, st
 
 
 def time_energy(xk, h, Cd, stream, warm, steps, torch):

@@ -216,6 +216,13 @@ struct xk_handle {
   xk::MixedState* mixed = nullptr;
   Slot slots[kSlots];
 
+  // one tensor-path build captured as a CUDA graph on first use (C in h->C,
+  // K and E_x in h->K, h->Ex), replayed while step timing is off; dropped
+  // when a launch argument changes (xk_set_wait_limit)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  uint64_t glaunches = 0;  // kernels in one replay
+  bool graph_off = false;  // capture failed once: enqueue directly
   // step timing (xk_timing_enable / xk_timing_read)
   bool timing = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
@@ -304,6 +311,16 @@ cudaError_t dalloc(xk_handle* h, T** p, size_t elems) {
 
 void fold_marks(xk_handle* h);
 
+// The handle's captured build graph, if any (its stream is idle or the
+// caller holds the handle's lock).
+void drop_graph(xk_handle* h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->gexec = nullptr;
+  h->graph = nullptr;
+  h->glaunches = 0;
+}
+
 void free_handle(xk_handle* h) {
   if (!h) return;
   DeviceGuard g(h->device);
@@ -315,6 +332,7 @@ void free_handle(xk_handle* h) {
     if (s.Ex) cudaFreeHost(s.Ex);
     if (s.st) cudaFreeHost(s.st);
   }
+  drop_graph(h);
   if (h->mixed) xk::mixed_destroy(h->mixed);
   fold_marks(h);
   for (void* p : h->allocs) cudaFree(p);
@@ -521,6 +539,43 @@ int enqueue_build(xk_handle* h) {
     if (rc != XK_OK) return rc;
     XK_CUDA(cudaMemcpyAsync(h->Ex + 1, h->Ex, 8, cudaMemcpyDeviceToDevice, h->stream));
     return XK_OK;
+  }
+  if (!h->timing && !h->graph_off && !std::getenv("XK_NO_GRAPH")) {
+    // the whole device part of a build as one graph: one launch from the
+    // host instead of ~25, and no gaps between the kernels
+    if (!h->gexec) {
+      const uint64_t l0 = xk::t_launches;
+      xk::StepHook none{nullptr, nullptr};
+      cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        e = xk::mixed_enqueue(h->mixed, h->C, h->K, h->Ex, h->stream, none);
+        if (e == cudaSuccess)
+          e = xk::neg_dot_f64(h->K, h->C, (long)h->N * h->n, h->red, h->Ex + 1, h->stream);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(h->stream, &graph);
+        if (e == cudaSuccess) e = ec;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gexec, graph, 0);
+        if (e == cudaSuccess) {
+          h->graph = graph;
+        } else if (graph) {
+          cudaGraphDestroy(graph);
+        }
+      }
+      const uint64_t captured = xk::t_launches - l0;
+      xk::g_launches.fetch_sub(captured);  // counted per replay below
+      if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        h->gexec = nullptr;
+        h->graph_off = true;  // enqueue directly from now on
+      } else {
+        h->glaunches = captured;
+      }
+    }
+    if (h->gexec) {
+      XK_CUDA(cudaGraphLaunch(h->gexec, h->stream));
+      xk::g_launches.fetch_add(h->glaunches);
+      return XK_OK;
+    }
   }
   xk::StepHook hook{h->timing ? &step_hook : nullptr, h};
   cudaError_t e = xk::mixed_enqueue(h->mixed, h->C, h->K, h->Ex, h->stream, hook);
@@ -1308,6 +1363,7 @@ int xk_set_wait_limit(xk_handle* h, int64_t cycles) {
   if (!h || cycles < 0) return fail(XK_EINVAL, "xk_set_wait_limit: NULL handle or negative limit");
   std::lock_guard<std::mutex> lk(h->mu);
   if (h->mixed) xk::mixed_set_wait_limit(h->mixed, (long long)cycles);
+  drop_graph(h);  // its kernels hold the old limit
   return XK_OK;
 }
 

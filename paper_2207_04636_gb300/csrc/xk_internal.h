@@ -10,9 +10,14 @@
 
 namespace xk {
 
-// Kernel launches issued since load (all translation units).
+// Kernel launches issued since load (all translation units), and by the
+// calling thread (a graph capture counts its own launches with it).
 extern std::atomic<uint64_t> g_launches;
-inline void count_launch(uint64_t k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+inline thread_local uint64_t t_launches = 0;
+inline void count_launch(uint64_t k = 1) {
+  g_launches.fetch_add(k, std::memory_order_relaxed);
+  t_launches += k;
+}
 
 // ---------------------------------------------------------------------------
 // FP64 SIMT path (xk_fp64.cu)
