@@ -7,6 +7,7 @@
 #include "xk_mixed.h"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -65,6 +66,15 @@ struct Slot {
   xk_ticket ticket = 0;
   std::chrono::steady_clock::time_point deadline;
   bool has_deadline = false;
+};
+
+// Set-ups in progress (any thread): while one runs, a handle does not capture
+// its build graph (capture and instantiation wait behind the set-up's large
+// host-to-device copies and stalled that build by up to seconds).
+std::atomic<int> g_setups_running{0};
+struct SetupMark {
+  SetupMark() { g_setups_running.fetch_add(1); }
+  ~SetupMark() { g_setups_running.fetch_sub(1); }
 };
 
 size_t g_admitted = 0;    // bytes held by live handles and reservations (all devices)
@@ -540,7 +550,8 @@ int enqueue_build(xk_handle* h) {
     XK_CUDA(cudaMemcpyAsync(h->Ex + 1, h->Ex, 8, cudaMemcpyDeviceToDevice, h->stream));
     return XK_OK;
   }
-  if (!h->timing && !h->graph_off && !std::getenv("XK_NO_GRAPH")) {
+  if (!h->timing && !h->graph_off && !std::getenv("XK_NO_GRAPH") &&
+      (h->gexec || g_setups_running.load() == 0)) {
     // the whole device part of a build as one graph: one launch from the
     // host instead of ~25, and no gaps between the kernels
     if (!h->gexec) {
@@ -619,6 +630,7 @@ static int setup_impl(int64_t Ng, int32_t N, int32_t n, int32_t Naux, const doub
                double queue_ms = -1.0) {
   if (!out) return fail(XK_EINVAL, "xk_setup: out is NULL");
   *out = nullptr;
+  const SetupMark running;  // builds elsewhere defer their graph capture meanwhile
   if (g1 < 0) g1 = Naux;
   const bool isdf = V == nullptr && W == nullptr && grid > 0;
   if (!phi || !idx || (!isdf && (!V || !W))) return fail(XK_EINVAL, "xk_setup: NULL table pointer");
