@@ -113,3 +113,68 @@ def test_setup_queued_waits_then_times_out(L, monkeypatch):
     assert setup(float("inf")) == xk.XK_EINVAL
     xk.admit_release(a)
     assert xk.admit_state()[1] == 0
+
+
+def test_head_timeout_admits_the_next(L, monkeypatch):
+    """The oldest request (700 of 1000, 600 held) times out and leaves the
+    queue; the request behind it (300, which fits beside the 600) is then
+    admitted without any release."""
+    monkeypatch.setenv("XK_HBM_BUDGET_BYTES", "1000")
+    base, _ = xk.admit_state()
+    a = xk.admit_reserve(600)
+    got = {}
+
+    def head():
+        got["head"] = _code(lambda: xk.admit_reserve(700, 150.0))
+
+    def second():
+        try:
+            got["second"] = xk.admit_reserve(300, 5000.0)
+            got["t"] = time.perf_counter()
+        except xk.XKError as e:
+            got["second_err"] = e.code
+
+    t1 = threading.Thread(target=head)
+    t1.start()
+    time.sleep(0.05)
+    t0 = time.perf_counter()
+    t2 = threading.Thread(target=second)
+    t2.start()
+    t1.join(5.0)
+    t2.join(5.0)
+    assert got["head"] == xk.XK_ETIMEDOUT
+    assert "second" in got, got
+    assert got["t"] - t0 < 2.0
+    xk.admit_release(got["second"])
+    xk.admit_release(a)
+    assert xk.admit_state() == (base, 0)
+
+
+def test_concurrent_reserve_release(L, monkeypatch):
+    """Sixteen threads reserve and release random amounts against a small
+    budget, some waiting and some timing out: no deadlock, no lost bytes."""
+    monkeypatch.setenv("XK_HBM_BUDGET_BYTES", "1000")
+    base, _ = xk.admit_state()
+    errors = []
+
+    def worker(seed):
+        rng = np.random.default_rng(seed)
+        for _ in range(40):
+            nbytes = int(rng.integers(1, 400))
+            try:
+                tok = xk.admit_reserve(nbytes, float(rng.choice([-1.0, 5.0, 200.0])))
+            except xk.XKError as e:
+                if e.code not in (xk.XK_ENOMEM, xk.XK_ETIMEDOUT):
+                    errors.append(e.code)
+                continue
+            time.sleep(float(rng.uniform(0, 0.002)))
+            xk.admit_release(tok)
+
+    ths = [threading.Thread(target=worker, args=(s,)) for s in range(16)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join(60.0)
+    assert not any(t.is_alive() for t in ths)
+    assert not errors
+    assert xk.admit_state() == (base, 0)
