@@ -2689,8 +2689,8 @@ struct MixedState {
   // for every n (the orbital product)
   __half *psi_l = nullptr, *psig_l = nullptr, *phi_l = nullptr, *CT_l = nullptr;
   __half *psigA_m = nullptr, *psigA_h = nullptr, *psigA_l = nullptr;  // all NaT points
-  CUtensorMap m_psigA64_m, m_psigA64_h, m_psigA128_m, m_psigA128_h, m_psigA128_l;
-  CUtensorMap m_TA_h, m_TA_l, m_TAmn_h, m_TAmn_l, m_TC_h, m_TC_l, m_psi128_l, m_psig128_l,
+  CUtensorMap m_psigA64_m, m_psigA64_h;
+  CUtensorMap m_TA_h, m_TA_l, m_TAmn_h, m_TAmn_l, m_TC_h, m_TC_l,
       m_phi_l, m_CT_l;
   // The T-product launches (tprod_kernel): T_A = f_AB V o (Psi_g Psi^T) and
   // T_C = f_C W o (Psi_g Psi_g^T); set up with T_A, T_C (n > 128: at
@@ -2717,7 +2717,7 @@ struct MixedState {
   float tuned_ms = 0.0f;  // pair launch time of the split the autotuner kept
   int kchunkL1 = 64, kchunkL23 = 64;
   CUtensorMap m_phi_m, m_phi_h, m_CT_m, m_CT_h, m_psi128_m, m_psi128_h, m_psi64_m, m_psi64_h,
-      m_psig128_m, m_psig128_h, m_psig64_m, m_psig64_h, m_VA, m_VB, m_VC, m_phiT_m, m_phiT_h,
+      m_psig64_m, m_psig64_h, m_VA, m_VB, m_VC, m_phiT_m, m_phiT_h,
       m_M1_m, m_M1_h, m_phigT_m, m_phigT_h, m_D23T_m, m_D23T_h;
 };
 
@@ -3194,14 +3194,10 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int NaT, int g0, int g1, cons
       {&m->m_psi128_h, m->psi_h, F16, 2, (long)ng, np_, 128, 64},
       {&m->m_psi64_m, m->psi_m, F16, 2, (long)ng, np_, 64, 64},
       {&m->m_psi64_h, m->psi_h, F16, 2, (long)ng, np_, 64, 64},
-      {&m->m_psig128_m, m->psig_m, F16, 2, (long)na, np_, 128, 64},
-      {&m->m_psig128_h, m->psig_h, F16, 2, (long)na, np_, 128, 64},
       {&m->m_psig64_m, m->psig_m, F16, 2, (long)na, np_, 64, 64},
       {&m->m_psig64_h, m->psig_h, F16, 2, (long)na, np_, 64, 64},
       {&m->m_psigA64_m, m->psigA_m, F16, 2, (long)nat, np_, 64, 64},
       {&m->m_psigA64_h, m->psigA_h, F16, 2, (long)nat, np_, 64, 64},
-      {&m->m_psigA128_m, m->psigA_m, F16, 2, (long)nat, np_, 128, 64},
-      {&m->m_psigA128_h, m->psigA_h, F16, 2, (long)nat, np_, 128, 64},
       {&m->m_phiT_m, m->phiT_m, F16, 2, N, p.Ng8, 128, 64},
       {&m->m_phiT_h, m->phiT_h, F16, 2, N, p.Ng8, 128, 64},
       // the line GEMMs' B operands: [256][64] boxes for the 128 x 256 tiles (n > 128)
@@ -3224,9 +3220,6 @@ cudaError_t mixed_create(int64_t Ng, int N, int n, int NaT, int g0, int g1, cons
         {&m->m_TAmn_l, m->TA_l, F16, 2, (long)na, p.Ng8, 64, 64},
         {&m->m_TC_h, m->TC_h, F16, 2, (long)na, p.NaT8, 128, 64},
         {&m->m_TC_l, m->TC_l, F16, 2, (long)na, p.NaT8, 128, 64},
-        {&m->m_psigA128_l, m->psigA_l, F16, 2, (long)nat, p.np, 128, 64},
-        {&m->m_psi128_l, m->psi_l, F16, 2, (long)ng, p.np, 128, 64},
-        {&m->m_psig128_l, m->psig_l, F16, 2, (long)na, p.np, 128, 64},
     };
     for (const MapSpec& ms : tspecs) {
       e = make_map(ms.m, ms.p, ms.t, ms.es, ms.rows, ms.ld, ms.br, ms.bc);
